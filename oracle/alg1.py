@@ -1,0 +1,121 @@
+"""Algorithm 1 and Algorithm 2 restated step by step on exact integers.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).  Small sizes only:
+every matrix is a numpy object array of Python integers, and every product is
+a plain ``@`` on those, so nothing rounds or overflows.
+
+``alg1_low_aat`` takes the steps of Algorithm 1 (Sec. 3) in the paper's order
+and notation: four additions with two multiplications by the skew-unitary Y,
+three recursive products P1, P2, P5 and two general products P3, P4, then the
+additions that form U1..U5.  The recursion stops after ``levels`` levels,
+where Low(A A^T) is taken from its definition.  It returns the intermediate
+blocks as well, so that tests can check the proof identities of Theorem 3.1.
+
+``two_m`` takes the steps of Algorithm 2 (Sec. 6.1) with K = R, E = C.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def _obj(A):
+    return np.asarray(A, dtype=object)
+
+
+def low(M):
+    """Low(M): entries with i >= j kept, the others set to 0 (Sec. 2)."""
+    M = _obj(M).copy()
+    n, m = M.shape
+    for i in range(n):
+        for j in range(i + 1, m):
+            M[i, j] = 0
+    return M
+
+
+def dense_y(ykind, ya, yb, p, kappa):
+    """Y as a dense kappa x kappa matrix of Python integers mod p.
+
+    ykind 1: Y = i I (Sec. 4.2).  ykind 2: Y = [[a, b], [-b, a]] (x) I_{kappa/2}
+    (Prop. 4.2)."""
+    Y = np.zeros((kappa, kappa), dtype=object)
+    if ykind == 1:
+        for j in range(kappa):
+            Y[j, j] = ya % p
+        return Y
+    if ykind == 2:
+        if kappa % 2:
+            raise ValueError("kappa must be even for the 2x2 (x) I form")
+        h = kappa // 2
+        for j in range(h):
+            Y[j, j] = ya % p
+            Y[j, j + h] = yb % p
+            Y[j + h, j] = (-yb) % p
+            Y[j + h, j + h] = ya % p
+        return Y
+    raise ValueError("unknown ykind")
+
+
+def alg1_low_aat(A, p, ykind, ya, yb, levels, trace=None):
+    """Low(A A^T) mod p by Algorithm 1 applied ``levels`` times.
+
+    ``trace`` (a list) receives, for the top level, a dict with S1..S4,
+    P1..P5, U1..U5 (all mod p) when given."""
+    A = _obj(A) % p
+    n, k = A.shape
+    need = 4 if ykind == 2 else 2
+    if levels == 0 or n % 2 or k % need or n == 0 or k == 0:
+        return low((A @ A.T) % p)
+    h, kap = n // 2, k // 2
+    A11, A12 = A[:h, :kap], A[:h, kap:]
+    A21, A22 = A[h:, :kap], A[h:, kap:]
+    Y = dense_y(ykind, ya, yb, p, kap)
+    # 4 additions and 2 multiplications by Y
+    S1 = ((A21 - A11) @ Y) % p
+    S2 = (A22 - A21 @ Y) % p
+    S3 = (S1 - A22) % p
+    S4 = (S3 + A12) % p
+    # 3 recursive and 2 general products
+    P1 = alg1_low_aat(A11, p, ykind, ya, yb, levels - 1)
+    P2 = alg1_low_aat(A12, p, ykind, ya, yb, levels - 1)
+    P3 = (A22 @ S4.T) % p
+    P4 = (S1 @ S2.T) % p
+    P5 = alg1_low_aat(S3, p, ykind, ya, yb, levels - 1)
+    # 3 half additions and 2 complete additions
+    U1_low = (P1 + P5) % p
+    U3_low = (P1 + P2) % p
+    U1 = U1_low.copy()
+    for i in range(h):            # Up(U1) <- Low(U1)^T forms the full U1
+        for j in range(i + 1, h):
+            U1[i, j] = U1_low[j, i]
+    U2 = (U1 + P4) % p
+    U4 = (U2 + P3) % p
+    U5_low = low((U2 + P4.T) % p)
+    C = np.zeros((n, n), dtype=object)
+    C[:h, :h] = low(U3_low)
+    C[h:, :h] = U4
+    C[h:, h:] = U5_low
+    if trace is not None:
+        trace.append(dict(S1=S1, S2=S2, S3=S3, S4=S4, P1=P1, P2=P2, P3=P3,
+                          P4=P4, P5=P5, U1=U1, U2=U2, U3=U3_low, U4=U4,
+                          U5=U5_low, Y=Y))
+    return C
+
+
+def two_m(Are, Aim, conj=True):
+    """Algorithm 2 with K = R, E = C, A + iB the complex input.
+
+    phi is the transposition on real matrices; on C it is the conjugate
+    transposition (eps = i phi(i) = 1) or the transposition (eps = i i = -1).
+    Returns (Re, Im) of (A + iB) phi(A + iB)."""
+    A = np.asarray(Are, dtype=np.float64)
+    B = np.asarray(Aim, dtype=np.float64)
+    eps = 1.0 if conj else -1.0
+    H = A @ B.T
+    G = (A + B) @ (A + eps * B).T
+    # (G - eps H - H^T) + H phi(i) + i H^T, with phi(i) = -i (conj) or i
+    re = G - eps * H - H.T
+    if conj:
+        im = H.T - H          # H (-i) + i H^T
+    else:
+        im = H + H.T          # H i + i H^T
+    return re, im

@@ -1,0 +1,454 @@
+"""Pins of the CPU oracle to facts other than itself (run with -m "not gpu").
+
+Each test checks the oracle against something the paper or the mathematics
+fixes: closed forms, exhaustive brute force on tiny inputs, invariants,
+independent library routines (numpy matmul on exact integers), and the proof
+identities of Theorem 3.1.  A dropped term, a wrong sign or index, or a
+transposed operand in the oracle fails at least one of them.
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import alg1
+from paper_2101_01025_gb300 import synth
+
+SMALL_PRIMES = [3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37, 41, 43, 47]
+CONFIG_PRIMES = [65521, 131071, 131041, 2**31 - 1]
+
+
+def _golden():
+    path = os.path.join(os.path.dirname(__file__), "golden", "paper_constants.txt")
+    out = {}
+    for line in open(path):
+        line = line.split("#")[0].strip()
+        if line:
+            k, v = line.split("=")
+            out[k.strip()] = float(v)
+    return out
+
+
+def _exact_low(A, p):
+    """Low(A A^T) mod p from numpy's matmul on Python integers."""
+    Ao = np.asarray(A, dtype=object) % p
+    return np.tril((Ao @ Ao.T) % p).astype(np.int64)
+
+
+# --------------------------------------------------------------- F_p core
+
+@pytest.mark.parametrize("p", [3, 5, 7])
+@pytest.mark.parametrize("n,k", [(1, 1), (2, 1), (1, 2), (2, 2), (3, 2), (2, 3)])
+def test_low_aat_exhaustive_tiny(p, n, k):
+    """Brute force: every matrix over F_p of the shape (sampled above 3^6),
+    against the sum of column outer products sum_l a_l a_l^T."""
+    cells = n * k
+    total = p ** cells
+    if total <= 20000:
+        mats = itertools.product(range(p), repeat=cells)
+    else:
+        rng = np.random.default_rng(p * 100 + cells)
+        mats = (tuple(rng.integers(0, p, cells)) for _ in range(3000))
+    for vals in mats:
+        A = np.array(vals, dtype=np.int32).reshape(n, k)
+        C = oracle.aat_modp_low(A, p)
+        ref = np.zeros((n, n), dtype=np.int64)
+        for l in range(k):
+            col = A[:, l].astype(np.int64)
+            ref += np.outer(col, col)
+        ref = np.tril(ref % p)
+        assert np.array_equal(C.astype(np.int64), ref), (vals, C, ref)
+
+
+@pytest.mark.parametrize("p", [131071, 65521, 2**31 - 1])
+def test_low_aat_closed_forms(p):
+    n, k = 9, 13
+    # [I | 0] gives the identity
+    A = np.zeros((n, k), dtype=np.int32)
+    A[:, :n] = np.eye(n, dtype=np.int32)
+    assert np.array_equal(oracle.aat_modp_low(A, p), np.eye(n, dtype=np.uint32))
+    # all ones gives k everywhere (lower part)
+    A = np.ones((n, k), dtype=np.int32)
+    assert np.array_equal(oracle.aat_modp_low(A, p),
+                          np.tril(np.full((n, n), k % p, dtype=np.uint32)))
+    # Sylvester Hadamard H (entries +-1): H H^T = m I
+    H = np.array([[1]], dtype=np.int64)
+    for _ in range(4):
+        H = np.block([[H, H], [H, -H]])
+    m = H.shape[0]
+    C = oracle.aat_modp_low(H.astype(np.int32), p)
+    assert np.array_equal(C, (np.eye(m, dtype=np.int64) * (m % p)).astype(np.uint32))
+    # rank one: A = u v^T gives (v.v) u u^T
+    rng = np.random.default_rng(1)
+    u = rng.integers(0, p, n).astype(object)
+    v = rng.integers(0, p, k).astype(object)
+    A = (np.outer(u, v) % p).astype(np.int64).astype(np.int32)
+    vv = int(sum(int(x) * int(x) for x in v)) % p
+    ref = np.tril((np.outer(u, u) * vv) % p).astype(np.int64)
+    assert np.array_equal(oracle.aat_modp_low(A, p).astype(np.int64), ref)
+    # diagonal matrix gives its square
+    d = rng.integers(0, p, n)
+    A = np.zeros((n, n), dtype=np.int32)
+    A[np.arange(n), np.arange(n)] = d
+    ref = np.diag([(int(x) * int(x)) % p for x in d]).astype(np.int64)
+    assert np.array_equal(oracle.aat_modp_low(A, p).astype(np.int64), ref)
+
+
+@pytest.mark.parametrize("p", [131071, 65521, 2**31 - 1, 97])
+def test_low_aat_matches_exact_integers(p):
+    """Against numpy matmul on exact Python integers, including entries next
+    to p - 1 where (p-1)^2 k overflows 64 bits for p = 2^31 - 1."""
+    rng = np.random.default_rng(p)
+    for n, k in [(1, 1), (5, 3), (17, 33), (31, 64)]:
+        A = rng.integers(0, p, (n, k)).astype(np.int64)
+        A[0, :] = p - 1
+        A = A.astype(np.int32)
+        assert np.array_equal(oracle.aat_modp_low(A, p).astype(np.int64), _exact_low(A, p))
+
+
+@pytest.mark.parametrize("p", [131071, 2**31 - 1])
+def test_low_aat_invariants(p):
+    rng = np.random.default_rng(7)
+    n, k = 12, 20
+    A = synth.residues(11, (n, k), p)
+    C = oracle.aat_modp_low(A, p).astype(np.int64)
+    # balanced representative, and adding multiples of p, change nothing
+    Ab = np.where(A > p // 2, A.astype(np.int64) - p, A).astype(np.int32)
+    assert np.array_equal(oracle.aat_modp_low(Ab, p).astype(np.int64), C)
+    # column permutation: A P P^T A^T = A A^T (catches A^T A)
+    perm = rng.permutation(k)
+    assert np.array_equal(oracle.aat_modp_low(A[:, perm].copy(), p).astype(np.int64), C)
+    # row permutation permutes rows and columns of the symmetric product
+    rp = rng.permutation(n)
+    full = C + np.tril(C, -1).T
+    Cp = oracle.aat_modp_low(A[rp].copy(), p).astype(np.int64)
+    assert np.array_equal(Cp, np.tril(full[np.ix_(rp, rp)]))
+    # scaling row 0 by c scales row/column 0 by c and C[0,0] by c^2
+    c = 12345 % p
+    As = A.astype(object)
+    As[0] = (As[0] * c) % p
+    Cs = oracle.aat_modp_low(As.astype(np.int64).astype(np.int32), p).astype(object)
+    assert Cs[0, 0] == (C[0, 0] * c * c) % p
+    for i in range(1, n):
+        assert Cs[i, 0] == (C[i, 0] * c) % p
+        assert Cs[i, i] == C[i, i]
+
+
+def test_entries_and_gemm_agree_with_definition():
+    p = 131071
+    A = synth.residues(5, (23, 41), p)
+    C = oracle.aat_modp_low(A, p)
+    ij = [(i, j) for i in range(23) for j in range(i + 1)]
+    e = oracle.aat_modp_entries(A, p, ij)
+    assert np.array_equal(e, np.array([C[i, j] for i, j in ij], dtype=np.uint32))
+    X = synth.residues(6, (7, 41), p)
+    Y = synth.residues(8, (9, 41), p)
+    G = oracle.gemm_modp(X, Y, p).astype(np.int64)
+    ref = ((X.astype(object) @ Y.astype(object).T) % p).astype(np.int64)
+    assert np.array_equal(G, ref)
+    # a general product with Y = X is the full symmetric product
+    F = oracle.gemm_modp(A, A, p).astype(np.int64)
+    assert np.array_equal(F, F.T)
+    assert np.array_equal(np.tril(F), C.astype(np.int64))
+
+
+def test_freivalds_detects_errors():
+    p = 131071
+    n, k = 40, 30
+    A = synth.residues(3, (n, k), p)
+    C = oracle.aat_modp_low(A, p).astype(np.int32)
+    xs = synth.vectors_mod_p(4, 4, n, p)
+    assert oracle.freivalds_modp(A, C, p, xs) == 0
+    bad = C.copy()
+    bad[17, 5] = (bad[17, 5] + 1) % p
+    assert oracle.freivalds_modp(A, bad, p, xs) == 4
+    bad = C.copy()
+    bad[3, 3] = (bad[3, 3] + p - 1) % p
+    assert oracle.freivalds_modp(A, bad, p, xs) == 4
+    # the strict upper triangle is ignored
+    up = C.copy()
+    up[0, 5] = 99
+    assert oracle.freivalds_modp(A, up, p, xs) == 0
+
+
+# --------------------------------------------------------- number theory
+
+def _sieve(m):
+    s = np.ones(m + 1, dtype=bool)
+    s[:2] = False
+    for i in range(2, int(m ** 0.5) + 1):
+        if s[i]:
+            s[i * i::i] = False
+    return s
+
+
+def test_is_prime_against_sieve():
+    s = _sieve(5000)
+    for q in range(5001):
+        assert oracle.is_prime(q) == bool(s[q]), q
+    for q in CONFIG_PRIMES:
+        assert oracle.is_prime(q)
+    assert not oracle.is_prime(2**31 - 3)   # 2147483645 = 5 * 429496729
+    assert not oracle.is_prime(65521 * 3)
+
+
+def test_legendre_and_sqrt_exhaustive():
+    s = _sieve(400)
+    for p in [q for q in range(3, 400) if s[q]]:
+        squares = {(x * x) % p for x in range(1, p)}
+        assert len(squares) == (p - 1) // 2        # Euler: half the units
+        for a in range(p):
+            r = oracle.sqrt_mod(a, p)
+            leg = oracle.legendre(a, p)
+            if a == 0:
+                assert leg == 0 and r == 0
+            elif a in squares:
+                assert leg == 1 and r is not None and (r * r) % p == a and r <= p - r
+            else:
+                assert leg == -1 and r is None
+
+
+@pytest.mark.parametrize("p", CONFIG_PRIMES)
+def test_sqrt_large_primes(p):
+    rng = np.random.default_rng(p)
+    for a in rng.integers(1, p, 200):
+        a = int(a)
+        r = oracle.sqrt_mod(a, p)
+        if r is None:
+            assert pow(a, (p - 1) // 2, p) == p - 1
+        else:
+            assert (r * r) % p == a
+
+
+def test_sqrt_minus_one_exists_iff_p_1_mod_4():
+    """Prop. 4.1: sqrt(-1) exists for p == 1 mod 4; (-1/p) = -1 for p == 3 mod 4."""
+    s = _sieve(3000)
+    for p in [q for q in range(3, 3000) if s[q]]:
+        r = oracle.sqrt_mod(-1, p)
+        if p % 4 == 1:
+            assert r is not None and (r * r + 1) % p == 0
+        else:
+            assert r is None
+
+
+def test_minus_two_square_for_p_3_mod_8():
+    """Lemma 4.3: p == 3 mod 8 implies -2 is a square."""
+    s = _sieve(5000)
+    for p in [q for q in range(3, 5000) if s[q] and q % 8 == 3]:
+        assert oracle.legendre(-2, p) == 1
+        r = oracle.sqrt_mod(-2, p)
+        assert (r * r + 2) % p == 0
+
+
+def test_sos_every_k_small_primes():
+    """Algorithm 3: a^2 + b^2 == k mod p for every k, every small prime."""
+    for p in SMALL_PRIMES:
+        for k in range(p):
+            a, b = oracle.sos_modp(k, p)
+            assert (a * a + b * b - k) % p == 0, (p, k, a, b)
+
+
+def test_sos_minus_one_many_primes():
+    s = _sieve(20000)
+    for p in [q for q in range(3, 20000) if s[q]] + CONFIG_PRIMES:
+        a, b = oracle.sos_modp(-1, p)
+        assert (a * a + b * b + 1) % p == 0, p
+        if p % 4 == 3:
+            assert b != 0  # -1 is not a square there
+
+
+def test_experiment_primes():
+    g = _golden()
+    p1 = int(g["prime_with_sqrt_minus_one"])
+    p2 = int(g["prime_without_sqrt_minus_one"])
+    assert oracle.is_prime(p1) and oracle.is_prime(p2)
+    assert oracle.skew_unitary_params(p1)[0] == 1
+    assert oracle.skew_unitary_params(p2)[0] == 2
+
+
+@pytest.mark.parametrize("p", CONFIG_PRIMES + [3, 7, 13, 103])
+def test_skew_unitary_y(p):
+    """Eq. (skewu): Y Y^T == -I for the Y the oracle builds."""
+    kind, a, b = oracle.skew_unitary_params(p)
+    for kappa in (2, 4, 6, 8):
+        Y = oracle.build_y(kind, a, b, p, kappa).astype(object)
+        prod = (Y @ Y.T) % p
+        assert np.array_equal(prod, (np.eye(kappa, dtype=object) * (p - 1)) % p)
+    # the identity is not skew-unitary (negative control)
+    I = np.eye(4, dtype=object)
+    assert not np.array_equal((I @ I.T) % p, (np.eye(4, dtype=object) * (p - 1)) % p)
+
+
+# ---------------------------------------------------------- Algorithm 1
+
+def _alg1_cases():
+    for p in [131071, 65521, 13, 2**31 - 1]:
+        for (n, k) in [(8, 8), (12, 8), (8, 16), (16, 12)]:
+            yield p, n, k
+
+
+@pytest.mark.parametrize("p,n,k", list(_alg1_cases()))
+def test_alg1_equals_definition(p, n, k):
+    kind, a, b = oracle.skew_unitary_params(p)
+    A = synth.residues(p % 1000 + n * 31 + k, (n, k), p)
+    ref = _exact_low(A, p)
+    for levels in (1, 2):
+        C = alg1.alg1_low_aat(A, p, kind, a, b, levels)
+        assert np.array_equal(C.astype(np.int64), ref), levels
+    # the C oracle's definition agrees too
+    assert np.array_equal(oracle.aat_modp_low(A, p).astype(np.int64), ref)
+
+
+@pytest.mark.parametrize("p", [131071, 65521, 2**31 - 1])
+def test_alg1_proof_identities(p):
+    """Theorem 3.1's proof identities on the blocks of one level."""
+    kind, a, b = oracle.skew_unitary_params(p)
+    n, k = 12, 16
+    A = synth.residues(99, (n, k), p).astype(object) % p
+    tr = []
+    alg1.alg1_low_aat(A, p, kind, a, b, 1, trace=tr)
+    t = tr[0]
+    h, kap = n // 2, k // 2
+    A11, A12, A21, A22 = A[:h, :kap], A[:h, kap:], A[h:, :kap], A[h:, kap:]
+    Y = t["Y"]
+    md = lambda M: M % p
+    eq = lambda X, Z: np.array_equal(md(X), md(Z))
+    # S blocks against the C oracle's S blocks
+    S = oracle.alg1_sblocks(A.astype(np.int64).astype(np.int32), p, kind, a, b)
+    for name, Sc in zip(("S1", "S2", "S3", "S4"), S):
+        assert eq(t[name], Sc.astype(object)), name
+    # S3 = -S2 - A11 Y (proof of Thm 3.1)
+    assert eq(t["S3"], -t["S2"] - A11 @ Y)
+    # U3 = A11 A11^T + A12 A12^T (Low)
+    assert eq(np.tril(t["U3"]), np.tril(A11 @ A11.T + A12 @ A12.T))
+    R1 = A11 @ Y @ t["S2"].T
+    assert eq(R1, A11 @ (Y @ A22.T + A21.T))
+    S2S2 = t["S2"] @ t["S2"].T
+    # U1 = S2 S2^T + R1^T + R1
+    assert eq(t["U1"], S2S2 + R1.T + R1)
+    R2 = A21 @ Y @ A22.T
+    assert eq(S2S2, A22 @ A22.T - A21 @ A21.T - R2 - R2.T)
+    assert eq(R1 + t["P4"], R2 + A21 @ A21.T)
+    # U5 = A22 A22^T + A21 A21^T (Low), U4 = A22 A12^T + A21 A11^T
+    assert eq(np.tril(t["U5"]), np.tril(A22 @ A22.T + A21 @ A21.T))
+    assert eq(t["U4"], A22 @ A12.T + A21 @ A11.T)
+
+
+def test_alg1_needs_skew_unitary_y():
+    """With Y = I (Y Y^T = +I, not -I) the recursion is wrong: the
+    skew-unitarity of Eq. (skewu) is what makes Algorithm 1 exact."""
+    p = 131071
+    A = synth.residues(5, (8, 8), p)
+    wrong = alg1.alg1_low_aat(A, p, 1, 1, 0, 1)   # Y = 1 * I
+    assert not np.array_equal(wrong.astype(np.int64), _exact_low(A, p))
+
+
+def test_alg1_complex_transpose_and_hermitian_negative():
+    """Sec. 4.1: over C, Y = i I is skew-unitary for the transposition, so
+    Algorithm 1 gives A A^T; for the conjugate transposition Y Y^H = +I and
+    the same recursion is wrong (no skew-unitary Y exists there)."""
+    rng = np.random.default_rng(3)
+    n, k = 6, 8
+    A = rng.integers(-3, 4, (n, k)) + 1j * rng.integers(-3, 4, (n, k))
+
+    def one_level(A, herm):
+        adj = (lambda M: M.conj().T) if herm else (lambda M: M.T)
+        h, kap = n // 2, k // 2
+        A11, A12, A21, A22 = A[:h, :kap], A[:h, kap:], A[h:, :kap], A[h:, kap:]
+        Y = 1j * np.eye(kap)
+        S1 = (A21 - A11) @ Y
+        S2 = A22 - A21 @ Y
+        S3 = S1 - A22
+        S4 = S3 + A12
+        P1, P2 = A11 @ adj(A11), A12 @ adj(A12)
+        P3, P4, P5 = A22 @ adj(S4), S1 @ adj(S2), S3 @ adj(S3)
+        U1 = P1 + P5
+        U2 = U1 + P4
+        U4 = U2 + P3
+        U5 = U2 + adj(P4)
+        U3 = P1 + P2
+        C = np.zeros((n, n), dtype=complex)
+        C[:h, :h], C[h:, :h], C[h:, h:] = np.tril(U3), U4, np.tril(U5)
+        return C
+
+    assert np.allclose(one_level(A, False), np.tril(A @ A.T))
+    assert not np.allclose(one_level(A, True), np.tril(A @ A.conj().T))
+
+
+def test_alg1_cost_recurrence_constants():
+    """Table 1 / Lemma 2.5: with classical products, the ring MACs of
+    Algorithm 1 satisfy s(l) = 3/8 s(l-1) + 2/8 with s(0) = 1/2 (lower SYRK),
+    so s(inf) = 0.4 n^3 MACs = 0.8 n^3 operations; classical D&C gives n^3."""
+    g = _golden()
+    s = 0.5
+    for _ in range(60):
+        s = 3.0 / 8.0 * s + 2.0 / 8.0
+    assert abs(2 * s - g["alg1_ff_ops_over_n3"]) < 1e-12
+    # Lemma (master theorem): b / (2^alpha - a) with a = 3, b = 2 MM(1) = 4
+    assert abs(4.0 / (2 ** 3 - 3) - g["alg1_ff_ops_over_n3"]) < 1e-12
+    assert abs(4.0 / (2 ** 3 - 4) - g["classical_ff_ops_over_n3"]) < 1e-12
+    # over C: 3 real ops per complex op ... Table 2 values
+    assert abs(3 * g["alg1_ff_ops_over_n3"] - g["alg1_complex_aat_ops_over_n3"]) < 1e-12
+    assert abs(2 * 2.0 - g["twoM_complex_ops_over_n3"]) < 1e-12
+
+
+# ------------------------------------------------------------------ C
+
+def test_complex_oracle_exact_small_integers():
+    """Small-integer complex inputs are exact in fp64: compare against Gaussian
+    integer arithmetic on Python ints."""
+    rng = np.random.default_rng(5)
+    n, k = 7, 11
+    re = rng.integers(-9, 10, (n, k))
+    im = rng.integers(-9, 10, (n, k))
+    A = re + 1j * im
+    for conj in (True, False):
+        C = oracle.complex_low(A, conj=conj)
+        for i in range(n):
+            for j in range(i + 1):
+                sr = si = 0
+                for l in range(k):
+                    ar, ai = int(re[i, l]), int(im[i, l])
+                    br, bi = int(re[j, l]), int(im[j, l])
+                    if conj:
+                        bi = -bi
+                    sr += ar * br - ai * bi
+                    si += ar * bi + ai * br
+                assert C[i, j] == complex(sr, si)
+                if conj and i == j:
+                    assert si == 0 and sr >= 0
+
+
+def test_complex_oracle_properties():
+    A = synth.complex_normal(17, (24, 40)).astype(np.complex128)
+    C = oracle.complex_low(A, conj=True)
+    # Re(A A^H) = [Re Im][Re Im]^T from an independent real matmul
+    RI = np.concatenate([A.real, A.imag], axis=1)
+    assert np.allclose(np.tril(C.real), np.tril(RI @ RI.T), rtol=1e-12, atol=1e-10)
+    assert np.allclose(np.tril(C), np.tril(A @ A.conj().T), rtol=1e-12, atol=1e-10)
+    assert np.all(np.diag(C).real >= 0) and np.all(np.diag(C).imag == 0)
+    # Hermitian: entry (j, i) is the conjugate of (i, j)
+    ij = [(3, 7), (7, 3), (20, 1), (1, 20)]
+    e = oracle.complex_entries(A, ij, conj=True)
+    assert np.isclose(e[0], np.conj(e[1])) and np.isclose(e[2], np.conj(e[3]))
+    # unitary DFT: F F^H = I
+    m = 16
+    F = np.exp(-2j * np.pi * np.outer(np.arange(m), np.arange(m)) / m) / np.sqrt(m)
+    assert np.allclose(oracle.complex_low(F, conj=True), np.eye(m), atol=1e-12)
+    # A A^T (no conjugation) is symmetric, not Hermitian
+    T = oracle.complex_low(A, conj=False)
+    assert np.allclose(np.tril(T), np.tril(A @ A.T), rtol=1e-12, atol=1e-10)
+
+
+def test_two_m_algorithm():
+    """Algorithm 2 (2M) returns A A^H (eps = 1) and A A^T (eps = -1)."""
+    rng = np.random.default_rng(8)
+    Are, Aim = rng.standard_normal((9, 13)), rng.standard_normal((9, 13))
+    A = Are + 1j * Aim
+    re, im = alg1.two_m(Are, Aim, conj=True)
+    assert np.allclose(re + 1j * im, A @ A.conj().T)
+    re, im = alg1.two_m(Are, Aim, conj=False)
+    assert np.allclose(re + 1j * im, A @ A.T)
