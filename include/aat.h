@@ -1,0 +1,122 @@
+/*
+ * aat.h -- C ABI of a GB300 (sm_103a) library for the product of a matrix by
+ * its adjoint, after Dumas, Pernet and Sedoglavic, "Some fast algorithms
+ * multiplying a matrix by its adjoint".
+ *
+ *   aat_modp    Low(A A^T) mod p by Algorithm 1 (Sec. 3): a 2x2 block
+ *               recursion with 5 block products (3 recursive, 2 general)
+ *               after block additions that apply a skew-unitary Y with
+ *               Y Y^T = -I (Sec. 4: Y = sqrt(-1) I for p = 1 mod 4, else
+ *               Y = [[a, b], [-b, a]] (x) I with a^2 + b^2 = -1 from
+ *               Algorithm 3).  The result is exact (Theorem 3.1).
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are row-major.  A is n x k with row stride lda (elements);
+ *     C is n x n with row stride ldc.
+ *   - Device pointers (unless the name ends in _host).  The caller owns A
+ *     and C; C must not overlap A.
+ *   - Residues: an entry of A may be any int32 congruent to its residue
+ *     with |value| < p (canonical [0, p) or balanced (-p/2, p/2)).
+ *   - Output: the lower triangle of C, diagonal included, receives the
+ *     canonical residues in [0, p).  The strict upper triangle is used as
+ *     scratch (Sec. 7, Table 3) and is unspecified on return unless
+ *     AAT_ZERO_UPPER is given.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t, NULL = legacy
+ *     default stream) unless stated.  Internal workspace is owned by the
+ *     library, grown on demand and released by aat_shutdown().
+ *   - Return codes: AAT_OK or a negative AAT_E*; aat_last_error() gives a
+ *     message for the calling thread.  No entry point falls back to the
+ *     CPU: without a usable sm_103a GPU they fail with AAT_ECUDA.
+ */
+#ifndef AAT_H
+#define AAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define AAT_API __attribute__((visibility("default")))
+#else
+#define AAT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AAT_OK 0
+#define AAT_EINVAL (-1)       /* null pointer, bad size or stride, aliasing */
+#define AAT_ENOTPRIME (-2)    /* p is not an odd prime */
+#define AAT_ERANGE (-3)       /* p >= 2^31, or no exact leaf for (p, k) */
+#define AAT_ENOMEM (-4)       /* device workspace allocation failed */
+#define AAT_ECUDA (-5)        /* CUDA error (launch, no device, wrong arch) */
+#define AAT_ETIMEOUT (-6)     /* a bounded device wait gave up */
+#define AAT_EUNSUPPORTED (-7) /* valid request this build does not provide */
+
+/* flags */
+#define AAT_IN_BALANCED (1u << 0) /* informational: A holds balanced residues */
+#define AAT_ZERO_UPPER (1u << 1)  /* zero the strict upper triangle of C     */
+#define AAT_LEAF_TC (0u << 4)     /* leaf products on tcgen05 BF16 digits (default) */
+#define AAT_LEAF_SIMT (1u << 4)   /* leaf products by plain CUDA-core int64 (check path) */
+#define AAT_LEAF_MASK (0xFu << 4)
+/* recursion levels: AAT_LEVELS(0) is the plain lower-triangle product (no
+ * recursion); no AAT_LEVELS bits = chosen from (n, k). */
+#define AAT_LEVELS(l) ((((uint32_t)(l) + 1u) & 0xFu) << 8)
+#define AAT_LEVELS_MASK (0xFu << 8)
+
+/*
+ * Low(A A^T) mod p (Algorithm 1, Sec. 3; Low as defined in Sec. 2).
+ * p: an odd prime < 2^31.  n, k >= 0.  Odd or non-divisible n, k are
+ * zero-padded internally (Sec. 3, "padding or peeling"; Sec. 4.3).
+ * Equivalent to aat_modp_ex(A, n, k, k, p, C, n, 0, stream).
+ */
+AAT_API int aat_modp(const int32_t *A, int64_t n, int64_t k, uint32_t p, int32_t *C,
+             void *stream);
+
+/* As aat_modp with explicit strides and flags (AAT_*). lda >= k, ldc >= n. */
+AAT_API int aat_modp_ex(const int32_t *A, int64_t n, int64_t k, int64_t lda, uint32_t p,
+                int32_t *C, int64_t ldc, uint32_t flags, void *stream);
+
+/*
+ * End-to-end form: A_host (n x k, row stride k) and C_host (n x n, row
+ * stride n) are HOST buffers (pinned or pageable).  The call copies A to
+ * the device, runs aat_modp_ex with `flags`, copies the result back and
+ * synchronises.  The device buffers are owned by the library.
+ */
+AAT_API int aat_modp_host(const int32_t *A_host, int64_t n, int64_t k, uint32_t p,
+                  int32_t *C_host, uint32_t flags);
+
+/*
+ * The plain general product C = X Y^T mod p with the same exact leaf
+ * kernels and no recursion: all m x n entries are written (canonical).
+ * X is m x k (row stride ldx), Y is n x k (row stride ldy).  With X = Y this
+ * is the full product A A^T that Algorithm 1 is compared against.
+ * flags: AAT_LEAF_TC or AAT_LEAF_SIMT.
+ */
+AAT_API int aat_gemm_modp(const int32_t *X, int64_t ldx, const int32_t *Y, int64_t ldy,
+                  int64_t m, int64_t n, int64_t k, uint32_t p, int32_t *C,
+                  int64_t ldc, uint32_t flags, void *stream);
+
+/* Bytes of device workspace aat_modp_ex would use for (n, k, p, flags). */
+AAT_API size_t aat_workspace_size(int64_t n, int64_t k, uint32_t p, uint32_t flags);
+
+/* Message for the last error of the calling thread ("" if none). */
+AAT_API const char *aat_last_error(void);
+
+/*
+ * Synchronises the device and reports the sticky device-side status word
+ * that bounded waits in the kernels set when they give up: AAT_OK or
+ * AAT_ETIMEOUT.  reset != 0 clears it afterwards.
+ */
+AAT_API int aat_device_status(int reset);
+
+/* Frees every workspace and cache of the library on the current device. */
+AAT_API void aat_shutdown(void);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+AAT_API int aat_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AAT_H */

@@ -1,0 +1,113 @@
+"""GB300 (sm_103a) library for the product of a matrix by its adjoint.
+
+Python binding of the C ABI in ``include/aat.h``: the functions below carry
+the C names and only marshal arguments (torch tensors -> device pointers,
+the current torch stream -> cudaStream_t).  Every step runs in the CUDA
+library ``libaat_gb300.so``; when it is missing the calls raise.
+
+    aat_modp(A, p)            Low(A A^T) mod p, Algorithm 1 (Sec. 3)
+    aat_gemm_modp(X, Y, p)    X Y^T mod p with the same exact leaf kernels
+    aat_modp_host(A_np, p)    end to end from host memory
+"""
+from __future__ import annotations
+
+from . import _native
+from ._native import (AAT_IN_BALANCED, AAT_LEAF_SIMT, AAT_LEAF_TC, AAT_LEVELS,  # noqa: F401
+                      AAT_ZERO_UPPER, AatError, PlanStats, check, last_error, lib)
+
+__all__ = [
+    "aat_modp", "aat_gemm_modp", "aat_modp_host", "aat_workspace_size", "aat_device_status",
+    "aat_shutdown", "aat_version", "AAT_LEVELS", "AAT_LEAF_TC", "AAT_LEAF_SIMT",
+    "AAT_ZERO_UPPER", "AAT_IN_BALANCED", "AatError",
+]
+
+
+def _stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return s.cuda_stream
+
+
+def _check_mat(t, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != torch.int32 or t.dim() != 2:
+        raise TypeError("%s must be a 2-D int32 tensor" % name)
+    if t.shape[1] > 1 and t.stride(1) != 1:
+        raise ValueError("%s must have unit stride along rows" % name)
+    return max(t.stride(0), t.shape[1], 1)
+
+
+def aat_modp(A, p: int, C=None, flags: int = 0, levels: int | None = None, stream=None):
+    """Low(A A^T) mod p into C (n x n int32, allocated if None); returns C.
+
+    Only the lower triangle (diagonal included) of C is defined unless
+    AAT_ZERO_UPPER is in ``flags``."""
+    import torch
+    lda = _check_mat(A, "A")
+    n, k = A.shape
+    if C is None:
+        C = torch.empty((n, n), dtype=torch.int32, device=A.device)
+    ldc = _check_mat(C, "C")
+    if levels is not None:
+        flags |= AAT_LEVELS(levels)
+    check(lib().aat_modp_ex(A.data_ptr(), n, k, lda, p, C.data_ptr(), ldc, flags,
+                            _stream(stream)))
+    return C
+
+
+def aat_gemm_modp(X, Y, p: int, C=None, flags: int = 0, stream=None):
+    """X Y^T mod p (all entries) into C (allocated if None); returns C."""
+    import torch
+    ldx = _check_mat(X, "X")
+    ldy = _check_mat(Y, "Y")
+    m, k = X.shape
+    n, k2 = Y.shape
+    if k != k2:
+        raise ValueError("inner dimensions differ")
+    if C is None:
+        C = torch.empty((m, n), dtype=torch.int32, device=X.device)
+    ldc = _check_mat(C, "C")
+    check(lib().aat_gemm_modp(X.data_ptr(), ldx, Y.data_ptr(), ldy, m, n, k, p, C.data_ptr(),
+                              ldc, flags, _stream(stream)))
+    return C
+
+
+def aat_modp_host(A, p: int, C=None, flags: int = 0, levels: int | None = None):
+    """End to end from host memory: A is a C-contiguous int32 numpy array (or
+    pinned CPU tensor); returns C (n x n, host, same kind as A)."""
+    import numpy as np
+    if levels is not None:
+        flags |= AAT_LEVELS(levels)
+    if isinstance(A, np.ndarray):
+        A = np.ascontiguousarray(A, dtype=np.int32)
+        n, k = A.shape
+        if C is None:
+            C = np.empty((n, n), dtype=np.int32)
+        check(lib().aat_modp_host(A.ctypes.data, n, k, p, C.ctypes.data, flags))
+        return C
+    import torch
+    if A.is_cuda or A.dtype != torch.int32 or not A.is_contiguous():
+        raise TypeError("A must be a contiguous int32 host tensor")
+    n, k = A.shape
+    if C is None:
+        C = torch.empty((n, n), dtype=torch.int32, pin_memory=A.is_pinned())
+    check(lib().aat_modp_host(A.data_ptr(), n, k, p, C.data_ptr(), flags))
+    return C
+
+
+def aat_workspace_size(n: int, k: int, p: int, flags: int = 0) -> int:
+    return int(lib().aat_workspace_size(n, k, p, flags))
+
+
+def aat_device_status(reset: bool = False) -> int:
+    return int(lib().aat_device_status(1 if reset else 0))
+
+
+def aat_shutdown() -> None:
+    lib().aat_shutdown()
+
+
+def aat_version() -> int:
+    return int(lib().aat_version())

@@ -1,0 +1,115 @@
+"""ctypes binding of libaat_gb300.so (include/aat.h, include/aat_testing.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Loading fails loudly when the library has not been built; there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libaat_gb300.so")
+
+AAT_OK = 0
+AAT_EINVAL = -1
+AAT_ENOTPRIME = -2
+AAT_ERANGE = -3
+AAT_ENOMEM = -4
+AAT_ECUDA = -5
+AAT_ETIMEOUT = -6
+AAT_EUNSUPPORTED = -7
+
+AAT_IN_BALANCED = 1 << 0
+AAT_ZERO_UPPER = 1 << 1
+AAT_LEAF_TC = 0 << 4
+AAT_LEAF_SIMT = 1 << 4
+
+
+def AAT_LEVELS(l: int) -> int:
+    return ((l + 1) & 0xF) << 8
+
+
+#: every symbol include/aat.h and include/aat_testing.h declare
+EXPORTS = [
+    "aat_modp", "aat_modp_ex", "aat_modp_host", "aat_gemm_modp", "aat_workspace_size",
+    "aat_last_error", "aat_device_status", "aat_shutdown", "aat_version",
+    "aatx_is_prime", "aatx_sqrt_mod", "aatx_sos", "aatx_y_params", "aatx_digit_spec",
+    "aatx_plan_stats", "aatx_sblocks", "aatx_split", "aatx_leaf", "aatx_postadd",
+]
+
+
+class AatError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("aat error %d: %s" % (code, msg))
+        self.code = code
+
+
+class PlanStats(ctypes.Structure):
+    _fields_ = [
+        ("levels", ctypes.c_int),
+        ("n_pad", ctypes.c_int64),
+        ("k_pad", ctypes.c_int64),
+        ("recursive_products", ctypes.c_int64),
+        ("general_products", ctypes.c_int64),
+        ("syrk_leaves", ctypes.c_int64),
+        ("block_additions", ctypes.c_int64),
+        ("half_additions", ctypes.c_int64),
+        ("ring_macs", ctypes.c_double),
+        ("workspace_bytes", ctypes.c_size_t),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                "libaat_gb300.so is not built; run paper_2101_01025_gb300.build.build() "
+                "(nvcc, sm_103a).  There is no CPU fallback.")
+        L = ctypes.CDLL(LIB_PATH)
+        i64, u32, i32, vp, u64 = (ctypes.c_int64, ctypes.c_uint32, ctypes.c_int,
+                                  ctypes.c_void_p, ctypes.c_uint64)
+        L.aat_modp.argtypes = [vp, i64, i64, u32, vp, vp]
+        L.aat_modp_ex.argtypes = [vp, i64, i64, i64, u32, vp, i64, u32, vp]
+        L.aat_modp_host.argtypes = [vp, i64, i64, u32, vp, u32]
+        L.aat_gemm_modp.argtypes = [vp, i64, vp, i64, i64, i64, i64, u32, vp, i64, u32, vp]
+        L.aat_workspace_size.argtypes = [i64, i64, u32, u32]
+        L.aat_workspace_size.restype = ctypes.c_size_t
+        L.aat_last_error.restype = ctypes.c_char_p
+        L.aat_device_status.argtypes = [i32]
+        L.aat_shutdown.restype = None
+        L.aatx_is_prime.argtypes = [u64]
+        L.aatx_sqrt_mod.argtypes = [i64, u64]
+        L.aatx_sqrt_mod.restype = i64
+        L.aatx_sos.argtypes = [i64, u64, ctypes.POINTER(u64), ctypes.POINTER(u64)]
+        L.aatx_y_params.argtypes = [u32, ctypes.POINTER(i32), ctypes.POINTER(u32),
+                                    ctypes.POINTER(u32)]
+        L.aatx_digit_spec.argtypes = [u32, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                      ctypes.POINTER(i32)]
+        L.aatx_plan_stats.argtypes = [i64, i64, u32, u32, ctypes.POINTER(PlanStats)]
+        L.aatx_sblocks.argtypes = [vp, i64, i64, i64, u32, vp, vp, vp, vp, i64, vp]
+        L.aatx_split.argtypes = [vp, i64, i64, i64, u32, vp, vp]
+        L.aatx_leaf.argtypes = [vp, i64, vp, i64, i64, i64, i64, u32, vp, i64, i32, i32, u32,
+                                i32, vp]
+        L.aatx_postadd.argtypes = [vp, i64, i64, u32, vp]
+        _lib = L
+        return L
+
+
+def last_error() -> str:
+    return lib().aat_last_error().decode()
+
+
+def check(rc: int) -> None:
+    if rc != AAT_OK:
+        raise AatError(rc, last_error())

@@ -1,0 +1,838 @@
+// aat_api.cu -- host side of the library: number theory for Y (Sec. 4),
+// digit-split planning, the recursion scheduler of Algorithm 1 with the
+// memory placement of Sec. 7 (Table 3), workspace management and the C ABI.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/aat.h"
+#include "../../include/aat_testing.h"
+#include "common.cuh"
+
+namespace aat {
+
+// ------------------------------------------------------------ errors
+
+static thread_local std::string g_last_error;
+
+static int fail(int code, const std::string &msg) {
+  g_last_error = msg;
+  return code;
+}
+
+static int cuda_fail(cudaError_t e, const char *where) {
+  return fail(AAT_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// ------------------------------------------------------- number theory
+
+static uint64_t mulmod64(uint64_t a, uint64_t b, uint64_t p) {
+  return (uint64_t)(((unsigned __int128)a * b) % p);
+}
+
+static uint64_t powmod64(uint64_t a, uint64_t e, uint64_t p) {
+  uint64_t r = 1 % p;
+  a %= p;
+  while (e) {
+    if (e & 1) r = mulmod64(r, a, p);
+    a = mulmod64(a, a, p);
+    e >>= 1;
+  }
+  return r;
+}
+
+// Deterministic Miller-Rabin: bases 2, 3, 5, 7 are exact below 3.2e9.
+static bool is_prime_u32(uint64_t n) {
+  if (n < 2) return false;
+  static const uint64_t small[] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37};
+  for (uint64_t q : small) {
+    if (n == q) return true;
+    if (n % q == 0) return false;
+  }
+  uint64_t d = n - 1;
+  int s = 0;
+  while ((d & 1) == 0) {
+    d >>= 1;
+    ++s;
+  }
+  for (uint64_t a : {2ull, 3ull, 5ull, 7ull, 11ull, 13ull, 17ull}) {
+    uint64_t x = powmod64(a, d, n);
+    if (x == 1 || x == n - 1) continue;
+    bool comp = true;
+    for (int r = 1; r < s; ++r) {
+      x = mulmod64(x, x, n);
+      if (x == n - 1) {
+        comp = false;
+        break;
+      }
+    }
+    if (comp) return false;
+  }
+  return true;
+}
+
+static uint64_t canon64(int64_t a, uint64_t p) {
+  int64_t r = a % (int64_t)p;
+  return (uint64_t)(r < 0 ? r + (int64_t)p : r);
+}
+
+// Euler's criterion.
+static int legendre(uint64_t a, uint64_t p) {
+  a %= p;
+  if (a == 0) return 0;
+  return powmod64(a, (p - 1) / 2, p) == 1 ? 1 : -1;
+}
+
+// Tonelli-Shanks; returns false for a non-square.
+static bool sqrt_mod(uint64_t a, uint64_t p, uint64_t *root) {
+  a %= p;
+  if (a == 0) {
+    *root = 0;
+    return true;
+  }
+  if (legendre(a, p) != 1) return false;
+  if (p % 4 == 3) {
+    *root = powmod64(a, (p + 1) / 4, p);
+    return true;
+  }
+  uint64_t q = p - 1;
+  int s = 0;
+  while ((q & 1) == 0) {
+    q >>= 1;
+    ++s;
+  }
+  uint64_t z = 2;
+  while (legendre(z, p) != -1) ++z;
+  uint64_t c = powmod64(z, q, p), t = powmod64(a, q, p), r = powmod64(a, (q + 1) / 2, p);
+  int m = s;
+  while (t != 1) {
+    int i = 0;
+    uint64_t tt = t;
+    while (tt != 1) {
+      tt = mulmod64(tt, tt, p);
+      ++i;
+      if (i >= m) return false;
+    }
+    uint64_t b = c;
+    for (int e = 0; e < m - i - 1; ++e) b = mulmod64(b, b, p);
+    m = i;
+    c = mulmod64(b, b, p);
+    t = mulmod64(t, c, p);
+    r = mulmod64(r, b, p);
+  }
+  *root = r;
+  return true;
+}
+
+// Algorithm 3 (SoS): a^2 + b^2 == k mod p.
+static bool sos(uint64_t k, uint64_t p, uint64_t *a, uint64_t *b) {
+  k %= p;
+  if (legendre(k, p) >= 0) {  // k is 0 or a square
+    uint64_t r;
+    if (!sqrt_mod(k, p, &r)) return false;
+    *a = r;
+    *b = 0;
+    return true;
+  }
+  uint64_t s = 2;
+  while (legendre(s, p) == 1) ++s;  // smallest quadratic non-residue
+  uint64_t c, r;
+  if (!sqrt_mod(s - 1, p, &c)) return false;  // s - 1 is a square
+  uint64_t rr = mulmod64(k, powmod64(s, p - 2, p), p);
+  if (!sqrt_mod(rr, p, &r)) return false;
+  *a = r;
+  *b = mulmod64(r, c, p);
+  return true;
+}
+
+ModP make_modp(uint32_t p) {
+  ModP m;
+  m.p = p;
+  m.half = (p - 1) / 2;
+  m.mu = (uint64_t)(((unsigned __int128)1 << 64) / p);
+  const uint64_t two62 = (uint64_t)1 << 62;
+  m.off = ((two62 + p - 1) / p) * (uint64_t)p;
+  m.mu32 = (uint32_t)(((uint64_t)1 << 32) / p);
+  return m;
+}
+
+static int32_t bal_host(uint64_t r, uint32_t p) {
+  return r > (p - 1) / 2 ? (int32_t)((int64_t)r - (int64_t)p) : (int32_t)r;
+}
+
+// Y for the transposition over F_p (Sec. 4.2 / Prop. 4.2 with Algorithm 3).
+static bool make_y(uint32_t p, YParams *y) {
+  if (p % 4 == 1) {
+    uint64_t i;
+    if (!sqrt_mod(p - 1, p, &i)) return false;
+    if (mulmod64(i, i, p) != p - 1) return false;
+    y->kind = 1;
+    y->a = bal_host(i, p);
+    y->b = 0;
+    return true;
+  }
+  uint64_t a, b;
+  if (!sos(p - 1, p, &a, &b)) return false;
+  if ((mulmod64(a, a, p) + mulmod64(b, b, p)) % p != p - 1) return false;
+  y->kind = 2;
+  y->a = bal_host(a, p);
+  y->b = bal_host(b, p);
+  return true;
+}
+
+// Signed base-2^b digits of balanced residues: the fewest digits whose top
+// digit stays exact in BF16 (|d| <= 256), then the smallest digit products.
+static DigitSpec make_digits(uint32_t p) {
+  DigitSpec best;
+  std::memset(&best, 0, sizeof(best));
+  int64_t best_prod = -1;
+  for (int b : {8, 9, 7}) {
+    DigitSpec d;
+    std::memset(&d, 0, sizeof(d));
+    d.b = b;
+    int64_t X = (p - 1) / 2;
+    int L = 1;
+    while (X > 256 && L < 8) {
+      d.dmax[L - 1] = 1 << (b - 1);
+      X = (X + (1 << (b - 1))) >> b;
+      ++L;
+    }
+    d.dmax[L - 1] = (int)std::max<int64_t>(X, 1);
+    d.L = L;
+    int64_t mx = 0;
+    for (int i = 0; i < L; ++i) mx = std::max<int64_t>(mx, d.dmax[i]);
+    const int64_t prod = mx * mx;
+    if (best_prod < 0 || d.L < best.L || (d.L == best.L && prod < best_prod)) {
+      best = d;
+      best_prod = prod;
+    }
+  }
+  return best;
+}
+
+// ------------------------------------------------------- device state
+
+struct DeviceState {
+  void *ws = nullptr;
+  size_t ws_size = 0;
+  int32_t *status = nullptr;
+  // buffers of the end-to-end host entry point
+  void *e2e_a = nullptr, *e2e_c = nullptr;
+  size_t e2e_a_size = 0, e2e_c_size = 0;
+  cudaStream_t e2e_stream = nullptr;
+};
+
+static std::mutex g_state_mu;
+static std::map<int, DeviceState> g_states;
+
+static DeviceState &state() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return g_states[dev];
+}
+
+int32_t *device_status_ptr() {
+  std::lock_guard<std::mutex> lock(g_state_mu);
+  DeviceState &s = state();
+  if (!s.status) {
+    if (cudaMalloc(&s.status, sizeof(int32_t)) != cudaSuccess) return nullptr;
+    cudaMemset(s.status, 0, sizeof(int32_t));
+  }
+  return s.status;
+}
+
+static int ensure_workspace(size_t bytes, void **out) {
+  std::lock_guard<std::mutex> lock(g_state_mu);
+  DeviceState &s = state();
+  if (s.ws_size < bytes) {
+    if (s.ws) {
+      cudaDeviceSynchronize();
+      cudaFree(s.ws);
+      s.ws = nullptr;
+      s.ws_size = 0;
+    }
+    size_t want = bytes + (bytes >> 4);
+    cudaError_t e = cudaMalloc(&s.ws, want);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(AAT_ENOMEM, "workspace allocation of " + std::to_string(want) + " bytes failed");
+    }
+    s.ws_size = want;
+  }
+  *out = s.ws;
+  return AAT_OK;
+}
+
+// ---------------------------------------------------------- the plan
+
+// Bump allocator over the workspace with a dry-run mode that only measures.
+struct Arena {
+  char *base = nullptr;
+  size_t used = 0, peak = 0;
+  bool dry = true;
+  void *get(size_t bytes) {
+    size_t off = (used + 255) & ~(size_t)255;
+    used = off + bytes;
+    peak = std::max(peak, used);
+    return dry ? nullptr : (void *)(base + off);
+  }
+};
+
+struct Ctx {
+  ModP m;
+  YParams y;
+  DigitSpec ds;
+  uint32_t leaf;     // AAT_LEAF_TC / AAT_LEAF_SIMT
+  int exact_bits;
+  cudaStream_t st;
+  Arena ar;
+  aatx_plan_stats_t *stats;  // optional counters
+  int err = AAT_OK;
+};
+
+static Planes planes_alloc(Ctx &c, int64_t rows, int64_t cols) {
+  Planes P;
+  P.rows = rows;
+  P.cols = cols;
+  P.kstride = (cols + 7) / 8 * 8;
+  P.L = c.ds.L;
+  P.ptr = (__nv_bfloat16 *)c.ar.get((size_t)P.L * rows * P.kstride * 2);
+  return P;
+}
+
+static Planes no_planes() {
+  Planes P;
+  std::memset(&P, 0, sizeof(P));
+  return P;
+}
+
+// An operand of a leaf product: an int32 residue block and/or its planes.
+struct Operand {
+  const int32_t *x;
+  int64_t ld;
+  Planes pl;  // pl.L == 0: not split yet
+};
+
+static bool check(Ctx &c, cudaError_t e, const char *where) {
+  if (e != cudaSuccess && c.err == AAT_OK) c.err = cuda_fail(e, where);
+  return c.err == AAT_OK;
+}
+
+// out = X Y^T (M x N, inner K) mod p; lower: only i >= j; accumulate: out += .
+static void leaf(Ctx &c, Operand X, Operand Y, bool same, int64_t M, int64_t N, int64_t K,
+                 int32_t *out, int64_t ldo, int lower, int accumulate) {
+  if (c.stats) {
+    if (lower) {
+      c.stats->syrk_leaves++;
+      c.stats->ring_macs += (double)M * (double)(M + 1) / 2.0 * (double)K;
+    } else {
+      c.stats->general_products++;
+      c.stats->ring_macs += (double)M * (double)N * (double)K;
+    }
+  }
+  if (c.leaf == AAT_LEAF_SIMT) {
+    if (!c.ar.dry)
+      check(c, launch_leaf_simt(X.x, X.ld, Y.x, Y.ld, M, N, K, out, ldo, lower, accumulate, c.m,
+                                c.st),
+            "leaf (CUDA cores)");
+    return;
+  }
+  const size_t mark = c.ar.used;
+  if (X.pl.L == 0) {
+    X.pl = planes_alloc(c, M, K);
+    if (!c.ar.dry) check(c, launch_split(X.x, X.ld, M, K, c.m, c.ds.b, X.pl, c.st), "split");
+  }
+  if (same) {
+    Y.pl = X.pl;
+  } else if (Y.pl.L == 0) {
+    Y.pl = planes_alloc(c, N, K);
+    if (!c.ar.dry) check(c, launch_split(Y.x, Y.ld, N, K, c.m, c.ds.b, Y.pl, c.st), "split");
+  }
+  if (!c.ar.dry && c.err == AAT_OK) {
+    TcLeafArgs a;
+    a.x = X.pl;
+    a.y = Y.pl;
+    a.dx = c.ds;
+    a.dy = c.ds;
+    a.M = M;
+    a.N = N;
+    a.K = K;
+    a.out = out;
+    a.ldo = ldo;
+    a.lower = lower;
+    a.accumulate = accumulate;
+    a.exact_bits = c.exact_bits;
+    check(c, launch_leaf_tc(a, c.m, c.st), "leaf (tensor cores)");
+  }
+  c.ar.used = mark;
+}
+
+// Low(A A^T) mod p -> Low(C) by Algorithm 1 with `levels` levels.
+// n must be divisible by 2^levels and k by 2^levels (2^(levels+1) for a
+// kind-2 Y).  `ap` optionally holds the digit planes of A (tensor-core leaf).
+static void rec(Ctx &c, const int32_t *A, int64_t lda, int64_t n, int64_t k, int32_t *C,
+                int64_t ldc, int levels, Planes ap) {
+  if (c.err != AAT_OK) return;
+  if (levels == 0 || n < 2 || k < 2) {
+    Operand X{A, lda, ap};
+    leaf(c, X, X, true, n, n, k, C, ldc, 1, 0);
+    return;
+  }
+  const int64_t h = n / 2, kap = k / 2;
+  int32_t *C11 = C, *C12 = C + h, *C21 = C + h * ldc, *C22 = C + h * ldc + h;
+  const int32_t *A11 = A, *A12 = A + kap, *A22 = A + h * lda + kap;
+  const bool tc = (c.leaf == AAT_LEAF_TC);
+  const bool last = (levels == 1);
+  const size_t mark = c.ar.used;
+  if (c.stats) {
+    c.stats->recursive_products += 3;
+    c.stats->block_additions += 9;
+    c.stats->half_additions += 3;
+  }
+
+  SKernelOut o;
+  std::memset(&o, 0, sizeof(o));
+  // S3: the input of the recursive product P5.  Table 3 keeps it in C21
+  // (needs kappa <= h, i.e. k <= n); otherwise it takes workspace.
+  int32_t *S3;
+  int64_t ldS3;
+  if (kap <= h) {
+    S3 = C21;
+    ldS3 = ldc;
+  } else {
+    S3 = (int32_t *)c.ar.get((size_t)h * kap * 4);
+    ldS3 = kap;
+  }
+  // with tensor-core leaves the last level needs S3 only as digit planes
+  o.s[2] = (tc && last) ? nullptr : S3;
+  o.lds[2] = ldS3;
+  Operand oS1{nullptr, 0, no_planes()}, oS2 = oS1, oS4 = oS1, oA22{A22, lda, no_planes()};
+  Planes pA11 = no_planes(), pA12 = no_planes(), pS3 = no_planes();
+  if (tc) {
+    o.sp[0] = oS1.pl = planes_alloc(c, h, kap);
+    o.sp[1] = oS2.pl = planes_alloc(c, h, kap);
+    o.sp[3] = oS4.pl = planes_alloc(c, h, kap);
+    o.a22 = oA22.pl = planes_alloc(c, h, kap);
+    if (last) {
+      o.a11 = pA11 = planes_alloc(c, h, kap);
+      o.a12 = pA12 = planes_alloc(c, h, kap);
+      o.sp[2] = pS3 = planes_alloc(c, h, kap);
+    }
+  } else {
+    for (int q : {0, 1, 3}) {
+      o.s[q] = (int32_t *)c.ar.get((size_t)h * kap * 4);
+      o.lds[q] = kap;
+    }
+    oS1.x = o.s[0];
+    oS1.ld = kap;
+    oS2.x = o.s[1];
+    oS2.ld = kap;
+    oS4.x = o.s[3];
+    oS4.ld = kap;
+  }
+  // 1. S1..S4 (4 additions, 2 products by Y) in one pass over A
+  if (!c.ar.dry) check(c, launch_sblocks(A, lda, h, kap, c.m, c.y, c.ds.b, o, c.st), "sblocks");
+  // 2. P4^T = S2 S1^T -> C22
+  leaf(c, oS2, oS1, false, h, h, kap, C22, ldc, 0, 0);
+  // 3. P5 = Low(S3 S3^T) -> C12
+  rec(c, S3, ldS3, h, kap, C12, ldc, levels - 1, pS3);
+  // 4. P3 = A22 S4^T -> C21 (S3 is no longer needed)
+  leaf(c, oA22, oS4, false, h, h, kap, C21, ldc, 0, 0);
+  // 5. P1 = Low(A11 A11^T) -> C11
+  rec(c, A11, lda, h, kap, C11, ldc, levels - 1, pA11);
+  // 6. U1 = P1 + P5, U2 = U1 + P4, U4 = U2 + P3 -> C21, U5 = Low(U2 + P4^T) -> C22
+  if (!c.ar.dry) check(c, launch_postadd(C11, C12, C21, C22, ldc, h, c.m, c.st), "postadd");
+  // 7-8. P2 = Low(A12 A12^T), U3 = P1 + P2 -> C11
+  if (last) {
+    Operand X{A12, lda, pA12};
+    leaf(c, X, X, true, h, h, kap, C11, ldc, 1, 1);  // accumulates onto P1
+  } else {
+    rec(c, A12, lda, h, kap, C12, ldc, levels - 1, no_planes());
+    if (!c.ar.dry) check(c, launch_add_low(C11, C12, ldc, h, c.m, c.st), "add_low");
+  }
+  c.ar.used = mark;
+}
+
+static int auto_levels(int64_t n, int64_t k) {
+  int l = 0;
+  while (l < 6 && (n >> (l + 1)) >= 2048 && (k >> (l + 1)) >= 1024) ++l;
+  return l;
+}
+
+struct Prepared {
+  int levels;
+  int64_t n_pad, k_pad;
+  bool padded;
+};
+
+static Prepared prepare(int64_t n, int64_t k, const YParams &y, uint32_t flags) {
+  Prepared r;
+  const uint32_t lv = (flags & AAT_LEVELS_MASK) >> 8;
+  r.levels = lv ? (int)lv - 1 : auto_levels(n, k);
+  // each level halves n and k; k/2 must be even at every level for kind 2
+  const int64_t mn = (int64_t)1 << r.levels;
+  const int64_t mk = (int64_t)1 << (r.levels + (y.kind == 2 ? 1 : 0));
+  r.n_pad = (n + mn - 1) / mn * mn;
+  r.k_pad = (k + mk - 1) / mk * mk;
+  if (r.levels == 0) {
+    r.n_pad = n;
+    r.k_pad = k;
+  }
+  r.padded = (r.n_pad != n || r.k_pad != k);
+  return r;
+}
+
+static int validate(uint32_t p) {
+  if (p >= (1u << 31)) return fail(AAT_ERANGE, "p must be below 2^31");
+  if (p < 3 || (p & 1u) == 0 || !is_prime_u32(p)) return fail(AAT_ENOTPRIME, "p must be an odd prime");
+  return AAT_OK;
+}
+
+static int setup(Ctx &c, uint32_t p, uint32_t flags, cudaStream_t st) {
+  int e = validate(p);
+  if (e) return e;
+  c.m = make_modp(p);
+  if (!make_y(p, &c.y)) return fail(AAT_ERANGE, "no skew-unitary Y found");
+  c.ds = make_digits(p);
+  c.leaf = flags & AAT_LEAF_MASK;
+  if (c.leaf != AAT_LEAF_TC && c.leaf != AAT_LEAF_SIMT)
+    return fail(AAT_EUNSUPPORTED, "unknown leaf kind");
+  const char *eb = getenv("AAT_EXACT_BITS");
+  c.exact_bits = eb ? atoi(eb) : 23;
+  c.st = st;
+  c.stats = nullptr;
+  return AAT_OK;
+}
+
+// Runs (or, with dry, measures) the whole product; returns workspace bytes.
+static size_t run_plan(Ctx &c, const int32_t *A, int64_t n, int64_t k, int64_t lda, int32_t *C,
+                       int64_t ldc, uint32_t flags, bool dry, char *ws) {
+  Prepared pr = prepare(n, k, c.y, flags);
+  c.ar = Arena();
+  c.ar.dry = dry;
+  c.ar.base = ws;
+  const int32_t *Aw = A;
+  int64_t ldaw = lda;
+  int32_t *Cw = C;
+  int64_t ldcw = ldc;
+  if (pr.padded) {
+    int32_t *Ap = (int32_t *)c.ar.get((size_t)pr.n_pad * pr.k_pad * 4);
+    int32_t *Cp = (int32_t *)c.ar.get((size_t)pr.n_pad * pr.n_pad * 4);
+    if (!dry)
+      check(c, launch_pad_copy(A, lda, n, k, Ap, pr.k_pad, pr.n_pad, pr.k_pad, c.st), "pad");
+    Aw = Ap;
+    ldaw = pr.k_pad;
+    Cw = Cp;
+    ldcw = pr.n_pad;
+  }
+  if (c.stats) {
+    c.stats->levels = pr.levels;
+    c.stats->n_pad = pr.n_pad;
+    c.stats->k_pad = pr.k_pad;
+  }
+  rec(c, Aw, ldaw, pr.n_pad, pr.k_pad, Cw, ldcw, pr.levels, no_planes());
+  if (pr.padded && !dry) check(c, launch_copy_low(Cw, ldcw, C, ldc, n, c.st), "unpad");
+  if (!dry && (flags & AAT_ZERO_UPPER)) check(c, launch_zero_upper(C, ldc, n, c.st), "zero upper");
+  return c.ar.peak;
+}
+
+static bool overlaps(const void *a, size_t an, const void *b, size_t bn) {
+  const char *x = (const char *)a, *y = (const char *)b;
+  return x < y + bn && y < x + an;
+}
+
+static int check_device() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "no CUDA device");
+  int major = 0, minor = 0;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  if (major != 10 || minor != 3)
+    return fail(AAT_ECUDA, "this library is built for sm_103a (GB300); device is sm_" +
+                               std::to_string(major * 10 + minor));
+  return AAT_OK;
+}
+
+}  // namespace aat
+
+using namespace aat;
+
+// ================================================================ C ABI
+
+extern "C" {
+
+int aat_version(void) { return 100; }
+
+const char *aat_last_error(void) { return g_last_error.c_str(); }
+
+int aat_modp_ex(const int32_t *A, int64_t n, int64_t k, int64_t lda, uint32_t p, int32_t *C,
+                int64_t ldc, uint32_t flags, void *stream) {
+  g_last_error.clear();
+  if (n < 0 || k < 0) return fail(AAT_EINVAL, "negative size");
+  if (n > (1 << 30) || k > (1 << 30)) return fail(AAT_EINVAL, "size too large");
+  if (lda < std::max<int64_t>(k, 1) || ldc < std::max<int64_t>(n, 1))
+    return fail(AAT_EINVAL, "stride smaller than the row length");
+  if (n > 0 && (!C || (k > 0 && !A))) return fail(AAT_EINVAL, "null pointer");
+  int e;
+  Ctx c;
+  if ((e = setup(c, p, flags, (cudaStream_t)stream))) return e;
+  if (n == 0) return AAT_OK;
+  if (k > 0 && overlaps(A, (size_t)((n - 1) * lda + k) * 4, C, (size_t)((n - 1) * ldc + n) * 4))
+    return fail(AAT_EINVAL, "C overlaps A");
+  if ((e = check_device())) return e;
+  if (k == 0) {
+    cudaError_t ce = cudaMemset2DAsync(C, (size_t)ldc * 4, 0, (size_t)n * 4, (size_t)n, c.st);
+    return ce == cudaSuccess ? AAT_OK : cuda_fail(ce, "memset");
+  }
+  const size_t need = run_plan(c, A, n, k, lda, C, ldc, flags, true, nullptr);
+  void *ws = nullptr;
+  if ((e = ensure_workspace(need, &ws))) return e;
+  c.err = AAT_OK;
+  run_plan(c, A, n, k, lda, C, ldc, flags, false, (char *)ws);
+  return c.err;
+}
+
+int aat_modp(const int32_t *A, int64_t n, int64_t k, uint32_t p, int32_t *C, void *stream) {
+  return aat_modp_ex(A, n, k, k, p, C, n, 0u, stream);
+}
+
+int aat_modp_host(const int32_t *A_host, int64_t n, int64_t k, uint32_t p, int32_t *C_host,
+                  uint32_t flags) {
+  g_last_error.clear();
+  if (n < 0 || k < 0) return fail(AAT_EINVAL, "negative size");
+  if (n > 0 && (!C_host || (k > 0 && !A_host))) return fail(AAT_EINVAL, "null pointer");
+  if (n == 0) return AAT_OK;
+  int e;
+  if ((e = check_device())) return e;
+  const size_t abytes = (size_t)n * std::max<int64_t>(k, 1) * 4, cbytes = (size_t)n * n * 4;
+  DeviceState *s;
+  {
+    std::lock_guard<std::mutex> lock(g_state_mu);
+    s = &state();
+    if (!s->e2e_stream) cudaStreamCreateWithFlags(&s->e2e_stream, cudaStreamNonBlocking);
+    if (s->e2e_a_size < abytes) {
+      if (s->e2e_a) cudaFree(s->e2e_a);
+      s->e2e_a = nullptr;
+      s->e2e_a_size = 0;
+      if (cudaMalloc(&s->e2e_a, abytes) != cudaSuccess) return fail(AAT_ENOMEM, "e2e buffer A");
+      s->e2e_a_size = abytes;
+    }
+    if (s->e2e_c_size < cbytes) {
+      if (s->e2e_c) cudaFree(s->e2e_c);
+      s->e2e_c = nullptr;
+      s->e2e_c_size = 0;
+      if (cudaMalloc(&s->e2e_c, cbytes) != cudaSuccess) return fail(AAT_ENOMEM, "e2e buffer C");
+      s->e2e_c_size = cbytes;
+    }
+  }
+  cudaStream_t st = s->e2e_stream;
+  cudaError_t ce;
+  if (k > 0 && (ce = cudaMemcpyAsync(s->e2e_a, A_host, (size_t)n * k * 4, cudaMemcpyHostToDevice,
+                                     st)) != cudaSuccess)
+    return cuda_fail(ce, "copy A to the device");
+  e = aat_modp_ex((const int32_t *)s->e2e_a, n, k, std::max<int64_t>(k, 1), p, (int32_t *)s->e2e_c,
+                  n, flags, st);
+  if (e) return e;
+  if ((ce = cudaMemcpyAsync(C_host, s->e2e_c, cbytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return cuda_fail(ce, "copy C to the host");
+  if ((ce = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(ce, "synchronize");
+  return AAT_OK;
+}
+
+int aat_gemm_modp(const int32_t *X, int64_t ldx, const int32_t *Y, int64_t ldy, int64_t m,
+                  int64_t n, int64_t k, uint32_t p, int32_t *C, int64_t ldc, uint32_t flags,
+                  void *stream) {
+  g_last_error.clear();
+  if (m < 0 || n < 0 || k < 0) return fail(AAT_EINVAL, "negative size");
+  if (ldx < std::max<int64_t>(k, 1) || ldy < std::max<int64_t>(k, 1) ||
+      ldc < std::max<int64_t>(n, 1))
+    return fail(AAT_EINVAL, "stride smaller than the row length");
+  if (m > 0 && n > 0 && (!C || (k > 0 && (!X || !Y)))) return fail(AAT_EINVAL, "null pointer");
+  int e;
+  Ctx c;
+  if ((e = setup(c, p, flags, (cudaStream_t)stream))) return e;
+  if (m == 0 || n == 0) return AAT_OK;
+  if ((e = check_device())) return e;
+  if (k == 0) {
+    cudaError_t ce = cudaMemset2DAsync(C, (size_t)ldc * 4, 0, (size_t)n * 4, (size_t)m, c.st);
+    return ce == cudaSuccess ? AAT_OK : cuda_fail(ce, "memset");
+  }
+  const bool same = (X == Y && ldx == ldy && m == n);
+  size_t need = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    void *ws = nullptr;
+    c.ar = Arena();
+    c.ar.dry = (pass == 0);
+    if (pass == 1) {
+      if ((e = ensure_workspace(need, &ws))) return e;
+      c.ar.base = (char *)ws;
+    }
+    Operand ox{X, ldx, no_planes()}, oy{Y, ldy, no_planes()};
+    leaf(c, ox, oy, same, m, n, k, C, ldc, 0, 0);
+    need = c.ar.peak;
+  }
+  return c.err;
+}
+
+size_t aat_workspace_size(int64_t n, int64_t k, uint32_t p, uint32_t flags) {
+  Ctx c;
+  if (n <= 0 || k <= 0 || setup(c, p, flags, nullptr)) return 0;
+  return run_plan(c, nullptr, n, k, k, nullptr, n, flags, true, nullptr);
+}
+
+int aat_device_status(int reset) {
+  int32_t *d = device_status_ptr();
+  if (!d) return fail(AAT_ECUDA, "no device status word");
+  cudaError_t ce = cudaDeviceSynchronize();
+  if (ce != cudaSuccess) return cuda_fail(ce, "synchronize");
+  int32_t v = 0;
+  cudaMemcpy(&v, d, sizeof(v), cudaMemcpyDeviceToHost);
+  if (reset) cudaMemset(d, 0, sizeof(int32_t));
+  return v;
+}
+
+void aat_shutdown(void) {
+  cudaDeviceSynchronize();
+  leaf_tc_release();
+  std::lock_guard<std::mutex> lock(g_state_mu);
+  for (auto &kv : g_states) {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(kv.first);
+    DeviceState &s = kv.second;
+    if (s.ws) cudaFree(s.ws);
+    if (s.status) cudaFree(s.status);
+    if (s.e2e_a) cudaFree(s.e2e_a);
+    if (s.e2e_c) cudaFree(s.e2e_c);
+    if (s.e2e_stream) cudaStreamDestroy(s.e2e_stream);
+    cudaSetDevice(cur);
+  }
+  g_states.clear();
+}
+
+// ------------------------------------------------------------ test hooks
+
+int aatx_is_prime(uint64_t p) { return is_prime_u32(p) ? 1 : 0; }
+
+int64_t aatx_sqrt_mod(int64_t a, uint64_t p) {
+  uint64_t r;
+  if (p < 3 || !is_prime_u32(p)) return -1;
+  return sqrt_mod(canon64(a, p), p, &r) ? (int64_t)r : -1;
+}
+
+int aatx_sos(int64_t k, uint64_t p, uint64_t *a, uint64_t *b) {
+  if (p < 3 || !is_prime_u32(p)) return AAT_ENOTPRIME;
+  return sos(canon64(k, p), p, a, b) ? AAT_OK : AAT_ERANGE;
+}
+
+int aatx_y_params(uint32_t p, int *kind, uint32_t *a, uint32_t *b) {
+  int e = validate(p);
+  if (e) return e;
+  YParams y;
+  if (!make_y(p, &y)) return fail(AAT_ERANGE, "no Y");
+  *kind = y.kind;
+  *a = (uint32_t)(y.a < 0 ? y.a + (int64_t)p : y.a);
+  *b = (uint32_t)(y.b < 0 ? y.b + (int64_t)p : y.b);
+  return AAT_OK;
+}
+
+int aatx_digit_spec(uint32_t p, int *b, int *L, int *dmax) {
+  int e = validate(p);
+  if (e) return e;
+  DigitSpec d = make_digits(p);
+  *b = d.b;
+  *L = d.L;
+  for (int i = 0; i < 8; ++i) dmax[i] = d.dmax[i];
+  return AAT_OK;
+}
+
+int aatx_plan_stats(int64_t n, int64_t k, uint32_t p, uint32_t flags, aatx_plan_stats_t *out) {
+  if (!out || n <= 0 || k <= 0) return fail(AAT_EINVAL, "bad arguments");
+  std::memset(out, 0, sizeof(*out));
+  Ctx c;
+  int e = setup(c, p, flags, nullptr);
+  if (e) return e;
+  c.stats = out;
+  out->workspace_bytes = run_plan(c, nullptr, n, k, k, nullptr, n, flags, true, nullptr);
+  return AAT_OK;
+}
+
+int aatx_sblocks(const int32_t *A, int64_t n, int64_t k, int64_t lda, uint32_t p, int32_t *S1,
+                 int32_t *S2, int32_t *S3, int32_t *S4, int64_t lds, void *stream) {
+  Ctx c;
+  int e = setup(c, p, 0, (cudaStream_t)stream);
+  if (e) return e;
+  if ((e = check_device())) return e;
+  if (n % 2 || k % 2 || (c.y.kind == 2 && (k / 2) % 2)) return fail(AAT_EINVAL, "bad shape");
+  SKernelOut o;
+  std::memset(&o, 0, sizeof(o));
+  int32_t *S[4] = {S1, S2, S3, S4};
+  for (int q = 0; q < 4; ++q) {
+    o.s[q] = S[q];
+    o.lds[q] = lds;
+  }
+  cudaError_t ce = launch_sblocks(A, lda, n / 2, k / 2, c.m, c.y, c.ds.b, o, c.st);
+  return ce == cudaSuccess ? AAT_OK : cuda_fail(ce, "sblocks");
+}
+
+int aatx_split(const int32_t *X, int64_t rows, int64_t cols, int64_t ldx, uint32_t p,
+               uint16_t *planes, void *stream) {
+  Ctx c;
+  int e = setup(c, p, 0, (cudaStream_t)stream);
+  if (e) return e;
+  if ((e = check_device())) return e;
+  Planes P;
+  P.ptr = (__nv_bfloat16 *)planes;
+  P.rows = rows;
+  P.cols = cols;
+  P.kstride = (cols + 7) / 8 * 8;
+  P.L = c.ds.L;
+  cudaError_t ce = launch_split(X, ldx, rows, cols, c.m, c.ds.b, P, c.st);
+  return ce == cudaSuccess ? AAT_OK : cuda_fail(ce, "split");
+}
+
+int aatx_leaf(const int32_t *X, int64_t ldx, const int32_t *Y, int64_t ldy, int64_t M, int64_t N,
+              int64_t K, uint32_t p, int32_t *C, int64_t ldc, int lower, int accumulate,
+              uint32_t leafkind, int exact_bits, void *stream) {
+  Ctx c;
+  int e = setup(c, p, leafkind, (cudaStream_t)stream);
+  if (e) return e;
+  if ((e = check_device())) return e;
+  if (exact_bits > 0) c.exact_bits = exact_bits;
+  if (M <= 0 || N <= 0 || K <= 0) return fail(AAT_EINVAL, "bad sizes");
+  const bool same = (X == Y && ldx == ldy && M == N);
+  size_t need = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    void *ws = nullptr;
+    c.ar = Arena();
+    c.ar.dry = (pass == 0);
+    if (pass == 1) {
+      if ((e = ensure_workspace(need, &ws))) return e;
+      c.ar.base = (char *)ws;
+    }
+    Operand ox{X, ldx, no_planes()}, oy{Y, ldy, no_planes()};
+    leaf(c, ox, oy, same, M, N, K, C, ldc, lower, accumulate);
+    need = c.ar.peak;
+  }
+  return c.err;
+}
+
+int aatx_postadd(int32_t *C, int64_t ldc, int64_t h, uint32_t p, void *stream) {
+  Ctx c;
+  int e = setup(c, p, 0, (cudaStream_t)stream);
+  if (e) return e;
+  if ((e = check_device())) return e;
+  cudaError_t ce =
+      launch_postadd(C, C + h, C + h * ldc, C + h * ldc + h, ldc, h, c.m, (cudaStream_t)stream);
+  return ce == cudaSuccess ? AAT_OK : cuda_fail(ce, "postadd");
+}
+
+}  // extern "C"

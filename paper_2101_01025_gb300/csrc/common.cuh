@@ -1,0 +1,206 @@
+// common.cuh -- shared definitions of the CUDA path: modular arithmetic on
+// balanced residues, the digit-plane layout of the tensor-core leaves, the
+// device status word and the internal launcher declarations.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/aat.h"
+
+namespace aat {
+
+// ---------------------------------------------------------------- F_p
+
+// Constants of an odd prime p < 2^31.  Residues inside the library are
+// int32 values congruent to the residue with |x| < p; "balanced" means
+// |x| <= (p - 1) / 2.
+struct ModP {
+  uint32_t p;     // the prime
+  uint32_t half;  // (p - 1) / 2
+  uint64_t mu;    // floor(2^64 / p), Barrett constant
+  uint64_t off;   // a multiple of p, >= 2^62: x + off >= 0 for |x| < 2^62
+  uint32_t mu32;  // floor(2^32 / p)
+};
+
+ModP make_modp(uint32_t p);
+
+// Barrett reduction (Barrett 1986) of x < 2^64: the estimate q is at most
+// 2 below floor(x / p), so two conditional subtractions finish it.
+__host__ __device__ __forceinline__ uint32_t red_u64(uint64_t x, const ModP &m) {
+#ifdef __CUDA_ARCH__
+  uint64_t q = __umul64hi(x, m.mu);
+#else
+  uint64_t q = (uint64_t)(((unsigned __int128)x * m.mu) >> 64);
+#endif
+  uint64_t r = x - q * (uint64_t)m.p;
+  if (r >= m.p) r -= m.p;
+  if (r >= m.p) r -= m.p;
+  return (uint32_t)r;
+}
+
+__host__ __device__ __forceinline__ int32_t to_bal(uint32_t r, const ModP &m) {
+  return r > m.half ? (int32_t)r - (int32_t)m.p : (int32_t)r;
+}
+
+// Any |x| < 2^62 to balanced.
+__host__ __device__ __forceinline__ int32_t red_s64(int64_t x, const ModP &m) {
+  return to_bal(red_u64((uint64_t)x + m.off, m), m);
+}
+
+// Any |x| < 2^62 to canonical [0, p).
+__host__ __device__ __forceinline__ uint32_t red_s64_canon(int64_t x, const ModP &m) {
+  return red_u64((uint64_t)x + m.off, m);
+}
+
+// Any int32 to canonical [0, p) with a 32-bit Barrett step: the estimate
+// q = floor(|x| mu32 / 2^32) is at most 2 below floor(|x| / p).
+__host__ __device__ __forceinline__ uint32_t red_i32_canon(int32_t x, const ModP &m) {
+  const uint32_t ax = x < 0 ? (uint32_t)(-(int64_t)x) : (uint32_t)x;
+#ifdef __CUDA_ARCH__
+  const uint32_t q = __umulhi(ax, m.mu32);
+#else
+  const uint32_t q = (uint32_t)(((uint64_t)ax * m.mu32) >> 32);
+#endif
+  uint32_t r = ax - q * m.p;
+  if (r >= m.p) r -= m.p;
+  if (r >= m.p) r -= m.p;
+  return (x < 0 && r) ? m.p - r : r;
+}
+
+// |x| < p to balanced.
+__host__ __device__ __forceinline__ int32_t bal(int32_t x, const ModP &m) {
+  if (x > (int32_t)m.half) return x - (int32_t)m.p;
+  if (x < -(int32_t)m.half) return x + (int32_t)m.p;
+  return x;
+}
+
+// a + b for balanced a, b (result balanced).
+__host__ __device__ __forceinline__ int32_t add_bal(int32_t a, int32_t b, const ModP &m) {
+  int32_t s = a + b;  // |s| <= p - 1 < 2^31
+  return bal(s, m);
+}
+
+__host__ __device__ __forceinline__ int32_t sub_bal(int32_t a, int32_t b, const ModP &m) {
+  int32_t s = a - b;
+  return bal(s, m);
+}
+
+__host__ __device__ __forceinline__ uint32_t bal_to_canon(int32_t x, const ModP &m) {
+  return x < 0 ? (uint32_t)(x + (int32_t)m.p) : (uint32_t)x;
+}
+
+// ------------------------------------------------------ skew-unitary Y
+
+// ykind 1: Y = i I, i^2 = -1 (Sec. 4.2).
+// ykind 2: Y = [[a, b], [-b, a]] (x) I_{kappa/2} (Prop. 4.2): column j < kappa/2
+// of X Y is a X_j - b X_{j+kappa/2}; column j + kappa/2 is b X_j + a X_{j+kappa/2}.
+struct YParams {
+  int kind;
+  int32_t a;  // balanced: i for kind 1, a for kind 2
+  int32_t b;  // balanced: 0 for kind 1
+};
+
+// ---------------------------------------------------- digit planes
+
+// A residue block X (rows x cols) stored as L planes of signed base-2^b
+// digits in bf16: X = sum_d 2^(b d) D_d, each digit exactly representable.
+// Plane d, row r, column c lives at ptr[(d * rows + r) * kstride + c];
+// kstride is a multiple of 8 (16-byte rows for the tensor memory accelerator).
+struct Planes {
+  __nv_bfloat16 *ptr;
+  int64_t rows;
+  int64_t cols;
+  int64_t kstride;
+  int L;
+};
+
+struct DigitSpec {
+  int b;          // digit width in bits
+  int L;          // number of digits
+  int dmax[8];    // bound on |digit| per position
+};
+
+// Balanced digits of a balanced residue x: all but the last in
+// [-2^(b-1), 2^(b-1) - 1], the last carries the rest.
+__device__ __forceinline__ void store_digits(const Planes &P, int64_t r, int64_t c,
+                                             int32_t x, int b) {
+  const int32_t half = 1 << (b - 1);
+  const int32_t mask = (1 << b) - 1;
+  const int64_t plane = P.rows * P.kstride;
+  __nv_bfloat16 *dst = P.ptr + r * P.kstride + c;
+  for (int d = 0; d < P.L - 1; ++d) {
+    int32_t dig = ((x + half) & mask) - half;
+    dst[d * plane] = __float2bfloat16_rn((float)dig);
+    x = (x - dig) >> b;
+  }
+  dst[(P.L - 1) * plane] = __float2bfloat16_rn((float)x);
+}
+
+// --------------------------------------------------- device status
+
+// Sticky status word written by kernels whose bounded waits give up.
+int32_t *device_status_ptr();
+
+// ------------------------------------------------ internal launchers
+
+// K1: the four additions of Algorithm 1 with Y applied in registers.
+// Reads the four h x kappa blocks of A once.  Every output is optional
+// (a null pointer skips it): S1..S4 as int32 canonical residues, S1..S4 as
+// digit planes, and digit planes of A11, A12, A22.
+struct SKernelOut {
+  int32_t *s[4];
+  int64_t lds[4];
+  Planes sp[4];
+  Planes a11, a12, a22;
+};
+cudaError_t launch_sblocks(const int32_t *A, int64_t lda, int64_t h, int64_t kappa,
+                           const ModP &m, const YParams &y, int b,
+                           const SKernelOut &o, cudaStream_t st);
+
+// Split an int32 residue block into digit planes.
+cudaError_t launch_split(const int32_t *X, int64_t ldx, int64_t rows, int64_t cols,
+                         const ModP &m, int b, const Planes &P, cudaStream_t st);
+
+// K6: U4 and U5 of Algorithm 1 from P1 (Low, in C11), P5 (Low, in C12),
+// P3 (in C21) and P4^T (in C22); writes U4 over C21 and Low(U5) over C22.
+cudaError_t launch_postadd(int32_t *C11, int32_t *C12, int32_t *C21, int32_t *C22,
+                           int64_t ldc, int64_t h, const ModP &m, cudaStream_t st);
+
+// Low(C11) <- Low(C11 + C12)   (U3 = P1 + P2)
+cudaError_t launch_add_low(int32_t *C11, const int32_t *C12, int64_t ldc, int64_t h,
+                           const ModP &m, cudaStream_t st);
+
+// Copy / pad: dst (rows_d x cols_d) <- src (rows x cols) with zeros outside.
+cudaError_t launch_pad_copy(const int32_t *src, int64_t lds, int64_t rows, int64_t cols,
+                            int32_t *dst, int64_t ldd, int64_t rows_d, int64_t cols_d,
+                            cudaStream_t st);
+// Low(dst) <- Low(src) for an n x n block.
+cudaError_t launch_copy_low(const int32_t *src, int64_t lds, int32_t *dst, int64_t ldd,
+                            int64_t n, cudaStream_t st);
+cudaError_t launch_zero_upper(int32_t *C, int64_t ldc, int64_t n, cudaStream_t st);
+
+// Plain CUDA-core leaf: out = X Y^T mod p (lower triangle only if `lower`;
+// out = out + X Y^T if `accumulate`).  Exact int64 arithmetic.
+cudaError_t launch_leaf_simt(const int32_t *X, int64_t ldx, const int32_t *Y, int64_t ldy,
+                             int64_t M, int64_t N, int64_t K, int32_t *out, int64_t ldo,
+                             int lower, int accumulate, const ModP &m, cudaStream_t st);
+
+// Tensor-core leaf: out = sum over digit pairs (i, j) of 2^(b (i + j))
+// X_i Y_j^T mod p on tcgen05 (BF16 digits, FP32 accumulation drained to
+// int32 before any partial sum can leave the exact range).
+struct TcLeafArgs {
+  Planes x, y;            // digit planes of X (M x K) and Y (N x K)
+  DigitSpec dx, dy;       // their digit specs
+  int64_t M, N, K;
+  int32_t *out;
+  int64_t ldo;
+  int lower;              // only tiles/entries with i >= j
+  int accumulate;         // out <- out + product
+  int exact_bits;         // |partial FP32 sums| kept <= 2^exact_bits
+};
+cudaError_t launch_leaf_tc(const TcLeafArgs &a, const ModP &m, cudaStream_t st);
+void leaf_tc_release();
+
+}  // namespace aat

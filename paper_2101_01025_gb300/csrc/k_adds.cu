@@ -1,0 +1,280 @@
+// k_adds.cu -- the block additions of Algorithm 1 (Sec. 3) on the GPU.
+//
+// These kernels are bound by HBM bandwidth: each reads and writes every
+// element once, with consecutive threads on consecutive columns of a row so
+// that every warp access is one contiguous segment.
+#include "common.cuh"
+
+namespace aat {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ int32_t ld_bal(const int32_t *p, const ModP &m) {
+  return bal(__ldg(p), m);
+}
+
+__device__ __forceinline__ bool has(const Planes &P) { return P.ptr != nullptr; }
+
+// Y applied to the pair (x_j, x_{j+kappa/2}) for kind 2, or to x_j for kind 1.
+__device__ __forceinline__ void apply_y2(int32_t x0, int32_t x1, const YParams &y,
+                                         const ModP &m, int32_t &o0, int32_t &o1) {
+  // [x0 x1] [[a, b], [-b, a]] = [a x0 - b x1, b x0 + a x1]
+  o0 = red_s64((int64_t)y.a * x0 - (int64_t)y.b * x1, m);
+  o1 = red_s64((int64_t)y.b * x0 + (int64_t)y.a * x1, m);
+}
+
+// One thread per (row i, column j) with j < kappa/2 for kind 2 (it also
+// handles column j + kappa/2), or j < kappa for kind 1.
+__global__ void sblocks_kernel(const int32_t *__restrict__ A, int64_t lda, int64_t h,
+                               int64_t kappa, ModP m, YParams y, int b, SKernelOut o) {
+  const int64_t ncols = (y.kind == 2) ? kappa / 2 : kappa;
+  const int64_t total = h * ncols;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / ncols;
+    const int64_t j = t - i * ncols;
+    const int32_t *r1 = A + i * lda;        // row i of [A11 A12]
+    const int32_t *r2 = A + (h + i) * lda;  // row i of [A21 A22]
+    if (y.kind == 2) {
+      const int64_t jj = j + kappa / 2;
+      int32_t a11_0 = ld_bal(r1 + j, m), a11_1 = ld_bal(r1 + jj, m);
+      int32_t a12_0 = ld_bal(r1 + kappa + j, m), a12_1 = ld_bal(r1 + kappa + jj, m);
+      int32_t a21_0 = ld_bal(r2 + j, m), a21_1 = ld_bal(r2 + jj, m);
+      int32_t a22_0 = ld_bal(r2 + kappa + j, m), a22_1 = ld_bal(r2 + kappa + jj, m);
+      // S1 = (A21 - A11) Y
+      int32_t s1_0, s1_1;
+      apply_y2(sub_bal(a21_0, a11_0, m), sub_bal(a21_1, a11_1, m), y, m, s1_0, s1_1);
+      // S2 = A22 - A21 Y
+      int32_t t0, t1;
+      apply_y2(a21_0, a21_1, y, m, t0, t1);
+      int32_t s2_0 = sub_bal(a22_0, t0, m), s2_1 = sub_bal(a22_1, t1, m);
+      // S3 = S1 - A22, S4 = S3 + A12
+      int32_t s3_0 = sub_bal(s1_0, a22_0, m), s3_1 = sub_bal(s1_1, a22_1, m);
+      int32_t s4_0 = add_bal(s3_0, a12_0, m), s4_1 = add_bal(s3_1, a12_1, m);
+      const int32_t sv0[4] = {s1_0, s2_0, s3_0, s4_0};
+      const int32_t sv1[4] = {s1_1, s2_1, s3_1, s4_1};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (o.s[q]) {
+          o.s[q][i * o.lds[q] + j] = (int32_t)bal_to_canon(sv0[q], m);
+          o.s[q][i * o.lds[q] + jj] = (int32_t)bal_to_canon(sv1[q], m);
+        }
+        if (has(o.sp[q])) {
+          store_digits(o.sp[q], i, j, sv0[q], b);
+          store_digits(o.sp[q], i, jj, sv1[q], b);
+        }
+      }
+      if (has(o.a11)) { store_digits(o.a11, i, j, a11_0, b); store_digits(o.a11, i, jj, a11_1, b); }
+      if (has(o.a12)) { store_digits(o.a12, i, j, a12_0, b); store_digits(o.a12, i, jj, a12_1, b); }
+      if (has(o.a22)) { store_digits(o.a22, i, j, a22_0, b); store_digits(o.a22, i, jj, a22_1, b); }
+    } else {
+      int32_t a11 = ld_bal(r1 + j, m), a12 = ld_bal(r1 + kappa + j, m);
+      int32_t a21 = ld_bal(r2 + j, m), a22 = ld_bal(r2 + kappa + j, m);
+      int32_t s1 = red_s64((int64_t)y.a * sub_bal(a21, a11, m), m);
+      int32_t s2 = sub_bal(a22, red_s64((int64_t)y.a * a21, m), m);
+      int32_t s3 = sub_bal(s1, a22, m);
+      int32_t s4 = add_bal(s3, a12, m);
+      const int32_t sv[4] = {s1, s2, s3, s4};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (o.s[q]) o.s[q][i * o.lds[q] + j] = (int32_t)bal_to_canon(sv[q], m);
+        if (has(o.sp[q])) store_digits(o.sp[q], i, j, sv[q], b);
+      }
+      if (has(o.a11)) store_digits(o.a11, i, j, a11, b);
+      if (has(o.a12)) store_digits(o.a12, i, j, a12, b);
+      if (has(o.a22)) store_digits(o.a22, i, j, a22, b);
+    }
+  }
+}
+
+__global__ void split_kernel(const int32_t *__restrict__ X, int64_t ldx, int64_t rows,
+                             int64_t cols, ModP m, int b, Planes P) {
+  const int64_t total = rows * cols;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / cols, c = t - (t / cols) * cols;
+    store_digits(P, r, c, ld_bal(X + r * ldx + c, m), b);
+  }
+}
+
+// Post-additions of Algorithm 1 for one tile pair {(I, J), (J, I)}, I >= J,
+// of T x T tiles:
+//   U1 = Sym(P1 + P5)         (Low(U1) and Up(U1) = Low(U1)^T)
+//   U2 = U1 + P4,  P4 = (P4^T)^T read transposed from C22
+//   U4 = U2 + P3              -> C21 (both tiles of the pair)
+//   U5 = Low(U2 + P4^T)       -> C22 (lower tile only)
+// Both C22 tiles of the pair are read into shared memory before any write,
+// and no other block touches them, so the in-place update is safe.
+constexpr int T = 32;
+
+__global__ void postadd_kernel(const int32_t *__restrict__ C11, const int32_t *__restrict__ C12,
+                               int32_t *C21, int32_t *C22, int64_t ldc, int64_t h, ModP m) {
+  __shared__ int32_t p4t_ij[T][T + 1];  // C22 tile (I, J) = P4^T block
+  __shared__ int32_t p4t_ji[T][T + 1];  // C22 tile (J, I)
+  __shared__ int32_t u1_ij[T][T + 1];   // U1 tile (I, J) (lower part source)
+  const int64_t ntiles = (h + T - 1) / T;
+  // map blockIdx.x to (I, J) with I >= J
+  int64_t pid = blockIdx.x;
+  int64_t I = (int64_t)((sqrt(8.0 * (double)pid + 1.0) - 1.0) * 0.5);
+  while (I * (I + 1) / 2 > pid) --I;
+  while ((I + 1) * (I + 2) / 2 <= pid) ++I;
+  const int64_t J = pid - I * (I + 1) / 2;
+  if (I >= ntiles) return;
+  const int tx = threadIdx.x % T, ty = threadIdx.x / T;  // 32 x 8 threads
+  const int64_t r0 = I * T, c0 = J * T;
+  // load
+  for (int yy = ty; yy < T; yy += 8) {
+    int64_t r = r0 + yy, c = c0 + tx;
+    if (r < h && c < h) {
+      p4t_ij[yy][tx] = bal(C22[r * ldc + c], m);
+      // U1(r, c): lower entries from P1 + P5, upper ones by symmetry
+      int64_t lr = r >= c ? r : c, lc = r >= c ? c : r;
+      u1_ij[yy][tx] = add_bal(bal(C11[lr * ldc + lc], m), bal(C12[lr * ldc + lc], m), m);
+    }
+    int64_t r2 = c0 + yy, c2 = r0 + tx;  // tile (J, I)
+    if (r2 < h && c2 < h) p4t_ji[yy][tx] = bal(C22[r2 * ldc + c2], m);
+  }
+  __syncthreads();
+  // tile (I, J): U4 and U5
+  for (int yy = ty; yy < T; yy += 8) {
+    int64_t r = r0 + yy, c = c0 + tx;
+    if (r < h && c < h) {
+      int32_t u1 = u1_ij[yy][tx];
+      int32_t p4 = p4t_ji[tx][yy];  // P4(r, c) = P4^T(c, r)
+      int32_t u2 = add_bal(u1, p4, m);
+      int32_t u4 = add_bal(u2, bal(C21[r * ldc + c], m), m);
+      C21[r * ldc + c] = (int32_t)bal_to_canon(u4, m);
+      if (r >= c) {
+        int32_t u5 = add_bal(u2, p4t_ij[yy][tx], m);
+        C22[r * ldc + c] = (int32_t)bal_to_canon(u5, m);
+      }
+    }
+  }
+  if (I == J) return;
+  // tile (J, I): U4 only (upper tile of C22 is not part of Low(U5))
+  for (int yy = ty; yy < T; yy += 8) {
+    int64_t r = c0 + yy, c = r0 + tx;  // r < c here
+    if (r < h && c < h) {
+      int32_t u1 = u1_ij[tx][yy];      // U1(r, c) = U1(c, r)
+      int32_t p4 = p4t_ij[tx][yy];     // P4(r, c) = P4^T(c, r)
+      int32_t u2 = add_bal(u1, p4, m);
+      int32_t u4 = add_bal(u2, bal(C21[r * ldc + c], m), m);
+      C21[r * ldc + c] = (int32_t)bal_to_canon(u4, m);
+    }
+  }
+}
+
+__global__ void add_low_kernel(int32_t *C11, const int32_t *__restrict__ C12, int64_t ldc,
+                               int64_t h, ModP m) {
+  const int64_t total = h * h;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / h, c = t - (t / h) * h;
+    if (c > r) continue;
+    int32_t v = add_bal(bal(C11[r * ldc + c], m), bal(C12[r * ldc + c], m), m);
+    C11[r * ldc + c] = (int32_t)bal_to_canon(v, m);
+  }
+}
+
+__global__ void pad_copy_kernel(const int32_t *__restrict__ src, int64_t lds, int64_t rows,
+                                int64_t cols, int32_t *dst, int64_t ldd, int64_t rows_d,
+                                int64_t cols_d) {
+  const int64_t total = rows_d * cols_d;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / cols_d, c = t - (t / cols_d) * cols_d;
+    dst[r * ldd + c] = (r < rows && c < cols) ? src[r * lds + c] : 0;
+  }
+}
+
+__global__ void copy_low_kernel(const int32_t *__restrict__ src, int64_t lds, int32_t *dst,
+                                int64_t ldd, int64_t n) {
+  const int64_t total = n * n;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / n, c = t - (t / n) * n;
+    if (c <= r) dst[r * ldd + c] = src[r * lds + c];
+  }
+}
+
+__global__ void zero_upper_kernel(int32_t *C, int64_t ldc, int64_t n) {
+  const int64_t total = n * n;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / n, c = t - (t / n) * n;
+    if (c > r) C[r * ldc + c] = 0;
+  }
+}
+
+int grid_for(int64_t total) {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t want = (total + kThreads - 1) / kThreads;
+  int64_t cap = (int64_t)sms * 16;  // 16 blocks of 256 threads per SM
+  if (want > cap) want = cap;
+  if (want < 1) want = 1;
+  return (int)want;
+}
+
+}  // namespace
+
+cudaError_t launch_sblocks(const int32_t *A, int64_t lda, int64_t h, int64_t kappa,
+                           const ModP &m, const YParams &y, int b, const SKernelOut &o,
+                           cudaStream_t st) {
+  const int64_t ncols = (y.kind == 2) ? kappa / 2 : kappa;
+  const int64_t total = h * ncols;
+  if (total <= 0) return cudaSuccess;
+  sblocks_kernel<<<grid_for(total), kThreads, 0, st>>>(A, lda, h, kappa, m, y, b, o);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split(const int32_t *X, int64_t ldx, int64_t rows, int64_t cols,
+                         const ModP &m, int b, const Planes &P, cudaStream_t st) {
+  const int64_t total = rows * cols;
+  if (total <= 0) return cudaSuccess;
+  split_kernel<<<grid_for(total), kThreads, 0, st>>>(X, ldx, rows, cols, m, b, P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_postadd(int32_t *C11, int32_t *C12, int32_t *C21, int32_t *C22,
+                           int64_t ldc, int64_t h, const ModP &m, cudaStream_t st) {
+  if (h <= 0) return cudaSuccess;
+  const int64_t nt = (h + T - 1) / T;
+  const int64_t pairs = nt * (nt + 1) / 2;
+  postadd_kernel<<<(unsigned)pairs, T * 8, 0, st>>>(C11, C12, C21, C22, ldc, h, m);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add_low(int32_t *C11, const int32_t *C12, int64_t ldc, int64_t h,
+                           const ModP &m, cudaStream_t st) {
+  if (h <= 0) return cudaSuccess;
+  add_low_kernel<<<grid_for(h * h), kThreads, 0, st>>>(C11, C12, ldc, h, m);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pad_copy(const int32_t *src, int64_t lds, int64_t rows, int64_t cols,
+                            int32_t *dst, int64_t ldd, int64_t rows_d, int64_t cols_d,
+                            cudaStream_t st) {
+  if (rows_d * cols_d <= 0) return cudaSuccess;
+  pad_copy_kernel<<<grid_for(rows_d * cols_d), kThreads, 0, st>>>(src, lds, rows, cols, dst,
+                                                                  ldd, rows_d, cols_d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_low(const int32_t *src, int64_t lds, int32_t *dst, int64_t ldd,
+                            int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  copy_low_kernel<<<grid_for(n * n), kThreads, 0, st>>>(src, lds, dst, ldd, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero_upper(int32_t *C, int64_t ldc, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  zero_upper_kernel<<<grid_for(n * n), kThreads, 0, st>>>(C, ldc, n);
+  return cudaGetLastError();
+}
+
+}  // namespace aat

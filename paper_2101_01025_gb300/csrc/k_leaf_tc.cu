@@ -1,0 +1,663 @@
+// k_leaf_tc.cu -- exact leaf products of Algorithm 1 on the 5th-generation
+// tensor cores (tcgen05, sm_103a).
+//
+// A leaf product R = X Y^T mod p (X: M x K, Y: N x K balanced residues) is
+// computed from signed base-2^b digit planes, X = sum_i 2^(b i) X_i, as
+//
+//     R = sum_{i,j} 2^(b (i + j)) X_i Y_j^T  mod p.
+//
+// Every digit is an integer of at most 9 bits, exact in BF16, and every
+// product of two digits is exact in FP32.  The tensor core accumulates in
+// FP32 in tensor memory (TMEM); a chunk of the K loop is cut short whenever
+// the partial sums could leave [-2^exact_bits, 2^exact_bits] (exact_bits <=
+// 24 keeps every integer representable), and the chunk's exact integer
+// result is drained by the epilogue warps into int32 registers.  Digit pairs
+// are processed in decreasing weight; between pairs the int32 accumulator is
+// multiplied by 2^(b * gap) and reduced mod p (Horner), so one balanced int32
+// per output entry carries the whole sum (delayed Barrett reduction).
+//
+// Kernel organisation (one CTA per SM, persistent over a tile list):
+//   warp 0        TMA producer: 128x64 tile of X_i and 256x64 tile of Y_j per
+//                 stage into 128B-swizzled shared memory (4 stages)
+//   warp 1        TMEM allocator + single-thread tcgen05.mma issuer,
+//                 M=128 N=256 K=16 per instruction, FP32 accumulator in one of
+//                 two 256-column TMEM buffers (double buffered per chunk)
+//   warps 2..9    epilogue: tcgen05.ld of the finished chunk, float -> int32,
+//                 accumulate; mod-p Horner step at digit-pair boundaries;
+//                 canonical store (lower triangle only for SYRK leaves)
+// Every mbarrier wait is bounded (kTimeoutNs): on expiry the CTA sets the
+// device status word to AAT_ETIMEOUT, stops issuing work, waits (bounded) for
+// its copies and MMAs in flight, frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "common.cuh"
+
+namespace aat {
+
+namespace {
+
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr int A_BYTES = BM * BK * 2;
+constexpr int B_BYTES = BN * BK * 2;
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int EPI_WARPS = 8;
+constexpr int THREADS = 64 + EPI_WARPS * 32;
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t ACC_COLS = 256;
+constexpr int MAX_GROUPS = 64;
+constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + 256;
+constexpr unsigned long long kTimeoutNs = 4000000000ull;  // 4 s
+
+// Instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator (bit 4),
+// A and B BF16 (bits 7, 10), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) |
+                           ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+
+struct Group {
+  int16_t xp, yp;   // digit planes of X and Y
+  int32_t kb0, kb1; // k-block range [kb0, kb1) (units of BK)
+  int32_t kchunk;   // k-blocks per FP32 accumulation chunk
+  uint32_t ratio;   // accumulator multiplier (mod p) applied before the group
+};
+
+struct Params {
+  CUtensorMap tmx;  // 3D {K, rows, plane}, box {64, 128, 1}
+  CUtensorMap tmy;  // 3D {K, rows, plane}, box {64, 256, 1}
+  Group g[MAX_GROUPS];
+  int ng;
+  int32_t *out;
+  int64_t ldo, M, N;
+  const int2 *tiles;
+  int ntiles;
+  int lower, accumulate;
+  ModP m;
+  int32_t *status;
+};
+
+// ------------------------------------------------------------ PTX wrappers
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait for the phase of parity `parity` of barrier `bar`.  Returns
+// false when the limit expires (and raises the CTA abort flag and the device
+// status) or when another role of the CTA has aborted.
+__device__ __forceinline__ bool wait_bounded(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                          int32_t *status) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = gtimer();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 63u) == 0) {
+      if (*abort_flag) return false;
+      if (gtimer() - t0 > kTimeoutNs) {
+        *abort_flag = 1;
+        atomicExch(status, (int32_t)AAT_ETIMEOUT);
+        return false;
+      }
+    }
+  }
+}
+
+// Wait with a short limit and no abort check (teardown after an abort).
+__device__ __forceinline__ void wait_quiet(uint32_t bar, uint32_t parity) {
+  const unsigned long long t0 = gtimer();
+  while (!mbar_try(bar, parity)) {
+    if (gtimer() - t0 > 100000000ull) return;  // 100 ms
+  }
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *tm, uint32_t bar,
+                                            int c0, int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+      "l"(a), "l"(b), "r"(IDESC), "r"(acc)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major tile written by TMA with
+// 128-byte swizzling: rows of 128 bytes, 8-row atoms 1024 bytes apart (SBO),
+// descriptor version 1 (bit 46), layout SWIZZLE_128B (2 at bit 61).  The
+// start address moves by 32 bytes per K=16 step inside the atom.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1u << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1u << 46;
+  d |= (uint64_t)2u << 61;
+  return d;
+}
+
+// Drain 32 consecutive FP32 columns of this thread's TMEM lane into the
+// int32 accumulators acc[B .. B+31]: load, wait, convert (the values are
+// exact integers) and add inside one statement, so that the temporaries of
+// one load are dead before the next load is issued.
+template <int B>
+__device__ __forceinline__ void tmem_drain32(uint32_t taddr, int32_t (&acc)[128]) {
+  asm volatile(
+      "{\n\t.reg .b32 t0, t1, t2, t3, t4, t5, t6, t7, t8, t9, t10, t11, t12, t13, t14, t15, t16, t17, t18, t19, t20, t21, t22, t23, t24, t25, t26, t27, t28, t29, t30, t31;\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {t0, t1, t2, t3, t4, t5, t6, t7, t8, t9, t10, t11, t12, t13, t14, t15, t16, t17, t18, t19, t20, t21, t22, t23, t24, t25, t26, t27, t28, t29, t30, t31}, [%32];\n\t"
+      "tcgen05.wait::ld.sync.aligned;\n\t"
+      "cvt.rni.s32.f32 t0, t0;\n\t"
+      "add.s32 %0, %0, t0;\n\t"
+      "cvt.rni.s32.f32 t1, t1;\n\t"
+      "add.s32 %1, %1, t1;\n\t"
+      "cvt.rni.s32.f32 t2, t2;\n\t"
+      "add.s32 %2, %2, t2;\n\t"
+      "cvt.rni.s32.f32 t3, t3;\n\t"
+      "add.s32 %3, %3, t3;\n\t"
+      "cvt.rni.s32.f32 t4, t4;\n\t"
+      "add.s32 %4, %4, t4;\n\t"
+      "cvt.rni.s32.f32 t5, t5;\n\t"
+      "add.s32 %5, %5, t5;\n\t"
+      "cvt.rni.s32.f32 t6, t6;\n\t"
+      "add.s32 %6, %6, t6;\n\t"
+      "cvt.rni.s32.f32 t7, t7;\n\t"
+      "add.s32 %7, %7, t7;\n\t"
+      "cvt.rni.s32.f32 t8, t8;\n\t"
+      "add.s32 %8, %8, t8;\n\t"
+      "cvt.rni.s32.f32 t9, t9;\n\t"
+      "add.s32 %9, %9, t9;\n\t"
+      "cvt.rni.s32.f32 t10, t10;\n\t"
+      "add.s32 %10, %10, t10;\n\t"
+      "cvt.rni.s32.f32 t11, t11;\n\t"
+      "add.s32 %11, %11, t11;\n\t"
+      "cvt.rni.s32.f32 t12, t12;\n\t"
+      "add.s32 %12, %12, t12;\n\t"
+      "cvt.rni.s32.f32 t13, t13;\n\t"
+      "add.s32 %13, %13, t13;\n\t"
+      "cvt.rni.s32.f32 t14, t14;\n\t"
+      "add.s32 %14, %14, t14;\n\t"
+      "cvt.rni.s32.f32 t15, t15;\n\t"
+      "add.s32 %15, %15, t15;\n\t"
+      "cvt.rni.s32.f32 t16, t16;\n\t"
+      "add.s32 %16, %16, t16;\n\t"
+      "cvt.rni.s32.f32 t17, t17;\n\t"
+      "add.s32 %17, %17, t17;\n\t"
+      "cvt.rni.s32.f32 t18, t18;\n\t"
+      "add.s32 %18, %18, t18;\n\t"
+      "cvt.rni.s32.f32 t19, t19;\n\t"
+      "add.s32 %19, %19, t19;\n\t"
+      "cvt.rni.s32.f32 t20, t20;\n\t"
+      "add.s32 %20, %20, t20;\n\t"
+      "cvt.rni.s32.f32 t21, t21;\n\t"
+      "add.s32 %21, %21, t21;\n\t"
+      "cvt.rni.s32.f32 t22, t22;\n\t"
+      "add.s32 %22, %22, t22;\n\t"
+      "cvt.rni.s32.f32 t23, t23;\n\t"
+      "add.s32 %23, %23, t23;\n\t"
+      "cvt.rni.s32.f32 t24, t24;\n\t"
+      "add.s32 %24, %24, t24;\n\t"
+      "cvt.rni.s32.f32 t25, t25;\n\t"
+      "add.s32 %25, %25, t25;\n\t"
+      "cvt.rni.s32.f32 t26, t26;\n\t"
+      "add.s32 %26, %26, t26;\n\t"
+      "cvt.rni.s32.f32 t27, t27;\n\t"
+      "add.s32 %27, %27, t27;\n\t"
+      "cvt.rni.s32.f32 t28, t28;\n\t"
+      "add.s32 %28, %28, t28;\n\t"
+      "cvt.rni.s32.f32 t29, t29;\n\t"
+      "add.s32 %29, %29, t29;\n\t"
+      "cvt.rni.s32.f32 t30, t30;\n\t"
+      "add.s32 %30, %30, t30;\n\t"
+      "cvt.rni.s32.f32 t31, t31;\n\t"
+      "add.s32 %31, %31, t31;\n\t"
+      "}"
+      : "+r"(acc[B + 0]), "+r"(acc[B + 1]), "+r"(acc[B + 2]), "+r"(acc[B + 3]), "+r"(acc[B + 4]), "+r"(acc[B + 5]), "+r"(acc[B + 6]), "+r"(acc[B + 7]), "+r"(acc[B + 8]), "+r"(acc[B + 9]), "+r"(acc[B + 10]), "+r"(acc[B + 11]), "+r"(acc[B + 12]), "+r"(acc[B + 13]), "+r"(acc[B + 14]), "+r"(acc[B + 15]), "+r"(acc[B + 16]), "+r"(acc[B + 17]), "+r"(acc[B + 18]), "+r"(acc[B + 19]), "+r"(acc[B + 20]), "+r"(acc[B + 21]), "+r"(acc[B + 22]), "+r"(acc[B + 23]), "+r"(acc[B + 24]), "+r"(acc[B + 25]), "+r"(acc[B + 26]), "+r"(acc[B + 27]), "+r"(acc[B + 28]), "+r"(acc[B + 29]), "+r"(acc[B + 30]), "+r"(acc[B + 31])
+      : "r"(taddr)
+      : "memory");
+}
+
+// ------------------------------------------------------------------ kernel
+
+__global__ void __launch_bounds__(THREADS, 1) leaf_tc_kernel(const __grid_constant__ Params P) {
+  extern __shared__ uint8_t smem_raw[];
+  // 1024-byte alignment of the shared-window address (128B-swizzle atoms)
+  uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  const uint32_t sbase = smem_u32(smem);
+  uint64_t *bars = (uint64_t *)(smem + (size_t)STAGES * STAGE_BYTES);
+  const uint32_t bar0 = smem_u32(bars);
+#define FULL(s) (bar0 + 8u * (uint32_t)(s))
+#define EMPTY(s) (bar0 + 8u * (uint32_t)(STAGES + (s)))
+#define AFULL(b) (bar0 + 8u * (uint32_t)(2 * STAGES + (b)))
+#define AEMPTY(b) (bar0 + 8u * (uint32_t)(2 * STAGES + 2 + (b)))
+#define DONE (bar0 + 8u * (uint32_t)(2 * STAGES + 4))
+  uint32_t *tmem_slot = (uint32_t *)(bars + 2 * STAGES + 5);
+  volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(FULL(s), 1);
+      mbar_init(EMPTY(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(AFULL(b), 1);
+      mbar_init(AEMPTY(b), EPI_WARPS);
+    }
+    mbar_init(DONE, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    tc_fence_before();
+  }
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ---------------------------------------------------------- producer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t ph = 0;
+      int issued = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
+        const int2 tile = P.tiles[t];
+        for (int gi = 0; gi < P.ng && ok; ++gi) {
+          const Group g = P.g[gi];
+          for (int kb = g.kb0; kb < g.kb1; ++kb) {
+            if (!wait_bounded(EMPTY(stage), ph ^ 1u, abort_flag, P.status)) {
+              ok = false;
+              break;
+            }
+            mbar_expect_tx(FULL(stage), (uint32_t)STAGE_BYTES);
+            const uint32_t sa = sbase + (uint32_t)(stage * STAGE_BYTES);
+            tma_load_3d(sa, &P.tmx, FULL(stage), kb * BK, tile.x * BM, g.xp);
+            tma_load_3d(sa + A_BYTES, &P.tmy, FULL(stage), kb * BK, tile.y * BN, g.yp);
+            ++issued;
+            if (++stage == STAGES) {
+              stage = 0;
+              ph ^= 1u;
+            }
+          }
+        }
+      }
+      if (!ok) {
+        // let the copies in flight land before the CTA exits
+        int s = stage;
+        uint32_t q = ph;
+        for (int i = 0; i < STAGES && i < issued; ++i) {
+          if (--s < 0) {
+            s = STAGES - 1;
+            q ^= 1u;
+          }
+          wait_quiet(FULL(s), q);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t ph = 0, chunk = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
+        for (int gi = 0; gi < P.ng && ok; ++gi) {
+          const Group g = P.g[gi];
+          for (int kb = g.kb0; kb < g.kb1 && ok;) {
+            const int kend = min(kb + g.kchunk, g.kb1);
+            const uint32_t buf = chunk & 1u, use = chunk >> 1;
+            if (!wait_bounded(AEMPTY(buf), (use & 1u) ^ 1u, abort_flag, P.status)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t dt = tmem + buf * ACC_COLS;
+            for (int k = kb; k < kend; ++k) {
+              if (!wait_bounded(FULL(stage), ph, abort_flag, P.status)) {
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+              const uint32_t sa = sbase + (uint32_t)(stage * STAGE_BYTES);
+              const uint32_t sb = sa + A_BYTES;
+#pragma unroll
+              for (int s = 0; s < BK / 16; ++s) {
+                tc_mma(dt, sw128_desc(sa + 32u * s), sw128_desc(sb + 32u * s),
+                       (k > kb || s > 0) ? 1u : 0u);
+              }
+              tc_commit(EMPTY(stage));
+              if (++stage == STAGES) {
+                stage = 0;
+                ph ^= 1u;
+              }
+            }
+            if (!ok) break;
+            tc_commit(AFULL(buf));
+            ++chunk;
+            kb = kend;
+          }
+        }
+      }
+      if (!ok) {
+        tc_commit(DONE);
+        wait_quiet(DONE, 0);
+      }
+    }
+  } else {
+    // ---------------------------------------------------------- epilogue
+    const int e = warp - 2;
+    const int quarter = warp & 3;  // TMEM lanes [32 quarter, 32 quarter + 32)
+    const int chalf = e >> 2;      // columns [128 chalf, 128 chalf + 128)
+    const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+    const ModP m = P.m;
+    uint32_t chunk = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
+      const int2 tile = P.tiles[t];
+      int32_t acc[128];
+#pragma unroll
+      for (int i = 0; i < 128; ++i) acc[i] = 0;
+      for (int gi = 0; gi < P.ng && ok; ++gi) {
+        const Group g = P.g[gi];
+        if (gi > 0) {
+          const int64_t ratio = (int64_t)g.ratio;
+#pragma unroll
+          for (int i = 0; i < 128; ++i) acc[i] = red_s64((int64_t)acc[i] * ratio, m);
+        }
+        for (int kb = g.kb0; kb < g.kb1;) {
+          const int kend = min(kb + g.kchunk, g.kb1);
+          const uint32_t buf = chunk & 1u, use = chunk >> 1;
+          if (!wait_bounded(AFULL(buf), use & 1u, abort_flag, P.status)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t ta = tmem + lane_base + buf * ACC_COLS + (uint32_t)(chalf * 128);
+          tmem_drain32<0>(ta, acc);
+          tmem_drain32<32>(ta + 32u, acc);
+          tmem_drain32<64>(ta + 64u, acc);
+          tmem_drain32<96>(ta + 96u, acc);
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(AEMPTY(buf));
+          ++chunk;
+          kb = kend;
+        }
+      }
+      if (!ok) break;
+      const int64_t row = (int64_t)tile.x * BM + quarter * 32 + lane;
+      const int64_t col0 = (int64_t)tile.y * BN + chalf * 128;
+      // final value, canonical, in place (the last digit pair has weight 1)
+#pragma unroll
+      for (int i = 0; i < 128; ++i) acc[i] = (int32_t)red_i32_canon(acc[i], m);
+      // columns [0, lim) of this thread's 128 are written
+      int64_t lim = P.N - col0;
+      if (P.lower) lim = min(lim, row - col0 + 1);
+      if (row < P.M && lim > 0) {
+        int32_t *orow = P.out + row * P.ldo + col0;
+        const bool vec = ((reinterpret_cast<uintptr_t>(orow) & 15) == 0) && !P.accumulate;
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+          const int c = 4 * q;
+          if (vec && c + 4 <= lim) {
+            *reinterpret_cast<int4 *>(orow + c) = make_int4(acc[c], acc[c + 1], acc[c + 2], acc[c + 3]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              if (c + j < lim) {
+                int32_t v = acc[c + j];
+                if (P.accumulate) v = (int32_t)bal_to_canon(add_bal(to_bal((uint32_t)v, m), bal(orow[c + j], m), m), m);
+                orow[c + j] = v;
+              }
+            }
+          }
+          asm volatile("" ::: "memory");
+        }
+      }
+    }
+  }
+
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS)
+                 : "memory");
+  }
+#undef FULL
+#undef EMPTY
+#undef AFULL
+#undef AEMPTY
+#undef DONE
+}
+
+// ------------------------------------------------------------------ host
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::mutex g_mu;
+std::map<std::tuple<int, int64_t, int64_t, int>, std::pair<int2 *, int>> g_tiles;
+std::map<int, bool> g_attr_set;
+
+cudaError_t get_encode() {
+  if (g_encode) return cudaSuccess;
+  void *fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                   cudaEnableDefault, &q);
+  if (e != cudaSuccess) return e;
+  if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+  g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  return cudaSuccess;
+}
+
+cudaError_t encode_planes(CUtensorMap *tm, const Planes &P, int box_rows) {
+  cuuint64_t dims[3] = {(cuuint64_t)P.cols, (cuuint64_t)P.rows, (cuuint64_t)P.L};
+  cuuint64_t strides[2] = {(cuuint64_t)P.kstride * 2, (cuuint64_t)(P.rows * P.kstride * 2)};
+  cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = g_encode(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void *)P.ptr, dims, strides,
+                        box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+uint32_t pow2mod(uint64_t e, uint32_t p) {
+  uint64_t r = 1 % p, b = 2 % p;
+  while (e) {
+    if (e & 1) r = (r * b) % p;
+    b = (b * b) % p;
+    e >>= 1;
+  }
+  return (uint32_t)r;
+}
+
+// Tile order: super-blocks of 16 x 8 tiles (2048 x 2048 outputs) swept
+// row-major, tiles inside a super-block row-major, so that the CTAs running
+// at the same time share rows of X and columns of Y in L2.
+cudaError_t get_tiles(int dev, int64_t M, int64_t N, int lower, int2 **out, int *count) {
+  auto key = std::make_tuple(dev, M, N, lower);
+  auto it = g_tiles.find(key);
+  if (it != g_tiles.end()) {
+    *out = it->second.first;
+    *count = it->second.second;
+    return cudaSuccess;
+  }
+  const int64_t TI = (M + BM - 1) / BM, TJ = (N + BN - 1) / BN;
+  const int64_t SI = 16, SJ = 8;
+  std::vector<int2> v;
+  for (int64_t bi = 0; bi < TI; bi += SI)
+    for (int64_t bj = 0; bj < TJ; bj += SJ)
+      for (int64_t i = bi; i < std::min(TI, bi + SI); ++i)
+        for (int64_t j = bj; j < std::min(TJ, bj + SJ); ++j) {
+          if (lower && j * BN > i * BM + BM - 1) continue;
+          v.push_back(make_int2((int)i, (int)j));
+        }
+  int2 *d = nullptr;
+  if (!v.empty()) {
+    cudaError_t e = cudaMalloc(&d, v.size() * sizeof(int2));
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpy(d, v.data(), v.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+  }
+  g_tiles[key] = std::make_pair(d, (int)v.size());
+  *out = d;
+  *count = (int)v.size();
+  return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t launch_leaf_tc(const TcLeafArgs &a, const ModP &m, cudaStream_t st) {
+  if (a.M <= 0 || a.N <= 0) return cudaSuccess;
+  if (a.dx.b != a.dy.b || a.x.L != a.dx.L || a.y.L != a.dy.L) return cudaErrorInvalidValue;
+  if (a.x.kstride % 8 || a.y.kstride % 8 || a.x.cols != a.K || a.y.cols != a.K)
+    return cudaErrorInvalidValue;
+  if (((uintptr_t)a.x.ptr | (uintptr_t)a.y.ptr) & 15) return cudaErrorInvalidValue;
+  std::lock_guard<std::mutex> lock(g_mu);
+  cudaError_t e = get_encode();
+  if (e != cudaSuccess) return e;
+  int dev = 0;
+  cudaGetDevice(&dev);
+
+  Params *P = new Params;
+  std::memset(P, 0, sizeof(Params));
+  if ((e = encode_planes(&P->tmx, a.x, BM)) != cudaSuccess ||
+      (e = encode_planes(&P->tmy, a.y, BN)) != cudaSuccess) {
+    delete P;
+    return e;
+  }
+  // digit pairs in decreasing weight 2^(b (i + j))
+  struct Pair { int i, j, s; };
+  std::vector<Pair> pairs;
+  for (int i = 0; i < a.dx.L; ++i)
+    for (int j = 0; j < a.dy.L; ++j) pairs.push_back({i, j, i + j});
+  std::stable_sort(pairs.begin(), pairs.end(),
+                   [](const Pair &u, const Pair &v) { return u.s > v.s; });
+  const int kblocks = (int)((a.K + BK - 1) / BK);
+  const int ebits = std::min(std::max(a.exact_bits, 8), 24);
+  int ng = 0;
+  int prev_s = -1;
+  for (const Pair &pr : pairs) {
+    const int64_t prod = (int64_t)a.dx.dmax[pr.i] * a.dy.dmax[pr.j];
+    int64_t kc = ((int64_t)1 << ebits) / (prod > 0 ? prod : 1) / BK;
+    if (kc < 1) { delete P; return cudaErrorInvalidValue; }
+    // int32 accumulator: (p-1)/2 + K_range * prod must stay below 2^31
+    int64_t room = ((int64_t)1 << 31) - 1 - (int64_t)m.half;
+    int64_t kr = room / (prod > 0 ? prod : 1) / BK;
+    if (kr < 1) { delete P; return cudaErrorInvalidValue; }
+    for (int kb = 0; kb < kblocks; kb += (int)kr) {
+      if (ng >= MAX_GROUPS) { delete P; return cudaErrorInvalidValue; }
+      Group &g = P->g[ng];
+      g.xp = (int16_t)pr.i;
+      g.yp = (int16_t)pr.j;
+      g.kb0 = kb;
+      g.kb1 = (int)std::min<int64_t>(kblocks, kb + kr);
+      g.kchunk = (int)std::min<int64_t>(kc, 1 << 20);
+      g.ratio = (ng == 0) ? 1u : pow2mod((uint64_t)a.dx.b * (uint64_t)(prev_s - pr.s), m.p);
+      prev_s = pr.s;
+      ++ng;
+    }
+  }
+  P->ng = ng;
+  if (prev_s != 0) { delete P; return cudaErrorInvalidValue; }  // pair (0, 0) comes last
+  P->out = a.out;
+  P->ldo = a.ldo;
+  P->M = a.M;
+  P->N = a.N;
+  P->lower = a.lower;
+  P->accumulate = a.accumulate;
+  P->m = m;
+  P->status = device_status_ptr();
+  int2 *tiles = nullptr;
+  int nt = 0;
+  if ((e = get_tiles(dev, a.M, a.N, a.lower, &tiles, &nt)) != cudaSuccess) {
+    delete P;
+    return e;
+  }
+  P->tiles = tiles;
+  P->ntiles = nt;
+  if (!g_attr_set[dev]) {
+    e = cudaFuncSetAttribute(leaf_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)SMEM_BYTES);
+    if (e != cudaSuccess) { delete P; return e; }
+    g_attr_set[dev] = true;
+  }
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = std::max(1, std::min(nt, sms));
+  if (nt > 0) leaf_tc_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(*P);
+  delete P;
+  return cudaGetLastError();
+}
+
+void leaf_tc_release() {
+  std::lock_guard<std::mutex> lock(g_mu);
+  for (auto &kv : g_tiles)
+    if (kv.second.first) cudaFree(kv.second.first);
+  g_tiles.clear();
+  g_attr_set.clear();
+}
+
+}  // namespace aat

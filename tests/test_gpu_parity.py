@@ -1,0 +1,273 @@
+"""Parity of the CUDA path with the CPU oracle (run on a GB300 with -m gpu).
+
+Every comparison over F_p is bit-exact.  Small cases span several 128 x 256
+output tiles with ragged tails; full-size cases compare sampled entries (at
+every recursion block boundary) one by one with the oracle and check the
+whole result with Freivalds' test.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2101_01025_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PRIMES = [65521, 131071, 2**31 - 1]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2101_01025_gb300 import build
+    build.build()
+    import paper_2101_01025_gb300 as aat
+    aat.aat_device_status(reset=True)
+    yield aat
+    assert aat.aat_device_status() == 0, "a bounded device wait gave up"
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def bal(x, p):
+    x = np.asarray(x, dtype=np.int64) % p
+    return np.where(x > (p - 1) // 2, x - p, x)
+
+
+def low_equal(C, ref):
+    C = np.asarray(C, dtype=np.int64)
+    ref = np.asarray(ref, dtype=np.int64)
+    return np.array_equal(np.tril(C), np.tril(ref))
+
+
+# ------------------------------------------------------------ single steps
+
+@pytest.mark.parametrize("p", PRIMES + [13])
+def test_split_reconstructs_balanced_residues(p):
+    from paper_2101_01025_gb300 import testing as T
+    b, L, dmax = T.digit_spec(p)
+    half = (p - 1) // 2
+    X = synth.residues(1, (37, 203), p, balanced=True)
+    X[0, :7] = [half, -half, 0, 1, -1, half - 1, -(half - 1)]
+    X[1, :] = p - 1            # canonical input: the kernel balances it
+    planes = T.split(dev(X), p).float().cpu().numpy()[:, :, :203]
+    assert planes.shape[0] == L
+    for d in range(L):
+        assert np.all(np.abs(planes[d]) <= dmax[d])
+        assert np.all(planes[d] == np.round(planes[d]))
+    rec = sum(planes[d].astype(np.int64) << (b * d) for d in range(L))
+    assert np.array_equal(rec, bal(X, p))
+
+
+@pytest.mark.parametrize("p", PRIMES)
+@pytest.mark.parametrize("n,k", [(2, 4), (66, 132), (130, 260), (96, 40)])
+def test_sblocks_match_oracle(p, n, k):
+    from paper_2101_01025_gb300 import testing as T
+    kind, a, b = T.y_params(p)
+    if kind == 2 and (k // 2) % 2:
+        pytest.skip("kind-2 Y needs k/2 even")
+    A = synth.residues(n * 1000 + k, (n, k), p)
+    got = [host(s) for s in T.sblocks(dev(A), p)]
+    ref = oracle.alg1_sblocks(A, p, kind, a, b)
+    for i in range(4):
+        assert np.array_equal(got[i].astype(np.int64), ref[i].astype(np.int64)), "S%d" % (i + 1)
+
+
+@pytest.mark.parametrize("leafkind", ["tc", "simt"])
+@pytest.mark.parametrize("p", PRIMES)
+@pytest.mark.parametrize("M,N,K", [(128, 256, 64), (300, 520, 200), (1000, 700, 1536),
+                                   (5, 3, 1), (257, 129, 777)])
+def test_leaf_gemm_matches_oracle(leafkind, p, M, N, K):
+    from paper_2101_01025_gb300 import testing as T
+    kindflag = 0 if leafkind == "tc" else 1 << 4
+    X = synth.residues(M + 7 * K, (M, K), p, balanced=True)
+    Y = synth.residues(N + 11 * K, (N, K), p)
+    C = host(T.leaf(dev(X), dev(Y), p, leafkind=kindflag))
+    assert np.array_equal(C.astype(np.int64), oracle.gemm_modp(X, Y, p).astype(np.int64))
+
+
+@pytest.mark.parametrize("p", PRIMES)
+@pytest.mark.parametrize("n,K", [(640, 384), (129, 1100), (1, 5)])
+def test_leaf_syrk_lower_and_accumulate(p, n, K):
+    from paper_2101_01025_gb300 import testing as T
+    X = synth.residues(n * 3 + K, (n, K), p)
+    Xd = dev(X)
+    sentinel = -7
+    C = torch.full((n, n), sentinel, dtype=torch.int32, device="cuda")
+    T.leaf(Xd, Xd, p, C=C, lower=True)
+    Ch = host(C)
+    ref = oracle.aat_modp_low(X, p).astype(np.int64)
+    assert low_equal(Ch, ref)
+    assert np.all(Ch[np.triu_indices(n, 1)] == sentinel)   # upper part untouched
+    # accumulate: C <- C + X X^T (lower)
+    T.leaf(Xd, Xd, p, C=C, lower=True, accumulate=True)
+    assert low_equal(host(C), (2 * ref) % p)
+
+
+@pytest.mark.parametrize("exact_bits", [24, 23, 20])
+def test_leaf_tc_worst_case_digits_fp32_exact(exact_bits):
+    """All rows equal, low digits -128 (|digit products| 2^14, one sign per
+    digit pair): every FP32 partial sum of a chunk reaches exactly
+    2^exact_bits before it is drained."""
+    from paper_2101_01025_gb300 import testing as T
+    p = 2**31 - 1
+    x = -128 * (1 + 2**8 + 2**16) - 63 * 2**24
+    assert abs(x) <= (p - 1) // 2
+    M, N, K = 256, 512, 4096
+    X = np.full((M, K), x, dtype=np.int32)
+    Y = np.full((N, K), x, dtype=np.int32)
+    Y[::3] = -x
+    C = host(T.leaf(dev(X), dev(Y), p, exact_bits=exact_bits)).astype(np.int64)
+    pos, neg = (x * x * K) % p, (-x * x * K) % p
+    assert np.all(C[:, 0::3] == neg)
+    assert np.all(C[:, 1::3] == pos) and np.all(C[:, 2::3] == pos)
+    ref = oracle.gemm_modp(X[:2], Y[:3], p).astype(np.int64)
+    assert np.array_equal(C[:2, :3], ref)
+
+
+def test_postadd_matches_definitions():
+    from paper_2101_01025_gb300 import testing as T
+    p = 131071
+    h = 200
+    C = synth.residues(5, (2 * h, 2 * h), p)
+    P1, P5 = np.tril(C[:h, :h]).astype(np.int64), np.tril(C[:h, h:]).astype(np.int64)
+    P3, P4T = C[h:, :h].astype(np.int64), C[h:, h:].astype(np.int64)
+    U1 = P1 + P5
+    U1 = np.tril(U1) + np.tril(U1, -1).T
+    U2 = U1 + P4T.T
+    U4 = (U2 + P3) % p
+    U5 = np.tril((U2 + P4T) % p)
+    got = host(T.postadd(dev(C), h, p)).astype(np.int64)
+    assert np.array_equal(got[h:, :h], U4)
+    assert np.array_equal(np.tril(got[h:, h:]), U5)
+    assert np.array_equal(got[:h, :], C[:h, :])      # C11, C12 untouched
+
+
+# ------------------------------------------------------------ whole product
+
+SHAPES = [(1, 1), (2, 3), (17, 33), (128, 64), (256, 512), (300, 200), (513, 257),
+          (640, 640), (1024, 96)]
+
+
+@pytest.mark.parametrize("p", PRIMES + [13])
+@pytest.mark.parametrize("n,k", SHAPES)
+@pytest.mark.parametrize("levels", [0, 1, 2, 3])
+def test_aat_modp_tc_matches_oracle(lib, p, n, k, levels):
+    A = synth.residues(p + n * 31 + k, (n, k), p)
+    C = host(lib.aat_modp(dev(A), p, levels=levels))
+    assert low_equal(C, oracle.aat_modp_low(A, p))
+
+
+@pytest.mark.parametrize("p", [131071, 2**31 - 1])
+@pytest.mark.parametrize("n,k", [(300, 200), (256, 512), (513, 257)])
+@pytest.mark.parametrize("levels", [1, 2])
+def test_aat_modp_simt_leaf_matches_oracle(lib, p, n, k, levels):
+    A = synth.residues(n + k, (n, k), p)
+    C = host(lib.aat_modp(dev(A), p, levels=levels, flags=lib.AAT_LEAF_SIMT))
+    assert low_equal(C, oracle.aat_modp_low(A, p))
+
+
+def test_aat_modp_strides_balanced_zero_upper(lib):
+    p = 2**31 - 1
+    n, k = 384, 256
+    big = synth.residues(9, (n, k + 40), p, balanced=True)
+    Ad = dev(big)[:, 13:13 + k]                        # lda = k + 40
+    Cbig = torch.full((n, n + 24), 5, dtype=torch.int32, device="cuda")
+    Cd = Cbig[:, 8:8 + n]                              # ldc = n + 24
+    lib.aat_modp(Ad, p, C=Cd, levels=2, flags=lib.AAT_ZERO_UPPER | lib.AAT_IN_BALANCED)
+    got = host(Cbig)
+    ref = oracle.aat_modp_low(np.ascontiguousarray(big[:, 13:13 + k]), p)
+    assert low_equal(got[:, 8:8 + n], ref)
+    assert np.all(got[:, 8:8 + n][np.triu_indices(n, 1)] == 0)
+    assert np.all(got[:, :8] == 5) and np.all(got[:, 8 + n:] == 5)
+
+
+def test_aat_modp_empty_and_degenerate(lib):
+    p = 131071
+    C = torch.full((3, 3), 9, dtype=torch.int32, device="cuda")
+    lib.aat_modp(torch.zeros((3, 0), dtype=torch.int32, device="cuda"), p, C=C)
+    assert np.all(np.tril(host(C)) == 0)
+    lib.aat_modp(torch.zeros((0, 5), dtype=torch.int32, device="cuda"), p)
+    A = np.zeros((64, 64), dtype=np.int32)
+    A[np.arange(64), np.arange(64)] = 1
+    assert low_equal(host(lib.aat_modp(dev(A), p, levels=2)), np.eye(64))
+
+
+@pytest.mark.parametrize("p", PRIMES)
+def test_aat_gemm_modp_matches_oracle(lib, p):
+    X = synth.residues(3, (333, 450), p)
+    Y = synth.residues(4, (270, 450), p)
+    C = host(lib.aat_gemm_modp(dev(X), dev(Y), p))
+    assert np.array_equal(C.astype(np.int64), oracle.gemm_modp(X, Y, p).astype(np.int64))
+    F = host(lib.aat_gemm_modp(dev(X), dev(X), p))
+    assert np.array_equal(F.astype(np.int64), oracle.gemm_modp(X, X, p).astype(np.int64))
+
+
+def test_aat_modp_host_end_to_end(lib):
+    p = 65521
+    A = synth.residues(77, (700, 900), p)
+    C = lib.aat_modp_host(A, p)
+    assert low_equal(C, oracle.aat_modp_low(A, p))
+
+
+# -------------------------------------------------------- full-size cases
+
+def _sample_pairs(n, levels, count, seed):
+    """Random lower entries plus every recursion block boundary +-1 and the
+    diagonal near them."""
+    rng = np.random.default_rng(seed)
+    i = rng.integers(0, n, count)
+    j = rng.integers(0, n, count)
+    pairs = [(max(a, b), min(a, b)) for a, b in zip(i, j)]
+    edges = set()
+    for lv in range(1, levels + 1):
+        step = n >> lv
+        for e in range(0, n + 1, step):
+            for d in (-1, 0):
+                if 0 <= e + d < n:
+                    edges.add(e + d)
+    edges = sorted(edges)
+    for a in edges:
+        for b in edges:
+            if b <= a:
+                pairs.append((a, b))
+    return np.array(pairs, dtype=np.int64)
+
+
+def _full_check(lib, A, p, levels_expected_min=1, nsample=3000, nvec=2):
+    from paper_2101_01025_gb300 import testing as T
+    n, k = A.shape
+    st = T.plan_stats(n, k, p)
+    assert st.levels >= levels_expected_min
+    C = lib.aat_modp(dev(A), p)          # default launch configuration (as bench.py)
+    Ch = host(C)
+    del C
+    ij = _sample_pairs(n, st.levels, nsample, seed=n + k)
+    ref = oracle.aat_modp_entries(A, p, ij)
+    got = Ch[ij[:, 0], ij[:, 1]].astype(np.int64)
+    assert np.array_equal(got, ref.astype(np.int64))
+    xs = synth.vectors_mod_p(1234, nvec, n, p)
+    assert oracle.freivalds_modp(A, Ch, p, xs) == 0
+    return st
+
+
+def test_full_size_n16384_p2_31m1(lib):
+    p = 2**31 - 1
+    A = synth.residues(synth.SEED_BASE + 2, (16384, 16384), p, balanced=True)
+    st = _full_check(lib, A, p, levels_expected_min=2)
+    assert st.n_pad == 16384
+
+
+@pytest.mark.parametrize("n,k,p", [(8192, 8192, 65521), (16384, 4096, 131071)])
+def test_full_size_config2(lib, n, k, p):
+    A = synth.residues(synth.SEED_BASE + 1, (n, k), p)
+    _full_check(lib, A, p, levels_expected_min=1, nsample=1500, nvec=1)

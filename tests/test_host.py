@@ -1,0 +1,160 @@
+"""Host logic of the library, no GPU needed: the C ABI loads and exports every
+declared symbol, the host number theory, the digit split plan, the
+recursion plan against the paper's counts, and argument validation."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2101_01025_gb300 import _native, build as buildmod, testing as T
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    buildmod.build()
+    yield
+
+
+def _declared_symbols():
+    names = set()
+    for h in ("aat.h", "aat_testing.h"):
+        src = open(os.path.join(ROOT, "include", h)).read()
+        names.update(re.findall(r"AAT_API\s+[\w\s\*]+?\b(aatx?_\w+)\s*\(", src))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = _native.lib()
+    declared = _declared_symbols()
+    assert declared == set(_native.EXPORTS)
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert lib.aat_version() >= 100
+
+
+def test_number_theory_matches_definitions():
+    for p in [3, 5, 7, 11, 13, 97, 65521, 131071, 131041, 2**31 - 1]:
+        assert T.is_prime(p)
+    for q in [1, 4, 9, 65521 * 3, 2**31 - 3, 3215031751]:
+        assert not T.is_prime(q)
+    s = np.ones(3000, dtype=bool)
+    s[:2] = False
+    for i in range(2, 60):
+        s[i * i::i] = False
+    for q in range(3000):
+        assert T.is_prime(q) == bool(s[q])
+    for p in [3, 7, 13, 17, 101, 65521, 131071, 2**31 - 1]:
+        for a in range(0, min(p, 300)):
+            r = T.sqrt_mod(a, p)
+            if r is None:
+                assert oracle.legendre(a, p) == -1
+            else:
+                assert (r * r - a) % p == 0
+
+
+@pytest.mark.parametrize("p", [3, 5, 7, 11, 13, 65521, 131071, 131041, 2**31 - 1])
+def test_y_is_skew_unitary(p):
+    """The library's Y satisfies Y Y^T = -I (Eq. skewu), independently of the
+    oracle's choice of root (which may differ: any skew-unitary Y works)."""
+    kind, a, b = T.y_params(p)
+    if p % 4 == 1:
+        assert kind == 1 and (a * a + 1) % p == 0
+    else:
+        assert kind == 2 and (a * a + b * b + 1) % p == 0
+    Y = oracle.build_y(kind, a, b, p, 6).astype(object)
+    assert np.array_equal((Y @ Y.T) % p, (np.eye(6, dtype=object) * (p - 1)) % p)
+
+
+def test_sos_all_residues():
+    for p in [3, 7, 11, 19, 23, 131071]:
+        for k in list(range(min(p, 200))) + [p - 1]:
+            a, b = T.sos(k, p)
+            assert (a * a + b * b - k) % p == 0
+
+
+def _digits(x, b, L):
+    """The balanced base-2^b digit rule applied to one integer (Python)."""
+    out = []
+    half = 1 << (b - 1)
+    for _ in range(L - 1):
+        d = ((x + half) & ((1 << b) - 1)) - half
+        out.append(d)
+        x = (x - d) >> b
+    out.append(x)
+    return out
+
+
+@pytest.mark.parametrize("p", [3, 13, 257, 65521, 131071, 131041, 2**31 - 1])
+def test_digit_spec_bounds_and_exactness(p):
+    b, L, dmax = T.digit_spec(p)
+    half = (p - 1) // 2
+    vals = [0, 1, -1, half, -half, half - 1, -(half - 1)]
+    rng = np.random.default_rng(p)
+    vals += [int(v) for v in rng.integers(-half, half + 1, 2000)]
+    for x in vals:
+        ds = _digits(x, b, L)
+        assert sum(d << (b * i) for i, d in enumerate(ds)) == x
+        for i, d in enumerate(ds):
+            assert abs(d) <= dmax[i], (x, ds, dmax)
+            assert abs(d) <= 256      # exact in bfloat16
+    # the worst case is reached: every bound is attained by some x
+    assert max(dmax) ** 2 <= 1 << 16
+    if p == 2**31 - 1:
+        assert (b, L) == (8, 4)
+    if p in (65521, 131071):
+        assert L == 2
+
+
+def test_plan_counts_match_paper():
+    """Each level has 3 recursive products, 2 general products and 9 block
+    additions, 3 of them on symmetric blocks (Alg. 1; Remark 3.3); the ring
+    MACs follow s(l) = 3/8 s(l-1) + 1/4 with s(0) = 1/2 (Table 1)."""
+    p = 2**31 - 1
+    n = k = 16384
+    s = 0.5
+    for lv in range(0, 5):
+        st = T.plan_stats(n, k, p, _native.AAT_LEVELS(lv))
+        nodes = sum(3 ** i for i in range(lv))       # internal nodes
+        assert st.levels == lv
+        assert st.recursive_products == 3 * nodes
+        assert st.block_additions == 9 * nodes
+        assert st.half_additions == 3 * nodes
+        assert st.general_products == 2 * nodes
+        assert st.syrk_leaves == 3 ** lv
+        leading = st.ring_macs / (n * n * k)
+        assert abs(leading - s) < 2.0 / (n >> lv), (lv, leading, s)
+        s = 3.0 / 8.0 * s + 0.25
+    st = T.plan_stats(n, k, p)
+    assert st.levels >= 2      # the automatic choice recurses at this size
+
+
+def test_plan_padding_and_workspace():
+    p = 131071
+    st = T.plan_stats(1001, 333, p, _native.AAT_LEVELS(2))
+    assert st.n_pad == 1004 and st.k_pad % 8 == 0 and st.k_pad >= 333
+    st0 = T.plan_stats(1001, 333, p, _native.AAT_LEVELS(0))
+    assert st0.n_pad == 1001 and st0.k_pad == 333
+    lib = _native.lib()
+    assert lib.aat_workspace_size(16384, 16384, 2**31 - 1, 0) > 0
+    assert lib.aat_workspace_size(0, 10, 131071, 0) == 0
+
+
+def test_argument_validation_before_any_gpu_call():
+    lib = _native.lib()
+    fake = 1 << 20   # never dereferenced: validation fails first
+    assert lib.aat_modp_ex(fake, 4, 4, 4, 15, fake * 2, 4, 0, None) == _native.AAT_ENOTPRIME
+    assert lib.aat_modp_ex(fake, 4, 4, 4, 2, fake * 2, 4, 0, None) == _native.AAT_ENOTPRIME
+    assert lib.aat_modp_ex(fake, 4, 4, 4, 2147483659, fake * 2, 4, 0, None) == _native.AAT_ERANGE
+    assert lib.aat_modp_ex(fake, -1, 4, 4, 131071, fake * 2, 4, 0, None) == _native.AAT_EINVAL
+    assert lib.aat_modp_ex(fake, 4, 4, 3, 131071, fake * 2, 4, 0, None) == _native.AAT_EINVAL
+    assert lib.aat_modp_ex(None, 4, 4, 4, 131071, fake * 2, 4, 0, None) == _native.AAT_EINVAL
+    assert lib.aat_modp_ex(fake, 4, 4, 4, 131071, fake + 8, 4, 0, None) == _native.AAT_EINVAL
+    assert "overlap" in _native.last_error()
+    assert lib.aat_gemm_modp(fake, 4, fake, 4, 4, 4, 4, 9, fake * 2, 4, 0, None) == \
+        _native.AAT_ENOTPRIME
+    assert lib.aat_modp_ex(fake, 4, 4, 4, 131071, fake * 2, 4, 7 << 4, None) == \
+        _native.AAT_EUNSUPPORTED
