@@ -110,6 +110,30 @@ AAT_API const char *aat_last_error(void);
  */
 AAT_API int aat_device_status(int reset);
 
+/*
+ * Optional instrumentation.  Between aat_profile_begin() and
+ * aat_profile_end(), every kernel launch of the library is bracketed by CUDA
+ * events recorded on its own stream; aat_profile_end() synchronises and
+ * returns, per kernel class, the launch count, the summed event time and the
+ * summed algorithmic work (tensor FLOPs for leaf products: 2 L^2 per ring
+ * multiply-add; bytes read + written for the addition kernels).
+ */
+#define AAT_K_SBLOCKS 0
+#define AAT_K_SPLIT 1
+#define AAT_K_LEAF_TC 2
+#define AAT_K_LEAF_SIMT 3
+#define AAT_K_POSTADD 4
+#define AAT_K_ADD_LOW 5
+#define AAT_K_COPY 6
+#define AAT_K_NCLASS 8
+typedef struct {
+  int64_t launches[AAT_K_NCLASS];
+  double ms[AAT_K_NCLASS];
+  double work[AAT_K_NCLASS];
+} aat_profile_t;
+AAT_API int aat_profile_begin(void);
+AAT_API int aat_profile_end(aat_profile_t *out);
+
 /* Frees every workspace and cache of the library on the current device. */
 AAT_API void aat_shutdown(void);
 

@@ -36,6 +36,7 @@ def AAT_LEVELS(l: int) -> int:
 EXPORTS = [
     "aat_modp", "aat_modp_ex", "aat_modp_host", "aat_gemm_modp", "aat_workspace_size",
     "aat_last_error", "aat_device_status", "aat_shutdown", "aat_version",
+    "aat_profile_begin", "aat_profile_end",
     "aatx_is_prime", "aatx_sqrt_mod", "aatx_sos", "aatx_y_params", "aatx_digit_spec",
     "aatx_plan_stats", "aatx_sblocks", "aatx_split", "aatx_leaf", "aatx_postadd",
 ]
@@ -60,6 +61,26 @@ class PlanStats(ctypes.Structure):
         ("ring_macs", ctypes.c_double),
         ("workspace_bytes", ctypes.c_size_t),
     ]
+
+
+#: kernel classes of aat_profile_t
+K_CLASSES = ["sblocks", "split", "leaf_tc", "leaf_simt", "postadd", "add_low", "copy", "unused"]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [
+        ("launches", ctypes.c_int64 * 8),
+        ("ms", ctypes.c_double * 8),
+        ("work", ctypes.c_double * 8),
+    ]
+
+    def as_dict(self):
+        out = {}
+        for i, name in enumerate(K_CLASSES):
+            if self.launches[i]:
+                out[name] = dict(launches=int(self.launches[i]), ms=float(self.ms[i]),
+                                 work=float(self.work[i]))
+        return out
 
 
 _lock = threading.Lock()
@@ -88,6 +109,7 @@ def lib():
         L.aat_last_error.restype = ctypes.c_char_p
         L.aat_device_status.argtypes = [i32]
         L.aat_shutdown.restype = None
+        L.aat_profile_end.argtypes = [ctypes.POINTER(Profile)]
         L.aatx_is_prime.argtypes = [u64]
         L.aatx_sqrt_mod.argtypes = [i64, u64]
         L.aatx_sqrt_mod.restype = i64

@@ -270,6 +270,45 @@ static int ensure_workspace(size_t bytes, void **out) {
   return AAT_OK;
 }
 
+// ---------------------------------------------------- instrumentation
+
+struct ProfRec {
+  int cls;
+  cudaStream_t st;
+  cudaEvent_t a, b;
+  double work;
+};
+static std::mutex g_prof_mu;
+static bool g_prof_on = false;
+static std::vector<ProfRec> g_prof;
+static std::vector<cudaEvent_t> g_event_pool;
+
+static cudaEvent_t pool_event() {
+  if (!g_event_pool.empty()) {
+    cudaEvent_t e = g_event_pool.back();
+    g_event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+ProfScope::ProfScope(int cls, cudaStream_t st, double work) : idx(-1) {
+  std::lock_guard<std::mutex> lock(g_prof_mu);
+  if (!g_prof_on) return;
+  ProfRec r{cls, st, pool_event(), pool_event(), work};
+  cudaEventRecord(r.a, st);
+  g_prof.push_back(r);
+  idx = (int)g_prof.size() - 1;
+}
+
+ProfScope::~ProfScope() {
+  if (idx < 0) return;
+  std::lock_guard<std::mutex> lock(g_prof_mu);
+  if (idx < (int)g_prof.size()) cudaEventRecord(g_prof[idx].b, g_prof[idx].st);
+}
+
 // ---------------------------------------------------------- the plan
 
 // Bump allocator over the workspace with a dry-run mode that only measures.
@@ -716,6 +755,37 @@ void aat_shutdown(void) {
     cudaSetDevice(cur);
   }
   g_states.clear();
+}
+
+int aat_profile_begin(void) {
+  std::lock_guard<std::mutex> lock(g_prof_mu);
+  for (auto &r : g_prof) {
+    g_event_pool.push_back(r.a);
+    g_event_pool.push_back(r.b);
+  }
+  g_prof.clear();
+  g_prof_on = true;
+  return AAT_OK;
+}
+
+int aat_profile_end(aat_profile_t *out) {
+  cudaError_t ce = cudaDeviceSynchronize();
+  std::lock_guard<std::mutex> lock(g_prof_mu);
+  g_prof_on = false;
+  if (out) std::memset(out, 0, sizeof(*out));
+  for (auto &r : g_prof) {
+    float ms = 0.f;
+    if (ce == cudaSuccess && out && r.cls >= 0 && r.cls < AAT_K_NCLASS &&
+        cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      out->launches[r.cls] += 1;
+      out->ms[r.cls] += ms;
+      out->work[r.cls] += r.work;
+    }
+    g_event_pool.push_back(r.a);
+    g_event_pool.push_back(r.b);
+  }
+  g_prof.clear();
+  return ce == cudaSuccess ? AAT_OK : cuda_fail(ce, "profile synchronize");
 }
 
 // ------------------------------------------------------------ test hooks

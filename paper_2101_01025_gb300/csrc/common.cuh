@@ -143,6 +143,17 @@ __device__ __forceinline__ void store_digits(const Planes &P, int64_t r, int64_t
 // Sticky status word written by kernels whose bounded waits give up.
 int32_t *device_status_ptr();
 
+// --------------------------------------------------- instrumentation
+
+// Brackets one kernel launch with CUDA events on its stream while profiling
+// is on (aat_profile_begin / aat_profile_end); `work` is the algorithmic
+// FLOPs or bytes of the launch.
+struct ProfScope {
+  int idx;
+  ProfScope(int cls, cudaStream_t st, double work);
+  ~ProfScope();
+};
+
 // ------------------------------------------------ internal launchers
 
 // K1: the four additions of Algorithm 1 with Y applied in registers.

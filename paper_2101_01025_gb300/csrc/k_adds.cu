@@ -227,6 +227,14 @@ cudaError_t launch_sblocks(const int32_t *A, int64_t lda, int64_t h, int64_t kap
   const int64_t ncols = (y.kind == 2) ? kappa / 2 : kappa;
   const int64_t total = h * ncols;
   if (total <= 0) return cudaSuccess;
+  double bytes = 16.0 * h * kappa;  // A11, A12, A21, A22 read once
+  for (int q = 0; q < 4; ++q) {
+    if (o.s[q]) bytes += 4.0 * h * kappa;
+    if (o.sp[q].ptr) bytes += 2.0 * o.sp[q].L * h * kappa;
+  }
+  for (const Planes *P : {&o.a11, &o.a12, &o.a22})
+    if (P->ptr) bytes += 2.0 * P->L * h * kappa;
+  ProfScope prof(AAT_K_SBLOCKS, st, bytes);
   sblocks_kernel<<<grid_for(total), kThreads, 0, st>>>(A, lda, h, kappa, m, y, b, o);
   return cudaGetLastError();
 }
@@ -235,6 +243,7 @@ cudaError_t launch_split(const int32_t *X, int64_t ldx, int64_t rows, int64_t co
                          const ModP &m, int b, const Planes &P, cudaStream_t st) {
   const int64_t total = rows * cols;
   if (total <= 0) return cudaSuccess;
+  ProfScope prof(AAT_K_SPLIT, st, (double)total * (4.0 + 2.0 * P.L));
   split_kernel<<<grid_for(total), kThreads, 0, st>>>(X, ldx, rows, cols, m, b, P);
   return cudaGetLastError();
 }
@@ -244,6 +253,8 @@ cudaError_t launch_postadd(int32_t *C11, int32_t *C12, int32_t *C21, int32_t *C2
   if (h <= 0) return cudaSuccess;
   const int64_t nt = (h + T - 1) / T;
   const int64_t pairs = nt * (nt + 1) / 2;
+  const double tri = 0.5 * (double)h * (double)(h + 1), sq = (double)h * h;
+  ProfScope prof(AAT_K_POSTADD, st, 4.0 * (3.0 * tri + 3.0 * sq));
   postadd_kernel<<<(unsigned)pairs, T * 8, 0, st>>>(C11, C12, C21, C22, ldc, h, m);
   return cudaGetLastError();
 }
@@ -251,6 +262,7 @@ cudaError_t launch_postadd(int32_t *C11, int32_t *C12, int32_t *C21, int32_t *C2
 cudaError_t launch_add_low(int32_t *C11, const int32_t *C12, int64_t ldc, int64_t h,
                            const ModP &m, cudaStream_t st) {
   if (h <= 0) return cudaSuccess;
+  ProfScope prof(AAT_K_ADD_LOW, st, 4.0 * 3.0 * 0.5 * (double)h * (double)(h + 1));
   add_low_kernel<<<grid_for(h * h), kThreads, 0, st>>>(C11, C12, ldc, h, m);
   return cudaGetLastError();
 }
@@ -259,6 +271,7 @@ cudaError_t launch_pad_copy(const int32_t *src, int64_t lds, int64_t rows, int64
                             int32_t *dst, int64_t ldd, int64_t rows_d, int64_t cols_d,
                             cudaStream_t st) {
   if (rows_d * cols_d <= 0) return cudaSuccess;
+  ProfScope prof(AAT_K_COPY, st, 4.0 * ((double)rows * cols + (double)rows_d * cols_d));
   pad_copy_kernel<<<grid_for(rows_d * cols_d), kThreads, 0, st>>>(src, lds, rows, cols, dst,
                                                                   ldd, rows_d, cols_d);
   return cudaGetLastError();
@@ -267,12 +280,14 @@ cudaError_t launch_pad_copy(const int32_t *src, int64_t lds, int64_t rows, int64
 cudaError_t launch_copy_low(const int32_t *src, int64_t lds, int32_t *dst, int64_t ldd,
                             int64_t n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
+  ProfScope prof(AAT_K_COPY, st, 8.0 * 0.5 * (double)n * (double)(n + 1));
   copy_low_kernel<<<grid_for(n * n), kThreads, 0, st>>>(src, lds, dst, ldd, n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_zero_upper(int32_t *C, int64_t ldc, int64_t n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
+  ProfScope prof(AAT_K_COPY, st, 4.0 * 0.5 * (double)n * (double)(n - 1));
   zero_upper_kernel<<<grid_for(n * n), kThreads, 0, st>>>(C, ldc, n);
   return cudaGetLastError();
 }

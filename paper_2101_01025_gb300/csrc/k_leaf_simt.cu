@@ -54,6 +54,8 @@ cudaError_t launch_leaf_simt(const int32_t *X, int64_t ldx, const int32_t *Y, in
                              int lower, int accumulate, const ModP &m, cudaStream_t st) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   dim3 grid((unsigned)((N + TS - 1) / TS), (unsigned)((M + TS - 1) / TS));
+  const double macs = lower ? 0.5 * (double)M * (double)(M + 1) * K : (double)M * N * K;
+  ProfScope prof(AAT_K_LEAF_SIMT, st, 2.0 * macs);
   leaf_simt_kernel<<<grid, 256, 0, st>>>(X, ldx, Y, ldy, M, N, K, out, ldo, lower,
                                          accumulate, m);
   return cudaGetLastError();

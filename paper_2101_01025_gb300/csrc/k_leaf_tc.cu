@@ -647,7 +647,12 @@ cudaError_t launch_leaf_tc(const TcLeafArgs &a, const ModP &m, cudaStream_t st) 
   int sms = 148;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = std::max(1, std::min(nt, sms));
-  if (nt > 0) leaf_tc_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(*P);
+  if (nt > 0) {
+    const double macs =
+        a.lower ? 0.5 * (double)a.M * (double)(a.M + 1) * a.K : (double)a.M * a.N * a.K;
+    ProfScope prof(AAT_K_LEAF_TC, st, 2.0 * a.dx.L * a.dy.L * macs);
+    leaf_tc_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(*P);
+  }
   delete P;
   return cudaGetLastError();
 }
