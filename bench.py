@@ -45,9 +45,12 @@ METRIC = "effective n²k GOPS for Low(A·Aᵀ) mod p at n=k=16384 vs plain GPU f
 N = K = 16384
 P = 2**31 - 1
 SEED_OFFSET = 2
-# Dominant kernel DRAM traffic per launch from ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum), see profiles/; None until captured for this kernel.
-LEAF_TC_TRAFFIC = None
+# DRAM traffic of the dominant kernel from one ncu capture of an 8192^3 leaf
+# product (dram__bytes_read.sum + dram__bytes_write.sum = 28.78 GB for
+# 17.59 TFLOP of algorithmic work, profiles/leaf_tc_kernel_gemm8192_p2p31m1.md),
+# scaled to the average launch of the step by its algorithmic work.  Set to
+# None whenever the kernel changes until it is captured again.
+LEAF_TC_BYTES_PER_FLOP = 28.78e9 / 17.59e12
 
 
 def parse():
@@ -285,7 +288,9 @@ def run_ours(args):
     roofline = {
         "bound": "tensor", "kernel": "leaf_tc_kernel (tcgen05 kind::f16, BF16 digits)",
         "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-        "peak_source": peak_src, "traffic": LEAF_TC_TRAFFIC,
+        "peak_source": peak_src,
+        "traffic": (None if LEAF_TC_BYTES_PER_FLOP is None else
+                    LEAF_TC_BYTES_PER_FLOP * leaf["work"] / max(leaf["launches"], 1)),
         "launches": leaf["launches"],
         "avg_launch_ms": leaf["ms"] / max(leaf["launches"], 1),
         "share_of_step": leaf["ms"] / max(ms_total, 1e-9),
