@@ -97,6 +97,35 @@ AAT_API int aat_gemm_modp(const int32_t *X, int64_t ldx, const int32_t *Y, int64
                   int64_t m, int64_t n, int64_t k, uint32_t p, int32_t *C,
                   int64_t ldc, uint32_t flags, void *stream);
 
+/*
+ * aat_gemm_modp without any device allocation.  The paper has no
+ * counterpart; this is an interface for callers that cannot allocate device
+ * memory when they call the library (a host application that gives all
+ * device memory to its own pool and forbids cudaMalloc from plug-ins, code
+ * that runs while another component owns the allocator, or a path that
+ * cannot afford a first-call allocation or the synchronisation cudaFree
+ * implies).  It computes the same C = X Y^T mod p as aat_gemm_modp on the
+ * tensor-core leaf, but keeps its scratch (the digit planes of X and Y and
+ * the tile list) in a fixed 32 MiB device array inside the library, which
+ * every GPU that loads the library holds until the process exits.
+ *   - Sizes: needs L * (m + n) * round8(k) * 2 bytes plus 8 bytes per
+ *     128 x 256 tile (L = 4 digit planes for p > 2^17, 2 for smaller p);
+ *     m = n = k = 1024 with p = 2^31 - 1 uses 16 MiB.  Larger requests are
+ *     rejected with AAT_ERANGE and a message giving the bytes needed.
+ *   - The first call on a device looks up the device address of the array
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture on the device.
+ *   - Every call shares the one array and overwrites it: calls that overlap
+ *     on the GPU (other streams, other host threads) race and give wrong
+ *     results.  The array keeps the last call's contents; each call rewrites
+ *     everything it reads and clears its status word.
+ *   - Calls no cudaMalloc, cudaFree or allocating library routine.
+ * Arguments, layout and return codes as aat_gemm_modp (tensor-core leaf).
+ */
+AAT_API int aat_gemm_modp_noalloc(const int32_t *X, int64_t ldx, const int32_t *Y, int64_t ldy,
+                                  int64_t m, int64_t n, int64_t k, uint32_t p, int32_t *C,
+                                  int64_t ldc, void *stream);
+
 /* Bytes of device workspace aat_modp_ex would use for (n, k, p, flags). */
 AAT_API size_t aat_workspace_size(int64_t n, int64_t k, uint32_t p, uint32_t flags);
 

@@ -603,6 +603,12 @@ static int check_device() {
   return AAT_OK;
 }
 
+// Accessors used by the allocation-free entry point (k_leaf_tc.cu).
+DigitSpec digits_for_prime(uint32_t p) { return make_digits(p); }
+int check_prime_arg(uint32_t p) { return validate(p); }
+int check_gb300() { return check_device(); }
+int report_error(int code, const char *msg) { return fail(code, msg); }
+
 }  // namespace aat
 
 using namespace aat;

@@ -214,4 +214,10 @@ struct TcLeafArgs {
 cudaError_t launch_leaf_tc(const TcLeafArgs &a, const ModP &m, cudaStream_t st);
 void leaf_tc_release();
 
+// Host helpers shared with the allocation-free entry point (aat_api.cu).
+DigitSpec digits_for_prime(uint32_t p);
+int check_prime_arg(uint32_t p);
+int check_gb300();
+int report_error(int code, const char *msg);
+
 }  // namespace aat

@@ -32,6 +32,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -666,3 +667,186 @@ void leaf_tc_release() {
 }
 
 }  // namespace aat
+
+// ======================================================================
+// Allocation-free variant of the general leaf product (aat_gemm_modp_noalloc).
+//
+// Some callers cannot allocate device memory when they call the library: a
+// host application that hands all device memory to its own pool and forbids
+// cudaMalloc from plug-ins, code running while another component owns the
+// allocator, or a latency-bound path where a first-call allocation (and the
+// device synchronisation cudaFree implies) is not acceptable.  This variant
+// keeps its scratch -- the digit planes of X and Y and the tile list -- in a
+// fixed file-scope device array instead of the library's workspace, and calls
+// no allocating routine.  The caller still passes X, Y and C.
+namespace aat {
+namespace {
+
+// 32 MiB of device memory, held by every GPU that loads the library until the
+// process exits.  m = n = k = 1024 with 4 digit planes (p = 2^31 - 1) needs
+// 16 MiB of it.
+constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+// Status word of this entry point's bounded waits (cleared by every call).
+static __device__ int32_t g_noalloc_status;
+
+struct NoAllocDevice {
+  bool ready = false;
+  unsigned char *scratch = nullptr;  // device address of g_noalloc_scratch
+  int32_t *status = nullptr;         // device address of g_noalloc_status
+};
+std::mutex g_noalloc_mu;
+NoAllocDevice g_noalloc_dev[64];
+
+size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+}  // namespace aat
+
+extern "C" AAT_API int aat_gemm_modp_noalloc(const int32_t *X, int64_t ldx, const int32_t *Y,
+                                             int64_t ldy, int64_t m, int64_t n, int64_t k,
+                                             uint32_t p, int32_t *C, int64_t ldc, void *stream) {
+  using namespace aat;
+  if (m < 0 || n < 0 || k < 0) return report_error(AAT_EINVAL, "negative size");
+  if (ldx < std::max<int64_t>(k, 1) || ldy < std::max<int64_t>(k, 1) ||
+      ldc < std::max<int64_t>(n, 1))
+    return report_error(AAT_EINVAL, "stride smaller than the row length");
+  if (m > 0 && n > 0 && (!C || (k > 0 && (!X || !Y)))) return report_error(AAT_EINVAL, "null pointer");
+  int e = check_prime_arg(p);
+  if (e) return e;
+  if (m == 0 || n == 0) return AAT_OK;
+  if ((e = check_gb300())) return e;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t ce;
+  if (k == 0) {
+    ce = cudaMemset2DAsync(C, (size_t)ldc * 4, 0, (size_t)n * 4, (size_t)m, st);
+    return ce == cudaSuccess ? AAT_OK : report_error(AAT_ECUDA, cudaGetErrorString(ce));
+  }
+  const DigitSpec ds = digits_for_prime(p);
+  const ModP mp = make_modp(p);
+  const bool same = (X == Y && ldx == ldy && m == n);
+  const int64_t ks = (k + 7) / 8 * 8;
+  const int64_t TI = (m + BM - 1) / BM, TJ = (n + BN - 1) / BN;
+  const size_t xbytes = round256((size_t)ds.L * m * ks * 2);
+  const size_t ybytes = same ? 0 : round256((size_t)ds.L * n * ks * 2);
+  const size_t tbytes = round256((size_t)TI * TJ * sizeof(int2));
+  if (xbytes + ybytes + tbytes > kNoAllocScratchBytes) {
+    char msg[256];
+    std::snprintf(msg, sizeof(msg),
+                  "aat_gemm_modp_noalloc: m=%lld n=%lld k=%lld needs %zu bytes of scratch, more "
+                  "than its fixed %zu bytes",
+                  (long long)m, (long long)n, (long long)k, xbytes + ybytes + tbytes,
+                  kNoAllocScratchBytes);
+    return report_error(AAT_ERANGE, msg);
+  }
+  int dev = 0;
+  if ((ce = cudaGetDevice(&dev)) != cudaSuccess || dev < 0 || dev >= 64)
+    return report_error(AAT_ECUDA, "no current device");
+  NoAllocDevice nd;
+  {
+    // First call on this device, with it current: the host names of the
+    // device arrays are not device addresses, so look the addresses up.
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    NoAllocDevice &d = g_noalloc_dev[dev];
+    if (!d.ready) {
+      void *ptr = nullptr;
+      if ((ce = cudaGetSymbolAddress(&ptr, g_noalloc_scratch)) != cudaSuccess)
+        return report_error(AAT_ECUDA, cudaGetErrorString(ce));
+      d.scratch = (unsigned char *)ptr;
+      if ((ce = cudaGetSymbolAddress(&ptr, g_noalloc_status)) != cudaSuccess)
+        return report_error(AAT_ECUDA, cudaGetErrorString(ce));
+      d.status = (int32_t *)ptr;
+      d.ready = true;
+    }
+    nd = d;
+  }
+  Planes px, py;
+  px.ptr = (__nv_bfloat16 *)nd.scratch;
+  px.rows = m;
+  px.cols = k;
+  px.kstride = ks;
+  px.L = ds.L;
+  py = px;
+  if (!same) {
+    py.ptr = (__nv_bfloat16 *)(nd.scratch + xbytes);
+    py.rows = n;
+  }
+  int2 *tiles_dev = (int2 *)(nd.scratch + xbytes + ybytes);
+
+  std::lock_guard<std::mutex> lock(g_mu);  // tensor-map encoder and kernel attribute
+  if ((ce = get_encode()) != cudaSuccess) return report_error(AAT_ECUDA, cudaGetErrorString(ce));
+  // the status word must start at zero; planes and tiles are fully rewritten
+  if ((ce = cudaMemsetAsync(nd.status, 0, sizeof(int32_t), st)) != cudaSuccess)
+    return report_error(AAT_ECUDA, cudaGetErrorString(ce));
+  // tile list, row-major, copied in pieces from a fixed host buffer
+  {
+    int2 buf[2048];
+    int64_t cnt = 0, done = 0;
+    for (int64_t i = 0; i < TI; ++i)
+      for (int64_t j = 0; j < TJ; ++j) {
+        buf[cnt++] = make_int2((int)i, (int)j);
+        if (cnt == 2048 || (i == TI - 1 && j == TJ - 1)) {
+          ce = cudaMemcpyAsync(tiles_dev + done, buf, (size_t)cnt * sizeof(int2),
+                               cudaMemcpyHostToDevice, st);
+          if (ce != cudaSuccess) return report_error(AAT_ECUDA, cudaGetErrorString(ce));
+          done += cnt;
+          cnt = 0;
+        }
+      }
+  }
+  if ((ce = launch_split(X, ldx, m, k, mp, ds.b, px, st)) != cudaSuccess)
+    return report_error(AAT_ECUDA, cudaGetErrorString(ce));
+  if (!same && (ce = launch_split(Y, ldy, n, k, mp, ds.b, py, st)) != cudaSuccess)
+    return report_error(AAT_ECUDA, cudaGetErrorString(ce));
+
+  Params P;
+  std::memset(&P, 0, sizeof(P));
+  if (encode_planes(&P.tmx, px, BM) != cudaSuccess || encode_planes(&P.tmy, py, BN) != cudaSuccess)
+    return report_error(AAT_ECUDA, "tensor map encoding failed");
+  // digit pairs in decreasing weight 2^(b (i + j)); Horner ratios between them
+  const int kblocks = (int)((k + BK - 1) / BK);
+  const int64_t room = ((int64_t)1 << 31) - 1 - (int64_t)mp.half;
+  int ng = 0, prev_s = -1;
+  for (int s = 2 * (ds.L - 1); s >= 0; --s)
+    for (int i = 0; i < ds.L; ++i) {
+      const int j = s - i;
+      if (j < 0 || j >= ds.L) continue;
+      const int64_t prod = std::max<int64_t>((int64_t)ds.dmax[i] * ds.dmax[j], 1);
+      const int64_t kc = std::max<int64_t>(((int64_t)1 << 23) / prod / BK, 1);
+      const int64_t kr = std::max<int64_t>(room / prod / BK, 1);
+      for (int kb = 0; kb < kblocks; kb += (int)kr) {
+        if (ng >= MAX_GROUPS) return report_error(AAT_ERANGE, "too many digit groups");
+        Group &g = P.g[ng++];
+        g.xp = (int16_t)i;
+        g.yp = (int16_t)j;
+        g.kb0 = kb;
+        g.kb1 = (int)std::min<int64_t>(kblocks, kb + kr);
+        g.kchunk = (int)std::min<int64_t>(kc, 1 << 20);
+        g.ratio = (prev_s < 0) ? 1u : pow2mod((uint64_t)ds.b * (uint64_t)(prev_s - s), mp.p);
+        prev_s = s;
+      }
+    }
+  P.ng = ng;
+  P.out = C;
+  P.ldo = ldc;
+  P.M = m;
+  P.N = n;
+  P.lower = 0;
+  P.accumulate = 0;
+  P.m = mp;
+  P.status = nd.status;
+  P.tiles = tiles_dev;
+  P.ntiles = (int)(TI * TJ);
+  if (!g_attr_set[dev]) {
+    ce = cudaFuncSetAttribute(leaf_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)SMEM_BYTES);
+    if (ce != cudaSuccess) return report_error(AAT_ECUDA, cudaGetErrorString(ce));
+    g_attr_set[dev] = true;
+  }
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = std::max(1, std::min(P.ntiles, sms));
+  leaf_tc_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(P);
+  ce = cudaGetLastError();
+  return ce == cudaSuccess ? AAT_OK : report_error(AAT_ECUDA, cudaGetErrorString(ce));
+}
