@@ -63,6 +63,9 @@ extern "C" {
  * recursion); no AAT_LEVELS bits = chosen from (n, k). */
 #define AAT_LEVELS(l) ((((uint32_t)(l) + 1u) & 0xFu) << 8)
 #define AAT_LEVELS_MASK (0xFu << 8)
+/* tensor-core leaf: one product per digit pair (i, j) instead of the
+ * pair-sum form that needs L + L(L-1)/2 products (comparison path). */
+#define AAT_DIGITS_PLAIN (1u << 12)
 
 /*
  * Low(A A^T) mod p (Algorithm 1, Sec. 3; Low as defined in Sec. 2).

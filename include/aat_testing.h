@@ -28,8 +28,10 @@ AAT_API int aatx_sos(int64_t k, uint64_t p, uint64_t *a, uint64_t *b);
  * are returned canonical.  Returns AAT_OK or an error code. */
 AAT_API int aatx_y_params(uint32_t p, int *kind, uint32_t *a, uint32_t *b);
 /* Digit split of balanced residues mod p for the tensor-core leaf: width b
- * bits, L digits, dmax[d] bounds |digit d|.  dmax must hold 8 entries. */
-AAT_API int aatx_digit_spec(uint32_t p, int *b, int *L, int *dmax);
+ * bits, L digits, dmax[d] bounds |digit d|.  dmax must hold 8 entries.  The
+ * planes also hold the pair sums d_i + d_j (i < j) when the leaf uses the
+ * pair-sum form: L(L-1)/2 of them, in the order (0,1), (0,2), ..., (L-2,L-1). */
+AAT_API int aatx_digit_spec(uint32_t p, int *b, int *L, int *dmax, int *nsum);
 
 /* Shape of the recursion aat_modp_ex would run (no GPU needed).  Counts are
  * totals over the whole recursion tree. */
@@ -56,14 +58,16 @@ AAT_API int aatx_sblocks(const int32_t *A, int64_t n, int64_t k, int64_t lda, ui
                  int32_t *S1, int32_t *S2, int32_t *S3, int32_t *S4, int64_t lds,
                  void *stream);
 
-/* Digit planes of the residue block X (rows x cols) as raw bf16 bits:
- * planes[(d * rows + r) * kstride + c], kstride = cols rounded up to 8. */
+/* Digit planes (then pair-sum planes) of the residue block X (rows x cols)
+ * as raw bf16 bits: planes[(d * rows + r) * kstride + c], kstride = cols
+ * rounded up to 8. */
 AAT_API int aatx_split(const int32_t *X, int64_t rows, int64_t cols, int64_t ldx, uint32_t p,
                uint16_t *planes, void *stream);
 
 /* One leaf product: C = X Y^T mod p (lower != 0: only i >= j written;
- * accumulate != 0: C <- C + X Y^T).  leaf: AAT_LEAF_TC or AAT_LEAF_SIMT.
- * exact_bits: bound 2^exact_bits on |FP32 partial sums| (0 = default). */
+ * accumulate != 0: C <- C + X Y^T).  leaf: AAT_LEAF_TC or AAT_LEAF_SIMT,
+ * optionally | AAT_DIGITS_PLAIN.  exact_bits: bound 2^exact_bits on |FP32
+ * partial sums| (0 = default, 24). */
 AAT_API int aatx_leaf(const int32_t *X, int64_t ldx, const int32_t *Y, int64_t ldy, int64_t M,
               int64_t N, int64_t K, uint32_t p, int32_t *C, int64_t ldc, int lower,
               int accumulate, uint32_t leaf, int exact_bits, void *stream);

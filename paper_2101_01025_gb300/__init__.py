@@ -12,8 +12,8 @@ library ``libaat_gb300.so``; when it is missing the calls raise.
 from __future__ import annotations
 
 from . import _native
-from ._native import (AAT_IN_BALANCED, AAT_LEAF_SIMT, AAT_LEAF_TC, AAT_LEVELS,  # noqa: F401
-                      AAT_ZERO_UPPER, AatError, PlanStats, check, last_error, lib)
+from ._native import (AAT_DIGITS_PLAIN, AAT_IN_BALANCED, AAT_LEAF_SIMT, AAT_LEAF_TC,  # noqa: F401
+                      AAT_LEVELS, AAT_ZERO_UPPER, AatError, PlanStats, check, last_error, lib)
 
 __all__ = [
     "aat_modp", "aat_gemm_modp", "aat_modp_host", "aat_workspace_size", "aat_device_status",

@@ -26,6 +26,7 @@ AAT_IN_BALANCED = 1 << 0
 AAT_ZERO_UPPER = 1 << 1
 AAT_LEAF_TC = 0 << 4
 AAT_LEAF_SIMT = 1 << 4
+AAT_DIGITS_PLAIN = 1 << 12
 
 
 def AAT_LEVELS(l: int) -> int:
@@ -119,7 +120,7 @@ def lib():
         L.aatx_y_params.argtypes = [u32, ctypes.POINTER(i32), ctypes.POINTER(u32),
                                     ctypes.POINTER(u32)]
         L.aatx_digit_spec.argtypes = [u32, ctypes.POINTER(i32), ctypes.POINTER(i32),
-                                      ctypes.POINTER(i32)]
+                                      ctypes.POINTER(i32), ctypes.POINTER(i32)]
         L.aatx_plan_stats.argtypes = [i64, i64, u32, u32, ctypes.POINTER(PlanStats)]
         L.aatx_sblocks.argtypes = [vp, i64, i64, i64, u32, vp, vp, vp, vp, i64, vp]
         L.aatx_split.argtypes = [vp, i64, i64, i64, u32, vp, vp]

@@ -24,6 +24,8 @@ def main(argv=None):
     ap.add_argument("--p", type=int, default=2**31 - 1)
     ap.add_argument("--levels", type=int, default=None)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--plain-digits", action="store_true",
+                    help="one product per digit pair instead of the pair-sum form")
     a = ap.parse_args(argv)
 
     import torch
@@ -34,18 +36,19 @@ def main(argv=None):
     build.build()
     torch.manual_seed(0x2101)
     n, k, p = a.n, a.k or a.n, a.p
+    flags = aat.AAT_DIGITS_PLAIN if a.plain_digits else 0
     half = (p - 1) // 2
     X = torch.randint(-half, half + 1, (n, k), dtype=torch.int32, device="cuda")
     C = torch.empty((n, n), dtype=torch.int32, device="cuda")
     if a.case == "leaf":
         Y = torch.randint(-half, half + 1, (n, k), dtype=torch.int32, device="cuda")
-        fn = lambda: testing.leaf(X, Y, p, C=C)  # noqa: E731
+        fn = lambda: testing.leaf(X, Y, p, C=C, leafkind=flags)  # noqa: E731
     elif a.case == "syrk":
-        fn = lambda: aat.aat_modp(X, p, C=C, levels=0)  # noqa: E731
+        fn = lambda: aat.aat_modp(X, p, C=C, levels=0, flags=flags)  # noqa: E731
     elif a.case == "aat":
-        fn = lambda: aat.aat_modp(X, p, C=C, levels=a.levels)  # noqa: E731
+        fn = lambda: aat.aat_modp(X, p, C=C, levels=a.levels, flags=flags)  # noqa: E731
     else:
-        fn = lambda: aat.aat_gemm_modp(X, X, p, C=C)  # noqa: E731
+        fn = lambda: aat.aat_gemm_modp(X, X, p, C=C, flags=flags)  # noqa: E731
     times = []
     for _ in range(a.reps):
         e0 = torch.cuda.Event(enable_timing=True)
@@ -56,6 +59,7 @@ def main(argv=None):
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
     print(json.dumps({"case": a.case, "n": n, "k": k, "p": p, "levels": a.levels,
+                      "plain_digits": a.plain_digits,
                       "ms": times, "status": aat.aat_device_status()}))
 
 

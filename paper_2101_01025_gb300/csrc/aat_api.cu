@@ -214,6 +214,21 @@ static DigitSpec make_digits(uint32_t p) {
       best_prod = prod;
     }
   }
+  // Pair sums: x_i y_j + x_j y_i = (x_i + x_j)(y_i + y_j) - x_i y_i - x_j y_j, so
+  // L + L(L-1)/2 plane products replace L^2 when every sum stays exact in
+  // bf16 (|d_i + d_j| <= 256).
+  bool ok = best.L >= 2 && best.L <= 4;
+  for (int i = 0; ok && i < best.L; ++i)
+    for (int j = i + 1; j < best.L; ++j)
+      if (best.dmax[i] + best.dmax[j] > 256) ok = false;
+  best.nsum = 0;
+  if (ok)
+    for (int i = 0; i < best.L; ++i)
+      for (int j = i + 1; j < best.L; ++j) {
+        best.si[best.nsum] = i;
+        best.sj[best.nsum] = j;
+        ++best.nsum;
+      }
   return best;
 }
 
@@ -336,12 +351,24 @@ struct Ctx {
   int err = AAT_OK;
 };
 
-static Planes planes_alloc(Ctx &c, int64_t rows, int64_t cols) {
+static Planes planes_for(const DigitSpec &ds, int64_t rows, int64_t cols) {
   Planes P;
+  std::memset(&P, 0, sizeof(P));
   P.rows = rows;
   P.cols = cols;
   P.kstride = (cols + 7) / 8 * 8;
-  P.L = c.ds.L;
+  P.nbase = ds.L;
+  P.nsum = ds.nsum;
+  P.L = ds.L + ds.nsum;
+  for (int q = 0; q < ds.nsum; ++q) {
+    P.si[q] = (int8_t)ds.si[q];
+    P.sj[q] = (int8_t)ds.sj[q];
+  }
+  return P;
+}
+
+static Planes planes_alloc(Ctx &c, int64_t rows, int64_t cols) {
+  Planes P = planes_for(c.ds, rows, cols);
   P.ptr = (__nv_bfloat16 *)c.ar.get((size_t)P.L * rows * P.kstride * 2);
   return P;
 }
@@ -543,11 +570,12 @@ static int setup(Ctx &c, uint32_t p, uint32_t flags, cudaStream_t st) {
   c.m = make_modp(p);
   if (!make_y(p, &c.y)) return fail(AAT_ERANGE, "no skew-unitary Y found");
   c.ds = make_digits(p);
+  if (flags & AAT_DIGITS_PLAIN) c.ds.nsum = 0;
   c.leaf = flags & AAT_LEAF_MASK;
   if (c.leaf != AAT_LEAF_TC && c.leaf != AAT_LEAF_SIMT)
     return fail(AAT_EUNSUPPORTED, "unknown leaf kind");
   const char *eb = getenv("AAT_EXACT_BITS");
-  c.exact_bits = eb ? atoi(eb) : 23;
+  c.exact_bits = eb ? atoi(eb) : 24;
   c.st = st;
   c.stats = nullptr;
   return AAT_OK;
@@ -823,13 +851,14 @@ int aatx_y_params(uint32_t p, int *kind, uint32_t *a, uint32_t *b) {
   return AAT_OK;
 }
 
-int aatx_digit_spec(uint32_t p, int *b, int *L, int *dmax) {
+int aatx_digit_spec(uint32_t p, int *b, int *L, int *dmax, int *nsum) {
   int e = validate(p);
   if (e) return e;
   DigitSpec d = make_digits(p);
   *b = d.b;
   *L = d.L;
   for (int i = 0; i < 8; ++i) dmax[i] = d.dmax[i];
+  *nsum = d.nsum;
   return AAT_OK;
 }
 
@@ -868,12 +897,8 @@ int aatx_split(const int32_t *X, int64_t rows, int64_t cols, int64_t ldx, uint32
   int e = setup(c, p, 0, (cudaStream_t)stream);
   if (e) return e;
   if ((e = check_device())) return e;
-  Planes P;
+  Planes P = planes_for(c.ds, rows, cols);
   P.ptr = (__nv_bfloat16 *)planes;
-  P.rows = rows;
-  P.cols = cols;
-  P.kstride = (cols + 7) / 8 * 8;
-  P.L = c.ds.L;
   cudaError_t ce = launch_split(X, ldx, rows, cols, c.m, c.ds.b, P, c.st);
   return ce == cudaSuccess ? AAT_OK : cuda_fail(ce, "split");
 }

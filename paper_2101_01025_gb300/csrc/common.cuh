@@ -104,38 +104,109 @@ struct YParams {
 
 // ---------------------------------------------------- digit planes
 
-// A residue block X (rows x cols) stored as L planes of signed base-2^b
-// digits in bf16: X = sum_d 2^(b d) D_d, each digit exactly representable.
-// Plane d, row r, column c lives at ptr[(d * rows + r) * kstride + c];
-// kstride is a multiple of 8 (16-byte rows for the tensor memory accelerator).
+// A residue block X (rows x cols) stored as digit planes in bf16: nbase
+// planes of signed base-2^b digits, X = sum_d 2^(b d) D_d, followed by nsum
+// planes of pair sums D_si[q] + D_sj[q]; every value is an integer of
+// magnitude <= 256, exactly representable in bf16.  Plane d, row r, column c
+// lives at ptr[(d * rows + r) * kstride + c]; kstride is a multiple of 8
+// (16-byte rows for the tensor memory accelerator).
 struct Planes {
   __nv_bfloat16 *ptr;
   int64_t rows;
   int64_t cols;
   int64_t kstride;
-  int L;
+  int L;        // planes stored (nbase + nsum)
+  int nbase;    // digit planes
+  int nsum;     // pair-sum planes
+  int8_t si[8], sj[8];
 };
 
 struct DigitSpec {
   int b;          // digit width in bits
   int L;          // number of digits
   int dmax[8];    // bound on |digit| per position
+  int nsum;       // pair-sum planes (0: every digit pair is its own product)
+  int si[8], sj[8];
 };
 
-// Balanced digits of a balanced residue x: all but the last in
-// [-2^(b-1), 2^(b-1) - 1], the last carries the rest.
+// Digit d of a register array indexed by a runtime d without local memory.
+template <int N>
+__device__ __forceinline__ int32_t pick(const int32_t (&v)[N], int d) {
+  int32_t r = 0;
+#pragma unroll
+  for (int q = 0; q < N; ++q) r = (q == d) ? v[q] : r;
+  return r;
+}
+
+// Balanced digits of a balanced residue x (all but the last in
+// [-2^(b-1), 2^(b-1) - 1], the last carries the rest), then the pair sums.
 __device__ __forceinline__ void store_digits(const Planes &P, int64_t r, int64_t c,
                                              int32_t x, int b) {
   const int32_t half = 1 << (b - 1);
   const int32_t mask = (1 << b) - 1;
   const int64_t plane = P.rows * P.kstride;
   __nv_bfloat16 *dst = P.ptr + r * P.kstride + c;
-  for (int d = 0; d < P.L - 1; ++d) {
-    int32_t dig = ((x + half) & mask) - half;
-    dst[d * plane] = __float2bfloat16_rn((float)dig);
-    x = (x - dig) >> b;
+  int32_t dig[8];
+#pragma unroll
+  for (int d = 0; d < 8; ++d) {
+    if (d < P.nbase - 1) {
+      dig[d] = ((x + half) & mask) - half;
+      x = (x - dig[d]) >> b;
+    } else {
+      dig[d] = (d == P.nbase - 1) ? x : 0;
+    }
+    if (d < P.nbase) dst[d * plane] = __float2bfloat16_rn((float)dig[d]);
   }
-  dst[(P.L - 1) * plane] = __float2bfloat16_rn((float)x);
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    if (q < P.nsum)
+      dst[(P.nbase + q) * plane] =
+          __float2bfloat16_rn((float)(pick(dig, P.si[q]) + pick(dig, P.sj[q])));
+}
+
+__device__ __forceinline__ uint2 pack4(float a, float b, float c, float d) {
+  __nv_bfloat162 lo = __floats2bfloat162_rn(a, b);
+  __nv_bfloat162 hi = __floats2bfloat162_rn(c, d);
+  uint2 u;
+  u.x = *reinterpret_cast<uint32_t *>(&lo);
+  u.y = *reinterpret_cast<uint32_t *>(&hi);
+  return u;
+}
+
+// The same for four consecutive columns c..c+3 (c a multiple of 4): one
+// 8-byte store per plane.
+__device__ __forceinline__ void store_digits4(const Planes &P, int64_t r, int64_t c,
+                                              const int32_t (&x0)[4], int b) {
+  const int32_t half = 1 << (b - 1);
+  const int32_t mask = (1 << b) - 1;
+  const int64_t plane = P.rows * P.kstride;
+  __nv_bfloat16 *dst = P.ptr + r * P.kstride + c;
+  int32_t x[4] = {x0[0], x0[1], x0[2], x0[3]};
+  int32_t dig[4][8];
+#pragma unroll
+  for (int d = 0; d < 8; ++d) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      if (d < P.nbase - 1) {
+        dig[v][d] = ((x[v] + half) & mask) - half;
+        x[v] = (x[v] - dig[v][d]) >> b;
+      } else {
+        dig[v][d] = (d == P.nbase - 1) ? x[v] : 0;
+      }
+    }
+    if (d < P.nbase)
+      *reinterpret_cast<uint2 *>(dst + d * plane) =
+          pack4((float)dig[0][d], (float)dig[1][d], (float)dig[2][d], (float)dig[3][d]);
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    if (q < P.nsum) {
+      const int i = P.si[q], j = P.sj[q];
+      *reinterpret_cast<uint2 *>(dst + (P.nbase + q) * plane) =
+          pack4((float)(pick(dig[0], i) + pick(dig[0], j)), (float)(pick(dig[1], i) + pick(dig[1], j)),
+                (float)(pick(dig[2], i) + pick(dig[2], j)), (float)(pick(dig[3], i) + pick(dig[3], j)));
+    }
+  }
 }
 
 // --------------------------------------------------- device status

@@ -25,77 +25,135 @@ __device__ __forceinline__ void apply_y2(int32_t x0, int32_t x1, const YParams &
   o1 = red_s64((int64_t)y.b * x0 + (int64_t)y.a * x1, m);
 }
 
-// One thread per (row i, column j) with j < kappa/2 for kind 2 (it also
-// handles column j + kappa/2), or j < kappa for kind 1.
+__device__ __forceinline__ void ld4_bal(const int32_t *p, const ModP &m, int32_t (&v)[4]) {
+  const int4 q = __ldg(reinterpret_cast<const int4 *>(p));
+  v[0] = bal(q.x, m);
+  v[1] = bal(q.y, m);
+  v[2] = bal(q.z, m);
+  v[3] = bal(q.w, m);
+}
+
+__device__ __forceinline__ void st4_canon(int32_t *p, const int32_t (&v)[4], const ModP &m) {
+  *reinterpret_cast<int4 *>(p) =
+      make_int4((int32_t)bal_to_canon(v[0], m), (int32_t)bal_to_canon(v[1], m),
+                (int32_t)bal_to_canon(v[2], m), (int32_t)bal_to_canon(v[3], m));
+}
+
+// Outputs of one group of V consecutive columns starting at column j.
+template <int V>
+__device__ __forceinline__ void sblocks_store(const SKernelOut &o, int64_t i, int64_t j,
+                                              const int32_t (&sv)[4][V], const int32_t (&a11)[V],
+                                              const int32_t (&a12)[V], const int32_t (&a22)[V],
+                                              const ModP &m, int b) {
+  if constexpr (V == 4) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (o.s[q]) st4_canon(o.s[q] + i * o.lds[q] + j, sv[q], m);
+      if (has(o.sp[q])) store_digits4(o.sp[q], i, j, sv[q], b);
+    }
+    if (has(o.a11)) store_digits4(o.a11, i, j, a11, b);
+    if (has(o.a12)) store_digits4(o.a12, i, j, a12, b);
+    if (has(o.a22)) store_digits4(o.a22, i, j, a22, b);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (o.s[q]) o.s[q][i * o.lds[q] + j] = (int32_t)bal_to_canon(sv[q][0], m);
+      if (has(o.sp[q])) store_digits(o.sp[q], i, j, sv[q][0], b);
+    }
+    if (has(o.a11)) store_digits(o.a11, i, j, a11[0], b);
+    if (has(o.a12)) store_digits(o.a12, i, j, a12[0], b);
+    if (has(o.a22)) store_digits(o.a22, i, j, a22[0], b);
+  }
+}
+
+template <int V>
+__device__ __forceinline__ void ldv_bal(const int32_t *p, const ModP &m, int32_t (&v)[V]) {
+  if constexpr (V == 4) {
+    ld4_bal(p, m, v);
+  } else {
+    v[0] = ld_bal(p, m);
+  }
+}
+
+// One thread per (row i, group of V columns at j): for kind 2, j < kappa/2
+// and the thread also handles columns j + kappa/2; for kind 1, j < kappa.
+// V = 4 needs kappa/2 (kind 2) or kappa (kind 1), lda, every output stride
+// and every plane stride to be multiples of 4 and 16-byte aligned bases.
+template <int V>
 __global__ void sblocks_kernel(const int32_t *__restrict__ A, int64_t lda, int64_t h,
                                int64_t kappa, ModP m, YParams y, int b, SKernelOut o) {
-  const int64_t ncols = (y.kind == 2) ? kappa / 2 : kappa;
+  const int64_t ncols = ((y.kind == 2) ? kappa / 2 : kappa) / V;
   const int64_t total = h * ncols;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = t / ncols;
-    const int64_t j = t - i * ncols;
+    const int64_t j = (t - i * ncols) * V;
     const int32_t *r1 = A + i * lda;        // row i of [A11 A12]
     const int32_t *r2 = A + (h + i) * lda;  // row i of [A21 A22]
     if (y.kind == 2) {
       const int64_t jj = j + kappa / 2;
-      int32_t a11_0 = ld_bal(r1 + j, m), a11_1 = ld_bal(r1 + jj, m);
-      int32_t a12_0 = ld_bal(r1 + kappa + j, m), a12_1 = ld_bal(r1 + kappa + jj, m);
-      int32_t a21_0 = ld_bal(r2 + j, m), a21_1 = ld_bal(r2 + jj, m);
-      int32_t a22_0 = ld_bal(r2 + kappa + j, m), a22_1 = ld_bal(r2 + kappa + jj, m);
-      // S1 = (A21 - A11) Y
-      int32_t s1_0, s1_1;
-      apply_y2(sub_bal(a21_0, a11_0, m), sub_bal(a21_1, a11_1, m), y, m, s1_0, s1_1);
-      // S2 = A22 - A21 Y
-      int32_t t0, t1;
-      apply_y2(a21_0, a21_1, y, m, t0, t1);
-      int32_t s2_0 = sub_bal(a22_0, t0, m), s2_1 = sub_bal(a22_1, t1, m);
-      // S3 = S1 - A22, S4 = S3 + A12
-      int32_t s3_0 = sub_bal(s1_0, a22_0, m), s3_1 = sub_bal(s1_1, a22_1, m);
-      int32_t s4_0 = add_bal(s3_0, a12_0, m), s4_1 = add_bal(s3_1, a12_1, m);
-      const int32_t sv0[4] = {s1_0, s2_0, s3_0, s4_0};
-      const int32_t sv1[4] = {s1_1, s2_1, s3_1, s4_1};
+      int32_t a11_0[V], a11_1[V], a12_0[V], a12_1[V], a21_0[V], a21_1[V], a22_0[V], a22_1[V];
+      ldv_bal<V>(r1 + j, m, a11_0);
+      ldv_bal<V>(r1 + jj, m, a11_1);
+      ldv_bal<V>(r1 + kappa + j, m, a12_0);
+      ldv_bal<V>(r1 + kappa + jj, m, a12_1);
+      ldv_bal<V>(r2 + j, m, a21_0);
+      ldv_bal<V>(r2 + jj, m, a21_1);
+      ldv_bal<V>(r2 + kappa + j, m, a22_0);
+      ldv_bal<V>(r2 + kappa + jj, m, a22_1);
+      int32_t sv0[4][V], sv1[4][V];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        if (o.s[q]) {
-          o.s[q][i * o.lds[q] + j] = (int32_t)bal_to_canon(sv0[q], m);
-          o.s[q][i * o.lds[q] + jj] = (int32_t)bal_to_canon(sv1[q], m);
-        }
-        if (has(o.sp[q])) {
-          store_digits(o.sp[q], i, j, sv0[q], b);
-          store_digits(o.sp[q], i, jj, sv1[q], b);
-        }
+      for (int v = 0; v < V; ++v) {
+        // S1 = (A21 - A11) Y
+        apply_y2(sub_bal(a21_0[v], a11_0[v], m), sub_bal(a21_1[v], a11_1[v], m), y, m,
+                 sv0[0][v], sv1[0][v]);
+        // S2 = A22 - A21 Y
+        int32_t t0, t1;
+        apply_y2(a21_0[v], a21_1[v], y, m, t0, t1);
+        sv0[1][v] = sub_bal(a22_0[v], t0, m);
+        sv1[1][v] = sub_bal(a22_1[v], t1, m);
+        // S3 = S1 - A22, S4 = S3 + A12
+        sv0[2][v] = sub_bal(sv0[0][v], a22_0[v], m);
+        sv1[2][v] = sub_bal(sv1[0][v], a22_1[v], m);
+        sv0[3][v] = add_bal(sv0[2][v], a12_0[v], m);
+        sv1[3][v] = add_bal(sv1[2][v], a12_1[v], m);
       }
-      if (has(o.a11)) { store_digits(o.a11, i, j, a11_0, b); store_digits(o.a11, i, jj, a11_1, b); }
-      if (has(o.a12)) { store_digits(o.a12, i, j, a12_0, b); store_digits(o.a12, i, jj, a12_1, b); }
-      if (has(o.a22)) { store_digits(o.a22, i, j, a22_0, b); store_digits(o.a22, i, jj, a22_1, b); }
+      sblocks_store<V>(o, i, j, sv0, a11_0, a12_0, a22_0, m, b);
+      sblocks_store<V>(o, i, jj, sv1, a11_1, a12_1, a22_1, m, b);
     } else {
-      int32_t a11 = ld_bal(r1 + j, m), a12 = ld_bal(r1 + kappa + j, m);
-      int32_t a21 = ld_bal(r2 + j, m), a22 = ld_bal(r2 + kappa + j, m);
-      int32_t s1 = red_s64((int64_t)y.a * sub_bal(a21, a11, m), m);
-      int32_t s2 = sub_bal(a22, red_s64((int64_t)y.a * a21, m), m);
-      int32_t s3 = sub_bal(s1, a22, m);
-      int32_t s4 = add_bal(s3, a12, m);
-      const int32_t sv[4] = {s1, s2, s3, s4};
+      int32_t a11[V], a12[V], a21[V], a22[V];
+      ldv_bal<V>(r1 + j, m, a11);
+      ldv_bal<V>(r1 + kappa + j, m, a12);
+      ldv_bal<V>(r2 + j, m, a21);
+      ldv_bal<V>(r2 + kappa + j, m, a22);
+      int32_t sv[4][V];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        if (o.s[q]) o.s[q][i * o.lds[q] + j] = (int32_t)bal_to_canon(sv[q], m);
-        if (has(o.sp[q])) store_digits(o.sp[q], i, j, sv[q], b);
+      for (int v = 0; v < V; ++v) {
+        sv[0][v] = red_s64((int64_t)y.a * sub_bal(a21[v], a11[v], m), m);
+        sv[1][v] = sub_bal(a22[v], red_s64((int64_t)y.a * a21[v], m), m);
+        sv[2][v] = sub_bal(sv[0][v], a22[v], m);
+        sv[3][v] = add_bal(sv[2][v], a12[v], m);
       }
-      if (has(o.a11)) store_digits(o.a11, i, j, a11, b);
-      if (has(o.a12)) store_digits(o.a12, i, j, a12, b);
-      if (has(o.a22)) store_digits(o.a22, i, j, a22, b);
+      sblocks_store<V>(o, i, j, sv, a11, a12, a22, m, b);
     }
   }
 }
 
+template <int V>
 __global__ void split_kernel(const int32_t *__restrict__ X, int64_t ldx, int64_t rows,
                              int64_t cols, ModP m, int b, Planes P) {
-  const int64_t total = rows * cols;
+  const int64_t ncol = cols / V;
+  const int64_t total = rows * ncol;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = t / cols, c = t - (t / cols) * cols;
-    store_digits(P, r, c, ld_bal(X + r * ldx + c, m), b);
+    const int64_t r = t / ncol, c = (t - (t / ncol) * ncol) * V;
+    if constexpr (V == 4) {
+      int32_t v[4];
+      ld4_bal(X + r * ldx + c, m, v);
+      store_digits4(P, r, c, v, b);
+    } else {
+      store_digits(P, r, c, ld_bal(X + r * ldx + c, m), b);
+    }
   }
 }
 
@@ -235,7 +293,19 @@ cudaError_t launch_sblocks(const int32_t *A, int64_t lda, int64_t h, int64_t kap
   for (const Planes *P : {&o.a11, &o.a12, &o.a22})
     if (P->ptr) bytes += 2.0 * P->L * h * kappa;
   ProfScope prof(AAT_K_SBLOCKS, st, bytes);
-  sblocks_kernel<<<grid_for(total), kThreads, 0, st>>>(A, lda, h, kappa, m, y, b, o);
+  // 16-byte vector path when every address it touches is aligned
+  auto al16 = [](const void *ptr) { return ((uintptr_t)ptr & 15) == 0; };
+  bool vec = (ncols % 4 == 0) && (lda % 4 == 0) && al16(A) && (kappa % 4 == 0);
+  for (int q = 0; q < 4; ++q) {
+    if (o.s[q]) vec = vec && (o.lds[q] % 4 == 0) && al16(o.s[q]);
+    if (o.sp[q].ptr) vec = vec && al16(o.sp[q].ptr);
+  }
+  for (const Planes *P : {&o.a11, &o.a12, &o.a22})
+    if (P->ptr) vec = vec && al16(P->ptr);
+  if (vec)
+    sblocks_kernel<4><<<grid_for(total / 4), kThreads, 0, st>>>(A, lda, h, kappa, m, y, b, o);
+  else
+    sblocks_kernel<1><<<grid_for(total), kThreads, 0, st>>>(A, lda, h, kappa, m, y, b, o);
   return cudaGetLastError();
 }
 
@@ -244,7 +314,12 @@ cudaError_t launch_split(const int32_t *X, int64_t ldx, int64_t rows, int64_t co
   const int64_t total = rows * cols;
   if (total <= 0) return cudaSuccess;
   ProfScope prof(AAT_K_SPLIT, st, (double)total * (4.0 + 2.0 * P.L));
-  split_kernel<<<grid_for(total), kThreads, 0, st>>>(X, ldx, rows, cols, m, b, P);
+  const bool vec = (cols % 4 == 0) && (ldx % 4 == 0) && (((uintptr_t)X & 15) == 0) &&
+                   (((uintptr_t)P.ptr & 15) == 0);
+  if (vec)
+    split_kernel<4><<<grid_for(total / 4), kThreads, 0, st>>>(X, ldx, rows, cols, m, b, P);
+  else
+    split_kernel<1><<<grid_for(total), kThreads, 0, st>>>(X, ldx, rows, cols, m, b, P);
   return cudaGetLastError();
 }
 

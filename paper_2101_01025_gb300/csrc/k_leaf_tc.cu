@@ -53,7 +53,7 @@ constexpr int EPI_WARPS = 8;
 constexpr int THREADS = 64 + EPI_WARPS * 32;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t ACC_COLS = 256;
-constexpr int MAX_GROUPS = 64;
+constexpr int MAX_GROUPS = 160;
 constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + 256;
 constexpr unsigned long long kTimeoutNs = 4000000000ull;  // 4 s
 
@@ -589,40 +589,91 @@ cudaError_t launch_leaf_tc(const TcLeafArgs &a, const ModP &m, cudaStream_t st) 
     delete P;
     return e;
   }
-  // digit pairs in decreasing weight 2^(b (i + j))
-  struct Pair { int i, j, s; };
-  std::vector<Pair> pairs;
-  for (int i = 0; i < a.dx.L; ++i)
-    for (int j = 0; j < a.dy.L; ++j) pairs.push_back({i, j, i + j});
-  std::stable_sort(pairs.begin(), pairs.end(),
-                   [](const Pair &u, const Pair &v) { return u.s > v.s; });
+  // The terms of the product: plane pairs with integer weights.
+  //   plain:     X_i Y_j^T with weight z^(i+j), z = 2^b
+  //   pair sums: X_i Y_i^T with weight z^(2i) - sum_{j != i} z^(i+j), and
+  //              (X_i + X_j)(Y_i + Y_j)^T with weight z^(i+j) for i < j
+  struct Term { int xp, yp; int64_t w; int64_t prod; };
+  std::vector<Term> terms;
+  const int L = a.dx.L;
+  auto zp = [&](int e) { return (int64_t)1 << (a.dx.b * e); };
+  const bool sums = a.dx.nsum > 0 && a.dy.nsum == a.dx.nsum && a.dy.L == L &&
+                    a.x.nsum == a.dx.nsum && a.y.nsum == a.dy.nsum;
+  if (sums) {
+    for (int i = 0; i < L; ++i) {
+      int64_t w = zp(2 * i);
+      for (int j = 0; j < L; ++j)
+        if (j != i) w -= zp(i + j);
+      terms.push_back({i, i, w, (int64_t)a.dx.dmax[i] * a.dy.dmax[i]});
+    }
+    for (int q = 0; q < a.dx.nsum; ++q) {
+      const int i = a.dx.si[q], j = a.dx.sj[q];
+      const int64_t bx = a.dx.dmax[i] + a.dx.dmax[j], by = a.dy.dmax[i] + a.dy.dmax[j];
+      terms.push_back({L + q, L + q, zp(i + j), bx * by});
+    }
+  } else {
+    for (int s2 = 2 * (L - 1); s2 >= 0; --s2)
+      for (int i = 0; i < L; ++i) {
+        const int j = s2 - i;
+        if (j < 0 || j >= a.dy.L) continue;
+        terms.push_back({i, j, zp(s2), (int64_t)a.dx.dmax[i] * a.dy.dmax[j]});
+      }
+  }
+  auto modw = [&](int64_t w) {
+    int64_t r = w % (int64_t)m.p;
+    return (uint32_t)(r < 0 ? r + (int64_t)m.p : r);
+  };
+  auto mulm = [&](uint32_t x, uint32_t y) { return (uint32_t)((uint64_t)x * y % m.p); };
+  auto invm = [&](uint32_t x) {
+    uint64_t r = 1, bb = x, e = m.p - 2;
+    while (e) {
+      if (e & 1) r = r * bb % m.p;
+      bb = bb * bb % m.p;
+      e >>= 1;
+    }
+    return (uint32_t)r;
+  };
+  // Groups: K segments of at most 8192 (for L2 reuse of the planes), each
+  // term split further so that (p-1)/2 + K_range * max|product| < 2^31; the
+  // epilogue multiplies its accumulator by w_prev / w_cur between groups and
+  // by the last weight in a final group without K blocks (Horner).
   const int kblocks = (int)((a.K + BK - 1) / BK);
+  const int kseg = 8192 / BK;
   const int ebits = std::min(std::max(a.exact_bits, 8), 24);
+  const int64_t room = ((int64_t)1 << 31) - 1 - (int64_t)m.half;
   int ng = 0;
-  int prev_s = -1;
-  for (const Pair &pr : pairs) {
-    const int64_t prod = (int64_t)a.dx.dmax[pr.i] * a.dy.dmax[pr.j];
-    int64_t kc = ((int64_t)1 << ebits) / (prod > 0 ? prod : 1) / BK;
-    if (kc < 1) { delete P; return cudaErrorInvalidValue; }
-    // int32 accumulator: (p-1)/2 + K_range * prod must stay below 2^31
-    int64_t room = ((int64_t)1 << 31) - 1 - (int64_t)m.half;
-    int64_t kr = room / (prod > 0 ? prod : 1) / BK;
-    if (kr < 1) { delete P; return cudaErrorInvalidValue; }
-    for (int kb = 0; kb < kblocks; kb += (int)kr) {
-      if (ng >= MAX_GROUPS) { delete P; return cudaErrorInvalidValue; }
-      Group &g = P->g[ng];
-      g.xp = (int16_t)pr.i;
-      g.yp = (int16_t)pr.j;
-      g.kb0 = kb;
-      g.kb1 = (int)std::min<int64_t>(kblocks, kb + kr);
-      g.kchunk = (int)std::min<int64_t>(kc, 1 << 20);
-      g.ratio = (ng == 0) ? 1u : pow2mod((uint64_t)a.dx.b * (uint64_t)(prev_s - pr.s), m.p);
-      prev_s = pr.s;
-      ++ng;
+  uint32_t wprev = 0;
+  for (int seg = 0; seg < kblocks; seg += kseg) {
+    const int segend = std::min(kblocks, seg + kseg);
+    for (const Term &t : terms) {
+      const uint32_t w = modw(t.w);
+      if (w == 0) continue;  // the term vanishes mod p
+      const int64_t prod = std::max<int64_t>(t.prod, 1);
+      const int64_t kc = ((int64_t)1 << ebits) / prod / BK;
+      const int64_t kr = room / prod / BK;
+      if (kc < 1 || kr < 1) { delete P; return cudaErrorInvalidValue; }
+      for (int kb = seg; kb < segend; kb += (int)kr) {
+        if (ng >= MAX_GROUPS - 1) { delete P; return cudaErrorInvalidValue; }
+        Group &g = P->g[ng];
+        g.xp = (int16_t)t.xp;
+        g.yp = (int16_t)t.yp;
+        g.kb0 = kb;
+        g.kb1 = (int)std::min<int64_t>(segend, kb + kr);
+        g.kchunk = (int)std::min<int64_t>(kc, 1 << 20);
+        g.ratio = (ng == 0) ? 1u : mulm(wprev, invm(w));
+        wprev = w;
+        ++ng;
+      }
     }
   }
+  if (ng > 0 && wprev != 1u) {  // final multiplier: a group without K blocks
+    Group &g = P->g[ng++];
+    g.xp = g.yp = 0;
+    g.kb0 = g.kb1 = 0;
+    g.kchunk = 1;
+    g.ratio = wprev;
+  }
   P->ng = ng;
-  if (prev_s != 0) { delete P; return cudaErrorInvalidValue; }  // pair (0, 0) comes last
   P->out = a.out;
   P->ldo = a.ldo;
   P->M = a.M;
@@ -649,9 +700,14 @@ cudaError_t launch_leaf_tc(const TcLeafArgs &a, const ModP &m, cudaStream_t st) 
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = std::max(1, std::min(nt, sms));
   if (nt > 0) {
+    // algorithmic tensor work: one BF16 product of the ring MACs per plane
+    // product with a non-zero weight
+    int nprod = 0;
+    for (const Term &t : terms)
+      if (modw(t.w) != 0) ++nprod;
     const double macs =
         a.lower ? 0.5 * (double)a.M * (double)(a.M + 1) * a.K : (double)a.M * a.N * a.K;
-    ProfScope prof(AAT_K_LEAF_TC, st, 2.0 * a.dx.L * a.dy.L * macs);
+    ProfScope prof(AAT_K_LEAF_TC, st, 2.0 * nprod * macs);
     leaf_tc_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(*P);
   }
   delete P;
@@ -761,6 +817,8 @@ extern "C" AAT_API int aat_gemm_modp_noalloc(const int32_t *X, int64_t ldx, cons
     nd = d;
   }
   Planes px, py;
+  std::memset(&px, 0, sizeof(px));
+  px.nbase = ds.L;
   px.ptr = (__nv_bfloat16 *)nd.scratch;
   px.rows = m;
   px.cols = k;

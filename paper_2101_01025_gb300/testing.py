@@ -28,11 +28,14 @@ def y_params(p: int):
     return int(kind.value), int(a.value), int(b.value)
 
 
-def digit_spec(p: int):
-    b, L = ctypes.c_int(), ctypes.c_int()
+def digit_spec(p: int, with_sums: bool = False):
+    """(b, L, dmax) of the digit split mod p; with_sums adds the number of
+    pair-sum planes (0 when every digit pair is its own product)."""
+    b, L, ns = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     dmax = (ctypes.c_int * 8)()
-    check(lib().aatx_digit_spec(p, ctypes.byref(b), ctypes.byref(L), dmax))
-    return int(b.value), int(L.value), [int(dmax[i]) for i in range(L.value)]
+    check(lib().aatx_digit_spec(p, ctypes.byref(b), ctypes.byref(L), dmax, ctypes.byref(ns)))
+    out = (int(b.value), int(L.value), [int(dmax[i]) for i in range(L.value)])
+    return out + (int(ns.value),) if with_sums else out
 
 
 def plan_stats(n: int, k: int, p: int, flags: int = 0) -> PlanStats:
@@ -61,9 +64,9 @@ def split(X, p: int):
     """Digit planes of X as a (L, rows, kstride) bfloat16 CUDA tensor."""
     import torch
     rows, cols = X.shape
-    _, L, _ = digit_spec(p)
+    _, L, _, ns = digit_spec(p, with_sums=True)
     ks = (cols + 7) // 8 * 8
-    planes = torch.zeros((L, rows, ks), dtype=torch.int16, device=X.device)
+    planes = torch.zeros((L + ns, rows, ks), dtype=torch.int16, device=X.device)
     check(lib().aatx_split(X.data_ptr(), rows, cols, X.stride(0), p, planes.data_ptr(),
                            _stream()))
     return planes.view(torch.bfloat16)

@@ -54,18 +54,24 @@ def low_equal(C, ref):
 @pytest.mark.parametrize("p", PRIMES + [13])
 def test_split_reconstructs_balanced_residues(p):
     from paper_2101_01025_gb300 import testing as T
-    b, L, dmax = T.digit_spec(p)
+    b, L, dmax, ns = T.digit_spec(p, with_sums=True)
     half = (p - 1) // 2
     X = synth.residues(1, (37, 203), p, balanced=True)
     X[0, :7] = [half, -half, 0, 1, -1, half - 1, -(half - 1)]
     X[1, :] = p - 1            # canonical input: the kernel balances it
     planes = T.split(dev(X), p).float().cpu().numpy()[:, :, :203]
-    assert planes.shape[0] == L
+    assert planes.shape[0] == L + ns
     for d in range(L):
         assert np.all(np.abs(planes[d]) <= dmax[d])
         assert np.all(planes[d] == np.round(planes[d]))
     rec = sum(planes[d].astype(np.int64) << (b * d) for d in range(L))
     assert np.array_equal(rec, bal(X, p))
+    pairs = [(i, j) for i in range(L) for j in range(i + 1, L)]
+    assert ns in (0, len(pairs))
+    for q in range(ns):
+        i, j = pairs[q]
+        assert np.array_equal(planes[L + q], planes[i] + planes[j])
+        assert np.all(np.abs(planes[L + q]) <= 256)
 
 
 @pytest.mark.parametrize("p", PRIMES)
@@ -82,13 +88,18 @@ def test_sblocks_match_oracle(p, n, k):
         assert np.array_equal(got[i].astype(np.int64), ref[i].astype(np.int64)), "S%d" % (i + 1)
 
 
-@pytest.mark.parametrize("leafkind", ["tc", "simt"])
+LEAFKINDS = {"tc": 0, "tc_plain": 1 << 12, "simt": 1 << 4}
+
+
+@pytest.mark.parametrize("leafkind", list(LEAFKINDS))
 @pytest.mark.parametrize("p", PRIMES)
 @pytest.mark.parametrize("M,N,K", [(128, 256, 64), (300, 520, 200), (1000, 700, 1536),
-                                   (5, 3, 1), (257, 129, 777)])
+                                   (5, 3, 1), (257, 129, 777), (640, 512, 9000)])
 def test_leaf_gemm_matches_oracle(leafkind, p, M, N, K):
     from paper_2101_01025_gb300 import testing as T
-    kindflag = 0 if leafkind == "tc" else 1 << 4
+    if leafkind == "simt" and K > 2000:
+        pytest.skip("slow check path")
+    kindflag = LEAFKINDS[leafkind]
     X = synth.residues(M + 7 * K, (M, K), p, balanced=True)
     Y = synth.residues(N + 11 * K, (N, K), p)
     C = host(T.leaf(dev(X), dev(Y), p, leafkind=kindflag))
@@ -113,8 +124,9 @@ def test_leaf_syrk_lower_and_accumulate(p, n, K):
     assert low_equal(host(C), (2 * ref) % p)
 
 
+@pytest.mark.parametrize("scheme", [0, 1 << 12])
 @pytest.mark.parametrize("exact_bits", [24, 23, 20])
-def test_leaf_tc_worst_case_digits_fp32_exact(exact_bits):
+def test_leaf_tc_worst_case_digits_fp32_exact(exact_bits, scheme):
     """All rows equal, low digits -128 (|digit products| 2^14, one sign per
     digit pair): every FP32 partial sum of a chunk reaches exactly
     2^exact_bits before it is drained."""
@@ -126,7 +138,7 @@ def test_leaf_tc_worst_case_digits_fp32_exact(exact_bits):
     X = np.full((M, K), x, dtype=np.int32)
     Y = np.full((N, K), x, dtype=np.int32)
     Y[::3] = -x
-    C = host(T.leaf(dev(X), dev(Y), p, exact_bits=exact_bits)).astype(np.int64)
+    C = host(T.leaf(dev(X), dev(Y), p, leafkind=scheme, exact_bits=exact_bits)).astype(np.int64)
     pos, neg = (x * x * K) % p, (-x * x * K) % p
     assert np.all(C[:, 0::3] == neg)
     assert np.all(C[:, 1::3] == pos) and np.all(C[:, 2::3] == pos)
@@ -173,6 +185,15 @@ def test_aat_modp_tc_matches_oracle(lib, p, n, k, levels):
 def test_aat_modp_simt_leaf_matches_oracle(lib, p, n, k, levels):
     A = synth.residues(n + k, (n, k), p)
     C = host(lib.aat_modp(dev(A), p, levels=levels, flags=lib.AAT_LEAF_SIMT))
+    assert low_equal(C, oracle.aat_modp_low(A, p))
+
+
+@pytest.mark.parametrize("p", [65521, 2**31 - 1])
+@pytest.mark.parametrize("n,k", [(300, 200), (640, 640)])
+@pytest.mark.parametrize("levels", [0, 1, 2])
+def test_aat_modp_plain_digit_pairs_matches_oracle(lib, p, n, k, levels):
+    A = synth.residues(7 * n + k, (n, k), p)
+    C = host(lib.aat_modp(dev(A), p, levels=levels, flags=lib.AAT_DIGITS_PLAIN))
     assert low_equal(C, oracle.aat_modp_low(A, p))
 
 

@@ -107,6 +107,14 @@ def test_digit_spec_bounds_and_exactness(p):
         assert (b, L) == (8, 4)
     if p in (65521, 131071):
         assert L == 2
+    # pair sums are used exactly when every d_i + d_j stays within 256
+    ns = T.digit_spec(p, with_sums=True)[3]
+    ok = 2 <= L <= 4 and all(dmax[i] + dmax[j] <= 256 for i in range(L) for j in range(i + 1, L))
+    assert ns == (L * (L - 1) // 2 if ok else 0)
+    if p == 2**31 - 1:
+        assert ns == 6          # 10 plane products instead of 16
+    if p == 131071:
+        assert ns == 0          # d_1 reaches 256: plain pairs
 
 
 def test_plan_counts_match_paper():
