@@ -49,6 +49,15 @@ typedef struct {
 AAT_API int aatx_plan_stats(int64_t n, int64_t k, uint32_t p, uint32_t flags,
                     aatx_plan_stats_t *out);
 
+/* The groups the tensor-core leaf runs for inner dimension K mod p (host
+ * only): per group, in processing order, six int32 (X plane, Y plane, first
+ * and one-past-last K block of 64, K blocks per FP32 chunk, Horner ratio mod
+ * p applied to the accumulator before the group).  flags may hold
+ * AAT_DIGITS_PLAIN.  Returns the group count or a negative error; *nprod
+ * receives the number of plane products. */
+AAT_API int aatx_leaf_groups(uint32_t p, int64_t K, uint32_t flags, int exact_bits,
+                             int32_t *out, int max_groups, int *nprod);
+
 /* ---- single GPU steps (device pointers, asynchronous on stream) ---- */
 
 /* The four additions of Algorithm 1 on A (n x k, even n, k; k/2 even for

@@ -40,7 +40,7 @@ EXPORTS = [
     "aat_last_error", "aat_device_status", "aat_shutdown", "aat_version",
     "aat_profile_begin", "aat_profile_end",
     "aatx_is_prime", "aatx_sqrt_mod", "aatx_sos", "aatx_y_params", "aatx_digit_spec",
-    "aatx_plan_stats", "aatx_sblocks", "aatx_split", "aatx_leaf", "aatx_postadd",
+    "aatx_plan_stats", "aatx_leaf_groups", "aatx_sblocks", "aatx_split", "aatx_leaf", "aatx_postadd",
 ]
 
 
@@ -122,6 +122,7 @@ def lib():
         L.aatx_digit_spec.argtypes = [u32, ctypes.POINTER(i32), ctypes.POINTER(i32),
                                       ctypes.POINTER(i32), ctypes.POINTER(i32)]
         L.aatx_plan_stats.argtypes = [i64, i64, u32, u32, ctypes.POINTER(PlanStats)]
+        L.aatx_leaf_groups.argtypes = [u32, i64, u32, i32, vp, i32, ctypes.POINTER(i32)]
         L.aatx_sblocks.argtypes = [vp, i64, i64, i64, u32, vp, vp, vp, vp, i64, vp]
         L.aatx_split.argtypes = [vp, i64, i64, i64, u32, vp, vp]
         L.aatx_leaf.argtypes = [vp, i64, vp, i64, i64, i64, i64, u32, vp, i64, i32, i32, u32,

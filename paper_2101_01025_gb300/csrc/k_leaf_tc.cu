@@ -568,27 +568,10 @@ cudaError_t get_tiles(int dev, int64_t M, int64_t N, int lower, int2 **out, int 
   return cudaSuccess;
 }
 
-}  // namespace
-
-cudaError_t launch_leaf_tc(const TcLeafArgs &a, const ModP &m, cudaStream_t st) {
-  if (a.M <= 0 || a.N <= 0) return cudaSuccess;
-  if (a.dx.b != a.dy.b || a.x.L != a.dx.L || a.y.L != a.dy.L) return cudaErrorInvalidValue;
-  if (a.x.kstride % 8 || a.y.kstride % 8 || a.x.cols != a.K || a.y.cols != a.K)
-    return cudaErrorInvalidValue;
-  if (((uintptr_t)a.x.ptr | (uintptr_t)a.y.ptr) & 15) return cudaErrorInvalidValue;
-  std::lock_guard<std::mutex> lock(g_mu);
-  cudaError_t e = get_encode();
-  if (e != cudaSuccess) return e;
-  int dev = 0;
-  cudaGetDevice(&dev);
-
-  Params *P = new Params;
-  std::memset(P, 0, sizeof(Params));
-  if ((e = encode_planes(&P->tmx, a.x, BM)) != cudaSuccess ||
-      (e = encode_planes(&P->tmy, a.y, BN)) != cudaSuccess) {
-    delete P;
-    return e;
-  }
+// Groups of the leaf product: plane pairs with integer weights turned into a
+// Horner sequence (see the file header).  Returns false when the product does
+// not fit the group table or a bound cannot be met.
+bool build_groups(const TcLeafArgs &a, const ModP &m, Group *out, int *ng_out, int *nprod_out) {
   // The terms of the product: plane pairs with integer weights.
   //   plain:     X_i Y_j^T with weight z^(i+j), z = 2^b
   //   pair sums: X_i Y_i^T with weight z^(2i) - sum_{j != i} z^(i+j), and
@@ -651,10 +634,10 @@ cudaError_t launch_leaf_tc(const TcLeafArgs &a, const ModP &m, cudaStream_t st) 
       const int64_t prod = std::max<int64_t>(t.prod, 1);
       const int64_t kc = ((int64_t)1 << ebits) / prod / BK;
       const int64_t kr = room / prod / BK;
-      if (kc < 1 || kr < 1) { delete P; return cudaErrorInvalidValue; }
+      if (kc < 1 || kr < 1) return false;
       for (int kb = seg; kb < segend; kb += (int)kr) {
-        if (ng >= MAX_GROUPS - 1) { delete P; return cudaErrorInvalidValue; }
-        Group &g = P->g[ng];
+        if (ng >= MAX_GROUPS - 1) return false;
+        Group &g = out[ng];
         g.xp = (int16_t)t.xp;
         g.yp = (int16_t)t.yp;
         g.kb0 = kb;
@@ -667,11 +650,47 @@ cudaError_t launch_leaf_tc(const TcLeafArgs &a, const ModP &m, cudaStream_t st) 
     }
   }
   if (ng > 0 && wprev != 1u) {  // final multiplier: a group without K blocks
-    Group &g = P->g[ng++];
+    Group &g = out[ng++];
     g.xp = g.yp = 0;
     g.kb0 = g.kb1 = 0;
     g.kchunk = 1;
     g.ratio = wprev;
+  }
+  int nprod = 0;
+  for (const Term &t : terms)
+    if (modw(t.w) != 0) ++nprod;
+  *ng_out = ng;
+  *nprod_out = nprod;
+  return true;
+}
+
+}  // namespace
+
+cudaError_t launch_leaf_tc(const TcLeafArgs &a, const ModP &m, cudaStream_t st) {
+  if (a.M <= 0 || a.N <= 0) return cudaSuccess;
+  if (a.dx.b != a.dy.b || a.x.nbase != a.dx.L || a.y.nbase != a.dy.L ||
+      a.x.L != a.x.nbase + a.x.nsum || a.y.L != a.y.nbase + a.y.nsum)
+    return cudaErrorInvalidValue;
+  if (a.x.kstride % 8 || a.y.kstride % 8 || a.x.cols != a.K || a.y.cols != a.K)
+    return cudaErrorInvalidValue;
+  if (((uintptr_t)a.x.ptr | (uintptr_t)a.y.ptr) & 15) return cudaErrorInvalidValue;
+  std::lock_guard<std::mutex> lock(g_mu);
+  cudaError_t e = get_encode();
+  if (e != cudaSuccess) return e;
+  int dev = 0;
+  cudaGetDevice(&dev);
+
+  Params *P = new Params;
+  std::memset(P, 0, sizeof(Params));
+  if ((e = encode_planes(&P->tmx, a.x, BM)) != cudaSuccess ||
+      (e = encode_planes(&P->tmy, a.y, BN)) != cudaSuccess) {
+    delete P;
+    return e;
+  }
+  int ng = 0, nprod = 0;
+  if (!build_groups(a, m, P->g, &ng, &nprod)) {
+    delete P;
+    return cudaErrorInvalidValue;
   }
   P->ng = ng;
   P->out = a.out;
@@ -702,9 +721,6 @@ cudaError_t launch_leaf_tc(const TcLeafArgs &a, const ModP &m, cudaStream_t st) 
   if (nt > 0) {
     // algorithmic tensor work: one BF16 product of the ring MACs per plane
     // product with a non-zero weight
-    int nprod = 0;
-    for (const Term &t : terms)
-      if (modw(t.w) != 0) ++nprod;
     const double macs =
         a.lower ? 0.5 * (double)a.M * (double)(a.M + 1) * a.K : (double)a.M * a.N * a.K;
     ProfScope prof(AAT_K_LEAF_TC, st, 2.0 * nprod * macs);
@@ -907,4 +923,40 @@ extern "C" AAT_API int aat_gemm_modp_noalloc(const int32_t *X, int64_t ldx, cons
   leaf_tc_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(P);
   ce = cudaGetLastError();
   return ce == cudaSuccess ? AAT_OK : report_error(AAT_ECUDA, cudaGetErrorString(ce));
+}
+
+// ---------------------------------------------------------------- test hook
+
+extern "C" AAT_API int aatx_leaf_groups(uint32_t p, int64_t K, uint32_t flags, int exact_bits,
+                                        int32_t *out, int max_groups, int *nprod) {
+  using namespace aat;
+  int e = check_prime_arg(p);
+  if (e) return e;
+  if (K <= 0 || !out || !nprod) return report_error(AAT_EINVAL, "bad arguments");
+  DigitSpec ds = digits_for_prime(p);
+  if (flags & AAT_DIGITS_PLAIN) ds.nsum = 0;
+  TcLeafArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.dx = a.dy = ds;
+  a.x.nbase = a.y.nbase = ds.L;
+  a.x.nsum = a.y.nsum = ds.nsum;
+  a.x.L = a.y.L = ds.L + ds.nsum;
+  a.M = a.N = 1;
+  a.K = K;
+  a.exact_bits = exact_bits > 0 ? exact_bits : 24;
+  std::vector<Group> g(MAX_GROUPS);
+  int ng = 0;
+  if (!build_groups(a, make_modp(p), g.data(), &ng, nprod))
+    return report_error(AAT_ERANGE, "leaf product does not fit the group table");
+  if (ng > max_groups) return report_error(AAT_ERANGE, "output too small");
+  for (int i = 0; i < ng; ++i) {
+    int32_t *o = out + 6 * i;
+    o[0] = g[i].xp;
+    o[1] = g[i].yp;
+    o[2] = g[i].kb0;
+    o[3] = g[i].kb1;
+    o[4] = g[i].kchunk;
+    o[5] = (int32_t)g[i].ratio;
+  }
+  return ng;
 }

@@ -44,6 +44,18 @@ def plan_stats(n: int, k: int, p: int, flags: int = 0) -> PlanStats:
     return st
 
 
+def leaf_groups(p: int, K: int, flags: int = 0, exact_bits: int = 0):
+    """The leaf's group plan: (list of (xplane, yplane, kb0, kb1, kchunk, ratio),
+    number of plane products)."""
+    import numpy as np
+    out = np.zeros((256, 6), dtype=np.int32)
+    nprod = ctypes.c_int()
+    ng = lib().aatx_leaf_groups(p, K, flags, exact_bits, out.ctypes.data, 256,
+                                ctypes.byref(nprod))
+    check(ng if ng < 0 else 0)
+    return [tuple(int(v) for v in row) for row in out[:ng]], int(nprod.value)
+
+
 def _stream():
     import torch
     return torch.cuda.current_stream().cuda_stream

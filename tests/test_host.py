@@ -166,3 +166,44 @@ def test_argument_validation_before_any_gpu_call():
         _native.AAT_ENOTPRIME
     assert lib.aat_modp_ex(fake, 4, 4, 4, 131071, fake * 2, 4, 7 << 4, None) == \
         _native.AAT_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("p", [2**31 - 1, 65521, 131071, 13, 1000003])
+@pytest.mark.parametrize("K", [1, 64, 1000, 8192, 20000])
+@pytest.mark.parametrize("plain", [False, True])
+def test_leaf_group_plan_reproduces_the_product(p, K, plain):
+    """Simulate the leaf epilogue on random digits: per group the exact
+    integer sum over its K range, Horner ratios between groups; the result
+    must be sum_k x_k y_k mod p.  Also checks the FP32 and int32 bounds."""
+    b, L, dmax, ns = T.digit_spec(p, with_sums=True)
+    groups, nprod = T.leaf_groups(p, K, _native.AAT_DIGITS_PLAIN if plain else 0)
+    use_sums = ns > 0 and not plain
+    assert nprod == (L + ns if use_sums else L * L)
+    pairs = [(i, j) for i in range(L) for j in range(i + 1, L)]
+    rng = np.random.default_rng(p + K)
+    half = (p - 1) // 2
+    x = [int(v) for v in rng.integers(-half, half + 1, K)]
+    y = [int(v) for v in rng.integers(-half, half + 1, K)]
+    x[0], y[0] = -half, half
+    dx = [_digits(v, b, L) for v in x]
+    dy = [_digits(v, b, L) for v in y]
+
+    def plane(d, q):
+        return d[q] if q < L else d[pairs[q - L][0]] + d[pairs[q - L][1]]
+
+    pmax = dmax + [dmax[i] + dmax[j] for i, j in pairs]
+    acc = 0
+    for gi, (xp, yp, kb0, kb1, kc, ratio) in enumerate(groups):
+        if gi > 0:
+            acc = acc * ratio % p
+            acc = acc - p if acc > half else acc
+        prod = pmax[xp] * pmax[yp]
+        assert kc * 64 * prod <= 1 << 24            # FP32 partial sums stay exact
+        assert half + (kb1 - kb0) * 64 * prod < 2**31  # int32 accumulator
+        for k0 in range(kb0 * 64, min(kb1 * 64, K), kc * 64):
+            chunk = sum(plane(dx[k], xp) * plane(dy[k], yp)
+                        for k in range(k0, min(k0 + kc * 64, kb1 * 64, K)))
+            assert abs(chunk) <= 1 << 24
+            acc += chunk
+        assert abs(acc) < 2**31
+    assert acc % p == sum(a * c for a, c in zip(x, y)) % p
