@@ -118,7 +118,7 @@ struct Planes {
   int L;        // planes stored (nbase + nsum)
   int nbase;    // digit planes
   int nsum;     // pair-sum planes
-  int8_t si[8], sj[8];
+  int8_t si[8], sj[8];  // pair of plane nbase + q (always (0,1), (0,2), ...)
 };
 
 struct DigitSpec {
@@ -129,41 +129,6 @@ struct DigitSpec {
   int si[8], sj[8];
 };
 
-// Digit d of a register array indexed by a runtime d without local memory.
-template <int N>
-__device__ __forceinline__ int32_t pick(const int32_t (&v)[N], int d) {
-  int32_t r = 0;
-#pragma unroll
-  for (int q = 0; q < N; ++q) r = (q == d) ? v[q] : r;
-  return r;
-}
-
-// Balanced digits of a balanced residue x (all but the last in
-// [-2^(b-1), 2^(b-1) - 1], the last carries the rest), then the pair sums.
-__device__ __forceinline__ void store_digits(const Planes &P, int64_t r, int64_t c,
-                                             int32_t x, int b) {
-  const int32_t half = 1 << (b - 1);
-  const int32_t mask = (1 << b) - 1;
-  const int64_t plane = P.rows * P.kstride;
-  __nv_bfloat16 *dst = P.ptr + r * P.kstride + c;
-  int32_t dig[8];
-#pragma unroll
-  for (int d = 0; d < 8; ++d) {
-    if (d < P.nbase - 1) {
-      dig[d] = ((x + half) & mask) - half;
-      x = (x - dig[d]) >> b;
-    } else {
-      dig[d] = (d == P.nbase - 1) ? x : 0;
-    }
-    if (d < P.nbase) dst[d * plane] = __float2bfloat16_rn((float)dig[d]);
-  }
-#pragma unroll
-  for (int q = 0; q < 8; ++q)
-    if (q < P.nsum)
-      dst[(P.nbase + q) * plane] =
-          __float2bfloat16_rn((float)(pick(dig, P.si[q]) + pick(dig, P.sj[q])));
-}
-
 __device__ __forceinline__ uint2 pack4(float a, float b, float c, float d) {
   __nv_bfloat162 lo = __floats2bfloat162_rn(a, b);
   __nv_bfloat162 hi = __floats2bfloat162_rn(c, d);
@@ -173,39 +138,51 @@ __device__ __forceinline__ uint2 pack4(float a, float b, float c, float d) {
   return u;
 }
 
-// The same for four consecutive columns c..c+3 (c a multiple of 4): one
-// 8-byte store per plane.
-__device__ __forceinline__ void store_digits4(const Planes &P, int64_t r, int64_t c,
-                                              const int32_t (&x0)[4], int b) {
+// Balanced digits of V consecutive balanced residues x[0..V-1] at columns
+// c..c+V-1 (all digits but the last in [-2^(b-1), 2^(b-1) - 1], the last
+// carries the rest), written to the NB digit planes; then, if P.nsum > 0,
+// the pair sums d_i + d_j for i < j in the order (0,1), (0,2), ...,
+// (NB-2,NB-1).  V = 4 needs c % 4 == 0 and 8-byte aligned rows (one 8-byte
+// store per plane).
+template <int NB, int V>
+__device__ __forceinline__ void store_digits_t(const Planes &P, int64_t r, int64_t c,
+                                               const int32_t (&x0)[V], int b) {
   const int32_t half = 1 << (b - 1);
   const int32_t mask = (1 << b) - 1;
   const int64_t plane = P.rows * P.kstride;
   __nv_bfloat16 *dst = P.ptr + r * P.kstride + c;
-  int32_t x[4] = {x0[0], x0[1], x0[2], x0[3]};
-  int32_t dig[4][8];
+  int32_t dig[NB][V];
 #pragma unroll
-  for (int d = 0; d < 8; ++d) {
+  for (int v = 0; v < V; ++v) {
+    int32_t x = x0[v];
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      if (d < P.nbase - 1) {
-        dig[v][d] = ((x[v] + half) & mask) - half;
-        x[v] = (x[v] - dig[v][d]) >> b;
-      } else {
-        dig[v][d] = (d == P.nbase - 1) ? x[v] : 0;
-      }
+    for (int d = 0; d < NB - 1; ++d) {
+      dig[d][v] = ((x + half) & mask) - half;
+      x = (x - dig[d][v]) >> b;
     }
-    if (d < P.nbase)
-      *reinterpret_cast<uint2 *>(dst + d * plane) =
-          pack4((float)dig[0][d], (float)dig[1][d], (float)dig[2][d], (float)dig[3][d]);
+    dig[NB - 1][v] = x;
   }
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    if (q < P.nsum) {
-      const int i = P.si[q], j = P.sj[q];
-      *reinterpret_cast<uint2 *>(dst + (P.nbase + q) * plane) =
-          pack4((float)(pick(dig[0], i) + pick(dig[0], j)), (float)(pick(dig[1], i) + pick(dig[1], j)),
-                (float)(pick(dig[2], i) + pick(dig[2], j)), (float)(pick(dig[3], i) + pick(dig[3], j)));
+  auto put = [&](int pl, const int32_t (&w)[V]) {
+    if constexpr (V == 4) {
+      *reinterpret_cast<uint2 *>(dst + pl * plane) =
+          pack4((float)w[0], (float)w[1], (float)w[2], (float)w[3]);
+    } else {
+      dst[pl * plane] = __float2bfloat16_rn((float)w[0]);
     }
+  };
+#pragma unroll
+  for (int d = 0; d < NB; ++d) put(d, dig[d]);
+  if (P.nsum > 0) {
+    int q = NB;
+#pragma unroll
+    for (int i = 0; i < NB; ++i)
+#pragma unroll
+      for (int j = i + 1; j < NB; ++j) {
+        int32_t w[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) w[v] = dig[i][v] + dig[j][v];
+        put(q++, w);
+      }
   }
 }
 

@@ -40,30 +40,25 @@ __device__ __forceinline__ void st4_canon(int32_t *p, const int32_t (&v)[4], con
 }
 
 // Outputs of one group of V consecutive columns starting at column j.
-template <int V>
+template <int V, int NB>
 __device__ __forceinline__ void sblocks_store(const SKernelOut &o, int64_t i, int64_t j,
                                               const int32_t (&sv)[4][V], const int32_t (&a11)[V],
                                               const int32_t (&a12)[V], const int32_t (&a22)[V],
                                               const ModP &m, int b) {
-  if constexpr (V == 4) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (o.s[q]) st4_canon(o.s[q] + i * o.lds[q] + j, sv[q], m);
-      if (has(o.sp[q])) store_digits4(o.sp[q], i, j, sv[q], b);
+  for (int q = 0; q < 4; ++q) {
+    if (o.s[q]) {
+      if constexpr (V == 4) {
+        st4_canon(o.s[q] + i * o.lds[q] + j, sv[q], m);
+      } else {
+        o.s[q][i * o.lds[q] + j] = (int32_t)bal_to_canon(sv[q][0], m);
+      }
     }
-    if (has(o.a11)) store_digits4(o.a11, i, j, a11, b);
-    if (has(o.a12)) store_digits4(o.a12, i, j, a12, b);
-    if (has(o.a22)) store_digits4(o.a22, i, j, a22, b);
-  } else {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (o.s[q]) o.s[q][i * o.lds[q] + j] = (int32_t)bal_to_canon(sv[q][0], m);
-      if (has(o.sp[q])) store_digits(o.sp[q], i, j, sv[q][0], b);
-    }
-    if (has(o.a11)) store_digits(o.a11, i, j, a11[0], b);
-    if (has(o.a12)) store_digits(o.a12, i, j, a12[0], b);
-    if (has(o.a22)) store_digits(o.a22, i, j, a22[0], b);
+    if (has(o.sp[q])) store_digits_t<NB, V>(o.sp[q], i, j, sv[q], b);
   }
+  if (has(o.a11)) store_digits_t<NB, V>(o.a11, i, j, a11, b);
+  if (has(o.a12)) store_digits_t<NB, V>(o.a12, i, j, a12, b);
+  if (has(o.a22)) store_digits_t<NB, V>(o.a22, i, j, a22, b);
 }
 
 template <int V>
@@ -79,7 +74,8 @@ __device__ __forceinline__ void ldv_bal(const int32_t *p, const ModP &m, int32_t
 // and the thread also handles columns j + kappa/2; for kind 1, j < kappa.
 // V = 4 needs kappa/2 (kind 2) or kappa (kind 1), lda, every output stride
 // and every plane stride to be multiples of 4 and 16-byte aligned bases.
-template <int V>
+// NB: digits per residue of every plane output.
+template <int V, int NB>
 __global__ void sblocks_kernel(const int32_t *__restrict__ A, int64_t lda, int64_t h,
                                int64_t kappa, ModP m, YParams y, int b, SKernelOut o) {
   const int64_t ncols = ((y.kind == 2) ? kappa / 2 : kappa) / V;
@@ -118,8 +114,8 @@ __global__ void sblocks_kernel(const int32_t *__restrict__ A, int64_t lda, int64
         sv0[3][v] = add_bal(sv0[2][v], a12_0[v], m);
         sv1[3][v] = add_bal(sv1[2][v], a12_1[v], m);
       }
-      sblocks_store<V>(o, i, j, sv0, a11_0, a12_0, a22_0, m, b);
-      sblocks_store<V>(o, i, jj, sv1, a11_1, a12_1, a22_1, m, b);
+      sblocks_store<V, NB>(o, i, j, sv0, a11_0, a12_0, a22_0, m, b);
+      sblocks_store<V, NB>(o, i, jj, sv1, a11_1, a12_1, a22_1, m, b);
     } else {
       int32_t a11[V], a12[V], a21[V], a22[V];
       ldv_bal<V>(r1 + j, m, a11);
@@ -134,12 +130,12 @@ __global__ void sblocks_kernel(const int32_t *__restrict__ A, int64_t lda, int64
         sv[2][v] = sub_bal(sv[0][v], a22[v], m);
         sv[3][v] = add_bal(sv[2][v], a12[v], m);
       }
-      sblocks_store<V>(o, i, j, sv, a11, a12, a22, m, b);
+      sblocks_store<V, NB>(o, i, j, sv, a11, a12, a22, m, b);
     }
   }
 }
 
-template <int V>
+template <int V, int NB>
 __global__ void split_kernel(const int32_t *__restrict__ X, int64_t ldx, int64_t rows,
                              int64_t cols, ModP m, int b, Planes P) {
   const int64_t ncol = cols / V;
@@ -147,13 +143,9 @@ __global__ void split_kernel(const int32_t *__restrict__ X, int64_t ldx, int64_t
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = t / ncol, c = (t - (t / ncol) * ncol) * V;
-    if constexpr (V == 4) {
-      int32_t v[4];
-      ld4_bal(X + r * ldx + c, m, v);
-      store_digits4(P, r, c, v, b);
-    } else {
-      store_digits(P, r, c, ld_bal(X + r * ldx + c, m), b);
-    }
+    int32_t v[V];
+    ldv_bal<V>(X + r * ldx + c, m, v);
+    store_digits_t<NB, V>(P, r, c, v, b);
   }
 }
 
@@ -302,10 +294,27 @@ cudaError_t launch_sblocks(const int32_t *A, int64_t lda, int64_t h, int64_t kap
   }
   for (const Planes *P : {&o.a11, &o.a12, &o.a22})
     if (P->ptr) vec = vec && al16(P->ptr);
-  if (vec)
-    sblocks_kernel<4><<<grid_for(total / 4), kThreads, 0, st>>>(A, lda, h, kappa, m, y, b, o);
-  else
-    sblocks_kernel<1><<<grid_for(total), kThreads, 0, st>>>(A, lda, h, kappa, m, y, b, o);
+  int nb = 0;
+  for (const Planes *P : {&o.sp[0], &o.sp[1], &o.sp[2], &o.sp[3], &o.a11, &o.a12, &o.a22})
+    if (P->ptr) {
+      if (nb && P->nbase != nb) return cudaErrorInvalidValue;
+      nb = P->nbase;
+    }
+  if (nb == 0) nb = 1;
+  const int g = grid_for(vec ? total / 4 : total);
+#define AAT_SB(NBV)                                                                     \
+  case NBV:                                                                             \
+    if (vec)                                                                            \
+      sblocks_kernel<4, NBV><<<g, kThreads, 0, st>>>(A, lda, h, kappa, m, y, b, o);     \
+    else                                                                                \
+      sblocks_kernel<1, NBV><<<g, kThreads, 0, st>>>(A, lda, h, kappa, m, y, b, o);     \
+    break;
+  switch (nb) {
+    AAT_SB(1) AAT_SB(2) AAT_SB(3) AAT_SB(4) AAT_SB(5)
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef AAT_SB
   return cudaGetLastError();
 }
 
@@ -316,10 +325,20 @@ cudaError_t launch_split(const int32_t *X, int64_t ldx, int64_t rows, int64_t co
   ProfScope prof(AAT_K_SPLIT, st, (double)total * (4.0 + 2.0 * P.L));
   const bool vec = (cols % 4 == 0) && (ldx % 4 == 0) && (((uintptr_t)X & 15) == 0) &&
                    (((uintptr_t)P.ptr & 15) == 0);
-  if (vec)
-    split_kernel<4><<<grid_for(total / 4), kThreads, 0, st>>>(X, ldx, rows, cols, m, b, P);
-  else
-    split_kernel<1><<<grid_for(total), kThreads, 0, st>>>(X, ldx, rows, cols, m, b, P);
+  const int g = grid_for(vec ? total / 4 : total);
+#define AAT_SP(NBV)                                                                     \
+  case NBV:                                                                             \
+    if (vec)                                                                            \
+      split_kernel<4, NBV><<<g, kThreads, 0, st>>>(X, ldx, rows, cols, m, b, P);       \
+    else                                                                                \
+      split_kernel<1, NBV><<<g, kThreads, 0, st>>>(X, ldx, rows, cols, m, b, P);       \
+    break;
+  switch (P.nbase) {
+    AAT_SP(1) AAT_SP(2) AAT_SP(3) AAT_SP(4) AAT_SP(5)
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef AAT_SP
   return cudaGetLastError();
 }
 
