@@ -50,7 +50,7 @@ SEED_OFFSET = 2
 # 17.59 TFLOP of algorithmic work, profiles/leaf_tc_kernel_gemm8192_p2p31m1.md),
 # scaled to the average launch of the step by its algorithmic work.  Set to
 # None whenever the kernel changes until it is captured again.
-LEAF_TC_BYTES_PER_FLOP = 28.78e9 / 17.59e12
+LEAF_TC_BYTES_PER_FLOP = None
 
 
 def parse():
