@@ -129,6 +129,34 @@ AAT_API int aat_gemm_modp_noalloc(const int32_t *X, int64_t ldx, const int32_t *
                                   int64_t m, int64_t n, int64_t k, uint32_t p, int32_t *C,
                                   int64_t ldc, void *stream);
 
+/* ------------------------------------------------------------------ C
+ * Complex inputs and outputs are complex64, interleaved (re, im) floats,
+ * row-major with strides in complex elements.  Real products run on the
+ * tensor cores with BF16 pieces of the FP32 values (flags):
+ *   AAT_C_FP32    3 pieces, 6 piece products (close to FP32 accuracy)
+ *   AAT_C_BF16X3  2 pieces, 3 piece products
+ *   AAT_C_BF16    1 piece (plain BF16 products)
+ * with FP32 accumulation.  Only the lower triangle of C (diagonal included)
+ * is written.
+ */
+#define AAT_C_PREC_MASK (3u << 16)
+#define AAT_C_FP32 (0u << 16)
+#define AAT_C_BF16X3 (1u << 16)
+#define AAT_C_BF16 (2u << 16)
+
+/* Low(A A^H) by Algorithm 2 (Sec. 6.1, "2M", eps = i conj(i) = 1): two real
+ * products H = Re Im^T and G = Low((Re + Im)(Re + Im)^T), then
+ * Re C = G - H - H^T, Im C = H^T - H; the diagonal sum_l |a_il|^2 is summed in
+ * FP64 (real, >= 0).  There is no skew-unitary Y for the conjugate
+ * transposition over C (Sec. 4), so Algorithm 1 does not apply. */
+AAT_API int aah_complex(const void *A, int64_t n, int64_t k, void *C, void *stream);
+AAT_API int aah_complex_ex(const void *A, int64_t n, int64_t k, int64_t lda, void *C,
+                           int64_t ldc, uint32_t flags, void *stream);
+/* Low(A A^T) over C by Algorithm 2 with eps = i i = -1: H = Re Im^T,
+ * G = Low((Re + Im)(Re - Im)^T), Re C = G + H - H^T, Im C = H + H^T. */
+AAT_API int aat_complex_2m(const void *A, int64_t n, int64_t k, int64_t lda, void *C,
+                           int64_t ldc, uint32_t flags, void *stream);
+
 /* Bytes of device workspace aat_modp_ex would use for (n, k, p, flags). */
 AAT_API size_t aat_workspace_size(int64_t n, int64_t k, uint32_t p, uint32_t flags);
 
@@ -147,8 +175,9 @@ AAT_API int aat_device_status(int reset);
  * aat_profile_end(), every kernel launch of the library is bracketed by CUDA
  * events recorded on its own stream; aat_profile_end() synchronises and
  * returns, per kernel class, the launch count, the summed event time and the
- * summed algorithmic work (tensor FLOPs for leaf products: 2 L^2 per ring
- * multiply-add; bytes read + written for the addition kernels).
+ * summed algorithmic work (tensor FLOPs for leaf products: 2 per ring
+ * multiply-add and plane product; bytes read + written for the addition
+ * kernels).
  */
 #define AAT_K_SBLOCKS 0
 #define AAT_K_SPLIT 1
@@ -157,6 +186,7 @@ AAT_API int aat_device_status(int reset);
 #define AAT_K_POSTADD 4
 #define AAT_K_ADD_LOW 5
 #define AAT_K_COPY 6
+#define AAT_K_LEAF_F32 7
 #define AAT_K_NCLASS 8
 typedef struct {
   int64_t launches[AAT_K_NCLASS];

@@ -8,16 +8,17 @@ library ``libaat_gb300.so``; when it is missing the calls raise.
     aat_modp(A, p)            Low(A A^T) mod p, Algorithm 1 (Sec. 3)
     aat_gemm_modp(X, Y, p)    X Y^T mod p with the same exact leaf kernels
     aat_modp_host(A_np, p)    end to end from host memory
+    aah_complex(A)            Low(A A^H) over C, Algorithm 2 (Sec. 6.1)
 """
 from __future__ import annotations
 
 from . import _native
-from ._native import (AAT_DIGITS_PLAIN, AAT_IN_BALANCED, AAT_LEAF_SIMT, AAT_LEAF_TC,  # noqa: F401
-                      AAT_LEVELS, AAT_ZERO_UPPER, AatError, PlanStats, check, last_error, lib)
+from ._native import (AAT_C_BF16, AAT_C_BF16X3, AAT_C_FP32, AAT_DIGITS_PLAIN,  # noqa: F401
+                      AAT_IN_BALANCED, AAT_LEAF_SIMT, AAT_LEAF_TC, AAT_LEVELS, AAT_ZERO_UPPER, AatError, PlanStats, check, last_error, lib)
 
 __all__ = [
     "aat_modp", "aat_gemm_modp", "aat_modp_host", "aat_workspace_size", "aat_device_status",
-    "aat_shutdown", "aat_version", "AAT_LEVELS", "AAT_LEAF_TC", "AAT_LEAF_SIMT",
+    "aat_shutdown", "aat_version", "aah_complex", "aat_complex_2m", "AAT_LEVELS", "AAT_LEAF_TC", "AAT_LEAF_SIMT",
     "AAT_ZERO_UPPER", "AAT_IN_BALANCED", "AatError",
 ]
 
@@ -94,6 +95,45 @@ def aat_modp_host(A, p: int, C=None, flags: int = 0, levels: int | None = None):
     if C is None:
         C = torch.empty((n, n), dtype=torch.int32, pin_memory=A.is_pinned())
     check(lib().aat_modp_host(A.data_ptr(), n, k, p, C.data_ptr(), flags))
+    return C
+
+
+def _check_cmat(t, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != torch.complex64 or t.dim() != 2:
+        raise TypeError("%s must be a 2-D complex64 tensor" % name)
+    if t.shape[1] > 1 and t.stride(1) != 1:
+        raise ValueError("%s must have unit stride along rows" % name)
+    return max(t.stride(0), t.shape[1], 1)
+
+
+def aah_complex(A, C=None, flags: int = 0, stream=None):
+    """Low(A A^H) for a complex64 CUDA matrix A by Algorithm 2 (2M); returns C.
+
+    flags: AAT_C_FP32 (default), AAT_C_BF16X3 or AAT_C_BF16."""
+    import torch
+    lda = _check_cmat(A, "A")
+    n, k = A.shape
+    if C is None:
+        C = torch.empty((n, n), dtype=torch.complex64, device=A.device)
+    ldc = _check_cmat(C, "C")
+    check(lib().aah_complex_ex(A.data_ptr(), n, k, lda, C.data_ptr(), ldc, flags,
+                               _stream(stream)))
+    return C
+
+
+def aat_complex_2m(A, C=None, flags: int = 0, stream=None):
+    """Low(A A^T) for a complex64 CUDA matrix A by Algorithm 2 with eps = -1."""
+    import torch
+    lda = _check_cmat(A, "A")
+    n, k = A.shape
+    if C is None:
+        C = torch.empty((n, n), dtype=torch.complex64, device=A.device)
+    ldc = _check_cmat(C, "C")
+    check(lib().aat_complex_2m(A.data_ptr(), n, k, lda, C.data_ptr(), ldc, flags,
+                               _stream(stream)))
     return C
 
 

@@ -27,6 +27,9 @@ AAT_ZERO_UPPER = 1 << 1
 AAT_LEAF_TC = 0 << 4
 AAT_LEAF_SIMT = 1 << 4
 AAT_DIGITS_PLAIN = 1 << 12
+AAT_C_FP32 = 0 << 16
+AAT_C_BF16X3 = 1 << 16
+AAT_C_BF16 = 2 << 16
 
 
 def AAT_LEVELS(l: int) -> int:
@@ -38,7 +41,7 @@ EXPORTS = [
     "aat_modp", "aat_modp_ex", "aat_modp_host", "aat_gemm_modp", "aat_gemm_modp_noalloc",
     "aat_workspace_size",
     "aat_last_error", "aat_device_status", "aat_shutdown", "aat_version",
-    "aat_profile_begin", "aat_profile_end",
+    "aat_profile_begin", "aat_profile_end", "aah_complex", "aah_complex_ex", "aat_complex_2m",
     "aatx_is_prime", "aatx_sqrt_mod", "aatx_sos", "aatx_y_params", "aatx_digit_spec",
     "aatx_plan_stats", "aatx_leaf_groups", "aatx_sblocks", "aatx_split", "aatx_leaf", "aatx_postadd",
 ]
@@ -66,7 +69,7 @@ class PlanStats(ctypes.Structure):
 
 
 #: kernel classes of aat_profile_t
-K_CLASSES = ["sblocks", "split", "leaf_tc", "leaf_simt", "postadd", "add_low", "copy", "unused"]
+K_CLASSES = ["sblocks", "split", "leaf_tc", "leaf_simt", "postadd", "add_low", "copy", "leaf_f32"]
 
 
 class Profile(ctypes.Structure):
@@ -113,6 +116,9 @@ def lib():
         L.aat_device_status.argtypes = [i32]
         L.aat_shutdown.restype = None
         L.aat_profile_end.argtypes = [ctypes.POINTER(Profile)]
+        L.aah_complex.argtypes = [vp, i64, i64, vp, vp]
+        L.aah_complex_ex.argtypes = [vp, i64, i64, i64, vp, i64, u32, vp]
+        L.aat_complex_2m.argtypes = [vp, i64, i64, i64, vp, i64, u32, vp]
         L.aatx_is_prime.argtypes = [u64]
         L.aatx_sqrt_mod.argtypes = [i64, u64]
         L.aatx_sqrt_mod.restype = i64

@@ -18,12 +18,14 @@ import json
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["leaf", "syrk", "aat", "full"])
+    ap.add_argument("case", choices=["leaf", "syrk", "aat", "full", "aah", "aatc2m"])
     ap.add_argument("n", type=int)
     ap.add_argument("--k", type=int, default=None)
     ap.add_argument("--p", type=int, default=2**31 - 1)
     ap.add_argument("--levels", type=int, default=None)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16x3", "bf16"],
+                    help="complex cases: BF16 pieces per FP32 value (3, 2, 1)")
     ap.add_argument("--plain-digits", action="store_true",
                     help="one product per digit pair instead of the pair-sum form")
     a = ap.parse_args(argv)
@@ -38,9 +40,18 @@ def main(argv=None):
     n, k, p = a.n, a.k or a.n, a.p
     flags = aat.AAT_DIGITS_PLAIN if a.plain_digits else 0
     half = (p - 1) // 2
-    X = torch.randint(-half, half + 1, (n, k), dtype=torch.int32, device="cuda")
-    C = torch.empty((n, n), dtype=torch.int32, device="cuda")
-    if a.case == "leaf":
+    if a.case in ("aah", "aatc2m"):
+        cflags = {"fp32": aat.AAT_C_FP32, "bf16x3": aat.AAT_C_BF16X3, "bf16": aat.AAT_C_BF16}[a.prec]
+        Z = torch.randn((n, k), dtype=torch.complex64, device="cuda")
+        CZ = torch.empty((n, n), dtype=torch.complex64, device="cuda")
+        f = aat.aah_complex if a.case == "aah" else aat.aat_complex_2m
+        fn = lambda: f(Z, C=CZ, flags=cflags)  # noqa: E731
+    else:
+        X = torch.randint(-half, half + 1, (n, k), dtype=torch.int32, device="cuda")
+        C = torch.empty((n, n), dtype=torch.int32, device="cuda")
+    if a.case in ("aah", "aatc2m"):
+        pass
+    elif a.case == "leaf":
         Y = torch.randint(-half, half + 1, (n, k), dtype=torch.int32, device="cuda")
         fn = lambda: testing.leaf(X, Y, p, C=C, leafkind=flags)  # noqa: E731
     elif a.case == "syrk":
@@ -59,7 +70,7 @@ def main(argv=None):
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
     print(json.dumps({"case": a.case, "n": n, "k": k, "p": p, "levels": a.levels,
-                      "plain_digits": a.plain_digits,
+                      "plain_digits": a.plain_digits, "prec": a.prec,
                       "ms": times, "status": aat.aat_device_status()}))
 
 

@@ -636,6 +636,7 @@ DigitSpec digits_for_prime(uint32_t p) { return make_digits(p); }
 int check_prime_arg(uint32_t p) { return validate(p); }
 int check_gb300() { return check_device(); }
 int report_error(int code, const char *msg) { return fail(code, msg); }
+int workspace_get(size_t bytes, void **out) { return ensure_workspace(bytes, out); }
 
 }  // namespace aat
 
@@ -778,6 +779,7 @@ int aat_device_status(int reset) {
 void aat_shutdown(void) {
   cudaDeviceSynchronize();
   leaf_tc_release();
+  leaf_f32_release();
   std::lock_guard<std::mutex> lock(g_state_mu);
   for (auto &kv : g_states) {
     int cur = 0;

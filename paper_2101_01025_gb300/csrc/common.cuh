@@ -261,11 +261,14 @@ struct TcLeafArgs {
 };
 cudaError_t launch_leaf_tc(const TcLeafArgs &a, const ModP &m, cudaStream_t st);
 void leaf_tc_release();
+void leaf_f32_release();
 
 // Host helpers shared with the allocation-free entry point (aat_api.cu).
 DigitSpec digits_for_prime(uint32_t p);
 int check_prime_arg(uint32_t p);
 int check_gb300();
 int report_error(int code, const char *msg);
+// The library's device workspace, grown to at least `bytes`.
+int workspace_get(size_t bytes, void **out);
 
 }  // namespace aat

@@ -40,10 +40,13 @@
 #include <vector>
 
 #include "common.cuh"
+#include "tc_ptx.cuh"
 
 namespace aat {
 
 namespace {
+
+using namespace tc;
 
 constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
 constexpr int A_BYTES = BM * BK * 2;
@@ -55,7 +58,6 @@ constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t ACC_COLS = 256;
 constexpr int MAX_GROUPS = 160;
 constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + 256;
-constexpr unsigned long long kTimeoutNs = 4000000000ull;  // 4 s
 
 // Instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator (bit 4),
 // A and B BF16 (bits 7, 10), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
@@ -82,195 +84,6 @@ struct Params {
   ModP m;
   int32_t *status;
 };
-
-// ------------------------------------------------------------ PTX wrappers
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ unsigned long long gtimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Bounded wait for the phase of parity `parity` of barrier `bar`.  Returns
-// false when the limit expires (and raises the CTA abort flag and the device
-// status) or when another role of the CTA has aborted.
-__device__ __forceinline__ bool wait_bounded(uint32_t bar, uint32_t parity, volatile int *abort_flag,
-                                          int32_t *status) {
-  if (mbar_try(bar, parity)) return true;
-  const unsigned long long t0 = gtimer();
-  for (uint32_t it = 1;; ++it) {
-    if (mbar_try(bar, parity)) return true;
-    if ((it & 63u) == 0) {
-      if (*abort_flag) return false;
-      if (gtimer() - t0 > kTimeoutNs) {
-        *abort_flag = 1;
-        atomicExch(status, (int32_t)AAT_ETIMEOUT);
-        return false;
-      }
-    }
-  }
-}
-
-// Wait with a short limit and no abort check (teardown after an abort).
-__device__ __forceinline__ void wait_quiet(uint32_t bar, uint32_t parity) {
-  const unsigned long long t0 = gtimer();
-  while (!mbar_try(bar, parity)) {
-    if (gtimer() - t0 > 100000000ull) return;  // 100 ms
-  }
-}
-
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *tm, uint32_t bar,
-                                            int c0, int c1, int c2) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
-      : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-__device__ __forceinline__ void tc_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                   bar)
-               : "memory");
-}
-
-__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-      "l"(a), "l"(b), "r"(IDESC), "r"(acc)
-      : "memory");
-}
-
-// Shared-memory matrix descriptor of a K-major tile written by TMA with
-// 128-byte swizzling: rows of 128 bytes, 8-row atoms 1024 bytes apart (SBO),
-// descriptor version 1 (bit 46), layout SWIZZLE_128B (2 at bit 61).  The
-// start address moves by 32 bytes per K=16 step inside the atom.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1u << 16;
-  d |= (uint64_t)(1024u >> 4) << 32;
-  d |= (uint64_t)1u << 46;
-  d |= (uint64_t)2u << 61;
-  return d;
-}
-
-// Drain 32 consecutive FP32 columns of this thread's TMEM lane into the
-// int32 accumulators acc[B .. B+31]: load, wait, convert (the values are
-// exact integers) and add inside one statement, so that the temporaries of
-// one load are dead before the next load is issued.
-template <int B>
-__device__ __forceinline__ void tmem_drain32(uint32_t taddr, int32_t (&acc)[128]) {
-  asm volatile(
-      "{\n\t.reg .b32 t0, t1, t2, t3, t4, t5, t6, t7, t8, t9, t10, t11, t12, t13, t14, t15, t16, t17, t18, t19, t20, t21, t22, t23, t24, t25, t26, t27, t28, t29, t30, t31;\n\t"
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {t0, t1, t2, t3, t4, t5, t6, t7, t8, t9, t10, t11, t12, t13, t14, t15, t16, t17, t18, t19, t20, t21, t22, t23, t24, t25, t26, t27, t28, t29, t30, t31}, [%32];\n\t"
-      "tcgen05.wait::ld.sync.aligned;\n\t"
-      "cvt.rni.s32.f32 t0, t0;\n\t"
-      "add.s32 %0, %0, t0;\n\t"
-      "cvt.rni.s32.f32 t1, t1;\n\t"
-      "add.s32 %1, %1, t1;\n\t"
-      "cvt.rni.s32.f32 t2, t2;\n\t"
-      "add.s32 %2, %2, t2;\n\t"
-      "cvt.rni.s32.f32 t3, t3;\n\t"
-      "add.s32 %3, %3, t3;\n\t"
-      "cvt.rni.s32.f32 t4, t4;\n\t"
-      "add.s32 %4, %4, t4;\n\t"
-      "cvt.rni.s32.f32 t5, t5;\n\t"
-      "add.s32 %5, %5, t5;\n\t"
-      "cvt.rni.s32.f32 t6, t6;\n\t"
-      "add.s32 %6, %6, t6;\n\t"
-      "cvt.rni.s32.f32 t7, t7;\n\t"
-      "add.s32 %7, %7, t7;\n\t"
-      "cvt.rni.s32.f32 t8, t8;\n\t"
-      "add.s32 %8, %8, t8;\n\t"
-      "cvt.rni.s32.f32 t9, t9;\n\t"
-      "add.s32 %9, %9, t9;\n\t"
-      "cvt.rni.s32.f32 t10, t10;\n\t"
-      "add.s32 %10, %10, t10;\n\t"
-      "cvt.rni.s32.f32 t11, t11;\n\t"
-      "add.s32 %11, %11, t11;\n\t"
-      "cvt.rni.s32.f32 t12, t12;\n\t"
-      "add.s32 %12, %12, t12;\n\t"
-      "cvt.rni.s32.f32 t13, t13;\n\t"
-      "add.s32 %13, %13, t13;\n\t"
-      "cvt.rni.s32.f32 t14, t14;\n\t"
-      "add.s32 %14, %14, t14;\n\t"
-      "cvt.rni.s32.f32 t15, t15;\n\t"
-      "add.s32 %15, %15, t15;\n\t"
-      "cvt.rni.s32.f32 t16, t16;\n\t"
-      "add.s32 %16, %16, t16;\n\t"
-      "cvt.rni.s32.f32 t17, t17;\n\t"
-      "add.s32 %17, %17, t17;\n\t"
-      "cvt.rni.s32.f32 t18, t18;\n\t"
-      "add.s32 %18, %18, t18;\n\t"
-      "cvt.rni.s32.f32 t19, t19;\n\t"
-      "add.s32 %19, %19, t19;\n\t"
-      "cvt.rni.s32.f32 t20, t20;\n\t"
-      "add.s32 %20, %20, t20;\n\t"
-      "cvt.rni.s32.f32 t21, t21;\n\t"
-      "add.s32 %21, %21, t21;\n\t"
-      "cvt.rni.s32.f32 t22, t22;\n\t"
-      "add.s32 %22, %22, t22;\n\t"
-      "cvt.rni.s32.f32 t23, t23;\n\t"
-      "add.s32 %23, %23, t23;\n\t"
-      "cvt.rni.s32.f32 t24, t24;\n\t"
-      "add.s32 %24, %24, t24;\n\t"
-      "cvt.rni.s32.f32 t25, t25;\n\t"
-      "add.s32 %25, %25, t25;\n\t"
-      "cvt.rni.s32.f32 t26, t26;\n\t"
-      "add.s32 %26, %26, t26;\n\t"
-      "cvt.rni.s32.f32 t27, t27;\n\t"
-      "add.s32 %27, %27, t27;\n\t"
-      "cvt.rni.s32.f32 t28, t28;\n\t"
-      "add.s32 %28, %28, t28;\n\t"
-      "cvt.rni.s32.f32 t29, t29;\n\t"
-      "add.s32 %29, %29, t29;\n\t"
-      "cvt.rni.s32.f32 t30, t30;\n\t"
-      "add.s32 %30, %30, t30;\n\t"
-      "cvt.rni.s32.f32 t31, t31;\n\t"
-      "add.s32 %31, %31, t31;\n\t"
-      "}"
-      : "+r"(acc[B + 0]), "+r"(acc[B + 1]), "+r"(acc[B + 2]), "+r"(acc[B + 3]), "+r"(acc[B + 4]), "+r"(acc[B + 5]), "+r"(acc[B + 6]), "+r"(acc[B + 7]), "+r"(acc[B + 8]), "+r"(acc[B + 9]), "+r"(acc[B + 10]), "+r"(acc[B + 11]), "+r"(acc[B + 12]), "+r"(acc[B + 13]), "+r"(acc[B + 14]), "+r"(acc[B + 15]), "+r"(acc[B + 16]), "+r"(acc[B + 17]), "+r"(acc[B + 18]), "+r"(acc[B + 19]), "+r"(acc[B + 20]), "+r"(acc[B + 21]), "+r"(acc[B + 22]), "+r"(acc[B + 23]), "+r"(acc[B + 24]), "+r"(acc[B + 25]), "+r"(acc[B + 26]), "+r"(acc[B + 27]), "+r"(acc[B + 28]), "+r"(acc[B + 29]), "+r"(acc[B + 30]), "+r"(acc[B + 31])
-      : "r"(taddr)
-      : "memory");
-}
 
 // ------------------------------------------------------------------ kernel
 
@@ -385,7 +198,7 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_tc_kernel(const __grid_consta
               const uint32_t sb = sa + A_BYTES;
 #pragma unroll
               for (int s = 0; s < BK / 16; ++s) {
-                tc_mma(dt, sw128_desc(sa + 32u * s), sw128_desc(sb + 32u * s),
+                tc_mma(dt, sw128_desc(sa + 32u * s), sw128_desc(sb + 32u * s), IDESC,
                        (k > kb || s > 0) ? 1u : 0u);
               }
               tc_commit(EMPTY(stage));

@@ -1,0 +1,99 @@
+"""Parity of the complex products with the FP64 oracle (GPU).
+
+Error metric (per result): relative Frobenius error of the lower triangle,
+||Low(C) - Low(C_ref)||_F / ||Low(C_ref)||_F, against the oracle's fp64
+sums.  Bounds: 1e-5 for AAT_C_FP32 (3 BF16 pieces, 6 piece products),
+1e-4 for AAT_C_BF16X3 (2 pieces: dropped terms of relative size 2^-16),
+3e-3 for AAT_C_BF16.  Small-integer inputs are exact in every mode.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2101_01025_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-5, 1 << 16: 1e-4, 2 << 16: 3e-3}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2101_01025_gb300 import build
+    build.build()
+    import paper_2101_01025_gb300 as aat
+    aat.aat_device_status(reset=True)
+    yield aat
+    assert aat.aat_device_status() == 0
+
+
+def rel_low_err(C, ref):
+    d = np.tril(C.astype(np.complex128) - ref)
+    return np.linalg.norm(d) / max(np.linalg.norm(np.tril(ref)), 1e-300)
+
+
+def run(lib, A, herm, flags):
+    Ad = torch.from_numpy(np.ascontiguousarray(A.astype(np.complex64))).cuda()
+    fn = lib.aah_complex if herm else lib.aat_complex_2m
+    C = fn(Ad, flags=flags)
+    torch.cuda.synchronize()
+    return C.cpu().numpy()
+
+
+@pytest.mark.parametrize("herm", [True, False])
+@pytest.mark.parametrize("flags", [0, 1 << 16, 2 << 16])
+@pytest.mark.parametrize("n,k", [(1, 1), (17, 33), (300, 200), (513, 640), (128, 64)])
+def test_complex_matches_oracle(lib, herm, flags, n, k):
+    A = synth.complex_normal(n * 7 + k, (n, k))
+    C = run(lib, A, herm, flags)
+    ref = oracle.complex_low(A.astype(np.complex128), conj=herm)
+    err = rel_low_err(C, ref)
+    assert err <= TOL[flags], err
+    if herm:
+        d = np.diag(C)
+        assert np.all(d.imag == 0) and np.all(d.real >= 0)
+        # the diagonal is summed in FP64: close to the oracle's sums
+        assert np.allclose(d.real, np.diag(ref).real, rtol=1e-6, atol=0)
+
+
+@pytest.mark.parametrize("herm", [True, False])
+@pytest.mark.parametrize("flags", [0, 1 << 16])
+def test_complex_ill_scaled_rows(lib, herm, flags):
+    A = synth.complex_normal(99, (400, 300), ill_scaled=True)
+    C = run(lib, A, herm, flags)
+    ref = oracle.complex_low(A.astype(np.complex128), conj=herm)
+    assert rel_low_err(C, ref) <= TOL[flags]
+
+
+@pytest.mark.parametrize("herm", [True, False])
+@pytest.mark.parametrize("flags", [0, 1 << 16, 2 << 16])
+def test_complex_small_integers_exact(lib, herm, flags):
+    """Integers |x| <= 8 are exact in BF16 and every partial sum here is an
+    integer below 2^24, so every mode is exact."""
+    rng = np.random.default_rng(4)
+    n, k = 260, 300
+    A = rng.integers(-8, 9, (n, k)) + 1j * rng.integers(-8, 9, (n, k))
+    C = run(lib, A, herm, flags)
+    ref = oracle.complex_low(A.astype(np.complex128), conj=herm)
+    assert np.array_equal(np.tril(C.astype(np.complex128)), np.tril(ref))
+
+
+def test_complex_full_size_sampled(lib):
+    """8192 x 8192 complex A (Re, Im i.i.d. N(0, 1)): sampled entries at
+    every 32-row boundary and random positions against the oracle."""
+    n = k = 8192
+    A = synth.complex_normal(synth.SEED_BASE + 3, (n, k))
+    for herm in (True, False):
+        C = run(lib, A, herm, 0)
+        rng = np.random.default_rng(5)
+        i = rng.integers(0, n, 3000)
+        j = rng.integers(0, n, 3000)
+        ij = np.stack([np.maximum(i, j), np.minimum(i, j)], 1)
+        ij = np.concatenate([ij, np.array([[r, r] for r in range(0, n, 97)])])
+        ref = oracle.complex_entries(A.astype(np.complex128), ij, conj=herm)
+        got = C[ij[:, 0], ij[:, 1]].astype(np.complex128)
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert err <= 1e-5, err

@@ -23,7 +23,7 @@ def _declared_symbols():
     names = set()
     for h in ("aat.h", "aat_testing.h"):
         src = open(os.path.join(ROOT, "include", h)).read()
-        names.update(re.findall(r"AAT_API\s+[\w\s\*]+?\b(aatx?_\w+)\s*\(", src))
+        names.update(re.findall(r"AAT_API\s+[\w\s\*]+?\b(aa[a-z]*_\w+)\s*\(", src))
     return names
 
 
