@@ -13,9 +13,10 @@
 // into P BF16 pieces x = x0 + x1 + x2 (x1 = bf16(x - x0), ...), and the
 // product keeps the piece products of weight >= 2^-16: P = 3 gives x0y0,
 // x0y1, x1y0, x0y2, x1y1, x2y0 (close to FP32), P = 2 gives x0y0, x0y1, x1y0,
-// P = 1 is plain BF16.  All piece products of a tile accumulate into one
-// FP32 accumulator in TMEM (sign per product from the instruction's negate
-// bit), drained once per tile.  The Hermitian diagonal sum_l |a_il|^2 is
+// P = 1 is plain BF16.  The piece products of a tile accumulate in FP32 in
+// TMEM (sign per product from the instruction's negate bit), drained every
+// 2 K blocks into FP32 registers (round to nearest) while the next chunk
+// accumulates in the other TMEM buffer.  The Hermitian diagonal sum_l |a_il|^2 is
 // computed in FP64 (real and >= 0).
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -65,6 +66,7 @@ struct FParams {
   FGroup g[MAX_FGROUPS];
   int ng;
   int kblocks;
+  int kchunk;  // K blocks per FP32 TMEM accumulation before it is drained
   float *out;
   int64_t ldo, M, N;
   const int2 *tiles;
@@ -155,22 +157,25 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_f32_kernel(const __grid_const
       }
     }
   } else if (warp == 1) {
-    if (lane == 0) {  // MMA issuer
+    if (lane == 0) {  // MMA issuer: chunks of kchunk K blocks over (group, K block)
       int stage = 0;
-      uint32_t ph = 0, tcount = 0;
+      uint32_t ph = 0, chunk = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
-        const uint32_t buf = tcount & 1u, use = tcount >> 1;
-        if (!wait_bounded(AEMPTY(buf), (use & 1u) ^ 1u, abort_flag, P.status)) {
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        const uint32_t dt = tmem + buf * ACC_COLS;
-        bool first = true;
+        int inchunk = 0;
+        uint32_t dt = 0;
         for (int gi = 0; gi < P.ng && ok; ++gi) {
           const uint32_t idesc = IDESC_F | (P.g[gi].neg ? NEG_A : 0u);
           for (int kb = 0; kb < P.kblocks; ++kb) {
+            if (inchunk == 0) {
+              const uint32_t buf = chunk & 1u, use = chunk >> 1;
+              if (!wait_bounded(AEMPTY(buf), (use & 1u) ^ 1u, abort_flag, P.status)) {
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+              dt = tmem + buf * ACC_COLS;
+            }
             if (!wait_bounded(FULL(stage), ph, abort_flag, P.status)) {
               ok = false;
               break;
@@ -181,67 +186,80 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_f32_kernel(const __grid_const
 #pragma unroll
             for (int s = 0; s < BK / 16; ++s) {
               tc_mma(dt, sw128_desc(sa + 32u * s), sw128_desc(sb + 32u * s), idesc,
-                     (first && s == 0) ? 0u : 1u);
+                     (inchunk == 0 && s == 0) ? 0u : 1u);
             }
-            first = false;
             tc_commit(EMPTY(stage));
             if (++stage == STAGES) {
               stage = 0;
               ph ^= 1u;
             }
+            const bool last = (gi == P.ng - 1) && (kb == P.kblocks - 1);
+            if (++inchunk == P.kchunk || last) {
+              tc_commit(AFULL(chunk & 1u));
+              ++chunk;
+              inchunk = 0;
+            }
           }
         }
-        if (!ok) break;
-        tc_commit(AFULL(buf));
-        ++tcount;
       }
       if (!ok) {
         tc_commit(DONE);
         wait_quiet(DONE, 0);
       }
     }
-  } else {  // epilogue: FP32 accumulator -> global, lower triangle if asked
+  } else {  // epilogue: chunks -> FP32 registers -> global (lower if asked)
     const int e = warp - 2;
     const int quarter = warp & 3;
     const int chalf = e >> 2;
     const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
-    uint32_t tcount = 0;
-    for (int t = blockIdx.x; t < P.ntiles; t += gridDim.x) {
+    const int total_kb = P.ng * P.kblocks;
+    const int nchunks = (total_kb + P.kchunk - 1) / P.kchunk;
+    uint32_t chunk = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
       const int2 tile = P.tiles[t];
-      const uint32_t buf = tcount & 1u, use = tcount >> 1;
-      if (!wait_bounded(AFULL(buf), use & 1u, abort_flag, P.status)) break;
-      tc_fence_after();
+      float acc[128];
+#pragma unroll
+      for (int i = 0; i < 128; ++i) acc[i] = 0.0f;
+      for (int c = 0; c < nchunks; ++c) {
+        const uint32_t buf = chunk & 1u, use = chunk >> 1;
+        if (!wait_bounded(AFULL(buf), use & 1u, abort_flag, P.status)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t ta = tmem + lane_base + buf * ACC_COLS + (uint32_t)(chalf * 128);
+        tmem_accum32f<0>(ta, acc);
+        tmem_accum32f<32>(ta + 32u, acc);
+        tmem_accum32f<64>(ta + 64u, acc);
+        tmem_accum32f<96>(ta + 96u, acc);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(AEMPTY(buf));
+        ++chunk;
+      }
+      if (!ok) break;
       const int64_t row = (int64_t)tile.x * BM + quarter * 32 + lane;
       const int64_t col0 = (int64_t)tile.y * BN + chalf * 128;
       int64_t lim = P.N - col0;
       if (P.lower) lim = min(lim, row - col0 + 1);
-      float *orow = P.out + row * P.ldo + col0;
-      const bool vec = ((reinterpret_cast<uintptr_t>(orow) & 15) == 0);
-      const uint32_t ta = tmem + lane_base + buf * ACC_COLS + (uint32_t)(chalf * 128);
+      if (row < P.M && lim > 0) {
+        float *orow = P.out + row * P.ldo + col0;
+        const bool vec = ((reinterpret_cast<uintptr_t>(orow) & 15) == 0);
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        uint32_t r[32];
-        tmem_ld32(ta + 32u * c, r);
-        if (row < P.M && lim > 0) {
+        for (int q = 0; q < 32; ++q) {
+          const int cc = 4 * q;
+          if (vec && cc + 4 <= lim) {
+            *reinterpret_cast<float4 *>(orow + cc) =
+                make_float4(acc[cc], acc[cc + 1], acc[cc + 2], acc[cc + 3]);
+          } else {
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const int cc = 32 * c + 4 * q;
-            if (vec && cc + 4 <= lim) {
-              *reinterpret_cast<float4 *>(orow + cc) =
-                  make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
-                              __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
-            } else {
-#pragma unroll
-              for (int j = 0; j < 4; ++j)
-                if (cc + j < lim) orow[cc + j] = __uint_as_float(r[4 * q + j]);
-            }
+            for (int j = 0; j < 4; ++j)
+              if (cc + j < lim) orow[cc + j] = acc[cc + j];
           }
+          asm volatile("" ::: "memory");
         }
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(AEMPTY(buf));
-      ++tcount;
     }
   }
 
@@ -476,6 +494,10 @@ static cudaError_t launch_leaf_f32(const std::vector<FTerm> &terms, int np, int6
   }
   P->ng = ng;
   P->kblocks = (int)((K + BK - 1) / BK);
+  // FP32 accumulation in the tensor core drifts over long K loops (its
+  // rounding is not to nearest); draining every 2 K blocks into FP32
+  // registers keeps the error of a K = 8192 product near FP32 rounding.
+  P->kchunk = 2;
   P->out = out;
   P->ldo = ldo;
   P->M = M;

@@ -217,5 +217,53 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
       : "memory");
 }
 
+
+// Add 32 consecutive FP32 TMEM columns of this thread's lane into the FP32
+// registers acc[B .. B+31] (round to nearest), load, wait and add in one
+// statement.
+template <int B>
+__device__ __forceinline__ void tmem_accum32f(uint32_t taddr, float (&acc)[128]) {
+  asm volatile(
+      "{\n\t.reg .f32 t0, t1, t2, t3, t4, t5, t6, t7, t8, t9, t10, t11, t12, t13, t14, t15, t16, t17, t18, t19, t20, t21, t22, t23, t24, t25, t26, t27, t28, t29, t30, t31;\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {t0, t1, t2, t3, t4, t5, t6, t7, t8, t9, t10, t11, t12, t13, t14, t15, t16, t17, t18, t19, t20, t21, t22, t23, t24, t25, t26, t27, t28, t29, t30, t31}, [%32];\n\t"
+      "tcgen05.wait::ld.sync.aligned;\n\t"
+      "add.f32 %0, %0, t0;\n\t"
+      "add.f32 %1, %1, t1;\n\t"
+      "add.f32 %2, %2, t2;\n\t"
+      "add.f32 %3, %3, t3;\n\t"
+      "add.f32 %4, %4, t4;\n\t"
+      "add.f32 %5, %5, t5;\n\t"
+      "add.f32 %6, %6, t6;\n\t"
+      "add.f32 %7, %7, t7;\n\t"
+      "add.f32 %8, %8, t8;\n\t"
+      "add.f32 %9, %9, t9;\n\t"
+      "add.f32 %10, %10, t10;\n\t"
+      "add.f32 %11, %11, t11;\n\t"
+      "add.f32 %12, %12, t12;\n\t"
+      "add.f32 %13, %13, t13;\n\t"
+      "add.f32 %14, %14, t14;\n\t"
+      "add.f32 %15, %15, t15;\n\t"
+      "add.f32 %16, %16, t16;\n\t"
+      "add.f32 %17, %17, t17;\n\t"
+      "add.f32 %18, %18, t18;\n\t"
+      "add.f32 %19, %19, t19;\n\t"
+      "add.f32 %20, %20, t20;\n\t"
+      "add.f32 %21, %21, t21;\n\t"
+      "add.f32 %22, %22, t22;\n\t"
+      "add.f32 %23, %23, t23;\n\t"
+      "add.f32 %24, %24, t24;\n\t"
+      "add.f32 %25, %25, t25;\n\t"
+      "add.f32 %26, %26, t26;\n\t"
+      "add.f32 %27, %27, t27;\n\t"
+      "add.f32 %28, %28, t28;\n\t"
+      "add.f32 %29, %29, t29;\n\t"
+      "add.f32 %30, %30, t30;\n\t"
+      "add.f32 %31, %31, t31;\n\t"
+      "}"
+      : "+f"(acc[B + 0]), "+f"(acc[B + 1]), "+f"(acc[B + 2]), "+f"(acc[B + 3]), "+f"(acc[B + 4]), "+f"(acc[B + 5]), "+f"(acc[B + 6]), "+f"(acc[B + 7]), "+f"(acc[B + 8]), "+f"(acc[B + 9]), "+f"(acc[B + 10]), "+f"(acc[B + 11]), "+f"(acc[B + 12]), "+f"(acc[B + 13]), "+f"(acc[B + 14]), "+f"(acc[B + 15]), "+f"(acc[B + 16]), "+f"(acc[B + 17]), "+f"(acc[B + 18]), "+f"(acc[B + 19]), "+f"(acc[B + 20]), "+f"(acc[B + 21]), "+f"(acc[B + 22]), "+f"(acc[B + 23]), "+f"(acc[B + 24]), "+f"(acc[B + 25]), "+f"(acc[B + 26]), "+f"(acc[B + 27]), "+f"(acc[B + 28]), "+f"(acc[B + 29]), "+f"(acc[B + 30]), "+f"(acc[B + 31])
+      : "r"(taddr)
+      : "memory");
+}
+
 }  // namespace tc
 }  // namespace aat

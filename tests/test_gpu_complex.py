@@ -4,7 +4,10 @@ Error metric (per result): relative Frobenius error of the lower triangle,
 ||Low(C) - Low(C_ref)||_F / ||Low(C_ref)||_F, against the oracle's fp64
 sums.  Bounds: 1e-5 for AAT_C_FP32 (3 BF16 pieces, 6 piece products),
 1e-4 for AAT_C_BF16X3 (2 pieces: dropped terms of relative size 2^-16),
-3e-3 for AAT_C_BF16.  Small-integer inputs are exact in every mode.
+3e-3 for AAT_C_BF16 with A A^H.  A A^T by 2M with plain BF16 gets 5e-3:
+there Re C = G + H - H^T adds the BF16 rounding errors (2^-9 per input) of
+three products of the same size as the result, and no FP64 diagonal takes
+a large share of the norm.  Small-integer inputs are exact in every mode.
 """
 import numpy as np
 import pytest
@@ -16,6 +19,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL = {0: 1e-5, 1 << 16: 1e-4, 2 << 16: 3e-3}
+TOL_T_BF16 = 5e-3   # A A^T by 2M, plain BF16
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -51,7 +55,8 @@ def test_complex_matches_oracle(lib, herm, flags, n, k):
     C = run(lib, A, herm, flags)
     ref = oracle.complex_low(A.astype(np.complex128), conj=herm)
     err = rel_low_err(C, ref)
-    assert err <= TOL[flags], err
+    tol = TOL_T_BF16 if (not herm and flags == 2 << 16) else TOL[flags]
+    assert err <= tol, err
     if herm:
         d = np.diag(C)
         assert np.all(d.imag == 0) and np.all(d.real >= 0)
