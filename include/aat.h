@@ -157,6 +157,15 @@ AAT_API int aah_complex_ex(const void *A, int64_t n, int64_t k, int64_t lda, voi
 AAT_API int aat_complex_2m(const void *A, int64_t n, int64_t k, int64_t lda, void *C,
                            int64_t ldc, uint32_t flags, void *stream);
 
+/* Low(A A^T) over C by Algorithm 1 (Sec. 3) with phi the transposition and
+ * Y = i I (Sec. 4.1: multiplying by Y swaps real and imaginary parts with one
+ * sign flip).  The general products P3, P4 use 3 real products (3M), the
+ * recursion ends in Algorithm 2 (eps = -1).  flags: AAT_C_* precision, and
+ * AAT_LEVELS(l) (no level bits: one level once n/2 >= 4096, k/2 >= 2048). */
+AAT_API int aat_complex(const void *A, int64_t n, int64_t k, void *C, void *stream);
+AAT_API int aat_complex_ex(const void *A, int64_t n, int64_t k, int64_t lda, void *C,
+                           int64_t ldc, uint32_t flags, void *stream);
+
 /* Bytes of device workspace aat_modp_ex would use for (n, k, p, flags). */
 AAT_API size_t aat_workspace_size(int64_t n, int64_t k, uint32_t p, uint32_t flags);
 

@@ -18,7 +18,7 @@ from ._native import (AAT_C_BF16, AAT_C_BF16X3, AAT_C_FP32, AAT_DIGITS_PLAIN,  #
 
 __all__ = [
     "aat_modp", "aat_gemm_modp", "aat_modp_host", "aat_workspace_size", "aat_device_status",
-    "aat_shutdown", "aat_version", "aah_complex", "aat_complex_2m", "AAT_LEVELS", "AAT_LEAF_TC", "AAT_LEAF_SIMT",
+    "aat_shutdown", "aat_version", "aah_complex", "aat_complex_2m", "aat_complex", "AAT_LEVELS", "AAT_LEAF_TC", "AAT_LEAF_SIMT",
     "AAT_ZERO_UPPER", "AAT_IN_BALANCED", "AatError",
 ]
 
@@ -133,6 +133,21 @@ def aat_complex_2m(A, C=None, flags: int = 0, stream=None):
         C = torch.empty((n, n), dtype=torch.complex64, device=A.device)
     ldc = _check_cmat(C, "C")
     check(lib().aat_complex_2m(A.data_ptr(), n, k, lda, C.data_ptr(), ldc, flags,
+                               _stream(stream)))
+    return C
+
+
+def aat_complex(A, C=None, flags: int = 0, levels: int | None = None, stream=None):
+    """Low(A A^T) for a complex64 CUDA matrix A by Algorithm 1 with Y = i I."""
+    import torch
+    lda = _check_cmat(A, "A")
+    n, k = A.shape
+    if C is None:
+        C = torch.empty((n, n), dtype=torch.complex64, device=A.device)
+    ldc = _check_cmat(C, "C")
+    if levels is not None:
+        flags |= AAT_LEVELS(levels)
+    check(lib().aat_complex_ex(A.data_ptr(), n, k, lda, C.data_ptr(), ldc, flags,
                                _stream(stream)))
     return C
 

@@ -42,6 +42,7 @@ EXPORTS = [
     "aat_workspace_size",
     "aat_last_error", "aat_device_status", "aat_shutdown", "aat_version",
     "aat_profile_begin", "aat_profile_end", "aah_complex", "aah_complex_ex", "aat_complex_2m",
+    "aat_complex", "aat_complex_ex",
     "aatx_is_prime", "aatx_sqrt_mod", "aatx_sos", "aatx_y_params", "aatx_digit_spec",
     "aatx_plan_stats", "aatx_leaf_groups", "aatx_sblocks", "aatx_split", "aatx_leaf", "aatx_postadd",
 ]
@@ -119,6 +120,8 @@ def lib():
         L.aah_complex.argtypes = [vp, i64, i64, vp, vp]
         L.aah_complex_ex.argtypes = [vp, i64, i64, i64, vp, i64, u32, vp]
         L.aat_complex_2m.argtypes = [vp, i64, i64, i64, vp, i64, u32, vp]
+        L.aat_complex.argtypes = [vp, i64, i64, vp, vp]
+        L.aat_complex_ex.argtypes = [vp, i64, i64, i64, vp, i64, u32, vp]
         L.aatx_is_prime.argtypes = [u64]
         L.aatx_sqrt_mod.argtypes = [i64, u64]
         L.aatx_sqrt_mod.restype = i64

@@ -26,6 +26,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <string>
 #include <tuple>
 #include <vector>
 
@@ -549,81 +550,359 @@ static int pieces_for(uint32_t flags) {
   }
 }
 
-// Algorithm 2 for A (n x k complex64): Low(A A^H) (herm) or Low(A A^T).
-static int two_m(const float2 *A, int64_t n, int64_t k, int64_t lda, float2 *C, int64_t ldc,
-                 uint32_t flags, int herm, cudaStream_t st) {
-  const int np = pieces_for(flags);
-  const int64_t ks = (k + 7) / 8 * 8;
-  // workspace: X planes [Ar pieces | Ar+Ai pieces], Y planes [Ai pieces |
-  // Ar+Ai or Ar-Ai pieces], H and G in FP32
-  const size_t set = (size_t)np * n * ks * 2;
-  auto r256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
-  const size_t xbytes = r256(2 * set), ybytes = r256(2 * set), hbytes = r256((size_t)n * n * 4);
-  void *ws = nullptr;
-  int e = workspace_get(xbytes + ybytes + 2 * hbytes, &ws);
-  if (e) return e;
-  char *base = (char *)ws;
-  auto planes_at = [&](char *p, int sets) {
-    Planes P;
-    std::memset(&P, 0, sizeof(P));
-    P.ptr = (__nv_bfloat16 *)p;
-    P.rows = n;
-    P.cols = k;
-    P.kstride = ks;
-    P.L = np * sets;
-    P.nbase = P.L;
-    return P;
-  };
-  Planes X = planes_at(base, 2), Y = planes_at(base + xbytes, 2);
-  Planes Xr = X, Xs = X, Yi = Y, Ysd = Y;
-  Xr.L = Xs.L = Yi.L = Ysd.L = np;
-  Xs.ptr = X.ptr + (size_t)np * n * ks;
-  Ysd.ptr = Y.ptr + (size_t)np * n * ks;
-  float *H = (float *)(base + xbytes + ybytes);
-  float *G = (float *)(base + xbytes + ybytes + hbytes);
-  CSplitOut ox, oy;
-  std::memset(&ox, 0, sizeof(ox));
-  std::memset(&oy, 0, sizeof(oy));
-  ox.re = Xr;
-  ox.s = Xs;
-  oy.im = Yi;
-  if (herm)
-    oy.s = Ysd;
-  else
-    oy.d = Ysd;
-  cudaError_t ce;
-  {
-    ProfScope prof(AAT_K_SPLIT, st, (double)n * k * (8.0 + 2.0 * 4 * np));
-    csplit_kernel<<<grid_c(n * k, 256), 256, 0, st>>>(A, lda, n, k, np, ox);
+// ---------------------------------------------- complex elementwise kernels
+
+namespace {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// multiplication by Y = i I: (x + iy) i = -y + ix
+__device__ __forceinline__ float2 ci(float2 a) { return make_float2(-a.y, a.x); }
+
+// The four additions of Algorithm 1 over C with Y = i I (Sec. 4.1):
+// S1 = (A21 - A11) i, S2 = A22 - A21 i, S3 = S1 - A22, S4 = S3 + A12.
+__global__ void csblocks_kernel(const float2 *__restrict__ A, int64_t lda, int64_t h, int64_t kap,
+                                float2 *S1, float2 *S2, float2 *S3, float2 *S4, int64_t ld1,
+                                int64_t ld2, int64_t ld3, int64_t ld4) {
+  const int64_t total = h * kap;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / kap, j = t - (t / kap) * kap;
+    const float2 a11 = A[i * lda + j], a12 = A[i * lda + kap + j];
+    const float2 a21 = A[(h + i) * lda + j], a22 = A[(h + i) * lda + kap + j];
+    const float2 s1 = ci(csub(a21, a11));
+    const float2 s2 = csub(a22, ci(a21));
+    const float2 s3 = csub(s1, a22);
+    const float2 s4 = cadd(s3, a12);
+    if (S1) S1[i * ld1 + j] = s1;
+    if (S2) S2[i * ld2 + j] = s2;
+    if (S3) S3[i * ld3 + j] = s3;
+    if (S4) S4[i * ld4 + j] = s4;
   }
-  if ((ce = cudaGetLastError()) != cudaSuccess) return report_error(AAT_ECUDA, cudaGetErrorString(ce));
-  {
-    ProfScope prof(AAT_K_SPLIT, st, (double)n * k * (8.0 + 2.0 * 4 * np));
-    csplit_kernel<<<grid_c(n * k, 256), 256, 0, st>>>(A, lda, n, k, np, oy);
+}
+
+// Post-additions of Algorithm 1 over C (phi = transposition, so Up(U1) is
+// the plain transpose of Low(U1)); same tile-pair scheme as over F_p.
+__global__ void cpostadd_kernel(const float2 *__restrict__ C11, const float2 *__restrict__ C12,
+                                float2 *C21, float2 *C22, int64_t ldc, int64_t h) {
+  __shared__ float2 p4t_ij[T][T + 1];
+  __shared__ float2 p4t_ji[T][T + 1];
+  __shared__ float2 u1_ij[T][T + 1];
+  const int64_t ntiles = (h + T - 1) / T;
+  int64_t pid = blockIdx.x;
+  int64_t I = (int64_t)((sqrt(8.0 * (double)pid + 1.0) - 1.0) * 0.5);
+  while (I * (I + 1) / 2 > pid) --I;
+  while ((I + 1) * (I + 2) / 2 <= pid) ++I;
+  const int64_t J = pid - I * (I + 1) / 2;
+  if (I >= ntiles) return;
+  const int tx = threadIdx.x % T, ty = threadIdx.x / T;
+  const int64_t r0 = I * T, c0 = J * T;
+  for (int yy = ty; yy < T; yy += 8) {
+    int64_t r = r0 + yy, c = c0 + tx;
+    if (r < h && c < h) {
+      p4t_ij[yy][tx] = C22[r * ldc + c];
+      const int64_t lr = r >= c ? r : c, lc = r >= c ? c : r;
+      u1_ij[yy][tx] = cadd(C11[lr * ldc + lc], C12[lr * ldc + lc]);
+    }
+    int64_t r2 = c0 + yy, c2 = r0 + tx;
+    if (r2 < h && c2 < h) p4t_ji[yy][tx] = C22[r2 * ldc + c2];
   }
-  if ((ce = cudaGetLastError()) != cudaSuccess) return report_error(AAT_ECUDA, cudaGetErrorString(ce));
-  // H = Ar Ai^T (all entries), G = (Ar + Ai)(Ar +- Ai)^T (lower tiles)
-  if ((ce = launch_leaf_f32({FTerm{&Xr, &Yi, false}}, np, n, n, k, H, n, 0, st)) != cudaSuccess)
-    return report_error(AAT_ECUDA, cudaGetErrorString(ce));
-  if ((ce = launch_leaf_f32({FTerm{&Xs, &Ysd, false}}, np, n, n, k, G, n, 1, st)) != cudaSuccess)
-    return report_error(AAT_ECUDA, cudaGetErrorString(ce));
-  {
-    const int64_t nt = (n + T - 1) / T;
-    ProfScope prof(AAT_K_POSTADD, st, (double)n * n * (4.0 * 1.5 + 8.0 * 0.5));
-    combine2m_kernel<<<(unsigned)(nt * (nt + 1) / 2), T * 8, 0, st>>>(G, H, n, n, C, ldc, herm);
+  __syncthreads();
+  for (int yy = ty; yy < T; yy += 8) {
+    int64_t r = r0 + yy, c = c0 + tx;
+    if (r < h && c < h) {
+      const float2 u2 = cadd(u1_ij[yy][tx], p4t_ji[tx][yy]);
+      C21[r * ldc + c] = cadd(u2, C21[r * ldc + c]);
+      if (r >= c) C22[r * ldc + c] = cadd(u2, p4t_ij[yy][tx]);
+    }
   }
-  if ((ce = cudaGetLastError()) != cudaSuccess) return report_error(AAT_ECUDA, cudaGetErrorString(ce));
-  if (herm) {
-    ProfScope prof(AAT_K_COPY, st, (double)n * k * 8.0);
-    herm_diag_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(A, lda, n, k, C, ldc);
-    if ((ce = cudaGetLastError()) != cudaSuccess)
-      return report_error(AAT_ECUDA, cudaGetErrorString(ce));
+  if (I == J) return;
+  for (int yy = ty; yy < T; yy += 8) {
+    int64_t r = c0 + yy, c = r0 + tx;
+    if (r < h && c < h) {
+      const float2 u2 = cadd(u1_ij[tx][yy], p4t_ij[tx][yy]);
+      C21[r * ldc + c] = cadd(u2, C21[r * ldc + c]);
+    }
   }
-  return AAT_OK;
+}
+
+__global__ void cadd_low_kernel(float2 *C11, const float2 *__restrict__ C12, int64_t ldc,
+                                int64_t h) {
+  const int64_t total = h * h;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / h, c = t - (t / h) * h;
+    if (c <= r) C11[r * ldc + c] = cadd(C11[r * ldc + c], C12[r * ldc + c]);
+  }
+}
+
+// 3M: X Y^T = (T1 - T2) + i (T3 - T1 - T2) with T1 = Xr Yr^T, T2 = Xi Yi^T,
+// T3 = (Xr + Xi)(Yr + Yi)^T.
+__global__ void combine3m_kernel(const float *__restrict__ T1, const float *__restrict__ T2,
+                                 const float *__restrict__ T3, int64_t ldt, int64_t M, int64_t N,
+                                 float2 *C, int64_t ldc) {
+  const int64_t total = M * N;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / N, c = t - (t / N) * N;
+    const float t1 = T1[r * ldt + c], t2 = T2[r * ldt + c], t3 = T3[r * ldt + c];
+    C[r * ldc + c] = make_float2(t1 - t2, t3 - t1 - t2);
+  }
+}
+
+__global__ void cpad_kernel(const float2 *__restrict__ src, int64_t lds, int64_t rows, int64_t cols,
+                            float2 *dst, int64_t ldd, int64_t rows_d, int64_t cols_d) {
+  const int64_t total = rows_d * cols_d;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / cols_d, c = t - (t / cols_d) * cols_d;
+    dst[r * ldd + c] = (r < rows && c < cols) ? src[r * lds + c] : make_float2(0.f, 0.f);
+  }
+}
+
+__global__ void ccopy_low_kernel(const float2 *__restrict__ src, int64_t lds, float2 *dst,
+                                 int64_t ldd, int64_t n) {
+  const int64_t total = n * n;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / n, c = t - (t / n) * n;
+    if (c <= r) dst[r * ldd + c] = src[r * lds + c];
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ host plans
+
+// Bump allocator over the workspace; the dry run only measures.
+struct CArena {
+  char *base = nullptr;
+  size_t used = 0, peak = 0;
+  bool dry = true;
+  void *get(size_t bytes) {
+    const size_t off = (used + 255) & ~(size_t)255;
+    used = off + bytes;
+    peak = std::max(peak, used);
+    return dry ? nullptr : (void *)(base + off);
+  }
+};
+
+struct CCtx {
+  int np;
+  cudaStream_t st;
+  CArena ar;
+  int err = AAT_OK;
+};
+
+static bool cchk(CCtx &c, cudaError_t e, const char *where) {
+  if (e != cudaSuccess && c.err == AAT_OK) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    c.err = report_error(AAT_ECUDA, m.c_str());
+  }
+  return c.err == AAT_OK;
+}
+
+static Planes cplanes(CCtx &c, int64_t rows, int64_t cols, int sets) {
+  Planes P;
+  std::memset(&P, 0, sizeof(P));
+  P.rows = rows;
+  P.cols = cols;
+  P.kstride = (cols + 7) / 8 * 8;
+  P.L = c.np * sets;
+  P.nbase = P.L;
+  P.ptr = (__nv_bfloat16 *)c.ar.get((size_t)P.L * rows * P.kstride * 2);
+  return P;
+}
+
+static Planes subset(const Planes &P, int set, int np) {
+  Planes Q = P;
+  Q.L = Q.nbase = np;
+  if (Q.ptr) Q.ptr = P.ptr + (size_t)set * np * P.rows * P.kstride;
+  return Q;
+}
+
+static void csplit(CCtx &c, const float2 *A, int64_t lda, int64_t rows, int64_t cols,
+                   const CSplitOut &o) {
+  if (c.ar.dry) return;
+  int nsets = (o.re.ptr != nullptr) + (o.im.ptr != nullptr) + (o.s.ptr != nullptr) +
+              (o.d.ptr != nullptr);
+  ProfScope prof(AAT_K_SPLIT, c.st, (double)rows * cols * (8.0 + 2.0 * c.np * nsets));
+  csplit_kernel<<<grid_c(rows * cols, 256), 256, 0, c.st>>>(A, lda, rows, cols, c.np, o);
+  cchk(c, cudaGetLastError(), "complex split");
+}
+
+// Algorithm 2: Low(X phi(X)) into C (herm: phi = conjugate transposition).
+static void c_two_m(CCtx &c, const float2 *A, int64_t lda, int64_t n, int64_t k, float2 *C,
+                    int64_t ldc, int herm) {
+  if (c.err) return;
+  const size_t mark = c.ar.used;
+  Planes X = cplanes(c, n, k, 2), Y = cplanes(c, n, k, 2);
+  Planes Xr = subset(X, 0, c.np), Xs = subset(X, 1, c.np);
+  Planes Yi = subset(Y, 0, c.np), Ysd = subset(Y, 1, c.np);
+  float *H = (float *)c.ar.get((size_t)n * n * 4);
+  float *G = (float *)c.ar.get((size_t)n * n * 4);
+  if (!c.ar.dry) {
+    CSplitOut ox, oy;
+    std::memset(&ox, 0, sizeof(ox));
+    std::memset(&oy, 0, sizeof(oy));
+    ox.re = Xr;
+    ox.s = Xs;
+    oy.im = Yi;
+    if (herm)
+      oy.s = Ysd;
+    else
+      oy.d = Ysd;
+    csplit(c, A, lda, n, k, ox);
+    csplit(c, A, lda, n, k, oy);
+    // H = Ar Ai^T (all entries), G = (Ar + Ai)(Ar +- Ai)^T (lower tiles)
+    if (c.err == AAT_OK)
+      cchk(c, launch_leaf_f32({FTerm{&Xr, &Yi, false}}, c.np, n, n, k, H, n, 0, c.st), "2M H");
+    if (c.err == AAT_OK)
+      cchk(c, launch_leaf_f32({FTerm{&Xs, &Ysd, false}}, c.np, n, n, k, G, n, 1, c.st), "2M G");
+    if (c.err == AAT_OK) {
+      const int64_t nt = (n + T - 1) / T;
+      ProfScope prof(AAT_K_POSTADD, c.st, (double)n * n * (4.0 * 1.5 + 8.0 * 0.5));
+      combine2m_kernel<<<(unsigned)(nt * (nt + 1) / 2), T * 8, 0, c.st>>>(G, H, n, n, C, ldc,
+                                                                           herm);
+      cchk(c, cudaGetLastError(), "2M combine");
+    }
+    if (herm && c.err == AAT_OK) {
+      ProfScope prof(AAT_K_COPY, c.st, (double)n * k * 8.0);
+      herm_diag_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, c.st>>>(A, lda, n, k, C, ldc);
+      cchk(c, cudaGetLastError(), "Hermitian diagonal");
+    }
+  }
+  c.ar.used = mark;
+}
+
+// 3M: C = X Y^T (complex, M x N, inner K), all entries.
+static void c_gen_leaf(CCtx &c, const float2 *X, int64_t ldx, const float2 *Y, int64_t ldy,
+                       int64_t M, int64_t N, int64_t K, float2 *C, int64_t ldc) {
+  if (c.err) return;
+  const size_t mark = c.ar.used;
+  Planes PX = cplanes(c, M, K, 3), PY = cplanes(c, N, K, 3);
+  Planes Xr = subset(PX, 0, c.np), Xi = subset(PX, 1, c.np), Xs = subset(PX, 2, c.np);
+  Planes Yr = subset(PY, 0, c.np), Yi = subset(PY, 1, c.np), Ys = subset(PY, 2, c.np);
+  float *T1 = (float *)c.ar.get((size_t)M * N * 4);
+  float *T2 = (float *)c.ar.get((size_t)M * N * 4);
+  float *T3 = (float *)c.ar.get((size_t)M * N * 4);
+  if (!c.ar.dry) {
+    CSplitOut ox, oy;
+    std::memset(&ox, 0, sizeof(ox));
+    std::memset(&oy, 0, sizeof(oy));
+    ox.re = Xr;
+    ox.im = Xi;
+    ox.s = Xs;
+    oy.re = Yr;
+    oy.im = Yi;
+    oy.s = Ys;
+    csplit(c, X, ldx, M, K, ox);
+    csplit(c, Y, ldy, N, K, oy);
+    if (c.err == AAT_OK)
+      cchk(c, launch_leaf_f32({FTerm{&Xr, &Yr, false}}, c.np, M, N, K, T1, N, 0, c.st), "3M T1");
+    if (c.err == AAT_OK)
+      cchk(c, launch_leaf_f32({FTerm{&Xi, &Yi, false}}, c.np, M, N, K, T2, N, 0, c.st), "3M T2");
+    if (c.err == AAT_OK)
+      cchk(c, launch_leaf_f32({FTerm{&Xs, &Ys, false}}, c.np, M, N, K, T3, N, 0, c.st), "3M T3");
+    if (c.err == AAT_OK) {
+      ProfScope prof(AAT_K_POSTADD, c.st, (double)M * N * (12.0 + 8.0));
+      combine3m_kernel<<<grid_c(M * N, 256), 256, 0, c.st>>>(T1, T2, T3, N, M, N, C, ldc);
+      cchk(c, cudaGetLastError(), "3M combine");
+    }
+  }
+  c.ar.used = mark;
+}
+
+// Algorithm 1 over C with phi = transposition and Y = i I (Sec. 4.1):
+// Low(A A^T) -> Low(C).  n divisible by 2^levels, k by 2^levels.
+static void c_rec(CCtx &c, const float2 *A, int64_t lda, int64_t n, int64_t k, float2 *C,
+                  int64_t ldc, int levels) {
+  if (c.err) return;
+  if (levels == 0 || n < 2 || k < 2) {
+    c_two_m(c, A, lda, n, k, C, ldc, 0);
+    return;
+  }
+  const int64_t h = n / 2, kap = k / 2;
+  float2 *C11 = C, *C12 = C + h, *C21 = C + h * ldc, *C22 = C + h * ldc + h;
+  const float2 *A11 = A, *A12 = A + kap, *A22 = A + h * lda + kap;
+  const size_t mark = c.ar.used;
+  float2 *S1 = (float2 *)c.ar.get((size_t)h * kap * 8);
+  float2 *S2 = (float2 *)c.ar.get((size_t)h * kap * 8);
+  float2 *S4 = (float2 *)c.ar.get((size_t)h * kap * 8);
+  float2 *S3;
+  int64_t ld3;
+  if (kap <= h) {  // Table 3: S3 in C21
+    S3 = C21;
+    ld3 = ldc;
+  } else {
+    S3 = (float2 *)c.ar.get((size_t)h * kap * 8);
+    ld3 = kap;
+  }
+  if (!c.ar.dry) {
+    ProfScope prof(AAT_K_SBLOCKS, c.st, (double)h * kap * 8.0 * 8.0);
+    csblocks_kernel<<<grid_c(h * kap, 256), 256, 0, c.st>>>(A, lda, h, kap, S1, S2, S3, S4, kap,
+                                                            kap, ld3, kap);
+    cchk(c, cudaGetLastError(), "complex S blocks");
+  }
+  c_gen_leaf(c, S2, kap, S1, kap, h, h, kap, C22, ldc);  // P4^T = S2 S1^T
+  c_rec(c, S3, ld3, h, kap, C12, ldc, levels - 1);       // P5 = Low(S3 S3^T)
+  c_gen_leaf(c, A22, lda, S4, kap, h, h, kap, C21, ldc);  // P3 = A22 S4^T
+  c_rec(c, A11, lda, h, kap, C11, ldc, levels - 1);      // P1 = Low(A11 A11^T)
+  if (!c.ar.dry && c.err == AAT_OK) {                    // U4 -> C21, Low(U5) -> C22
+    const int64_t nt = (h + T - 1) / T;
+    ProfScope prof(AAT_K_POSTADD, c.st, (double)h * h * 8.0 * 4.5);
+    cpostadd_kernel<<<(unsigned)(nt * (nt + 1) / 2), T * 8, 0, c.st>>>(C11, C12, C21, C22, ldc,
+                                                                       h);
+    cchk(c, cudaGetLastError(), "complex post-additions");
+  }
+  c_rec(c, A12, lda, h, kap, C12, ldc, levels - 1);  // P2 = Low(A12 A12^T)
+  if (!c.ar.dry && c.err == AAT_OK) {                // Low(U3) = Low(P1 + P2)
+    ProfScope prof(AAT_K_ADD_LOW, c.st, (double)h * h * 8.0 * 1.5);
+    cadd_low_kernel<<<grid_c(h * h, 256), 256, 0, c.st>>>(C11, C12, ldc, h);
+    cchk(c, cudaGetLastError(), "complex U3");
+  }
+  c.ar.used = mark;
+}
+
+// Runs (or measures, with dry) a complex product: method 0 = 2M A A^H,
+// 1 = 2M A A^T, 2 = Algorithm 1 A A^T with `levels`.
+static size_t c_plan(CCtx &c, int method, const float2 *A, int64_t n, int64_t k, int64_t lda,
+                     float2 *C, int64_t ldc, int levels, bool dry, char *ws) {
+  c.ar = CArena();
+  c.ar.dry = dry;
+  c.ar.base = ws;
+  if (method < 2) {
+    c_two_m(c, A, lda, n, k, C, ldc, method == 0 ? 1 : 0);
+    return c.ar.peak;
+  }
+  const int64_t m = (int64_t)1 << levels;
+  const int64_t np_ = (n + m - 1) / m * m, kp = (k + m - 1) / m * m;
+  const bool pad = (np_ != n || kp != k) && levels > 0;
+  const float2 *Aw = A;
+  float2 *Cw = C;
+  int64_t ldaw = lda, ldcw = ldc;
+  if (pad) {
+    float2 *Ap = (float2 *)c.ar.get((size_t)np_ * kp * 8);
+    float2 *Cp = (float2 *)c.ar.get((size_t)np_ * np_ * 8);
+    if (!dry) {
+      cpad_kernel<<<grid_c(np_ * kp, 256), 256, 0, c.st>>>(A, lda, n, k, Ap, kp, np_, kp);
+      cchk(c, cudaGetLastError(), "complex pad");
+    }
+    Aw = Ap;
+    Cw = Cp;
+    ldaw = kp;
+    ldcw = np_;
+  }
+  c_rec(c, Aw, ldaw, pad ? np_ : n, pad ? kp : k, Cw, ldcw, levels);
+  if (pad && !dry && c.err == AAT_OK) {
+    ccopy_low_kernel<<<grid_c(n * n, 256), 256, 0, c.st>>>(Cw, ldcw, C, ldc, n);
+    cchk(c, cudaGetLastError(), "complex unpad");
+  }
+  return c.ar.peak;
 }
 
 static int complex_entry(const void *A, int64_t n, int64_t k, int64_t lda, void *C, int64_t ldc,
-                         uint32_t flags, void *stream, int herm) {
+                         uint32_t flags, void *stream, int method) {
   if (n < 0 || k < 0) return report_error(AAT_EINVAL, "negative size");
   if (lda < std::max<int64_t>(k, 1) || ldc < std::max<int64_t>(n, 1))
     return report_error(AAT_EINVAL, "stride smaller than the row length");
@@ -639,10 +918,28 @@ static int complex_entry(const void *A, int64_t n, int64_t k, int64_t lda, void 
     cudaError_t ce = cudaMemset2DAsync(C, (size_t)ldc * 8, 0, (size_t)n * 8, (size_t)n, st);
     return ce == cudaSuccess ? AAT_OK : report_error(AAT_ECUDA, cudaGetErrorString(ce));
   }
-  const char *a = (const char *)A, *c = (const char *)C;
-  if (a < c + ((n - 1) * ldc + n) * 8 && c < a + ((n - 1) * lda + k) * 8)
+  const char *a = (const char *)A, *cc = (const char *)C;
+  if (a < cc + ((n - 1) * ldc + n) * 8 && cc < a + ((n - 1) * lda + k) * 8)
     return report_error(AAT_EINVAL, "C overlaps A");
-  return two_m((const float2 *)A, n, k, lda, (float2 *)C, ldc, flags, herm, st);
+  int levels = 0;
+  if (method == 2) {
+    const uint32_t lv = (flags & AAT_LEVELS_MASK) >> 8;
+    if (lv) {
+      levels = (int)lv - 1;
+    } else {  // one level pays off once the leaves stay large
+      while (levels < 4 && (n >> (levels + 1)) >= 4096 && (k >> (levels + 1)) >= 2048) ++levels;
+    }
+  }
+  CCtx c;
+  c.np = pieces_for(flags);
+  c.st = st;
+  const size_t need = c_plan(c, method, (const float2 *)A, n, k, lda, (float2 *)C, ldc, levels,
+                             true, nullptr);
+  void *ws = nullptr;
+  if ((e = workspace_get(need, &ws))) return e;
+  c.err = AAT_OK;
+  c_plan(c, method, (const float2 *)A, n, k, lda, (float2 *)C, ldc, levels, false, (char *)ws);
+  return c.err;
 }
 
 }  // namespace aat
@@ -653,7 +950,7 @@ extern "C" {
 
 AAT_API int aah_complex_ex(const void *A, int64_t n, int64_t k, int64_t lda, void *C, int64_t ldc,
                            uint32_t flags, void *stream) {
-  return complex_entry(A, n, k, lda, C, ldc, flags, stream, 1);
+  return complex_entry(A, n, k, lda, C, ldc, flags, stream, 0);
 }
 
 AAT_API int aah_complex(const void *A, int64_t n, int64_t k, void *C, void *stream) {
@@ -662,7 +959,16 @@ AAT_API int aah_complex(const void *A, int64_t n, int64_t k, void *C, void *stre
 
 AAT_API int aat_complex_2m(const void *A, int64_t n, int64_t k, int64_t lda, void *C, int64_t ldc,
                            uint32_t flags, void *stream) {
-  return complex_entry(A, n, k, lda, C, ldc, flags, stream, 0);
+  return complex_entry(A, n, k, lda, C, ldc, flags, stream, 1);
+}
+
+AAT_API int aat_complex_ex(const void *A, int64_t n, int64_t k, int64_t lda, void *C, int64_t ldc,
+                           uint32_t flags, void *stream) {
+  return complex_entry(A, n, k, lda, C, ldc, flags, stream, 2);
+}
+
+AAT_API int aat_complex(const void *A, int64_t n, int64_t k, void *C, void *stream) {
+  return aat_complex_ex(A, n, k, k, C, n, 0u, stream);
 }
 
 }  // extern "C"

@@ -102,3 +102,35 @@ def test_complex_full_size_sampled(lib):
         got = C[ij[:, 0], ij[:, 1]].astype(np.complex128)
         err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
         assert err <= 1e-5, err
+
+
+# ----------------------------------------- A A^T over C by Algorithm 1 (Y = iI)
+
+TOL_ALG1 = {0: 1e-5, 1 << 16: 1e-4, 2 << 16: 1e-2}
+
+
+@pytest.mark.parametrize("flags", [0, 1 << 16, 2 << 16])
+@pytest.mark.parametrize("n,k", [(300, 200), (513, 640), (256, 512), (128, 64), (3, 5)])
+@pytest.mark.parametrize("levels", [0, 1, 2])
+def test_aat_complex_alg1_matches_oracle(lib, flags, n, k, levels):
+    A = synth.complex_normal(n * 3 + k + levels, (n, k))
+    Ad = torch.from_numpy(np.ascontiguousarray(A)).cuda()
+    C = lib.aat_complex(Ad, flags=flags, levels=levels)
+    torch.cuda.synchronize()
+    ref = oracle.complex_low(A.astype(np.complex128), conj=False)
+    err = rel_low_err(C.cpu().numpy(), ref)
+    assert err <= TOL_ALG1[flags], err
+
+
+def test_aat_complex_alg1_small_integers_exact(lib):
+    """Y = i I only swaps parts and flips a sign, so with small integers every
+    intermediate value of the recursion is an exact integer."""
+    rng = np.random.default_rng(12)
+    n, k = 256, 192
+    A = rng.integers(-4, 5, (n, k)) + 1j * rng.integers(-4, 5, (n, k))
+    Ad = torch.from_numpy(A.astype(np.complex64)).cuda()
+    for levels in (1, 2):
+        C = lib.aat_complex(Ad, levels=levels)
+        torch.cuda.synchronize()
+        ref = oracle.complex_low(A.astype(np.complex128), conj=False)
+        assert np.array_equal(np.tril(C.cpu().numpy().astype(np.complex128)), np.tril(ref))
