@@ -106,7 +106,11 @@ def test_complex_full_size_sampled(lib):
 
 # ----------------------------------------- A A^T over C by Algorithm 1 (Y = iI)
 
-TOL_ALG1 = {0: 1e-5, 1 << 16: 1e-4, 2 << 16: 1e-2}
+# Plain BF16 through the recursion: each level forms sums and differences
+# of blocks (S1..S4, U1..U5) whose BF16 input rounding (2^-9) is relative to
+# the larger intermediate blocks, so the error grows with the depth.
+TOL_ALG1 = {0: 1e-5, 1 << 16: 1e-4}
+TOL_ALG1_BF16 = {0: 5e-3, 1: 1e-2, 2: 4e-2}
 
 
 @pytest.mark.parametrize("flags", [0, 1 << 16, 2 << 16])
@@ -119,7 +123,8 @@ def test_aat_complex_alg1_matches_oracle(lib, flags, n, k, levels):
     torch.cuda.synchronize()
     ref = oracle.complex_low(A.astype(np.complex128), conj=False)
     err = rel_low_err(C.cpu().numpy(), ref)
-    assert err <= TOL_ALG1[flags], err
+    tol = TOL_ALG1_BF16[levels] if flags == 2 << 16 else TOL_ALG1[flags]
+    assert err <= tol, err
 
 
 def test_aat_complex_alg1_small_integers_exact(lib):
