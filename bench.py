@@ -46,11 +46,11 @@ N = K = 16384
 P = 2**31 - 1
 SEED_OFFSET = 2
 # DRAM traffic of the dominant kernel from one ncu capture of an 8192^3 leaf
-# product (dram__bytes_read.sum + dram__bytes_write.sum = 28.78 GB for
-# 17.59 TFLOP of algorithmic work, profiles/leaf_tc_kernel_gemm8192_p2p31m1.md),
+# product (dram__bytes_read.sum + dram__bytes_write.sum = 16.05 GB for
+# 10.995 TFLOP of algorithmic work, profiles/leaf_tc_kernel_gemm8192_p2p31m1.md),
 # scaled to the average launch of the step by its algorithmic work.  Set to
 # None whenever the kernel changes until it is captured again.
-LEAF_TC_BYTES_PER_FLOP = None
+LEAF_TC_BYTES_PER_FLOP = 16.05e9 / 10.995e12
 
 
 def parse():
