@@ -166,6 +166,33 @@ AAT_API int aat_complex(const void *A, int64_t n, int64_t k, void *C, void *stre
 AAT_API int aat_complex_ex(const void *A, int64_t n, int64_t k, int64_t lda, void *C,
                            int64_t ldc, uint32_t flags, void *stream);
 
+/* ------------------------------------------------------------- batches
+ * Many independent products in one plan.  A plan is built once for a fixed
+ * list of problems (their pointers, sizes and flags) and executed any number
+ * of times; each execution recomputes every C from the current contents of
+ * every A.  F_p problems whose recursion depth is 0 share ONE persistent
+ * tensor-core leaf launch over all their tiles; the others run their own
+ * launches.  Execution is one CUDA graph launch on the given stream (no
+ * allocation, no host synchronisation).  The plan owns its workspace.
+ */
+#define AAT_KIND_MODP 0   /* Low(A A^T) mod p: int32 A and C, field p */
+#define AAT_KIND_AAH 1    /* Low(A A^H): complex64 A and C, 2M        */
+#define AAT_KIND_AAT_C 2  /* Low(A A^T) over C: complex64, Algorithm 1 */
+typedef struct {
+  int kind;
+  const void *A;
+  void *C;
+  int64_t n, k, lda, ldc;
+  uint32_t p;      /* AAT_KIND_MODP only */
+  uint32_t flags;  /* as for the single-problem entry points */
+} aat_problem_t;
+typedef struct aat_plan aat_plan_t;
+AAT_API int aat_plan_create(const aat_problem_t *probs, int count, aat_plan_t **plan);
+AAT_API int aat_plan_execute(aat_plan_t *plan, void *stream);
+/* problems in the shared leaf launch, problems run on their own, workspace */
+AAT_API int aat_plan_info(const aat_plan_t *plan, int *batched, int *solo, size_t *workspace);
+AAT_API void aat_plan_destroy(aat_plan_t *plan);
+
 /* Bytes of device workspace aat_modp_ex would use for (n, k, p, flags). */
 AAT_API size_t aat_workspace_size(int64_t n, int64_t k, uint32_t p, uint32_t flags);
 

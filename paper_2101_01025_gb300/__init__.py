@@ -18,7 +18,7 @@ from ._native import (AAT_C_BF16, AAT_C_BF16X3, AAT_C_FP32, AAT_DIGITS_PLAIN,  #
 
 __all__ = [
     "aat_modp", "aat_gemm_modp", "aat_modp_host", "aat_workspace_size", "aat_device_status",
-    "aat_shutdown", "aat_version", "aah_complex", "aat_complex_2m", "aat_complex", "AAT_LEVELS", "AAT_LEAF_TC", "AAT_LEAF_SIMT",
+    "aat_shutdown", "aat_version", "aah_complex", "aat_complex_2m", "aat_complex", "Plan", "AAT_LEVELS", "AAT_LEAF_TC", "AAT_LEAF_SIMT",
     "AAT_ZERO_UPPER", "AAT_IN_BALANCED", "AatError",
 ]
 
@@ -150,6 +150,52 @@ def aat_complex(A, C=None, flags: int = 0, levels: int | None = None, stream=Non
     check(lib().aat_complex_ex(A.data_ptr(), n, k, lda, C.data_ptr(), ldc, flags,
                                _stream(stream)))
     return C
+
+
+class Plan:
+    """A batch of independent products executed as one CUDA graph launch.
+
+    problems: list of (kind, A, C, p, flags) with kind "modp" (int32 CUDA
+    tensors, field p), "aah" or "aat_c" (complex64 CUDA tensors).  The
+    tensors must stay alive and keep their storage while the plan lives."""
+
+    KINDS = {"modp": _native.AAT_KIND_MODP, "aah": _native.AAT_KIND_AAH,
+             "aat_c": _native.AAT_KIND_AAT_C}
+
+    def __init__(self, problems):
+        import ctypes
+        arr = (_native.Problem * len(problems))()
+        self._keep = []
+        for i, (kind, A, C, p, flags) in enumerate(problems):
+            chk = _check_mat if kind == "modp" else _check_cmat
+            lda = chk(A, "A")
+            ldc = chk(C, "C")
+            arr[i] = _native.Problem(self.KINDS[kind], A.data_ptr(), C.data_ptr(), A.shape[0],
+                                     A.shape[1], lda, ldc, p or 0, flags)
+            self._keep += [A, C]
+        h = ctypes.c_void_p()
+        check(lib().aat_plan_create(arr, len(problems), ctypes.byref(h)))
+        self._h = h
+
+    def execute(self, stream=None):
+        check(lib().aat_plan_execute(self._h, _stream(stream)))
+
+    def info(self):
+        import ctypes
+        b, s, w = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
+        check(lib().aat_plan_info(self._h, ctypes.byref(b), ctypes.byref(s), ctypes.byref(w)))
+        return {"batched": b.value, "solo": s.value, "workspace": w.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().aat_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def aat_workspace_size(n: int, k: int, p: int, flags: int = 0) -> int:

@@ -42,10 +42,30 @@ EXPORTS = [
     "aat_workspace_size",
     "aat_last_error", "aat_device_status", "aat_shutdown", "aat_version",
     "aat_profile_begin", "aat_profile_end", "aah_complex", "aah_complex_ex", "aat_complex_2m",
-    "aat_complex", "aat_complex_ex",
+    "aat_complex", "aat_complex_ex", "aat_plan_create", "aat_plan_execute", "aat_plan_info",
+    "aat_plan_destroy",
     "aatx_is_prime", "aatx_sqrt_mod", "aatx_sos", "aatx_y_params", "aatx_digit_spec",
     "aatx_plan_stats", "aatx_leaf_groups", "aatx_sblocks", "aatx_split", "aatx_leaf", "aatx_postadd",
 ]
+
+
+AAT_KIND_MODP = 0
+AAT_KIND_AAH = 1
+AAT_KIND_AAT_C = 2
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int),
+        ("A", ctypes.c_void_p),
+        ("C", ctypes.c_void_p),
+        ("n", ctypes.c_int64),
+        ("k", ctypes.c_int64),
+        ("lda", ctypes.c_int64),
+        ("ldc", ctypes.c_int64),
+        ("p", ctypes.c_uint32),
+        ("flags", ctypes.c_uint32),
+    ]
 
 
 class AatError(RuntimeError):
@@ -121,6 +141,12 @@ def lib():
         L.aah_complex_ex.argtypes = [vp, i64, i64, i64, vp, i64, u32, vp]
         L.aat_complex_2m.argtypes = [vp, i64, i64, i64, vp, i64, u32, vp]
         L.aat_complex.argtypes = [vp, i64, i64, vp, vp]
+        L.aat_plan_create.argtypes = [ctypes.POINTER(Problem), i32, ctypes.POINTER(vp)]
+        L.aat_plan_execute.argtypes = [vp, vp]
+        L.aat_plan_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                    ctypes.POINTER(ctypes.c_size_t)]
+        L.aat_plan_destroy.argtypes = [vp]
+        L.aat_plan_destroy.restype = None
         L.aat_complex_ex.argtypes = [vp, i64, i64, i64, vp, i64, u32, vp]
         L.aatx_is_prime.argtypes = [u64]
         L.aatx_sqrt_mod.argtypes = [i64, u64]

@@ -18,7 +18,7 @@ import json
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["leaf", "syrk", "aat", "full", "aah", "aatc2m"])
+    ap.add_argument("case", choices=["leaf", "syrk", "aat", "full", "aah", "aatc2m", "batch"])
     ap.add_argument("n", type=int)
     ap.add_argument("--k", type=int, default=None)
     ap.add_argument("--p", type=int, default=2**31 - 1)
@@ -40,6 +40,8 @@ def main(argv=None):
     n, k, p = a.n, a.k or a.n, a.p
     flags = aat.AAT_DIGITS_PLAIN if a.plain_digits else 0
     half = (p - 1) // 2
+    if a.case == "batch":
+        return batch_case(a)
     if a.case in ("aah", "aatc2m"):
         cflags = {"fp32": aat.AAT_C_FP32, "bf16x3": aat.AAT_C_BF16X3, "bf16": aat.AAT_C_BF16}[a.prec]
         Z = torch.randn((n, k), dtype=torch.complex64, device="cuda")
@@ -72,6 +74,49 @@ def main(argv=None):
     print(json.dumps({"case": a.case, "n": n, "k": k, "p": p, "levels": a.levels,
                       "plain_digits": a.plain_digits, "prec": a.prec,
                       "ms": times, "status": aat.aat_device_status()}))
+
+
+def batch_case(a):
+    """n problems over F_65521 (n, k log-uniform in [64, 2048] x [64, 4096])
+    plus n // 4 complex A A^H problems of the same spread, one plan; prints
+    sum n^2 k / time for the whole batch and for each kind alone."""
+    import torch
+
+    import paper_2101_01025_gb300 as aat
+    from paper_2101_01025_gb300 import synth
+
+    count = a.n
+    p = 65521
+    ns = synth.log_uniform_ints(synth.SEED_BASE + 4, count, 64, 2048)
+    ks = synth.log_uniform_ints(synth.SEED_BASE + 5, count, 64, 4096)
+    cn = synth.log_uniform_ints(synth.SEED_BASE + 6, count // 4, 64, 2048)
+    ck = synth.log_uniform_ints(synth.SEED_BASE + 7, count // 4, 64, 4096)
+    torch.manual_seed(0x2101)
+    fp = [("modp", torch.randint(0, p, (int(n), int(k)), dtype=torch.int32, device="cuda"),
+           torch.empty((int(n), int(n)), dtype=torch.int32, device="cuda"), p, 0)
+          for n, k in zip(ns, ks)]
+    cx = [("aah", torch.randn((int(n), int(k)), dtype=torch.complex64, device="cuda"),
+           torch.empty((int(n), int(n)), dtype=torch.complex64, device="cuda"), 0, 0)
+          for n, k in zip(cn, ck)]
+    out = {"case": "batch", "problems": count, "complex": count // 4}
+    for name, probs in (("modp", fp), ("aah", cx), ("all", fp + cx)):
+        plan = aat.Plan(probs)
+        work = sum(float(A.shape[0]) ** 2 * A.shape[1] for _, A, _, _, _ in probs)
+        plan.execute()
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(a.reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            plan.execute()
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        out[name] = {"ms": times, "gops": work / (min(times) * 1e-3) / 1e9, "info": plan.info()}
+        plan.close()
+    out["status"] = aat.aat_device_status()
+    print(json.dumps(out))
 
 
 if __name__ == "__main__":

@@ -312,6 +312,11 @@ static cudaEvent_t pool_event() {
 ProfScope::ProfScope(int cls, cudaStream_t st, double work) : idx(-1) {
   std::lock_guard<std::mutex> lock(g_prof_mu);
   if (!g_prof_on) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return;  // no timing events inside a graph capture
+  }
   ProfRec r{cls, st, pool_event(), pool_event(), work};
   cudaEventRecord(r.a, st);
   g_prof.push_back(r);
@@ -629,6 +634,32 @@ static int check_device() {
     return fail(AAT_ECUDA, "this library is built for sm_103a (GB300); device is sm_" +
                                std::to_string(major * 10 + minor));
   return AAT_OK;
+}
+
+// Used by the batched plans (aat_plan.cu).
+int modp_levels(int64_t n, int64_t k, uint32_t flags) {
+  const uint32_t lv = (flags & AAT_LEVELS_MASK) >> 8;
+  return lv ? (int)lv - 1 : auto_levels(n, k);
+}
+
+Planes planes_layout(const DigitSpec &ds, int64_t rows, int64_t cols) {
+  return planes_for(ds, rows, cols);
+}
+
+DigitSpec digits_for_flags(uint32_t p, uint32_t flags) {
+  DigitSpec d = make_digits(p);
+  if (flags & AAT_DIGITS_PLAIN) d.nsum = 0;
+  return d;
+}
+
+int modp_run(const int32_t *A, int64_t n, int64_t k, int64_t lda, uint32_t p, int32_t *C,
+             int64_t ldc, uint32_t flags, cudaStream_t st, char *ws, bool dry, size_t *need) {
+  Ctx c;
+  int e = setup(c, p, flags, st);
+  if (e) return e;
+  const size_t peak = run_plan(c, A, n, k, lda, C, ldc, flags, dry, ws);
+  if (need) *need = peak;
+  return c.err;
 }
 
 // Accessors used by the allocation-free entry point (k_leaf_tc.cu).

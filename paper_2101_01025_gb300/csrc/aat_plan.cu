@@ -1,0 +1,269 @@
+// aat_plan.cu -- batched execution of many independent products of a matrix
+// by its adjoint: one plan built once, executed as one CUDA graph launch.
+//
+// At creation the plan sorts its problems:
+//   * F_p problems whose recursion depth is 0 (the leaves are the whole
+//     product) join one batch: one batched split kernel writes every digit
+//     plane set, and ONE persistent tensor-core leaf launch walks a single
+//     tile list spanning all of them (per-problem tensor maps, group tables
+//     and outputs live in device tables), heaviest tiles first;
+//   * every other problem (recursive F_p products, complex products) runs
+//     its own sequence of launches.
+// The plan owns its workspace (the batch's planes, plus one region reused by
+// the other problems in turn), runs everything once eagerly (so every cache
+// and kernel attribute exists), then captures the same sequence into a CUDA
+// graph.  aat_plan_execute launches that graph on the caller's stream: no
+// allocation, no host synchronisation.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/aat.h"
+#include "common.cuh"
+
+namespace aat {
+
+struct Plan {
+  int dev = 0;
+  cudaStream_t st = nullptr;
+  void *ws = nullptr;
+  size_t ws_size = 0;
+  std::vector<aat_problem_t> probs;
+  std::vector<int> solo;          // problems run on their own
+  std::vector<int> batched;       // F_p problems in the batched leaf launch
+  std::vector<TcLeafArgs> leaf_args;
+  std::vector<ModP> leaf_mods;
+  SplitDesc *split_dev = nullptr;
+  int nsplit = 0;
+  int64_t split_max = 0;
+  double split_bytes = 0.0;
+  LeafBatch leaf;
+  size_t solo_off = 0;            // workspace offset of the shared region
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+static int enqueue(Plan &P, cudaStream_t st) {
+  cudaError_t ce;
+  if (P.nsplit > 0) {
+    if ((ce = launch_split_batch(P.split_dev, P.nsplit, P.split_max, P.split_bytes, st)) !=
+        cudaSuccess)
+      return report_error(AAT_ECUDA, cudaGetErrorString(ce));
+    if ((ce = leaf_tc_batch_launch(P.leaf, st)) != cudaSuccess)
+      return report_error(AAT_ECUDA, cudaGetErrorString(ce));
+  }
+  char *region = (char *)P.ws + P.solo_off;
+  for (int i : P.solo) {
+    const aat_problem_t &q = P.probs[i];
+    int e;
+    if (q.kind == AAT_KIND_MODP)
+      e = modp_run((const int32_t *)q.A, q.n, q.k, q.lda, q.p, (int32_t *)q.C, q.ldc, q.flags, st,
+                   region, false, nullptr);
+    else
+      e = complex_run(q.kind == AAT_KIND_AAH ? 0 : 2, q.A, q.n, q.k, q.lda, q.C, q.ldc, q.flags,
+                      st, region, false, nullptr);
+    if (e) return e;
+  }
+  return AAT_OK;
+}
+
+static void destroy(Plan *P) {
+  if (!P) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(P->dev);
+  if (P->exec) cudaGraphExecDestroy(P->exec);
+  if (P->graph) cudaGraphDestroy(P->graph);
+  leaf_tc_batch_free(&P->leaf);
+  if (P->split_dev) cudaFree(P->split_dev);
+  if (P->ws) cudaFree(P->ws);
+  if (P->st) cudaStreamDestroy(P->st);
+  cudaSetDevice(cur);
+  delete P;
+}
+
+static int create(const aat_problem_t *probs, int count, Plan **out) {
+  if (!out || count < 0 || (count > 0 && !probs)) return report_error(AAT_EINVAL, "bad arguments");
+  int e = check_gb300();
+  if (e) return e;
+  Plan *P = new Plan;
+  cudaGetDevice(&P->dev);
+  P->probs.assign(probs, probs + count);
+  auto r256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  // validate and sort the problems; size the batch's planes
+  size_t batch_bytes = 0, solo_bytes = 0;
+  std::vector<size_t> plane_off(count, 0);
+  for (int i = 0; i < count; ++i) {
+    const aat_problem_t &q = P->probs[i];
+    const bool fp = q.kind == AAT_KIND_MODP;
+    if (q.kind != AAT_KIND_MODP && q.kind != AAT_KIND_AAH && q.kind != AAT_KIND_AAT_C) {
+      destroy(P);
+      return report_error(AAT_EINVAL, "unknown problem kind");
+    }
+    if (q.n <= 0 || q.k <= 0 || !q.A || !q.C || q.lda < q.k || q.ldc < q.n) {
+      destroy(P);
+      return report_error(AAT_EINVAL, ("bad sizes, strides or pointers in problem " +
+                                        std::to_string(i)).c_str());
+    }
+    if (fp) {
+      if ((e = check_prime_arg(q.p))) {
+        destroy(P);
+        return e;
+      }
+      const bool tc = (q.flags & AAT_LEAF_MASK) == AAT_LEAF_TC;
+      const bool extra = (q.flags & AAT_ZERO_UPPER) != 0;
+      if (tc && !extra && modp_levels(q.n, q.k, q.flags) == 0) {
+        const DigitSpec ds = digits_for_flags(q.p, q.flags);
+        const Planes pl = planes_layout(ds, q.n, q.k);
+        plane_off[i] = batch_bytes;
+        batch_bytes += r256((size_t)pl.L * pl.rows * pl.kstride * 2);
+        P->batched.push_back(i);
+        continue;
+      }
+    }
+    size_t need = 0;
+    if (fp)
+      e = modp_run((const int32_t *)q.A, q.n, q.k, q.lda, q.p, (int32_t *)q.C, q.ldc, q.flags,
+                   nullptr, nullptr, true, &need);
+    else
+      e = complex_run(q.kind == AAT_KIND_AAH ? 0 : 2, q.A, q.n, q.k, q.lda, q.C, q.ldc, q.flags,
+                      nullptr, nullptr, true, &need);
+    if (e) {
+      destroy(P);
+      return e;
+    }
+    solo_bytes = std::max(solo_bytes, need);
+    P->solo.push_back(i);
+  }
+  P->solo_off = r256(batch_bytes);
+  P->ws_size = P->solo_off + solo_bytes + 256;
+  cudaError_t ce;
+  if ((ce = cudaMalloc(&P->ws, P->ws_size)) != cudaSuccess) {
+    cudaGetLastError();
+    destroy(P);
+    return report_error(AAT_ENOMEM, "plan workspace");
+  }
+  if ((ce = cudaStreamCreateWithFlags(&P->st, cudaStreamNonBlocking)) != cudaSuccess) {
+    destroy(P);
+    return report_error(AAT_ECUDA, cudaGetErrorString(ce));
+  }
+  // the batch: split descriptors and leaf tables
+  if (!P->batched.empty()) {
+    std::vector<SplitDesc> sd;
+    for (int i : P->batched) {
+      const aat_problem_t &q = P->probs[i];
+      const DigitSpec ds = digits_for_flags(q.p, q.flags);
+      Planes pl = planes_layout(ds, q.n, q.k);
+      pl.ptr = (__nv_bfloat16 *)((char *)P->ws + plane_off[i]);
+      SplitDesc d;
+      d.X = (const int32_t *)q.A;
+      d.ldx = q.lda;
+      d.rows = q.n;
+      d.cols = q.k;
+      d.m = make_modp(q.p);
+      d.b = ds.b;
+      d.P = pl;
+      sd.push_back(d);
+      P->split_max = std::max<int64_t>(P->split_max, q.n * q.k);
+      P->split_bytes += (double)q.n * q.k * (4.0 + 2.0 * pl.L);
+      TcLeafArgs a;
+      std::memset(&a, 0, sizeof(a));
+      a.x = a.y = pl;
+      a.dx = a.dy = ds;
+      a.M = a.N = q.n;
+      a.K = q.k;
+      a.out = (int32_t *)q.C;
+      a.ldo = q.ldc;
+      a.lower = 1;
+      a.accumulate = 0;
+      a.exact_bits = 24;
+      P->leaf_args.push_back(a);
+      P->leaf_mods.push_back(d.m);
+    }
+    P->nsplit = (int)sd.size();
+    if ((ce = cudaMalloc(&P->split_dev, sizeof(SplitDesc) * sd.size())) != cudaSuccess ||
+        (ce = cudaMemcpy(P->split_dev, sd.data(), sizeof(SplitDesc) * sd.size(),
+                         cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (ce = leaf_tc_batch_build(P->leaf_args.data(), P->leaf_mods.data(),
+                                  (int)P->leaf_args.size(), &P->leaf)) != cudaSuccess) {
+      destroy(P);
+      return report_error(AAT_ECUDA, cudaGetErrorString(ce));
+    }
+  }
+  // eager run (creates every cache the captured launches use), then capture
+  if ((e = enqueue(*P, P->st))) {
+    destroy(P);
+    return e;
+  }
+  if ((ce = cudaStreamSynchronize(P->st)) != cudaSuccess) {
+    destroy(P);
+    return report_error(AAT_ECUDA, cudaGetErrorString(ce));
+  }
+  if ((ce = cudaStreamBeginCapture(P->st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+    destroy(P);
+    return report_error(AAT_ECUDA, cudaGetErrorString(ce));
+  }
+  e = enqueue(*P, P->st);
+  cudaGraph_t g = nullptr;
+  ce = cudaStreamEndCapture(P->st, &g);
+  if (e || ce != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    destroy(P);
+    return e ? e : report_error(AAT_ECUDA, cudaGetErrorString(ce));
+  }
+  P->graph = g;
+  if ((ce = cudaGraphInstantiate(&P->exec, g, 0)) != cudaSuccess) {
+    destroy(P);
+    return report_error(AAT_ECUDA, cudaGetErrorString(ce));
+  }
+  *out = P;
+  return AAT_OK;
+}
+
+}  // namespace aat
+
+using namespace aat;
+
+struct aat_plan {
+  Plan *p;
+};
+
+extern "C" {
+
+AAT_API int aat_plan_create(const aat_problem_t *probs, int count, aat_plan_t **plan) {
+  if (!plan) return report_error(AAT_EINVAL, "null plan");
+  *plan = nullptr;
+  Plan *P = nullptr;
+  int e = create(probs, count, &P);
+  if (e) return e;
+  *plan = new aat_plan{P};
+  return AAT_OK;
+}
+
+AAT_API int aat_plan_execute(aat_plan_t *plan, void *stream) {
+  if (!plan || !plan->p || !plan->p->exec) return report_error(AAT_EINVAL, "null plan");
+  cudaError_t ce = cudaGraphLaunch(plan->p->exec, (cudaStream_t)stream);
+  return ce == cudaSuccess ? AAT_OK : report_error(AAT_ECUDA, cudaGetErrorString(ce));
+}
+
+AAT_API int aat_plan_info(const aat_plan_t *plan, int *batched, int *solo, size_t *workspace) {
+  if (!plan || !plan->p) return report_error(AAT_EINVAL, "null plan");
+  if (batched) *batched = (int)plan->p->batched.size();
+  if (solo) *solo = (int)plan->p->solo.size();
+  if (workspace) *workspace = plan->p->ws_size;
+  return AAT_OK;
+}
+
+AAT_API void aat_plan_destroy(aat_plan_t *plan) {
+  if (!plan) return;
+  if (plan->p) {
+    cudaDeviceSynchronize();
+    destroy(plan->p);
+  }
+  delete plan;
+}
+
+}  // extern "C"

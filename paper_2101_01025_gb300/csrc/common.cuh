@@ -261,7 +261,41 @@ struct TcLeafArgs {
 };
 cudaError_t launch_leaf_tc(const TcLeafArgs &a, const ModP &m, cudaStream_t st);
 void leaf_tc_release();
+
+// A batched tensor-core leaf launch: device tables (per-problem tensor maps,
+// group tables, one tile list over every problem) built once, then one
+// persistent launch over all tiles per call.
+struct LeafBatch {
+  void *impl = nullptr;
+};
+cudaError_t leaf_tc_batch_build(const TcLeafArgs *args, const ModP *mods, int count,
+                                LeafBatch *out);
+cudaError_t leaf_tc_batch_launch(const LeafBatch &lb, cudaStream_t st);
+void leaf_tc_batch_free(LeafBatch *lb);
+
+// Batched split: one launch, problem q in blockIdx.y.
+struct SplitDesc {
+  const int32_t *X;
+  int64_t ldx, rows, cols;
+  ModP m;
+  int b;
+  Planes P;
+};
+cudaError_t launch_split_batch(const SplitDesc *descs_dev, int count, int64_t max_elems,
+                               double bytes, cudaStream_t st);
 void leaf_f32_release();
+
+// Host helpers of the batched plans.
+int modp_levels(int64_t n, int64_t k, uint32_t flags);
+Planes planes_layout(const DigitSpec &ds, int64_t rows, int64_t cols);
+DigitSpec digits_for_flags(uint32_t p, uint32_t flags);
+// One Low(A A^T) mod p with an explicit workspace (dry: only *need).
+int modp_run(const int32_t *A, int64_t n, int64_t k, int64_t lda, uint32_t p, int32_t *C,
+             int64_t ldc, uint32_t flags, cudaStream_t st, char *ws, bool dry, size_t *need);
+// One complex product (method 0: A A^H by 2M, 1: A A^T by 2M, 2: A A^T by
+// Algorithm 1) with an explicit workspace (dry: only *need).
+int complex_run(int method, const void *A, int64_t n, int64_t k, int64_t lda, void *C,
+                int64_t ldc, uint32_t flags, cudaStream_t st, char *ws, bool dry, size_t *need);
 
 // Host helpers shared with the allocation-free entry point (aat_api.cu).
 DigitSpec digits_for_prime(uint32_t p);

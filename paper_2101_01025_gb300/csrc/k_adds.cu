@@ -3,6 +3,8 @@
 // These kernels are bound by HBM bandwidth: each reads and writes every
 // element once, with consecutive threads on consecutive columns of a row so
 // that every warp access is one contiguous segment.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace aat {
@@ -146,6 +148,25 @@ __global__ void split_kernel(const int32_t *__restrict__ X, int64_t ldx, int64_t
     int32_t v[V];
     ldv_bal<V>(X + r * ldx + c, m, v);
     store_digits_t<NB, V>(P, r, c, v, b);
+  }
+}
+
+// Batched split: problem blockIdx.y, elements strided over blockIdx.x.
+__global__ void split_batch_kernel(const SplitDesc *__restrict__ descs) {
+  const SplitDesc &d = descs[blockIdx.y];
+  const int64_t total = d.rows * d.cols;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / d.cols, c = t - (t / d.cols) * d.cols;
+    const int32_t x[1] = {bal(d.X[r * d.ldx + c], d.m)};
+    switch (d.P.nbase) {
+      case 1: store_digits_t<1, 1>(d.P, r, c, x, d.b); break;
+      case 2: store_digits_t<2, 1>(d.P, r, c, x, d.b); break;
+      case 3: store_digits_t<3, 1>(d.P, r, c, x, d.b); break;
+      case 4: store_digits_t<4, 1>(d.P, r, c, x, d.b); break;
+      case 5: store_digits_t<5, 1>(d.P, r, c, x, d.b); break;
+      default: break;
+    }
   }
 }
 
@@ -339,6 +360,21 @@ cudaError_t launch_split(const int32_t *X, int64_t ldx, int64_t rows, int64_t co
       return cudaErrorInvalidValue;
   }
 #undef AAT_SP
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_batch(const SplitDesc *descs_dev, int count, int64_t max_elems,
+                               double bytes, cudaStream_t st) {
+  if (count <= 0 || max_elems <= 0) return cudaSuccess;
+  if (count > 65535) return cudaErrorInvalidValue;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // enough blocks per problem for the largest one, capped by the GPU's width
+  int64_t bx = (max_elems + kThreads - 1) / kThreads;
+  bx = std::min<int64_t>(bx, std::max<int64_t>(1, (int64_t)sms * 16 / count + 1));
+  ProfScope prof(AAT_K_SPLIT, st, bytes);
+  split_batch_kernel<<<dim3((unsigned)bx, (unsigned)count), kThreads, 0, st>>>(descs_dev);
   return cudaGetLastError();
 }
 

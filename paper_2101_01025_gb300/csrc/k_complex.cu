@@ -901,6 +901,26 @@ static size_t c_plan(CCtx &c, int method, const float2 *A, int64_t n, int64_t k,
   return c.ar.peak;
 }
 
+static int complex_levels(int64_t n, int64_t k, uint32_t flags) {
+  const uint32_t lv = (flags & AAT_LEVELS_MASK) >> 8;
+  if (lv) return (int)lv - 1;
+  int levels = 0;  // one level pays off once the leaves stay large
+  while (levels < 4 && (n >> (levels + 1)) >= 4096 && (k >> (levels + 1)) >= 2048) ++levels;
+  return levels;
+}
+
+int complex_run(int method, const void *A, int64_t n, int64_t k, int64_t lda, void *C,
+                int64_t ldc, uint32_t flags, cudaStream_t st, char *ws, bool dry, size_t *need) {
+  CCtx c;
+  c.np = pieces_for(flags);
+  c.st = st;
+  const int levels = method == 2 ? complex_levels(n, k, flags) : 0;
+  const size_t peak = c_plan(c, method, (const float2 *)A, n, k, lda, (float2 *)C, ldc, levels,
+                             dry, ws);
+  if (need) *need = peak;
+  return c.err;
+}
+
 static int complex_entry(const void *A, int64_t n, int64_t k, int64_t lda, void *C, int64_t ldc,
                          uint32_t flags, void *stream, int method) {
   if (n < 0 || k < 0) return report_error(AAT_EINVAL, "negative size");
@@ -921,15 +941,7 @@ static int complex_entry(const void *A, int64_t n, int64_t k, int64_t lda, void 
   const char *a = (const char *)A, *cc = (const char *)C;
   if (a < cc + ((n - 1) * ldc + n) * 8 && cc < a + ((n - 1) * lda + k) * 8)
     return report_error(AAT_EINVAL, "C overlaps A");
-  int levels = 0;
-  if (method == 2) {
-    const uint32_t lv = (flags & AAT_LEVELS_MASK) >> 8;
-    if (lv) {
-      levels = (int)lv - 1;
-    } else {  // one level pays off once the leaves stay large
-      while (levels < 4 && (n >> (levels + 1)) >= 4096 && (k >> (levels + 1)) >= 2048) ++levels;
-    }
-  }
+  const int levels = method == 2 ? complex_levels(n, k, flags) : 0;
   CCtx c;
   c.np = pieces_for(flags);
   c.st = st;

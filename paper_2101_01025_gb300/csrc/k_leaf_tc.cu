@@ -71,6 +71,16 @@ struct Group {
   uint32_t ratio;   // accumulator multiplier (mod p) applied before the group
 };
 
+// One problem of a batched launch; its tensor maps live in global memory.
+struct alignas(64) BatchProb {
+  CUtensorMap tmx, tmy;
+  int32_t *out;
+  int64_t ldo, M, N;
+  int goff, ng;  // its groups: gtab[goff .. goff + ng)
+  int lower, accumulate;
+  ModP m;
+};
+
 struct Params {
   CUtensorMap tmx;  // 3D {K, rows, plane}, box {64, 128, 1}
   CUtensorMap tmy;  // 3D {K, rows, plane}, box {64, 256, 1}
@@ -83,10 +93,114 @@ struct Params {
   int lower, accumulate;
   ModP m;
   int32_t *status;
+  // batched launches: tiles are (problem, I, J) and every problem carries
+  // its own maps, groups and output
+  const BatchProb *probs;
+  const int4 *btiles;
+  const Group *gtab;
 };
+
+// What one tile of the launch reads.
+struct TileView {
+  const CUtensorMap *tmx, *tmy;
+  const Group *g;
+  int ng, I, J;
+};
+
+template <bool BATCH>
+__device__ __forceinline__ TileView tile_view(const Params &P, int t) {
+  TileView v;
+  if constexpr (BATCH) {
+    const int4 tl = P.btiles[t];
+    const BatchProb &b = P.probs[tl.x];
+    v.tmx = &b.tmx;
+    v.tmy = &b.tmy;
+    v.g = P.gtab + b.goff;
+    v.ng = b.ng;
+    v.I = tl.y;
+    v.J = tl.z;
+  } else {
+    const int2 tl = P.tiles[t];
+    v.tmx = &P.tmx;
+    v.tmy = &P.tmy;
+    v.g = P.g;
+    v.ng = P.ng;
+    v.I = tl.x;
+    v.J = tl.y;
+  }
+  return v;
+}
+
+// Group gi of tile t, and the group count (parameter loads when not batched).
+template <bool BATCH>
+__device__ __forceinline__ Group tile_group(const Params &P, int t, int gi) {
+  if constexpr (BATCH) {
+    return P.gtab[P.probs[P.btiles[t].x].goff + gi];
+  } else {
+    return P.g[gi];
+  }
+}
+
+template <bool BATCH>
+__device__ __forceinline__ int tile_ng(const Params &P, int t) {
+  if constexpr (BATCH) {
+    return P.probs[P.btiles[t].x].ng;
+  } else {
+    return P.ng;
+  }
+}
+
+template <bool BATCH>
+__device__ __forceinline__ int2 tile_ij(const Params &P, int t) {
+  if constexpr (BATCH) {
+    const int4 tl = P.btiles[t];
+    return make_int2(tl.y, tl.z);
+  } else {
+    return P.tiles[t];
+  }
+}
+
+template <bool BATCH>
+__device__ __forceinline__ const ModP &tile_modp(const Params &P, int t) {
+  if constexpr (BATCH) {
+    return P.probs[P.btiles[t].x].m;
+  } else {
+    return P.m;
+  }
+}
+
+// Where one tile writes.
+struct OutView {
+  int32_t *out;
+  int64_t ldo, M, N;
+  int lower, accumulate;
+};
+
+template <bool BATCH>
+__device__ __forceinline__ OutView tile_out(const Params &P, int t) {
+  OutView o;
+  if constexpr (BATCH) {
+    const BatchProb &b = P.probs[P.btiles[t].x];
+    o.out = b.out;
+    o.ldo = b.ldo;
+    o.M = b.M;
+    o.N = b.N;
+    o.lower = b.lower;
+    o.accumulate = b.accumulate;
+  } else {
+    o.out = P.out;
+    o.ldo = P.ldo;
+    o.M = P.M;
+    o.N = P.N;
+    o.lower = P.lower;
+    o.accumulate = P.accumulate;
+  }
+  return o;
+}
 
 // ------------------------------------------------------------------ kernel
 
+template <bool BATCH>
 __global__ void __launch_bounds__(THREADS, 1) leaf_tc_kernel(const __grid_constant__ Params P) {
   extern __shared__ uint8_t smem_raw[];
   // 1024-byte alignment of the shared-window address (128B-swizzle atoms)
@@ -137,9 +251,9 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_tc_kernel(const __grid_consta
       int issued = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
-        const int2 tile = P.tiles[t];
-        for (int gi = 0; gi < P.ng && ok; ++gi) {
-          const Group g = P.g[gi];
+        const TileView v = tile_view<BATCH>(P, t);
+        for (int gi = 0; gi < v.ng && ok; ++gi) {
+          const Group g = v.g[gi];
           for (int kb = g.kb0; kb < g.kb1; ++kb) {
             if (!wait_bounded(EMPTY(stage), ph ^ 1u, abort_flag, P.status)) {
               ok = false;
@@ -147,8 +261,8 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_tc_kernel(const __grid_consta
             }
             mbar_expect_tx(FULL(stage), (uint32_t)STAGE_BYTES);
             const uint32_t sa = sbase + (uint32_t)(stage * STAGE_BYTES);
-            tma_load_3d(sa, &P.tmx, FULL(stage), kb * BK, tile.x * BM, g.xp);
-            tma_load_3d(sa + A_BYTES, &P.tmy, FULL(stage), kb * BK, tile.y * BN, g.yp);
+            tma_load_3d(sa, v.tmx, FULL(stage), kb * BK, v.I * BM, g.xp);
+            tma_load_3d(sa + A_BYTES, v.tmy, FULL(stage), kb * BK, v.J * BN, g.yp);
             ++issued;
             if (++stage == STAGES) {
               stage = 0;
@@ -177,8 +291,9 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_tc_kernel(const __grid_consta
       uint32_t ph = 0, chunk = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
-        for (int gi = 0; gi < P.ng && ok; ++gi) {
-          const Group g = P.g[gi];
+        const int ng = tile_ng<BATCH>(P, t);
+        for (int gi = 0; gi < ng && ok; ++gi) {
+          const Group g = tile_group<BATCH>(P, t, gi);
           for (int kb = g.kb0; kb < g.kb1 && ok;) {
             const int kend = min(kb + g.kchunk, g.kb1);
             const uint32_t buf = chunk & 1u, use = chunk >> 1;
@@ -225,16 +340,17 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_tc_kernel(const __grid_consta
     const int quarter = warp & 3;  // TMEM lanes [32 quarter, 32 quarter + 32)
     const int chalf = e >> 2;      // columns [128 chalf, 128 chalf + 128)
     const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
-    const ModP m = P.m;
     uint32_t chunk = 0;
     bool ok = true;
+    ModP m = P.m;
     for (int t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
-      const int2 tile = P.tiles[t];
+      if constexpr (BATCH) m = tile_modp<BATCH>(P, t);
+      const int ng = tile_ng<BATCH>(P, t);
       int32_t acc[128];
 #pragma unroll
       for (int i = 0; i < 128; ++i) acc[i] = 0;
-      for (int gi = 0; gi < P.ng && ok; ++gi) {
-        const Group g = P.g[gi];
+      for (int gi = 0; gi < ng && ok; ++gi) {
+        const Group g = tile_group<BATCH>(P, t, gi);
         if (gi > 0) {
           const int64_t ratio = (int64_t)g.ratio;
 #pragma unroll
@@ -261,17 +377,19 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_tc_kernel(const __grid_consta
         }
       }
       if (!ok) break;
-      const int64_t row = (int64_t)tile.x * BM + quarter * 32 + lane;
-      const int64_t col0 = (int64_t)tile.y * BN + chalf * 128;
+      const int2 ij = tile_ij<BATCH>(P, t);
+      const int64_t row = (int64_t)ij.x * BM + quarter * 32 + lane;
+      const int64_t col0 = (int64_t)ij.y * BN + chalf * 128;
       // final value, canonical, in place (the last digit pair has weight 1)
 #pragma unroll
       for (int i = 0; i < 128; ++i) acc[i] = (int32_t)red_i32_canon(acc[i], m);
       // columns [0, lim) of this thread's 128 are written
-      int64_t lim = P.N - col0;
-      if (P.lower) lim = min(lim, row - col0 + 1);
-      if (row < P.M && lim > 0) {
-        int32_t *orow = P.out + row * P.ldo + col0;
-        const bool vec = ((reinterpret_cast<uintptr_t>(orow) & 15) == 0) && !P.accumulate;
+      const OutView o = tile_out<BATCH>(P, t);
+      int64_t lim = o.N - col0;
+      if (o.lower) lim = min(lim, row - col0 + 1);
+      if (row < o.M && lim > 0) {
+        int32_t *orow = o.out + row * o.ldo + col0;
+        const bool vec = ((reinterpret_cast<uintptr_t>(orow) & 15) == 0) && !o.accumulate;
 #pragma unroll
         for (int q = 0; q < 32; ++q) {
           const int c = 4 * q;
@@ -281,9 +399,9 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_tc_kernel(const __grid_consta
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
               if (c + j < lim) {
-                int32_t v = acc[c + j];
-                if (P.accumulate) v = (int32_t)bal_to_canon(add_bal(to_bal((uint32_t)v, m), bal(orow[c + j], m), m), m);
-                orow[c + j] = v;
+                int32_t x = acc[c + j];
+                if (o.accumulate) x = (int32_t)bal_to_canon(add_bal(to_bal((uint32_t)x, m), bal(orow[c + j], m), m), m);
+                orow[c + j] = x;
               }
             }
           }
@@ -523,7 +641,7 @@ cudaError_t launch_leaf_tc(const TcLeafArgs &a, const ModP &m, cudaStream_t st) 
   P->tiles = tiles;
   P->ntiles = nt;
   if (!g_attr_set[dev]) {
-    e = cudaFuncSetAttribute(leaf_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(leaf_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)SMEM_BYTES);
     if (e != cudaSuccess) { delete P; return e; }
     g_attr_set[dev] = true;
@@ -537,10 +655,130 @@ cudaError_t launch_leaf_tc(const TcLeafArgs &a, const ModP &m, cudaStream_t st) 
     const double macs =
         a.lower ? 0.5 * (double)a.M * (double)(a.M + 1) * a.K : (double)a.M * a.N * a.K;
     ProfScope prof(AAT_K_LEAF_TC, st, 2.0 * nprod * macs);
-    leaf_tc_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(*P);
+    leaf_tc_kernel<false><<<grid, THREADS, SMEM_BYTES, st>>>(*P);
   }
   delete P;
   return cudaGetLastError();
+}
+
+// ------------------------------------------------------- batched launches
+
+struct LeafBatchImpl {
+  BatchProb *probs = nullptr;
+  Group *gtab = nullptr;
+  int4 *tiles = nullptr;
+  int ntiles = 0;
+  double work = 0.0;
+};
+
+cudaError_t leaf_tc_batch_build(const TcLeafArgs *args, const ModP *mods, int count,
+                                LeafBatch *out) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  cudaError_t e = get_encode();
+  if (e != cudaSuccess) return e;
+  std::vector<BatchProb> probs(count);
+  std::vector<Group> gtab;
+  struct T4 { int4 t; double cost; };
+  std::vector<T4> tiles;
+  double work = 0.0;
+  std::vector<Group> tmp(MAX_GROUPS);
+  for (int i = 0; i < count; ++i) {
+    const TcLeafArgs &a = args[i];
+    BatchProb &b = probs[i];
+    std::memset(&b, 0, sizeof(b));
+    if ((e = encode_planes(&b.tmx, a.x, BM)) != cudaSuccess ||
+        (e = encode_planes(&b.tmy, a.y, BN)) != cudaSuccess)
+      return e;
+    int ng = 0, nprod = 0;
+    if (!build_groups(a, mods[i], tmp.data(), &ng, &nprod)) return cudaErrorInvalidValue;
+    b.goff = (int)gtab.size();
+    b.ng = ng;
+    gtab.insert(gtab.end(), tmp.begin(), tmp.begin() + ng);
+    b.out = a.out;
+    b.ldo = a.ldo;
+    b.M = a.M;
+    b.N = a.N;
+    b.lower = a.lower;
+    b.accumulate = a.accumulate;
+    b.m = mods[i];
+    const double kb = (double)((a.K + BK - 1) / BK);
+    const double cost = kb * nprod;  // K blocks x plane products per tile
+    const int64_t TI = (a.M + BM - 1) / BM, TJ = (a.N + BN - 1) / BN;
+    for (int64_t I = 0; I < TI; ++I)
+      for (int64_t J = 0; J < TJ; ++J) {
+        if (a.lower && J * BN > I * BM + BM - 1) continue;
+        tiles.push_back({make_int4(i, (int)I, (int)J, 0), cost});
+      }
+    const double macs =
+        a.lower ? 0.5 * (double)a.M * (double)(a.M + 1) * a.K : (double)a.M * a.N * a.K;
+    work += 2.0 * nprod * macs;
+  }
+  // the most expensive tiles first: the persistent CTAs take tiles round
+  // robin, so this spreads the heavy problems over every SM
+  std::stable_sort(tiles.begin(), tiles.end(),
+                   [](const T4 &u, const T4 &v) { return u.cost > v.cost; });
+  std::vector<int4> tl(tiles.size());
+  for (size_t i = 0; i < tiles.size(); ++i) tl[i] = tiles[i].t;
+  LeafBatchImpl *L = new LeafBatchImpl;
+  L->ntiles = (int)tl.size();
+  L->work = work;
+  if ((e = cudaMalloc(&L->probs, sizeof(BatchProb) * std::max(count, 1))) != cudaSuccess ||
+      (e = cudaMalloc(&L->gtab, sizeof(Group) * std::max<size_t>(gtab.size(), 1))) != cudaSuccess ||
+      (e = cudaMalloc(&L->tiles, sizeof(int4) * std::max<size_t>(tl.size(), 1))) != cudaSuccess) {
+    LeafBatch tmp;
+    tmp.impl = L;
+    leaf_tc_batch_free(&tmp);
+    return e;
+  }
+  cudaMemcpy(L->probs, probs.data(), sizeof(BatchProb) * count, cudaMemcpyHostToDevice);
+  if (!gtab.empty())
+    cudaMemcpy(L->gtab, gtab.data(), sizeof(Group) * gtab.size(), cudaMemcpyHostToDevice);
+  if (!tl.empty()) cudaMemcpy(L->tiles, tl.data(), sizeof(int4) * tl.size(), cudaMemcpyHostToDevice);
+  out->impl = L;
+  return cudaGetLastError();
+}
+
+cudaError_t leaf_tc_batch_launch(const LeafBatch &lb, cudaStream_t st) {
+  const LeafBatchImpl *L = (const LeafBatchImpl *)lb.impl;
+  if (!L || L->ntiles == 0) return cudaSuccess;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    static std::map<int, bool> attr;
+    if (!attr[dev]) {
+      cudaError_t e = cudaFuncSetAttribute(leaf_tc_kernel<true>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)SMEM_BYTES);
+      if (e != cudaSuccess) return e;
+      attr[dev] = true;
+    }
+  }
+  Params *P = new Params;
+  std::memset(P, 0, sizeof(Params));
+  P->probs = L->probs;
+  P->gtab = L->gtab;
+  P->btiles = L->tiles;
+  P->ntiles = L->ntiles;
+  P->status = device_status_ptr();
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  {
+    ProfScope prof(AAT_K_LEAF_TC, st, L->work);
+    leaf_tc_kernel<true><<<std::max(1, std::min(L->ntiles, sms)), THREADS, SMEM_BYTES, st>>>(*P);
+  }
+  delete P;
+  return cudaGetLastError();
+}
+
+void leaf_tc_batch_free(LeafBatch *lb) {
+  LeafBatchImpl *L = (LeafBatchImpl *)lb->impl;
+  if (!L) return;
+  if (L->probs) cudaFree(L->probs);
+  if (L->gtab) cudaFree(L->gtab);
+  if (L->tiles) cudaFree(L->tiles);
+  delete L;
+  lb->impl = nullptr;
 }
 
 void leaf_tc_release() {
@@ -725,7 +963,7 @@ extern "C" AAT_API int aat_gemm_modp_noalloc(const int32_t *X, int64_t ldx, cons
   P.tiles = tiles_dev;
   P.ntiles = (int)(TI * TJ);
   if (!g_attr_set[dev]) {
-    ce = cudaFuncSetAttribute(leaf_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    ce = cudaFuncSetAttribute(leaf_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)SMEM_BYTES);
     if (ce != cudaSuccess) return report_error(AAT_ECUDA, cudaGetErrorString(ce));
     g_attr_set[dev] = true;
@@ -733,7 +971,7 @@ extern "C" AAT_API int aat_gemm_modp_noalloc(const int32_t *X, int64_t ldx, cons
   int sms = 148;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = std::max(1, std::min(P.ntiles, sms));
-  leaf_tc_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(P);
+  leaf_tc_kernel<false><<<grid, THREADS, SMEM_BYTES, st>>>(P);
   ce = cudaGetLastError();
   return ce == cudaSuccess ? AAT_OK : report_error(AAT_ECUDA, cudaGetErrorString(ce));
 }
