@@ -9,11 +9,13 @@
 //     and outputs live in device tables), heaviest tiles first;
 //   * every other problem (recursive F_p products, complex products) runs
 //     its own sequence of launches.
-// The plan owns its workspace (the batch's planes, plus one region reused by
-// the other problems in turn), runs everything once eagerly (so every cache
-// and kernel attribute exists), then captures the same sequence into a CUDA
-// graph.  aat_plan_execute launches that graph on the caller's stream: no
-// allocation, no host synchronisation.
+// The other problems are spread round robin over up to kBranches side
+// streams, each with its own workspace region, so that the small launches of
+// different problems share the SMs; the batch runs on the main stream beside
+// them.  The plan owns its workspace, runs everything once eagerly (so every
+// cache and kernel attribute exists), then captures the same fork/join
+// sequence into a CUDA graph.  aat_plan_execute launches that graph on the
+// caller's stream: no allocation, no host synchronisation.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -26,9 +28,14 @@
 
 namespace aat {
 
+constexpr int kBranches = 8;
+
 struct Plan {
   int dev = 0;
   cudaStream_t st = nullptr;
+  std::vector<cudaStream_t> side;  // one per branch
+  std::vector<cudaEvent_t> ev;     // fork event + one join event per branch
+  size_t region = 0;               // bytes of one branch's workspace region
   void *ws = nullptr;
   size_t ws_size = 0;
   std::vector<aat_problem_t> probs;
@@ -48,6 +55,27 @@ struct Plan {
 
 static int enqueue(Plan &P, cudaStream_t st) {
   cudaError_t ce;
+  const int nb = (int)P.side.size();
+  if (nb > 0) {  // fork the side branches off the main stream
+    if ((ce = cudaEventRecord(P.ev[0], st)) != cudaSuccess)
+      return report_error(AAT_ECUDA, cudaGetErrorString(ce));
+    for (int b = 0; b < nb; ++b)
+      if ((ce = cudaStreamWaitEvent(P.side[b], P.ev[0], 0)) != cudaSuccess)
+        return report_error(AAT_ECUDA, cudaGetErrorString(ce));
+  }
+  for (size_t q = 0; q < P.solo.size(); ++q) {
+    const int b = (int)(q % (size_t)nb);
+    const aat_problem_t &pr = P.probs[P.solo[q]];
+    char *region = (char *)P.ws + P.solo_off + (size_t)b * P.region;
+    int e;
+    if (pr.kind == AAT_KIND_MODP)
+      e = modp_run((const int32_t *)pr.A, pr.n, pr.k, pr.lda, pr.p, (int32_t *)pr.C, pr.ldc,
+                   pr.flags, P.side[b], region, false, nullptr);
+    else
+      e = complex_run(pr.kind == AAT_KIND_AAH ? 0 : 2, pr.A, pr.n, pr.k, pr.lda, pr.C, pr.ldc,
+                      pr.flags, P.side[b], region, false, nullptr);
+    if (e) return e;
+  }
   if (P.nsplit > 0) {
     if ((ce = launch_split_batch(P.split_dev, P.nsplit, P.split_max, P.split_bytes, st)) !=
         cudaSuccess)
@@ -55,17 +83,10 @@ static int enqueue(Plan &P, cudaStream_t st) {
     if ((ce = leaf_tc_batch_launch(P.leaf, st)) != cudaSuccess)
       return report_error(AAT_ECUDA, cudaGetErrorString(ce));
   }
-  char *region = (char *)P.ws + P.solo_off;
-  for (int i : P.solo) {
-    const aat_problem_t &q = P.probs[i];
-    int e;
-    if (q.kind == AAT_KIND_MODP)
-      e = modp_run((const int32_t *)q.A, q.n, q.k, q.lda, q.p, (int32_t *)q.C, q.ldc, q.flags, st,
-                   region, false, nullptr);
-    else
-      e = complex_run(q.kind == AAT_KIND_AAH ? 0 : 2, q.A, q.n, q.k, q.lda, q.C, q.ldc, q.flags,
-                      st, region, false, nullptr);
-    if (e) return e;
+  for (int b = 0; b < nb; ++b) {  // join
+    if ((ce = cudaEventRecord(P.ev[1 + b], P.side[b])) != cudaSuccess ||
+        (ce = cudaStreamWaitEvent(st, P.ev[1 + b], 0)) != cudaSuccess)
+      return report_error(AAT_ECUDA, cudaGetErrorString(ce));
   }
   return AAT_OK;
 }
@@ -80,6 +101,8 @@ static void destroy(Plan *P) {
   leaf_tc_batch_free(&P->leaf);
   if (P->split_dev) cudaFree(P->split_dev);
   if (P->ws) cudaFree(P->ws);
+  for (cudaEvent_t e : P->ev) cudaEventDestroy(e);
+  for (cudaStream_t s : P->side) cudaStreamDestroy(s);
   if (P->st) cudaStreamDestroy(P->st);
   cudaSetDevice(cur);
   delete P;
@@ -138,8 +161,10 @@ static int create(const aat_problem_t *probs, int count, Plan **out) {
     solo_bytes = std::max(solo_bytes, need);
     P->solo.push_back(i);
   }
+  const int nb = std::min<int>(kBranches, (int)P->solo.size());
+  P->region = r256(solo_bytes);
   P->solo_off = r256(batch_bytes);
-  P->ws_size = P->solo_off + solo_bytes + 256;
+  P->ws_size = P->solo_off + (size_t)nb * P->region + 256;
   cudaError_t ce;
   if ((ce = cudaMalloc(&P->ws, P->ws_size)) != cudaSuccess) {
     cudaGetLastError();
@@ -149,6 +174,22 @@ static int create(const aat_problem_t *probs, int count, Plan **out) {
   if ((ce = cudaStreamCreateWithFlags(&P->st, cudaStreamNonBlocking)) != cudaSuccess) {
     destroy(P);
     return report_error(AAT_ECUDA, cudaGetErrorString(ce));
+  }
+  for (int b = 0; b < nb; ++b) {
+    cudaStream_t s2 = nullptr;
+    if ((ce = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking)) != cudaSuccess) {
+      destroy(P);
+      return report_error(AAT_ECUDA, cudaGetErrorString(ce));
+    }
+    P->side.push_back(s2);
+  }
+  for (int b = 0; b < (nb ? nb + 1 : 0); ++b) {
+    cudaEvent_t ev = nullptr;
+    if ((ce = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) {
+      destroy(P);
+      return report_error(AAT_ECUDA, cudaGetErrorString(ce));
+    }
+    P->ev.push_back(ev);
   }
   // the batch: split descriptors and leaf tables
   if (!P->batched.empty()) {
