@@ -58,6 +58,8 @@ extern "C" {
 #define AAT_ZERO_UPPER (1u << 1)  /* zero the strict upper triangle of C     */
 #define AAT_LEAF_TC (0u << 4)     /* leaf products on tcgen05 BF16 digits (default) */
 #define AAT_LEAF_SIMT (1u << 4)   /* leaf products by plain CUDA-core int64 (check path) */
+#define AAT_LEAF_I8 (2u << 4)     /* INT8 digits on mma.sync, exact INT32 accumulation */
+#define AAT_LEAF_F64 (3u << 4)    /* FP64 on mma.sync (DMMA); needs ((p-1)/2)^2 < 2^49 */
 #define AAT_LEAF_MASK (0xFu << 4)
 /* recursion levels: AAT_LEVELS(0) is the plain lower-triangle product (no
  * recursion); no AAT_LEVELS bits = chosen from (n, k). */
@@ -223,7 +225,8 @@ AAT_API int aat_device_status(int reset);
 #define AAT_K_ADD_LOW 5
 #define AAT_K_COPY 6
 #define AAT_K_LEAF_F32 7
-#define AAT_K_NCLASS 8
+#define AAT_K_LEAF_MMA 8
+#define AAT_K_NCLASS 10
 typedef struct {
   int64_t launches[AAT_K_NCLASS];
   double ms[AAT_K_NCLASS];

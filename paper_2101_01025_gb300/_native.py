@@ -26,6 +26,8 @@ AAT_IN_BALANCED = 1 << 0
 AAT_ZERO_UPPER = 1 << 1
 AAT_LEAF_TC = 0 << 4
 AAT_LEAF_SIMT = 1 << 4
+AAT_LEAF_I8 = 2 << 4
+AAT_LEAF_F64 = 3 << 4
 AAT_DIGITS_PLAIN = 1 << 12
 AAT_C_FP32 = 0 << 16
 AAT_C_BF16X3 = 1 << 16
@@ -90,14 +92,15 @@ class PlanStats(ctypes.Structure):
 
 
 #: kernel classes of aat_profile_t
-K_CLASSES = ["sblocks", "split", "leaf_tc", "leaf_simt", "postadd", "add_low", "copy", "leaf_f32"]
+K_CLASSES = ["sblocks", "split", "leaf_tc", "leaf_simt", "postadd", "add_low", "copy", "leaf_f32",
+             "leaf_mma", "unused"]
 
 
 class Profile(ctypes.Structure):
     _fields_ = [
-        ("launches", ctypes.c_int64 * 8),
-        ("ms", ctypes.c_double * 8),
-        ("work", ctypes.c_double * 8),
+        ("launches", ctypes.c_int64 * 10),
+        ("ms", ctypes.c_double * 10),
+        ("work", ctypes.c_double * 10),
     ]
 
     def as_dict(self):

@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libaat_gb300.so")
-SOURCES = ["aat_api.cu", "k_adds.cu", "k_leaf_simt.cu", "k_leaf_tc.cu", "k_complex.cu", "aat_plan.cu"]
+SOURCES = ["aat_api.cu", "k_adds.cu", "k_leaf_simt.cu", "k_leaf_tc.cu", "k_complex.cu", "aat_plan.cu", "k_leaf_mma.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                      "-Xcompiler", "-fvisibility=hidden", "--expt-relaxed-constexpr"]

@@ -415,6 +415,23 @@ static void leaf(Ctx &c, Operand X, Operand Y, bool same, int64_t M, int64_t N, 
             "leaf (CUDA cores)");
     return;
   }
+  if (c.leaf == AAT_LEAF_I8) {
+    const size_t mark = c.ar.used;
+    void *ws = c.ar.get(leaf_i8_workspace(M, N, K, c.m.p));
+    if (!c.ar.dry)
+      check(c, launch_leaf_i8(X.x, X.ld, Y.x, Y.ld, M, N, K, out, ldo, lower, accumulate, c.m, ws,
+                              c.st),
+            "leaf (INT8 mma.sync)");
+    c.ar.used = mark;
+    return;
+  }
+  if (c.leaf == AAT_LEAF_F64) {
+    if (!c.ar.dry)
+      check(c, launch_leaf_f64(X.x, X.ld, Y.x, Y.ld, M, N, K, out, ldo, lower, accumulate, c.m,
+                               c.st),
+            "leaf (FP64 mma.sync)");
+    return;
+  }
   const size_t mark = c.ar.used;
   if (X.pl.L == 0) {
     X.pl = planes_alloc(c, M, K);
@@ -577,8 +594,12 @@ static int setup(Ctx &c, uint32_t p, uint32_t flags, cudaStream_t st) {
   c.ds = make_digits(p);
   if (flags & AAT_DIGITS_PLAIN) c.ds.nsum = 0;
   c.leaf = flags & AAT_LEAF_MASK;
-  if (c.leaf != AAT_LEAF_TC && c.leaf != AAT_LEAF_SIMT)
+  if (c.leaf != AAT_LEAF_TC && c.leaf != AAT_LEAF_SIMT && c.leaf != AAT_LEAF_I8 &&
+      c.leaf != AAT_LEAF_F64)
     return fail(AAT_EUNSUPPORTED, "unknown leaf kind");
+  // FP64 leaf: partial sums of 16 products of ((p-1)/2)^2 must stay below 2^53
+  if (c.leaf == AAT_LEAF_F64 && (double)c.m.half * (double)c.m.half * 16.0 >= 9.0e15)
+    return fail(AAT_ERANGE, "p too large for the exact FP64 leaf");
   const char *eb = getenv("AAT_EXACT_BITS");
   c.exact_bits = eb ? atoi(eb) : 24;
   c.st = st;

@@ -246,6 +246,18 @@ cudaError_t launch_leaf_simt(const int32_t *X, int64_t ldx, const int32_t *Y, in
                              int64_t M, int64_t N, int64_t K, int32_t *out, int64_t ldo,
                              int lower, int accumulate, const ModP &m, cudaStream_t st);
 
+// Warp-level mma.sync leaves (k_leaf_mma.cu): INT8 digits with exact INT32
+// accumulation (workspace: leaf_i8_workspace bytes), and FP64 (exact while
+// K ((p-1)/2)^2 < 2^53 per chunk).
+int i8_digits(uint32_t p);
+size_t leaf_i8_workspace(int64_t M, int64_t N, int64_t K, uint32_t p);
+cudaError_t launch_leaf_i8(const int32_t *X, int64_t ldx, const int32_t *Y, int64_t ldy,
+                           int64_t M, int64_t N, int64_t K, int32_t *out, int64_t ldo, int lower,
+                           int accumulate, const ModP &m, void *ws, cudaStream_t st);
+cudaError_t launch_leaf_f64(const int32_t *X, int64_t ldx, const int32_t *Y, int64_t ldy,
+                            int64_t M, int64_t N, int64_t K, int32_t *out, int64_t ldo, int lower,
+                            int accumulate, const ModP &m, cudaStream_t st);
+
 // Tensor-core leaf: out = sum over digit pairs (i, j) of 2^(b (i + j))
 // X_i Y_j^T mod p on tcgen05 (BF16 digits, FP32 accumulation drained to
 // int32 before any partial sum can leave the exact range).

@@ -88,7 +88,7 @@ def test_sblocks_match_oracle(p, n, k):
         assert np.array_equal(got[i].astype(np.int64), ref[i].astype(np.int64)), "S%d" % (i + 1)
 
 
-LEAFKINDS = {"tc": 0, "tc_plain": 1 << 12, "simt": 1 << 4}
+LEAFKINDS = {"tc": 0, "tc_plain": 1 << 12, "simt": 1 << 4, "i8": 2 << 4, "f64": 3 << 4}
 
 
 @pytest.mark.parametrize("leafkind", list(LEAFKINDS))
@@ -99,6 +99,11 @@ def test_leaf_gemm_matches_oracle(leafkind, p, M, N, K):
     from paper_2101_01025_gb300 import testing as T
     if leafkind == "simt" and K > 2000:
         pytest.skip("slow check path")
+    if leafkind == "f64" and p == 2**31 - 1:
+        with pytest.raises(Exception):      # ((p-1)/2)^2 K would round in FP64
+            T.leaf(dev(np.zeros((M, K), np.int32)), dev(np.zeros((N, K), np.int32)), p,
+                   leafkind=LEAFKINDS[leafkind])
+        return
     kindflag = LEAFKINDS[leafkind]
     X = synth.residues(M + 7 * K, (M, K), p, balanced=True)
     Y = synth.residues(N + 11 * K, (N, K), p)
@@ -185,6 +190,18 @@ def test_aat_modp_tc_matches_oracle(lib, p, n, k, levels):
 def test_aat_modp_simt_leaf_matches_oracle(lib, p, n, k, levels):
     A = synth.residues(n + k, (n, k), p)
     C = host(lib.aat_modp(dev(A), p, levels=levels, flags=lib.AAT_LEAF_SIMT))
+    assert low_equal(C, oracle.aat_modp_low(A, p))
+
+
+@pytest.mark.parametrize("leaf", ["i8", "f64"])
+@pytest.mark.parametrize("p", [65521, 131071, 2**31 - 1])
+@pytest.mark.parametrize("n,k", [(300, 200), (513, 257), (256, 512)])
+@pytest.mark.parametrize("levels", [0, 1, 2])
+def test_aat_modp_mma_leaves_match_oracle(lib, leaf, p, n, k, levels):
+    if leaf == "f64" and p == 2**31 - 1:
+        pytest.skip("no exact FP64 leaf for this p (checked on the host)")
+    A = synth.residues(5 * n + k + levels, (n, k), p)
+    C = host(lib.aat_modp(dev(A), p, levels=levels, flags=LEAFKINDS[leaf]))
     assert low_equal(C, oracle.aat_modp_low(A, p))
 
 

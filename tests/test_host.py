@@ -166,6 +166,9 @@ def test_argument_validation_before_any_gpu_call():
         _native.AAT_ENOTPRIME
     assert lib.aat_modp_ex(fake, 4, 4, 4, 131071, fake * 2, 4, 7 << 4, None) == \
         _native.AAT_EUNSUPPORTED
+    # the FP64 leaf is exact only while ((p-1)/2)^2 sums stay below 2^53
+    assert lib.aat_modp_ex(fake, 4, 4, 4, 2**31 - 1, fake * 2, 4, _native.AAT_LEAF_F64, None) == \
+        _native.AAT_ERANGE
 
 
 @pytest.mark.parametrize("p", [2**31 - 1, 65521, 131071, 13, 1000003])
