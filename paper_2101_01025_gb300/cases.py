@@ -26,6 +26,8 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16x3", "bf16"],
                     help="complex cases: BF16 pieces per FP32 value (3, 2, 1)")
+    ap.add_argument("--leaf", default="tc", choices=["tc", "i8", "f64", "simt"],
+                    help="leaf kind of the F_p cases")
     ap.add_argument("--plain-digits", action="store_true",
                     help="one product per digit pair instead of the pair-sum form")
     a = ap.parse_args(argv)
@@ -39,6 +41,8 @@ def main(argv=None):
     torch.manual_seed(0x2101)
     n, k, p = a.n, a.k or a.n, a.p
     flags = aat.AAT_DIGITS_PLAIN if a.plain_digits else 0
+    flags |= {"tc": aat.AAT_LEAF_TC, "i8": aat.AAT_LEAF_I8, "f64": aat.AAT_LEAF_F64,
+              "simt": aat.AAT_LEAF_SIMT}[a.leaf]
     half = (p - 1) // 2
     if a.case == "batch":
         return batch_case(a)
@@ -72,7 +76,7 @@ def main(argv=None):
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
     print(json.dumps({"case": a.case, "n": n, "k": k, "p": p, "levels": a.levels,
-                      "plain_digits": a.plain_digits, "prec": a.prec,
+                      "plain_digits": a.plain_digits, "prec": a.prec, "leaf": a.leaf,
                       "ms": times, "status": aat.aat_device_status()}))
 
 
