@@ -69,6 +69,7 @@ struct Group {
   int32_t kb0, kb1; // k-block range [kb0, kb1) (units of BK)
   int32_t kchunk;   // k-blocks per FP32 accumulation chunk
   uint32_t ratio;   // accumulator multiplier (mod p) applied before the group
+  uint32_t ratio_sh;  // floor(ratio 2^32 / p), Shoup's precomputed quotient
 };
 
 // One problem of a batched launch; its tensor maps live in global memory.
@@ -196,6 +197,19 @@ __device__ __forceinline__ OutView tile_out(const Params &P, int t) {
     o.accumulate = P.accumulate;
   }
   return o;
+}
+
+// a * w mod p, balanced, for any int32 a and a fixed w in [0, p) with
+// wsh = floor(w 2^32 / p) (Shoup's modular multiplication): with |a| < 2^32,
+// |a| w - floor(|a| wsh / 2^32) p lies in [0, 2p), so 32-bit arithmetic and
+// one conditional subtraction give the residue.
+__device__ __forceinline__ int32_t mulmod_shoup(int32_t a, uint32_t w, uint32_t wsh, const ModP &m) {
+  const uint32_t ax = a < 0 ? 0u - (uint32_t)a : (uint32_t)a;
+  const uint32_t q = __umulhi(ax, wsh);
+  uint32_t r = ax * w - q * m.p;
+  if (r >= m.p) r -= m.p;
+  const int32_t b = r > m.half ? (int32_t)r - (int32_t)m.p : (int32_t)r;
+  return a < 0 ? -b : b;
 }
 
 // ------------------------------------------------------------------ kernel
@@ -352,9 +366,8 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_tc_kernel(const __grid_consta
       for (int gi = 0; gi < ng && ok; ++gi) {
         const Group g = tile_group<BATCH>(P, t, gi);
         if (gi > 0) {
-          const int64_t ratio = (int64_t)g.ratio;
 #pragma unroll
-          for (int i = 0; i < 128; ++i) acc[i] = red_s64((int64_t)acc[i] * ratio, m);
+          for (int i = 0; i < 128; ++i) acc[i] = mulmod_shoup(acc[i], g.ratio, g.ratio_sh, m);
         }
         for (int kb = g.kb0; kb < g.kb1;) {
           const int kend = min(kb + g.kchunk, g.kb1);
@@ -365,10 +378,14 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_tc_kernel(const __grid_consta
           }
           tc_fence_after();
           const uint32_t ta = tmem + lane_base + buf * ACC_COLS + (uint32_t)(chalf * 128);
-          tmem_drain32<0>(ta, acc);
-          tmem_drain32<32>(ta + 32u, acc);
-          tmem_drain32<64>(ta + 64u, acc);
-          tmem_drain32<96>(ta + 96u, acc);
+          tmem_drain16<0>(ta, acc);
+          tmem_drain16<16>(ta + 16u, acc);
+          tmem_drain16<32>(ta + 32u, acc);
+          tmem_drain16<48>(ta + 48u, acc);
+          tmem_drain16<64>(ta + 64u, acc);
+          tmem_drain16<80>(ta + 80u, acc);
+          tmem_drain16<96>(ta + 96u, acc);
+          tmem_drain16<112>(ta + 112u, acc);
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(AEMPTY(buf));
@@ -499,6 +516,11 @@ cudaError_t get_tiles(int dev, int64_t M, int64_t N, int lower, int2 **out, int 
   return cudaSuccess;
 }
 
+// Shoup quotients of the Horner ratios.
+void set_shoup(Group *g, int ng, uint32_t p) {
+  for (int i = 0; i < ng; ++i) g[i].ratio_sh = (uint32_t)(((uint64_t)g[i].ratio << 32) / p);
+}
+
 // Groups of the leaf product: plane pairs with integer weights turned into a
 // Horner sequence (see the file header).  Returns false when the product does
 // not fit the group table or a bound cannot be met.
@@ -587,6 +609,7 @@ bool build_groups(const TcLeafArgs &a, const ModP &m, Group *out, int *ng_out, i
     g.kchunk = 1;
     g.ratio = wprev;
   }
+  set_shoup(out, ng, m.p);
   int nprod = 0;
   for (const Term &t : terms)
     if (modw(t.w) != 0) ++nprod;
@@ -951,6 +974,7 @@ extern "C" AAT_API int aat_gemm_modp_noalloc(const int32_t *X, int64_t ldx, cons
         prev_s = s;
       }
     }
+  set_shoup(P.g, ng, mp.p);
   P.ng = ng;
   P.out = C;
   P.ldo = ldc;

@@ -206,6 +206,54 @@ __device__ __forceinline__ void tmem_drain32(uint32_t taddr, int32_t (&acc)[128]
 
 
 
+// Drain 16 consecutive FP32 columns of this thread's TMEM lane into the
+// int32 accumulators acc[B .. B+15] (load, wait, convert, add in one
+// statement); half the temporaries of the 32-column form, so that the
+// 128 accumulators and the temporaries fit the epilogue's registers.
+template <int B>
+__device__ __forceinline__ void tmem_drain16(uint32_t taddr, int32_t (&acc)[128]) {
+  asm volatile(
+      "{\n\t.reg .b32 t0, t1, t2, t3, t4, t5, t6, t7, t8, t9, t10, t11, t12, t13, t14, t15;\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {t0, t1, t2, t3, t4, t5, t6, t7, t8, t9, t10, t11, t12, t13, t14, t15}, [%16];\n\t"
+      "tcgen05.wait::ld.sync.aligned;\n\t"
+      "cvt.rni.s32.f32 t0, t0;\n\t"
+      "add.s32 %0, %0, t0;\n\t"
+      "cvt.rni.s32.f32 t1, t1;\n\t"
+      "add.s32 %1, %1, t1;\n\t"
+      "cvt.rni.s32.f32 t2, t2;\n\t"
+      "add.s32 %2, %2, t2;\n\t"
+      "cvt.rni.s32.f32 t3, t3;\n\t"
+      "add.s32 %3, %3, t3;\n\t"
+      "cvt.rni.s32.f32 t4, t4;\n\t"
+      "add.s32 %4, %4, t4;\n\t"
+      "cvt.rni.s32.f32 t5, t5;\n\t"
+      "add.s32 %5, %5, t5;\n\t"
+      "cvt.rni.s32.f32 t6, t6;\n\t"
+      "add.s32 %6, %6, t6;\n\t"
+      "cvt.rni.s32.f32 t7, t7;\n\t"
+      "add.s32 %7, %7, t7;\n\t"
+      "cvt.rni.s32.f32 t8, t8;\n\t"
+      "add.s32 %8, %8, t8;\n\t"
+      "cvt.rni.s32.f32 t9, t9;\n\t"
+      "add.s32 %9, %9, t9;\n\t"
+      "cvt.rni.s32.f32 t10, t10;\n\t"
+      "add.s32 %10, %10, t10;\n\t"
+      "cvt.rni.s32.f32 t11, t11;\n\t"
+      "add.s32 %11, %11, t11;\n\t"
+      "cvt.rni.s32.f32 t12, t12;\n\t"
+      "add.s32 %12, %12, t12;\n\t"
+      "cvt.rni.s32.f32 t13, t13;\n\t"
+      "add.s32 %13, %13, t13;\n\t"
+      "cvt.rni.s32.f32 t14, t14;\n\t"
+      "add.s32 %14, %14, t14;\n\t"
+      "cvt.rni.s32.f32 t15, t15;\n\t"
+      "add.s32 %15, %15, t15;\n\t"
+      "}"
+      : "+r"(acc[B + 0]), "+r"(acc[B + 1]), "+r"(acc[B + 2]), "+r"(acc[B + 3]), "+r"(acc[B + 4]), "+r"(acc[B + 5]), "+r"(acc[B + 6]), "+r"(acc[B + 7]), "+r"(acc[B + 8]), "+r"(acc[B + 9]), "+r"(acc[B + 10]), "+r"(acc[B + 11]), "+r"(acc[B + 12]), "+r"(acc[B + 13]), "+r"(acc[B + 14]), "+r"(acc[B + 15])
+      : "r"(taddr)
+      : "memory");
+}
+
 // 32 consecutive 32-bit TMEM columns of this thread's lane, waited on in the
 // same statement so no register is read before it holds its value.
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
