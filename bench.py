@@ -46,11 +46,10 @@ N = K = 16384
 P = 2**31 - 1
 SEED_OFFSET = 2
 # DRAM traffic of the dominant kernel from one ncu capture of an 8192^3 leaf
-# product (dram__bytes_read.sum + dram__bytes_write.sum = 16.05 GB for
-# 10.995 TFLOP of algorithmic work, profiles/leaf_tc_kernel_gemm8192_p2p31m1.md),
-# scaled to the average launch of the step by its algorithmic work.  Set to
-# None whenever the kernel changes until it is captured again.
-LEAF_TC_BYTES_PER_FLOP = 16.05e9 / 10.995e12
+# product (dram__bytes_read.sum + dram__bytes_write.sum per algorithmic
+# FLOP), scaled to the average launch of the step by its algorithmic work.
+# None whenever the kernel has changed since the counters were taken.
+LEAF_TC_BYTES_PER_FLOP = None
 
 
 def parse():
@@ -286,7 +285,8 @@ def run_ours(args):
     else:
         peak, peak_src = 1700.0, "of fallback (bf16 sustained)"
     roofline = {
-        "bound": "tensor", "kernel": "leaf_tc_kernel (tcgen05 kind::f16, BF16 digits)",
+        "bound": "tensor",
+        "kernel": "leaf_tc_kernel (tcgen05 kind::f16, CTA pairs, BF16 digits)",
         "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
         "peak_source": peak_src,
         "traffic": (None if LEAF_TC_BYTES_PER_FLOP is None else
@@ -346,8 +346,11 @@ def run_ours(args):
         t_e2e = max_over_ranks(time.perf_counter() - t0) / args.steps
         e2e = {"value": world * N * N * K / t_e2e / 1e9, "unit": "GOPS",
                "ms_per_step": 1e3 * t_e2e,
-               "h2d_bytes_per_step": N * K * 4, "d2h_bytes_per_step": N * N * 4,
-               "api": "aat_modp_host (pinned host A and C; copies inside the call)"}
+               "h2d_bytes_per_step": N * K * 4,
+               "d2h_bytes_per_step": aat.aat_modp_host_d2h_bytes(N),
+               "api": "aat_modp_host (pinned host A and C; copies inside the call; the "
+                      "lower triangle of C comes back in row bands, the rows below n/2 "
+                      "while the last product runs)"}
 
     cpu = None
     if not args.no_extras and rank == 0 and world == 1:

@@ -84,12 +84,21 @@ AAT_API int aat_modp_ex(const int32_t *A, int64_t n, int64_t k, int64_t lda, uin
 
 /*
  * End-to-end form: A_host (n x k, row stride k) and C_host (n x n, row
- * stride n) are HOST buffers (pinned or pageable).  The call copies A to
- * the device, runs aat_modp_ex with `flags`, copies the result back and
- * synchronises.  The device buffers are owned by the library.
+ * stride n) are HOST buffers (pinned or pageable; pinned buffers let the
+ * copies overlap the computation).  The call copies A to the device, runs
+ * aat_modp_ex with `flags`, copies the result back and synchronises.  The
+ * device buffers are owned by the library.  Only the lower triangle of C is
+ * defined (its strict upper triangle is unspecified, as for aat_modp): it is
+ * copied back in bands of 512 rows, band [a, b) carrying columns [0, b), and
+ * when a recursion level runs, the rows below n/2 go back while the last
+ * product still computes.  With AAT_ZERO_UPPER the whole of C is copied
+ * (upper triangle zero) after the computation.
  */
 AAT_API int aat_modp_host(const int32_t *A_host, int64_t n, int64_t k, uint32_t p,
                   int32_t *C_host, uint32_t flags);
+
+/* Bytes that aat_modp_host copies from the device to the host for size n. */
+AAT_API int64_t aat_modp_host_d2h_bytes(int64_t n, uint32_t flags);
 
 /*
  * The plain general product C = X Y^T mod p with the same exact leaf

@@ -17,7 +17,8 @@ from ._native import (AAT_C_BF16, AAT_C_BF16X3, AAT_C_FP32, AAT_DIGITS_PLAIN,  #
                       AAT_IN_BALANCED, AAT_LEAF_F64, AAT_LEAF_I8, AAT_LEAF_SIMT, AAT_LEAF_TC, AAT_LEVELS, AAT_ZERO_UPPER, AatError, PlanStats, check, last_error, lib)
 
 __all__ = [
-    "aat_modp", "aat_gemm_modp", "aat_modp_host", "aat_workspace_size", "aat_device_status",
+    "aat_modp", "aat_gemm_modp", "aat_modp_host", "aat_modp_host_d2h_bytes", "aat_workspace_size",
+    "aat_device_status",
     "aat_shutdown", "aat_version", "aah_complex", "aat_complex_2m", "aat_complex", "Plan", "AAT_LEVELS", "AAT_LEAF_TC", "AAT_LEAF_SIMT",
     "AAT_ZERO_UPPER", "AAT_IN_BALANCED", "AatError",
 ]
@@ -77,7 +78,8 @@ def aat_gemm_modp(X, Y, p: int, C=None, flags: int = 0, stream=None):
 
 def aat_modp_host(A, p: int, C=None, flags: int = 0, levels: int | None = None):
     """End to end from host memory: A is a C-contiguous int32 numpy array (or
-    pinned CPU tensor); returns C (n x n, host, same kind as A)."""
+    pinned CPU tensor); returns C (n x n, host, same kind as A).  Only the
+    lower triangle of C is written unless AAT_ZERO_UPPER is set."""
     import numpy as np
     if levels is not None:
         flags |= AAT_LEVELS(levels)
@@ -96,6 +98,11 @@ def aat_modp_host(A, p: int, C=None, flags: int = 0, levels: int | None = None):
         C = torch.empty((n, n), dtype=torch.int32, pin_memory=A.is_pinned())
     check(lib().aat_modp_host(A.data_ptr(), n, k, p, C.data_ptr(), flags))
     return C
+
+
+def aat_modp_host_d2h_bytes(n: int, flags: int = 0) -> int:
+    """Bytes aat_modp_host copies back to the host for an n x n result."""
+    return int(lib().aat_modp_host_d2h_bytes(n, flags))
 
 
 def _check_cmat(t, name):

@@ -40,7 +40,8 @@ def AAT_LEVELS(l: int) -> int:
 
 #: every symbol include/aat.h and include/aat_testing.h declare
 EXPORTS = [
-    "aat_modp", "aat_modp_ex", "aat_modp_host", "aat_gemm_modp", "aat_gemm_modp_noalloc",
+    "aat_modp", "aat_modp_ex", "aat_modp_host", "aat_modp_host_d2h_bytes", "aat_gemm_modp",
+    "aat_gemm_modp_noalloc",
     "aat_workspace_size",
     "aat_last_error", "aat_device_status", "aat_shutdown", "aat_version",
     "aat_profile_begin", "aat_profile_end", "aah_complex", "aah_complex_ex", "aat_complex_2m",
@@ -132,6 +133,8 @@ def lib():
         L.aat_modp.argtypes = [vp, i64, i64, u32, vp, vp]
         L.aat_modp_ex.argtypes = [vp, i64, i64, i64, u32, vp, i64, u32, vp]
         L.aat_modp_host.argtypes = [vp, i64, i64, u32, vp, u32]
+        L.aat_modp_host_d2h_bytes.argtypes = [i64, u32]
+        L.aat_modp_host_d2h_bytes.restype = i64
         L.aat_gemm_modp.argtypes = [vp, i64, vp, i64, i64, i64, i64, u32, vp, i64, u32, vp]
         L.aat_gemm_modp_noalloc.argtypes = [vp, i64, vp, i64, i64, i64, i64, u32, vp, i64, vp]
         L.aat_workspace_size.argtypes = [i64, i64, u32, u32]

@@ -242,6 +242,8 @@ struct DeviceState {
   void *e2e_a = nullptr, *e2e_c = nullptr;
   size_t e2e_a_size = 0, e2e_c_size = 0;
   cudaStream_t e2e_stream = nullptr;
+  cudaStream_t e2e_stream2 = nullptr;  // copies rows that are final early
+  cudaEvent_t e2e_split = nullptr;
 };
 
 static std::mutex g_state_mu;
@@ -354,6 +356,11 @@ struct Ctx {
   Arena ar;
   aatx_plan_stats_t *stats;  // optional counters
   int err = AAT_OK;
+  // optional: recorded on `st` as soon as rows [split_row, n) of C are final
+  // (after the top level's post-additions; at the end when C is padded)
+  cudaEvent_t split_ev = nullptr;
+  int top_levels = -1;
+  int64_t split_row = 0;
 };
 
 static Planes planes_for(const DigitSpec &ds, int64_t rows, int64_t cols) {
@@ -537,6 +544,9 @@ static void rec(Ctx &c, const int32_t *A, int64_t lda, int64_t n, int64_t k, int
   rec(c, A11, lda, h, kap, C11, ldc, levels - 1, pA11);
   // 6. U1 = P1 + P5, U2 = U1 + P4, U4 = U2 + P3 -> C21, U5 = Low(U2 + P4^T) -> C22
   if (!c.ar.dry) check(c, launch_postadd(C11, C12, C21, C22, ldc, h, c.m, c.st), "postadd");
+  // rows [h, n) of the top level (C21 = U4, Low(C22) = Low(U5)) are final
+  if (c.split_ev && levels == c.top_levels && !c.ar.dry && c.err == AAT_OK)
+    cudaEventRecord(c.split_ev, c.st);
   // 7-8. P2 = Low(A12 A12^T), U3 = P1 + P2 -> C11
   if (last) {
     Operand X{A12, lda, pA12};
@@ -633,9 +643,13 @@ static size_t run_plan(Ctx &c, const int32_t *A, int64_t n, int64_t k, int64_t l
     c.stats->n_pad = pr.n_pad;
     c.stats->k_pad = pr.k_pad;
   }
+  const bool early = !pr.padded && pr.levels >= 1;
+  c.top_levels = early ? pr.levels : -1;
+  c.split_row = early ? pr.n_pad / 2 : n;
   rec(c, Aw, ldaw, pr.n_pad, pr.k_pad, Cw, ldcw, pr.levels, no_planes());
   if (pr.padded && !dry) check(c, launch_copy_low(Cw, ldcw, C, ldc, n, c.st), "unpad");
   if (!dry && (flags & AAT_ZERO_UPPER)) check(c, launch_zero_upper(C, ldc, n, c.st), "zero upper");
+  if (!dry && !early && c.split_ev && c.err == AAT_OK) cudaEventRecord(c.split_ev, c.st);
   return c.ar.peak;
 }
 
@@ -702,9 +716,11 @@ int aat_version(void) { return 100; }
 
 const char *aat_last_error(void) { return g_last_error.c_str(); }
 
-int aat_modp_ex(const int32_t *A, int64_t n, int64_t k, int64_t lda, uint32_t p, int32_t *C,
-                int64_t ldc, uint32_t flags, void *stream) {
-  g_last_error.clear();
+// aat_modp_ex with the optional early-rows event (aat_modp_host).
+static int modp_device(const int32_t *A, int64_t n, int64_t k, int64_t lda, uint32_t p, int32_t *C,
+                       int64_t ldc, uint32_t flags, cudaStream_t stream, cudaEvent_t split_ev,
+                       int64_t *split_row) {
+  if (split_row) *split_row = n;
   if (n < 0 || k < 0) return fail(AAT_EINVAL, "negative size");
   if (n > (1 << 30) || k > (1 << 30)) return fail(AAT_EINVAL, "size too large");
   if (lda < std::max<int64_t>(k, 1) || ldc < std::max<int64_t>(n, 1))
@@ -712,7 +728,7 @@ int aat_modp_ex(const int32_t *A, int64_t n, int64_t k, int64_t lda, uint32_t p,
   if (n > 0 && (!C || (k > 0 && !A))) return fail(AAT_EINVAL, "null pointer");
   int e;
   Ctx c;
-  if ((e = setup(c, p, flags, (cudaStream_t)stream))) return e;
+  if ((e = setup(c, p, flags, stream))) return e;
   if (n == 0) return AAT_OK;
   if (k > 0 && overlaps(A, (size_t)((n - 1) * lda + k) * 4, C, (size_t)((n - 1) * ldc + n) * 4))
     return fail(AAT_EINVAL, "C overlaps A");
@@ -725,8 +741,42 @@ int aat_modp_ex(const int32_t *A, int64_t n, int64_t k, int64_t lda, uint32_t p,
   void *ws = nullptr;
   if ((e = ensure_workspace(need, &ws))) return e;
   c.err = AAT_OK;
+  c.split_ev = split_ev;
   run_plan(c, A, n, k, lda, C, ldc, flags, false, (char *)ws);
+  if (split_row) *split_row = c.split_row;
   return c.err;
+}
+
+// Rows [r0, r1) of the lower triangle of the n x n matrix src (device, row
+// stride n) to dst (host, row stride n), in bands of kHostBand rows: band
+// [a, b) copies columns [0, b) of its rows, so a band carries b (b - a)
+// entries (the triangle plus (b - a)^2 / 2 entries above it).
+constexpr int64_t kHostBand = 512;
+
+static int64_t low_band_entries(int64_t r0, int64_t r1) {
+  int64_t total = 0;
+  for (int64_t a = r0; a < r1; a += kHostBand) {
+    const int64_t b = std::min(r1, a + kHostBand);
+    total += b * (b - a);
+  }
+  return total;
+}
+
+static cudaError_t copy_low_bands(int32_t *dst, const int32_t *src, int64_t n, int64_t r0,
+                                  int64_t r1, cudaStream_t st) {
+  for (int64_t a = r0; a < r1; a += kHostBand) {
+    const int64_t b = std::min(r1, a + kHostBand);
+    cudaError_t ce = cudaMemcpy2DAsync(dst + a * n, (size_t)n * 4, src + a * n, (size_t)n * 4,
+                                       (size_t)b * 4, (size_t)(b - a), cudaMemcpyDeviceToHost, st);
+    if (ce != cudaSuccess) return ce;
+  }
+  return cudaSuccess;
+}
+
+int aat_modp_ex(const int32_t *A, int64_t n, int64_t k, int64_t lda, uint32_t p, int32_t *C,
+                int64_t ldc, uint32_t flags, void *stream) {
+  g_last_error.clear();
+  return modp_device(A, n, k, lda, p, C, ldc, flags, (cudaStream_t)stream, nullptr, nullptr);
 }
 
 int aat_modp(const int32_t *A, int64_t n, int64_t k, uint32_t p, int32_t *C, void *stream) {
@@ -747,6 +797,10 @@ int aat_modp_host(const int32_t *A_host, int64_t n, int64_t k, uint32_t p, int32
     std::lock_guard<std::mutex> lock(g_state_mu);
     s = &state();
     if (!s->e2e_stream) cudaStreamCreateWithFlags(&s->e2e_stream, cudaStreamNonBlocking);
+    if (!s->e2e_stream2) cudaStreamCreateWithFlags(&s->e2e_stream2, cudaStreamNonBlocking);
+    if (!s->e2e_split) cudaEventCreateWithFlags(&s->e2e_split, cudaEventDisableTiming);
+    if (!s->e2e_stream || !s->e2e_stream2 || !s->e2e_split)
+      return fail(AAT_ECUDA, "e2e streams");
     if (s->e2e_a_size < abytes) {
       if (s->e2e_a) cudaFree(s->e2e_a);
       s->e2e_a = nullptr;
@@ -767,13 +821,40 @@ int aat_modp_host(const int32_t *A_host, int64_t n, int64_t k, uint32_t p, int32
   if (k > 0 && (ce = cudaMemcpyAsync(s->e2e_a, A_host, (size_t)n * k * 4, cudaMemcpyHostToDevice,
                                      st)) != cudaSuccess)
     return cuda_fail(ce, "copy A to the device");
-  e = aat_modp_ex((const int32_t *)s->e2e_a, n, k, std::max<int64_t>(k, 1), p, (int32_t *)s->e2e_c,
-                  n, flags, st);
-  if (e) return e;
-  if ((ce = cudaMemcpyAsync(C_host, s->e2e_c, cbytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
-    return cuda_fail(ce, "copy C to the host");
+  const int32_t *Cd = (const int32_t *)s->e2e_c;
+  if (flags & AAT_ZERO_UPPER) {
+    // the caller asked for the whole matrix: one copy at the end
+    e = modp_device((const int32_t *)s->e2e_a, n, k, std::max<int64_t>(k, 1), p, (int32_t *)Cd, n,
+                    flags, st, nullptr, nullptr);
+    if (e) return e;
+    if ((ce = cudaMemcpyAsync(C_host, Cd, cbytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+      return cuda_fail(ce, "copy C to the host");
+  } else {
+    // only the lower triangle is defined: copy it in row bands; the rows
+    // below the top-level split are final before the last product P2 runs
+    // and go back on a second stream meanwhile
+    int64_t split = n;
+    e = modp_device((const int32_t *)s->e2e_a, n, k, std::max<int64_t>(k, 1), p, (int32_t *)Cd, n,
+                    flags, st, s->e2e_split, &split);
+    if (e) return e;
+    if (split < n) {
+      if ((ce = cudaStreamWaitEvent(s->e2e_stream2, s->e2e_split, 0)) != cudaSuccess ||
+          (ce = copy_low_bands(C_host, Cd, n, split, n, s->e2e_stream2)) != cudaSuccess)
+        return cuda_fail(ce, "copy C to the host");
+    }
+    if ((ce = copy_low_bands(C_host, Cd, n, 0, split, st)) != cudaSuccess)
+      return cuda_fail(ce, "copy C to the host");
+    if ((ce = cudaStreamSynchronize(s->e2e_stream2)) != cudaSuccess)
+      return cuda_fail(ce, "synchronize");
+  }
   if ((ce = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(ce, "synchronize");
   return AAT_OK;
+}
+
+int64_t aat_modp_host_d2h_bytes(int64_t n, uint32_t flags) {
+  if (n <= 0) return 0;
+  if (flags & AAT_ZERO_UPPER) return n * n * 4;
+  return 4 * low_band_entries(0, n);
 }
 
 int aat_gemm_modp(const int32_t *X, int64_t ldx, const int32_t *Y, int64_t ldy, int64_t m,
@@ -843,6 +924,8 @@ void aat_shutdown(void) {
     if (s.e2e_a) cudaFree(s.e2e_a);
     if (s.e2e_c) cudaFree(s.e2e_c);
     if (s.e2e_stream) cudaStreamDestroy(s.e2e_stream);
+    if (s.e2e_stream2) cudaStreamDestroy(s.e2e_stream2);
+    if (s.e2e_split) cudaEventDestroy(s.e2e_split);
     cudaSetDevice(cur);
   }
   g_states.clear();

@@ -18,9 +18,11 @@
 //
 // Kernel organisation (one CTA per SM, persistent over a tile list):
 //   warp 0        TMA producer: 128x64 tile of X_i and 256x64 tile of Y_j per
-//                 stage into 128B-swizzled shared memory (4 stages)
+//                 stage into 128B-swizzled shared memory (4 stages); in the
+//                 CTA-pair form 128x64 of each per CTA (6 stages)
 //   warp 1        TMEM allocator + single-thread tcgen05.mma issuer,
-//                 M=128 N=256 K=16 per instruction, FP32 accumulator in one of
+//                 M=128 N=256 K=16 per instruction (CTA pair: M=256 across
+//                 the pair, issued by the leader), FP32 accumulator in one of
 //                 two 256-column TMEM buffers (double buffered per chunk)
 //   warps 2..9    epilogue: tcgen05.ld of the finished chunk, float -> int32,
 //                 accumulate; mod-p Horner step at digit-pair boundaries;
@@ -48,21 +50,12 @@ namespace {
 
 using namespace tc;
 
-constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
-constexpr int A_BYTES = BM * BK * 2;
-constexpr int B_BYTES = BN * BK * 2;
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int BM = 128, BN = 256, BK = 64;
 constexpr int EPI_WARPS = 8;
 constexpr int THREADS = 64 + EPI_WARPS * 32;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t ACC_COLS = 256;
 constexpr int MAX_GROUPS = 160;
-constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + 256;
-
-// Instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator (bit 4),
-// A and B BF16 (bits 7, 10), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) |
-                           ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 
 struct Group {
   int16_t xp, yp;   // digit planes of X and Y
@@ -84,7 +77,7 @@ struct alignas(64) BatchProb {
 
 struct Params {
   CUtensorMap tmx;  // 3D {K, rows, plane}, box {64, 128, 1}
-  CUtensorMap tmy;  // 3D {K, rows, plane}, box {64, 256, 1}
+  CUtensorMap tmy;  // 3D {K, rows, plane}, box {64, 256, 1} (CTA pair: {64, 128, 1})
   Group g[MAX_GROUPS];
   int ng;
   int32_t *out;
@@ -214,13 +207,41 @@ __device__ __forceinline__ int32_t mulmod_shoup(int32_t a, uint32_t w, uint32_t 
 
 // ------------------------------------------------------------------ kernel
 
-template <bool BATCH>
+// Two forms of the kernel share the code below.
+//   one CTA  (PAIR = false): a 128 x 256 output tile per CTA; each stage holds
+//            128 rows of X and 256 rows of Y (48 KB), 4 stages.
+//   CTA pair (PAIR = true):  a 256 x 256 output tile per cluster of 2 CTAs,
+//            tcgen05 cta_group::2: each CTA holds 128 rows of X and 128 rows
+//            of Y per stage (32 KB), so 6 stages fit and the copies in
+//            flight cover more of the DRAM latency; the leader CTA (rank 0)
+//            issues M=256 N=256 MMAs that read both CTAs' shared memory and
+//            write 128 TMEM lanes in each CTA.
+template <bool PAIR>
+struct Shape {
+  static constexpr int TM = PAIR ? 256 : 128;     // output tile rows
+  static constexpr int YROWS = PAIR ? 128 : 256;  // rows of Y per CTA and stage
+  static constexpr int STAGES = PAIR ? 6 : 4;
+  static constexpr int A_BYTES = BM * BK * 2;
+  static constexpr int B_BYTES = YROWS * BK * 2;
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + 256;
+  // Instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator
+  // (bit 4), A and B BF16 (bits 7, 10), both K-major, N >> 3 at bit 17,
+  // M >> 4 at bit 24.
+  static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) |
+                                    ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+};
+
+template <bool BATCH, bool PAIR>
 __global__ void __launch_bounds__(THREADS, 1) leaf_tc_kernel(const __grid_constant__ Params P) {
+  using S = Shape<PAIR>;
+  constexpr int STAGES = S::STAGES;
   extern __shared__ uint8_t smem_raw[];
-  // 1024-byte alignment of the shared-window address (128B-swizzle atoms)
+  // 1024-byte alignment of the shared-window address (128B-swizzle atoms);
+  // the same offset in both CTAs of a pair, as the pair MMA requires
   uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   const uint32_t sbase = smem_u32(smem);
-  uint64_t *bars = (uint64_t *)(smem + (size_t)STAGES * STAGE_BYTES);
+  uint64_t *bars = (uint64_t *)(smem + (size_t)STAGES * S::STAGE_BYTES);
   const uint32_t bar0 = smem_u32(bars);
 #define FULL(s) (bar0 + 8u * (uint32_t)(s))
 #define EMPTY(s) (bar0 + 8u * (uint32_t)(STAGES + (s)))
@@ -230,6 +251,15 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_tc_kernel(const __grid_consta
   uint32_t *tmem_slot = (uint32_t *)(bars + 2 * STAGES + 5);
   volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
 
+  // work units: tiles are taken round robin by CTAs (one CTA) or clusters
+  uint32_t rank = 0, unit0 = blockIdx.x, nunits = gridDim.x;
+  if constexpr (PAIR) {
+    rank = cluster_ctarank();
+    unit0 = cluster_id_x();
+    nunits = ncluster_x();
+  }
+  const bool leader = (rank == 0);
+
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -238,7 +268,7 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_tc_kernel(const __grid_consta
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(AFULL(b), 1);
-      mbar_init(AEMPTY(b), EPI_WARPS);
+      mbar_init(AEMPTY(b), PAIR ? 2 * EPI_WARPS : EPI_WARPS);
     }
     mbar_init(DONE, 1);
     *abort_flag = 0;
@@ -246,14 +276,25 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_tc_kernel(const __grid_consta
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(tmem_slot)),
-                 "r"(TMEM_COLS)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    if constexpr (PAIR) {
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       smem_u32(tmem_slot)),
+                   "r"(TMEM_COLS)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    } else {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       smem_u32(tmem_slot)),
+                   "r"(TMEM_COLS)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
     tc_fence_before();
   }
   __syncthreads();
+  // the peer's barriers must be initialised before any copy or arrival
+  // reaches them
+  if constexpr (PAIR) cluster_sync();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
@@ -264,19 +305,30 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_tc_kernel(const __grid_consta
       uint32_t ph = 0;
       int issued = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
+      // both CTAs' copies of a stage complete on the leader's FULL barrier
+      const uint32_t full0 = PAIR ? map_to_rank(FULL(0), 0) : FULL(0);
+      for (int t = (int)unit0; t < P.ntiles && ok; t += (int)nunits) {
         const TileView v = tile_view<BATCH>(P, t);
+        const int rowx = v.I * S::TM + (int)rank * BM;
+        const int rowy = v.J * BN + (int)rank * S::YROWS;
         for (int gi = 0; gi < v.ng && ok; ++gi) {
           const Group g = v.g[gi];
           for (int kb = g.kb0; kb < g.kb1; ++kb) {
-            if (!wait_bounded(EMPTY(stage), ph ^ 1u, abort_flag, P.status)) {
+            if (!wait_bounded<PAIR>(EMPTY(stage), ph ^ 1u, abort_flag, P.status)) {
               ok = false;
               break;
             }
-            mbar_expect_tx(FULL(stage), (uint32_t)STAGE_BYTES);
-            const uint32_t sa = sbase + (uint32_t)(stage * STAGE_BYTES);
-            tma_load_3d(sa, v.tmx, FULL(stage), kb * BK, v.I * BM, g.xp);
-            tma_load_3d(sa + A_BYTES, v.tmy, FULL(stage), kb * BK, v.J * BN, g.yp);
+            const uint32_t sa = sbase + (uint32_t)(stage * S::STAGE_BYTES);
+            const uint32_t fb = full0 + 8u * (uint32_t)stage;
+            if constexpr (PAIR) {
+              if (leader) mbar_expect_tx(FULL(stage), (uint32_t)(2 * S::STAGE_BYTES));
+              tma_load_3d_pair(sa, v.tmx, fb, kb * BK, rowx, g.xp);
+              tma_load_3d_pair(sa + S::A_BYTES, v.tmy, fb, kb * BK, rowy, g.yp);
+            } else {
+              mbar_expect_tx(FULL(stage), (uint32_t)S::STAGE_BYTES);
+              tma_load_3d(sa, v.tmx, fb, kb * BK, rowx, g.xp);
+              tma_load_3d(sa + S::A_BYTES, v.tmy, fb, kb * BK, rowy, g.yp);
+            }
             ++issued;
             if (++stage == STAGES) {
               stage = 0;
@@ -287,64 +339,84 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_tc_kernel(const __grid_consta
       }
       if (!ok) {
         // let the copies in flight land before the CTA exits
-        int s = stage;
-        uint32_t q = ph;
-        for (int i = 0; i < STAGES && i < issued; ++i) {
-          if (--s < 0) {
-            s = STAGES - 1;
-            q ^= 1u;
+        if (!PAIR || leader) {
+          int s = stage;
+          uint32_t q = ph;
+          for (int i = 0; i < STAGES && i < issued; ++i) {
+            if (--s < 0) {
+              s = STAGES - 1;
+              q ^= 1u;
+            }
+            wait_quiet(FULL(s), q);
           }
-          wait_quiet(FULL(s), q);
+        } else {
+          // the peer's copies complete on the leader's barriers: give them
+          // a fixed 20 ms to land
+          const unsigned long long t0 = gtimer();
+          while (gtimer() - t0 < 20000000ull) {
+          }
         }
       }
     }
   } else if (warp == 1) {
     // ---------------------------------------------------------- MMA issuer
-    if (lane == 0) {
+    if (lane == 0 && leader) {
       int stage = 0;
       uint32_t ph = 0, chunk = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
+      for (int t = (int)unit0; t < P.ntiles && ok; t += (int)nunits) {
         const int ng = tile_ng<BATCH>(P, t);
         for (int gi = 0; gi < ng && ok; ++gi) {
           const Group g = tile_group<BATCH>(P, t, gi);
           for (int kb = g.kb0; kb < g.kb1 && ok;) {
             const int kend = min(kb + g.kchunk, g.kb1);
             const uint32_t buf = chunk & 1u, use = chunk >> 1;
-            if (!wait_bounded(AEMPTY(buf), (use & 1u) ^ 1u, abort_flag, P.status)) {
+            if (!wait_bounded<PAIR>(AEMPTY(buf), (use & 1u) ^ 1u, abort_flag, P.status)) {
               ok = false;
               break;
             }
             tc_fence_after();
             const uint32_t dt = tmem + buf * ACC_COLS;
             for (int k = kb; k < kend; ++k) {
-              if (!wait_bounded(FULL(stage), ph, abort_flag, P.status)) {
+              if (!wait_bounded<PAIR>(FULL(stage), ph, abort_flag, P.status)) {
                 ok = false;
                 break;
               }
               tc_fence_after();
-              const uint32_t sa = sbase + (uint32_t)(stage * STAGE_BYTES);
-              const uint32_t sb = sa + A_BYTES;
+              const uint32_t sa = sbase + (uint32_t)(stage * S::STAGE_BYTES);
+              const uint32_t sb = sa + S::A_BYTES;
 #pragma unroll
               for (int s = 0; s < BK / 16; ++s) {
-                tc_mma(dt, sw128_desc(sa + 32u * s), sw128_desc(sb + 32u * s), IDESC,
-                       (k > kb || s > 0) ? 1u : 0u);
+                const uint32_t acc = (k > kb || s > 0) ? 1u : 0u;
+                if constexpr (PAIR)
+                  tc_mma_pair(dt, sw128_desc(sa + 32u * s), sw128_desc(sb + 32u * s), S::IDESC, acc);
+                else
+                  tc_mma(dt, sw128_desc(sa + 32u * s), sw128_desc(sb + 32u * s), S::IDESC, acc);
               }
-              tc_commit(EMPTY(stage));
+              if constexpr (PAIR)
+                tc_commit_pair(EMPTY(stage), 3);
+              else
+                tc_commit(EMPTY(stage));
               if (++stage == STAGES) {
                 stage = 0;
                 ph ^= 1u;
               }
             }
             if (!ok) break;
-            tc_commit(AFULL(buf));
+            if constexpr (PAIR)
+              tc_commit_pair(AFULL(buf), 3);
+            else
+              tc_commit(AFULL(buf));
             ++chunk;
             kb = kend;
           }
         }
       }
       if (!ok) {
-        tc_commit(DONE);
+        if constexpr (PAIR)
+          tc_commit_pair(DONE, 1);
+        else
+          tc_commit(DONE);
         wait_quiet(DONE, 0);
       }
     }
@@ -354,10 +426,12 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_tc_kernel(const __grid_consta
     const int quarter = warp & 3;  // TMEM lanes [32 quarter, 32 quarter + 32)
     const int chalf = e >> 2;      // columns [128 chalf, 128 chalf + 128)
     const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+    // the leader's MMA waits until the epilogues of both CTAs drained a buffer
+    const uint32_t aempty0 = PAIR ? map_to_rank(AEMPTY(0), 0) : AEMPTY(0);
     uint32_t chunk = 0;
     bool ok = true;
     ModP m = P.m;
-    for (int t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
+    for (int t = (int)unit0; t < P.ntiles && ok; t += (int)nunits) {
       if constexpr (BATCH) m = tile_modp<BATCH>(P, t);
       const int ng = tile_ng<BATCH>(P, t);
       int32_t acc[128];
@@ -372,7 +446,7 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_tc_kernel(const __grid_consta
         for (int kb = g.kb0; kb < g.kb1;) {
           const int kend = min(kb + g.kchunk, g.kb1);
           const uint32_t buf = chunk & 1u, use = chunk >> 1;
-          if (!wait_bounded(AFULL(buf), use & 1u, abort_flag, P.status)) {
+          if (!wait_bounded<PAIR>(AFULL(buf), use & 1u, abort_flag, P.status)) {
             ok = false;
             break;
           }
@@ -388,14 +462,19 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_tc_kernel(const __grid_consta
           tmem_drain16<112>(ta + 112u, acc);
           tc_fence_before();
           __syncwarp();
-          if (lane == 0) mbar_arrive(AEMPTY(buf));
+          if (lane == 0) {
+            if constexpr (PAIR)
+              mbar_arrive_cluster(aempty0 + 8u * buf);
+            else
+              mbar_arrive(AEMPTY(buf));
+          }
           ++chunk;
           kb = kend;
         }
       }
       if (!ok) break;
       const int2 ij = tile_ij<BATCH>(P, t);
-      const int64_t row = (int64_t)ij.x * BM + quarter * 32 + lane;
+      const int64_t row = (int64_t)ij.x * S::TM + (int64_t)rank * BM + quarter * 32 + lane;
       const int64_t col0 = (int64_t)ij.y * BN + chalf * 128;
       // final value, canonical, in place (the last digit pair has weight 1)
 #pragma unroll
@@ -429,11 +508,19 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_tc_kernel(const __grid_consta
   }
 
   __syncthreads();
+  // no CTA of a pair leaves (or frees TMEM) while its peer may still touch
+  // its shared memory or tensor memory
+  if constexpr (PAIR) cluster_sync();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(TMEM_COLS)
-                 : "memory");
+    if constexpr (PAIR)
+      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                   "r"(TMEM_COLS)
+                   : "memory");
+    else
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                   "r"(TMEM_COLS)
+                   : "memory");
   }
 #undef FULL
 #undef EMPTY
@@ -446,8 +533,9 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_tc_kernel(const __grid_consta
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 std::mutex g_mu;
-std::map<std::tuple<int, int64_t, int64_t, int>, std::pair<int2 *, int>> g_tiles;
+std::map<std::tuple<int, int64_t, int64_t, int, int>, std::pair<int2 *, int>> g_tiles;
 std::map<int, bool> g_attr_set;
+std::map<int, int> g_pair_units;  // co-resident CTA pairs per device
 
 cudaError_t get_encode() {
   if (g_encode) return cudaSuccess;
@@ -482,25 +570,26 @@ uint32_t pow2mod(uint64_t e, uint32_t p) {
   return (uint32_t)r;
 }
 
-// Tile order: super-blocks of 16 x 8 tiles (2048 x 2048 outputs) swept
-// row-major, tiles inside a super-block row-major, so that the CTAs running
-// at the same time share rows of X and columns of Y in L2.
-cudaError_t get_tiles(int dev, int64_t M, int64_t N, int lower, int2 **out, int *count) {
-  auto key = std::make_tuple(dev, M, N, lower);
+// Tile order: super-blocks of 2048 x 2048 outputs (16 x 8 tiles of 128 x 256,
+// or 8 x 8 of 256 x 256) swept row-major, tiles inside a super-block
+// row-major, so that the CTAs running at the same time share rows of X and
+// columns of Y in L2.  `tm` is the tile height (128 or 256).
+cudaError_t get_tiles(int dev, int64_t M, int64_t N, int lower, int tm, int2 **out, int *count) {
+  auto key = std::make_tuple(dev, M, N, lower, tm);
   auto it = g_tiles.find(key);
   if (it != g_tiles.end()) {
     *out = it->second.first;
     *count = it->second.second;
     return cudaSuccess;
   }
-  const int64_t TI = (M + BM - 1) / BM, TJ = (N + BN - 1) / BN;
-  const int64_t SI = 16, SJ = 8;
+  const int64_t TI = (M + tm - 1) / tm, TJ = (N + BN - 1) / BN;
+  const int64_t SI = 2048 / tm, SJ = 8;
   std::vector<int2> v;
   for (int64_t bi = 0; bi < TI; bi += SI)
     for (int64_t bj = 0; bj < TJ; bj += SJ)
       for (int64_t i = bi; i < std::min(TI, bi + SI); ++i)
         for (int64_t j = bj; j < std::min(TJ, bj + SJ); ++j) {
-          if (lower && j * BN > i * BM + BM - 1) continue;
+          if (lower && j * BN > i * tm + tm - 1) continue;
           v.push_back(make_int2((int)i, (int)j));
         }
   int2 *d = nullptr;
@@ -618,6 +707,43 @@ bool build_groups(const TcLeafArgs &a, const ModP &m, Group *out, int *ng_out, i
   return true;
 }
 
+// Co-resident CTA pairs of the pair kernel on this device (0: none).
+int pair_units(int dev) {
+  auto it = g_pair_units.find(dev);
+  if (it != g_pair_units.end()) return it->second;
+  int units = 0;
+  if (cudaFuncSetAttribute(leaf_tc_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)Shape<true>::SMEM) == cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(2, 1, 1);
+    cfg.blockDim = dim3(THREADS, 1, 1);
+    cfg.dynamicSmemBytes = Shape<true>::SMEM;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaOccupancyMaxActiveClusters(&units, leaf_tc_kernel<false, true>, &cfg) != cudaSuccess)
+      units = 0;
+  }
+  cudaGetLastError();
+  g_pair_units[dev] = units;
+  return units;
+}
+
+// AAT_LEAF_PAIR=0 keeps every leaf on the one-CTA form, =1 puts every leaf
+// with at least 256 rows on the CTA-pair form; unset: the pair form when its
+// tiles fill every co-resident pair at least once.
+int pair_override() {
+  static const int v = [] {
+    const char *e = getenv("AAT_LEAF_PAIR");
+    return e ? atoi(e) : -1;
+  }();
+  return v;
+}
+
 }  // namespace
 
 cudaError_t launch_leaf_tc(const TcLeafArgs &a, const ModP &m, cudaStream_t st) {
@@ -634,10 +760,22 @@ cudaError_t launch_leaf_tc(const TcLeafArgs &a, const ModP &m, cudaStream_t st) 
   int dev = 0;
   cudaGetDevice(&dev);
 
+  // the form: CTA pairs when there are enough 256 x 256 tiles to keep every
+  // co-resident pair busy
+  const int units = pair_units(dev);
+  bool pair = false;
+  if (units > 0 && a.M >= 256) {
+    const int64_t pt = ((a.M + 255) / 256) * ((a.N + BN - 1) / BN);
+    const int ov = pair_override();
+    pair = ov >= 0 ? ov > 0 : (a.lower ? pt / 2 : pt) >= units;
+  }
+  const int tm = pair ? Shape<true>::TM : Shape<false>::TM;
+
   Params *P = new Params;
   std::memset(P, 0, sizeof(Params));
   if ((e = encode_planes(&P->tmx, a.x, BM)) != cudaSuccess ||
-      (e = encode_planes(&P->tmy, a.y, BN)) != cudaSuccess) {
+      (e = encode_planes(&P->tmy, a.y, pair ? Shape<true>::YROWS : Shape<false>::YROWS)) !=
+          cudaSuccess) {
     delete P;
     return e;
   }
@@ -657,28 +795,44 @@ cudaError_t launch_leaf_tc(const TcLeafArgs &a, const ModP &m, cudaStream_t st) 
   P->status = device_status_ptr();
   int2 *tiles = nullptr;
   int nt = 0;
-  if ((e = get_tiles(dev, a.M, a.N, a.lower, &tiles, &nt)) != cudaSuccess) {
+  if ((e = get_tiles(dev, a.M, a.N, a.lower, tm, &tiles, &nt)) != cudaSuccess) {
     delete P;
     return e;
   }
   P->tiles = tiles;
   P->ntiles = nt;
   if (!g_attr_set[dev]) {
-    e = cudaFuncSetAttribute(leaf_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)SMEM_BYTES);
+    e = cudaFuncSetAttribute(leaf_tc_kernel<false, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Shape<false>::SMEM);
     if (e != cudaSuccess) { delete P; return e; }
     g_attr_set[dev] = true;
   }
   int sms = 148;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = std::max(1, std::min(nt, sms));
   if (nt > 0) {
     // algorithmic tensor work: one BF16 product of the ring MACs per plane
     // product with a non-zero weight
     const double macs =
         a.lower ? 0.5 * (double)a.M * (double)(a.M + 1) * a.K : (double)a.M * a.N * a.K;
     ProfScope prof(AAT_K_LEAF_TC, st, 2.0 * nprod * macs);
-    leaf_tc_kernel<false><<<grid, THREADS, SMEM_BYTES, st>>>(*P);
+    if (pair) {
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = 2;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3(2 * std::max(1, std::min(nt, units)), 1, 1);
+      cfg.blockDim = dim3(THREADS, 1, 1);
+      cfg.dynamicSmemBytes = Shape<true>::SMEM;
+      cfg.stream = st;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      e = cudaLaunchKernelEx(&cfg, leaf_tc_kernel<false, true>, *P);
+      if (e != cudaSuccess) { delete P; return e; }
+    } else {
+      leaf_tc_kernel<false, false><<<std::max(1, std::min(nt, sms)), THREADS, Shape<false>::SMEM, st>>>(*P);
+    }
   }
   delete P;
   return cudaGetLastError();
@@ -770,9 +924,9 @@ cudaError_t leaf_tc_batch_launch(const LeafBatch &lb, cudaStream_t st) {
     std::lock_guard<std::mutex> lock(g_mu);
     static std::map<int, bool> attr;
     if (!attr[dev]) {
-      cudaError_t e = cudaFuncSetAttribute(leaf_tc_kernel<true>,
+      cudaError_t e = cudaFuncSetAttribute(leaf_tc_kernel<true, false>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)SMEM_BYTES);
+                                           (int)Shape<false>::SMEM);
       if (e != cudaSuccess) return e;
       attr[dev] = true;
     }
@@ -788,7 +942,7 @@ cudaError_t leaf_tc_batch_launch(const LeafBatch &lb, cudaStream_t st) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   {
     ProfScope prof(AAT_K_LEAF_TC, st, L->work);
-    leaf_tc_kernel<true><<<std::max(1, std::min(L->ntiles, sms)), THREADS, SMEM_BYTES, st>>>(*P);
+    leaf_tc_kernel<true, false><<<std::max(1, std::min(L->ntiles, sms)), THREADS, Shape<false>::SMEM, st>>>(*P);
   }
   delete P;
   return cudaGetLastError();
@@ -810,6 +964,7 @@ void leaf_tc_release() {
     if (kv.second.first) cudaFree(kv.second.first);
   g_tiles.clear();
   g_attr_set.clear();
+  g_pair_units.clear();
 }
 
 }  // namespace aat
@@ -987,15 +1142,15 @@ extern "C" AAT_API int aat_gemm_modp_noalloc(const int32_t *X, int64_t ldx, cons
   P.tiles = tiles_dev;
   P.ntiles = (int)(TI * TJ);
   if (!g_attr_set[dev]) {
-    ce = cudaFuncSetAttribute(leaf_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)SMEM_BYTES);
+    ce = cudaFuncSetAttribute(leaf_tc_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)Shape<false>::SMEM);
     if (ce != cudaSuccess) return report_error(AAT_ECUDA, cudaGetErrorString(ce));
     g_attr_set[dev] = true;
   }
   int sms = 148;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = std::max(1, std::min(P.ntiles, sms));
-  leaf_tc_kernel<false><<<grid, THREADS, SMEM_BYTES, st>>>(P);
+  leaf_tc_kernel<false, false><<<grid, THREADS, Shape<false>::SMEM, st>>>(P);
   ce = cudaGetLastError();
   return ce == cudaSuccess ? AAT_OK : report_error(AAT_ECUDA, cudaGetErrorString(ce));
 }

@@ -257,6 +257,35 @@ def test_aat_modp_host_end_to_end(lib):
     assert low_equal(C, oracle.aat_modp_low(A, p))
 
 
+@pytest.mark.parametrize("levels", [1, 2])
+def test_aat_modp_host_early_rows_overlap(lib, levels):
+    """Pinned buffers, a recursion level: rows below n/2 are copied back on a
+    second stream while the last product runs; the lower triangle must equal
+    the device path's and sampled oracle entries (band edges, the split)."""
+    p = 2**31 - 1
+    n, k = 1536, 1024
+    A = synth.residues(91, (n, k), p, balanced=True)
+    Ah = torch.from_numpy(A).pin_memory()
+    Ch = torch.full((n, n), -7, dtype=torch.int32).pin_memory()
+    lib.aat_modp_host(Ah, p, C=Ch, levels=levels)
+    got = Ch.numpy()
+    ref_dev = host(lib.aat_modp(dev(A), p, levels=levels))
+    assert low_equal(got, ref_dev)
+    rows = sorted({0, 1, 511, 512, 513, n // 2 - 1, n // 2, n // 2 + 1, 1023, 1024, n - 1})
+    ij = np.array([(i, j) for i in rows for j in sorted({0, i // 2, i})], dtype=np.int64)
+    ref = oracle.aat_modp_entries(A, p, ij)
+    assert np.array_equal(got[ij[:, 0], ij[:, 1]].astype(np.int64), np.asarray(ref, dtype=np.int64))
+
+
+def test_aat_modp_host_zero_upper_copies_everything(lib):
+    p = 131071
+    A = synth.residues(92, (600, 400), p)
+    C = np.full((600, 600), 5, dtype=np.int32)
+    lib.aat_modp_host(A, p, C=C, flags=lib.AAT_ZERO_UPPER, levels=1)
+    assert low_equal(C, oracle.aat_modp_low(A, p))
+    assert not np.triu(C, 1).any()
+
+
 # -------------------------------------------------------- full-size cases
 
 def _sample_pairs(n, levels, count, seed):

@@ -210,3 +210,20 @@ def test_leaf_group_plan_reproduces_the_product(p, K, plain):
             acc += chunk
         assert abs(acc) < 2**31
     assert acc % p == sum(a * c for a, c in zip(x, y)) % p
+
+
+def test_host_copy_volume_is_the_lower_triangle_in_bands():
+    """aat_modp_host copies back only the lower triangle, in bands of 512
+    rows (band [a, b) carries columns [0, b)); with AAT_ZERO_UPPER the whole
+    matrix."""
+    import paper_2101_01025_gb300 as aat
+    for n in (1, 7, 511, 512, 513, 1000, 16384):
+        expect = 0
+        for a in range(0, n, 512):
+            b = min(n, a + 512)
+            expect += 4 * b * (b - a)
+        got = aat.aat_modp_host_d2h_bytes(n)
+        assert got == expect
+        assert 4 * n * (n + 1) // 2 <= got <= 4 * n * n
+        assert aat.aat_modp_host_d2h_bytes(n, aat.AAT_ZERO_UPPER) == 4 * n * n
+    assert aat.aat_modp_host_d2h_bytes(0) == 0
