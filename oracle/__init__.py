@@ -102,6 +102,18 @@ def aat_modp_low(A, p: int, threads: int = 0) -> np.ndarray:
     return C
 
 
+def syrk_modp_low(alpha: int, A, beta: int, C, p: int, threads: int = 0) -> np.ndarray:
+    """Low(alpha A A^T + beta C) mod p, canonical, strict upper part zero:
+    the SYRK update C <- alpha A A^T + beta C restricted to the lower
+    triangle (Sec. 7, Table 4), written out from its definition: the exact
+    product Low(A A^T) mod p, then each lower entry combined in exact
+    integer arithmetic.  C may hold any residues (its upper part is ignored)."""
+    P = aat_modp_low(A, p, threads).astype(np.int64)
+    Cl = np.tril(np.asarray(C, dtype=np.int64) % p)
+    out = ((alpha % p) * P + (beta % p) * Cl) % p
+    return np.tril(out).astype(np.uint32)
+
+
 def aat_modp_entries(A, p: int, ij, threads: int = 0) -> np.ndarray:
     """(A A^T)[i, j] mod p at the given (i, j) pairs (array of shape (t, 2))."""
     A = _i32(A)

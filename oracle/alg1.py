@@ -11,6 +11,9 @@ additions that form U1..U5.  The recursion stops after ``levels`` levels,
 where Low(A A^T) is taken from its definition.  It returns the intermediate
 blocks as well, so that tests can check the proof identities of Theorem 3.1.
 
+``syrk_table4`` takes the steps of the SYRK schedule of Table 4 (Sec. 7),
+one level, on the locations the table names.
+
 ``two_m`` takes the steps of Algorithm 2 (Sec. 6.1) with K = R, E = C.
 """
 from __future__ import annotations
@@ -99,6 +102,71 @@ def alg1_low_aat(A, p, ykind, ya, yb, levels, trace=None):
                           P4=P4, P5=P5, U1=U1, U2=U2, U3=U3_low, U4=U4,
                           U5=U5_low, Y=Y))
     return C
+
+
+def syrk_table4(alpha, A, beta, C, p, ykind, ya, yb, save_diagonal=True):
+    """Low(alpha A A^T + beta C) mod p by the schedule of Table 4 (Sec. 7),
+    one level of Algorithm 1 with the leaves from their definitions.
+
+    The locations of Table 4 are modelled as blocks of one n x n array M
+    (initially C) plus an h x h array tmp, and each step reads and writes only
+    the locations the table names, in its order.  Reading: Up(C11) includes
+    the diagonal (Sec. 2), which C11 still needs for P2 = alpha A12 A12^T +
+    beta C11, so the diagonal of Low(C22) is kept in a separate h-vector
+    (``save_diagonal``); with ``save_diagonal=False`` the schedule is taken
+    literally (Up(C11) <- Low(C22)^T over the diagonal), which loses C11's
+    diagonal (tests show that it does)."""
+    A = _obj(A) % p
+    n, k = A.shape
+    h, kap = n // 2, k // 2
+    al, be = alpha % p, beta % p
+    M = _obj(C) % p
+    A11, A12 = A[:h, :kap], A[:h, kap:]
+    A21, A22 = A[h:, :kap], A[h:, kap:]
+    Y = dense_y(ykind, ya, yb, p, kap)
+    C11 = lambda: M[:h, :h]          # noqa: E731  views of the locations
+    C12 = lambda: M[:h, h:]          # noqa: E731
+    C21 = lambda: M[h:, :h]          # noqa: E731
+    C22 = lambda: M[h:, h:]          # noqa: E731
+    tmp = np.zeros((h, kap if kap > h else h), dtype=object)
+    # left column of Table 4
+    S1 = ((A21 - A11) @ Y) % p                       # S1 -> tmp
+    tmp[:, :kap] = S1
+    C12()[:, :kap] = (A22 - A21 @ Y) % p              # S2 -> C12
+    S2 = C12()[:, :kap].copy()
+    dg = [C22()[i, i] for i in range(h)]
+    for i in range(h):                                # Up(C11) <- Low(C22)^T
+        for j in range(i, h):
+            if i == j and save_diagonal:
+                continue
+            C11()[i, j] = C22()[j, i]
+    C22()[:, :] = (al * (S2 @ S1.T)) % p             # P4^T = alpha S2 S1^T -> C22
+    tmp[:, :kap] = (tmp[:, :kap] - A22) % p           # S3 = S1 - A22 -> tmp
+    S3 = tmp[:, :kap].copy()
+    C12()[:, :] = low((al * (S3 @ S3.T)) % p)         # P5 = alpha S3 S3^T -> C12
+    tmp[:, :kap] = (tmp[:, :kap] + A12) % p           # S4 = S3 + A12 -> tmp
+    S4 = tmp[:, :kap].copy()
+    C21()[:, :] = (al * (A22 @ S4.T) + be * C21()) % p  # P3 -> C21
+    # right column of Table 4
+    tmp = np.zeros((h, h), dtype=object)
+    tmp[:, :] = low((al * (A11 @ A11.T)) % p)         # P1 -> tmp
+    U1 = low((tmp + C12()) % p)                       # U1 = P1 + P5 -> C12
+    for i in range(h):                                # Up(U1) <- Low(U1)^T
+        for j in range(i + 1, h):
+            U1[i, j] = U1[j, i]
+    C12()[:, :] = U1
+    P4T = C22().copy()
+    C12()[:, :] = (C12() + P4T.T) % p                 # U2 = U1 + P4 -> C12
+    U2 = C12().copy()
+    C21()[:, :] = (U2 + C21()) % p                    # U4 = U2 + P3 -> C21
+    old22 = np.zeros((h, h), dtype=object)            # beta Up(C11)^T (+ saved diagonal)
+    for i in range(h):
+        for j in range(i + 1):
+            old22[i, j] = (dg[i] if (i == j and save_diagonal) else C11()[j, i])
+    C22()[:, :] = low((U2 + P4T + be * old22) % p)    # U5 -> C22
+    C11()[:, :] = low((al * (A12 @ A12.T) + be * C11()) % p)  # P2 -> C11
+    C11()[:, :] = low((tmp + C11()) % p)              # U3 = P1 + P2 -> C11
+    return low(M)
 
 
 def two_m(Are, Aim, conj=True):

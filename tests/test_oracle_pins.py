@@ -452,3 +452,82 @@ def test_two_m_algorithm():
     assert np.allclose(re + 1j * im, A @ A.conj().T)
     re, im = alg1.two_m(Are, Aim, conj=False)
     assert np.allclose(re + 1j * im, A @ A.T)
+
+
+# ------------------------------------------------------------ SYRK (Sec. 7)
+
+def _brute_syrk(alpha, A, beta, C, p):
+    """alpha sum_l a_il a_jl + beta c_ij for i >= j, one entry at a time."""
+    n, k = len(A), len(A[0])
+    out = np.zeros((n, n), dtype=np.int64)
+    for i in range(n):
+        for j in range(i + 1):
+            acc = beta * int(C[i][j])
+            for l in range(k):
+                acc += alpha * int(A[i][l]) * int(A[j][l])
+            out[i, j] = acc % p
+    return out
+
+
+@pytest.mark.parametrize("p", [3, 5, 7])
+def test_syrk_oracle_exhaustive_tiny(p):
+    """Every alpha, beta and every 2 x 2 lower C with a fixed 2 x 2 A; the
+    upper triangle of C must not matter (an oracle that read C^T or the upper
+    part fails)."""
+    A = np.array([[1, p - 1], [2 % p, 1]], dtype=np.int32)
+    for alpha, beta in itertools.product(range(p), range(p)):
+        for c00, c10, c11, c01 in itertools.product(range(p), repeat=4):
+            C = np.array([[c00, c01], [c10, c11]], dtype=np.int64)
+            got = oracle.syrk_modp_low(alpha, A, beta, C, p).astype(np.int64)
+            assert np.array_equal(got, _brute_syrk(alpha, A, beta, C, p))
+
+
+def test_syrk_oracle_reduces_and_is_linear():
+    p = 131071
+    rng = np.random.default_rng(5)
+    A = synth.residues(31, (9, 7), p)
+    C = rng.integers(0, p, (9, 9))
+    base = oracle.aat_modp_low(A, p).astype(np.int64)
+    assert np.array_equal(oracle.syrk_modp_low(1, A, 0, C, p).astype(np.int64), base)
+    assert np.array_equal(oracle.syrk_modp_low(0, A, 1, C, p).astype(np.int64), np.tril(C))
+    a, b = 12345, 777
+    got = oracle.syrk_modp_low(a, A, b, C, p).astype(np.int64)
+    assert np.array_equal(got, np.tril((a * base + b * C) % p))
+    # alpha = -1, beta = 1 on C = Low(A A^T): the zero matrix
+    assert not oracle.syrk_modp_low(p - 1, A, 1, base, p).any()
+    # all-ones A (k columns): alpha k + beta c_ij
+    ones = np.ones((5, 11), dtype=np.int32)
+    got = oracle.syrk_modp_low(3, ones, 2, np.full((5, 5), 4), p).astype(np.int64)
+    assert np.array_equal(got, np.tril(np.full((5, 5), (3 * 11 + 2 * 4) % p)))
+
+
+@pytest.mark.parametrize("p", [13, 17, 131071, 65521])
+def test_syrk_table4_schedule_equals_definition(p):
+    """The Table 4 schedule (one level of Algorithm 1, the locations the
+    table names) gives Low(alpha A A^T + beta C), for Y of both kinds."""
+    ykind, ya, yb = oracle.skew_unitary_params(p)
+    # Table 4 holds for k <= n (S2 goes into C12)
+    A = synth.residues(41, (8, 4 if ykind == 1 else 8), p)
+    C = synth.residues(42, (8, 8), p).astype(np.int64)
+    for alpha, beta in [(1, 0), (1, 1), (5, 3), (p - 1, 2)]:
+        got = np.asarray(alg1.syrk_table4(alpha, A, beta, C, p, ykind, ya, yb), dtype=np.int64)
+        want = oracle.syrk_modp_low(alpha, A, beta, C, p).astype(np.int64)
+        assert np.array_equal(got, want), (alpha, beta)
+
+
+def test_syrk_table4_literal_reading_loses_the_diagonal():
+    """Taken literally, Up(C11) <- Low(C22)^T (Up includes the diagonal,
+    Sec. 2) overwrites C11's diagonal before P2 = alpha A12 A12^T + beta C11
+    reads it: the result is wrong whenever beta != 0 and the diagonals of
+    C11 and C22 differ.  Hence the separate diagonal vector."""
+    p = 131071
+    ykind, ya, yb = oracle.skew_unitary_params(p)
+    A = synth.residues(43, (8, 8), p)
+    C = synth.residues(44, (8, 8), p).astype(np.int64)
+    got = np.asarray(alg1.syrk_table4(1, A, 1, C, p, ykind, ya, yb, save_diagonal=False),
+                     dtype=np.int64)
+    want = oracle.syrk_modp_low(1, A, 1, C, p).astype(np.int64)
+    # only the diagonal of the C11 block is lost
+    assert not np.array_equal(np.diag(got)[:4], np.diag(want)[:4])
+    assert np.array_equal(np.diag(got)[4:], np.diag(want)[4:])
+    assert np.array_equal(np.tril(got, -1), np.tril(want, -1))
