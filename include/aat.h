@@ -83,6 +83,22 @@ AAT_API int aat_modp_ex(const int32_t *A, int64_t n, int64_t k, int64_t lda, uin
                 int32_t *C, int64_t ldc, uint32_t flags, void *stream);
 
 /*
+ * The SYRK form: Low(C) <- alpha Low(A A^T) + beta Low(C) mod p (Sec. 7, the
+ * update C <- alpha A A^T + beta C and its schedule of Table 4).  alpha and
+ * beta are any uint32 (reduced mod p); A as for aat_modp_ex; C (n x n, row
+ * stride ldc) holds on entry residues with |x| < p in its lower triangle
+ * (diagonal included) and receives the canonical update there.  Table 4's
+ * memory placement: C12, the upper triangle of C11 and one (n/2) x (n/2)
+ * temporary of the workspace hold intermediate blocks, so the strict upper
+ * triangle of C is unspecified on return (zeroed with AAT_ZERO_UPPER).  With
+ * beta = 0 this is alpha times aat_modp_ex.  flags as for aat_modp_ex.
+ * Asynchronous on `stream`.
+ */
+AAT_API int aat_syrk_modp(uint32_t alpha, const int32_t *A, int64_t n, int64_t k, int64_t lda,
+                  uint32_t beta, int32_t *C, int64_t ldc, uint32_t p, uint32_t flags,
+                  void *stream);
+
+/*
  * End-to-end form: A_host (n x k, row stride k) and C_host (n x n, row
  * stride n) are HOST buffers (pinned or pageable; pinned buffers let the
  * copies overlap the computation).  The call copies A to the device, runs
@@ -99,6 +115,43 @@ AAT_API int aat_modp_host(const int32_t *A_host, int64_t n, int64_t k, uint32_t 
 
 /* Bytes that aat_modp_host copies from the device to the host for size n. */
 AAT_API int64_t aat_modp_host_d2h_bytes(int64_t n, uint32_t flags);
+
+/*
+ * Autotuning of Low(A A^T) mod p on the tensor-core leaf for one shape.
+ * The choices tuned: the recursion depth (the cut-off of Algorithm 1's
+ * recursion, Sec. 3; the paper leaves it to the implementation, Sec. 7), the
+ * leaf kernel form (form 1: one CTA per 128 x 256 tile; form 2: CTA pairs,
+ * 256 x 256 tiles) and the digit-product form (plain_digits 1: one product
+ * per digit pair).  aat_tune_modp runs every candidate on synthetic balanced
+ * residues of shape n x k on `stream` (one untimed run, then `reps` timed
+ * ones; it allocates n k + n^2 int32 of device memory for the duration and
+ * synchronises), keeps the fastest in a per-process table and returns it
+ * with its time and the untuned choice's time (ms_default).  aat_modp_ex,
+ * aat_modp_host and the batched plans take levels, form and digit form from
+ * the table for a (n, k, p) it holds whenever their flags set neither
+ * AAT_LEVELS nor AAT_DIGITS_PLAIN.  flags: AAT_LEAF_TC only (others give
+ * AAT_EUNSUPPORTED); AAT_LEVELS, AAT_DIGITS_PLAIN and AAT_ZERO_UPPER are
+ * ignored.
+ * aat_tune_lookup: 1 and *out (may be NULL) if the table holds (n, k, p), else 0.
+ * aat_tune_save: writes the table as JSON (with the GPU's name); returns the
+ * entry count.  aat_tune_load: adds the entries of such a file, skipping a
+ * file written on another kind of GPU (returns 0) and invalid entries;
+ * returns the count added.  aat_tune_clear: empties the table.
+ */
+typedef struct {
+  int32_t levels;       /* recursion levels */
+  int32_t form;         /* leaf kernel form: 1 one CTA, 2 CTA pairs */
+  int32_t plain_digits; /* 1: one plane product per digit pair */
+  int32_t reserved;
+  double ms;            /* mean time of the chosen configuration */
+  double ms_default;    /* mean time of the untuned choice */
+} aat_tune_t;
+AAT_API int aat_tune_modp(int64_t n, int64_t k, uint32_t p, uint32_t flags, int reps,
+                  void *stream, aat_tune_t *out);
+AAT_API int aat_tune_lookup(int64_t n, int64_t k, uint32_t p, aat_tune_t *out);
+AAT_API int aat_tune_save(const char *path);
+AAT_API int aat_tune_load(const char *path);
+AAT_API void aat_tune_clear(void);
 
 /*
  * The plain general product C = X Y^T mod p with the same exact leaf

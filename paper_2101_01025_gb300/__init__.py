@@ -12,13 +12,16 @@ library ``libaat_gb300.so``; when it is missing the calls raise.
 """
 from __future__ import annotations
 
+import ctypes
+import os
+
 from . import _native
 from ._native import (AAT_C_BF16, AAT_C_BF16X3, AAT_C_FP32, AAT_DIGITS_PLAIN,  # noqa: F401
                       AAT_IN_BALANCED, AAT_LEAF_F64, AAT_LEAF_I8, AAT_LEAF_SIMT, AAT_LEAF_TC, AAT_LEVELS, AAT_ZERO_UPPER, AatError, PlanStats, check, last_error, lib)
 
 __all__ = [
-    "aat_modp", "aat_gemm_modp", "aat_modp_host", "aat_modp_host_d2h_bytes", "aat_workspace_size",
-    "aat_device_status",
+    "aat_modp", "aat_syrk_modp", "aat_gemm_modp", "aat_modp_host", "aat_modp_host_d2h_bytes", "aat_workspace_size",
+    "aat_device_status", "tune_modp", "tune_lookup", "tune_save", "tune_load", "tune_clear",
     "aat_shutdown", "aat_version", "aah_complex", "aat_complex_2m", "aat_complex", "Plan", "AAT_LEVELS", "AAT_LEAF_TC", "AAT_LEAF_SIMT",
     "AAT_ZERO_UPPER", "AAT_IN_BALANCED", "AatError",
 ]
@@ -76,6 +79,23 @@ def aat_gemm_modp(X, Y, p: int, C=None, flags: int = 0, stream=None):
     return C
 
 
+def aat_syrk_modp(alpha: int, A, beta: int, C, p: int, flags: int = 0,
+                  levels: int | None = None, stream=None):
+    """Low(C) <- alpha Low(A A^T) + beta Low(C) mod p in place (the SYRK
+    form); C is an n x n int32 CUDA tensor holding residues |x| < p in its
+    lower triangle; its strict upper triangle is used as scratch.  Returns C."""
+    if levels is not None:
+        flags |= AAT_LEVELS(levels)
+    lda = _check_mat(A, "A")
+    ldc = _check_mat(C, "C")
+    n, k = A.shape
+    if tuple(C.shape) != (n, n):
+        raise ValueError("C must be n x n")
+    check(lib().aat_syrk_modp(alpha % 2**32, A.data_ptr(), n, k, lda, beta % 2**32,
+                              C.data_ptr(), ldc, p, flags, _stream(stream)))
+    return C
+
+
 def aat_modp_host(A, p: int, C=None, flags: int = 0, levels: int | None = None):
     """End to end from host memory: A is a C-contiguous int32 numpy array (or
     pinned CPU tensor); returns C (n x n, host, same kind as A).  Only the
@@ -98,6 +118,39 @@ def aat_modp_host(A, p: int, C=None, flags: int = 0, levels: int | None = None):
         C = torch.empty((n, n), dtype=torch.int32, pin_memory=A.is_pinned())
     check(lib().aat_modp_host(A.data_ptr(), n, k, p, C.data_ptr(), flags))
     return C
+
+
+def tune_modp(n: int, k: int, p: int, flags: int = 0, reps: int = 3, stream=None) -> dict:
+    """Autotune Low(A A^T) mod p for shape (n, k): recursion levels, leaf
+    kernel form and digit-product form, timed on synthetic residues on the
+    GPU; the choice is kept for later calls of that shape and returned."""
+    from ._native import Tune
+    t = Tune()
+    check(lib().aat_tune_modp(n, k, p, flags, reps, _stream(stream), ctypes.byref(t)))
+    return t.as_dict()
+
+
+def tune_lookup(n: int, k: int, p: int):
+    """The tuned choice for (n, k, p), or None."""
+    from ._native import Tune
+    t = Tune()
+    return t.as_dict() if lib().aat_tune_lookup(n, k, p, ctypes.byref(t)) else None
+
+
+def tune_save(path: str) -> int:
+    r = lib().aat_tune_save(os.fsencode(path))
+    check(min(r, 0))
+    return r
+
+
+def tune_load(path: str) -> int:
+    r = lib().aat_tune_load(os.fsencode(path))
+    check(min(r, 0))
+    return r
+
+
+def tune_clear() -> None:
+    lib().aat_tune_clear()
 
 
 def aat_modp_host_d2h_bytes(n: int, flags: int = 0) -> int:

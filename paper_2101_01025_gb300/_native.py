@@ -40,8 +40,9 @@ def AAT_LEVELS(l: int) -> int:
 
 #: every symbol include/aat.h and include/aat_testing.h declare
 EXPORTS = [
-    "aat_modp", "aat_modp_ex", "aat_modp_host", "aat_modp_host_d2h_bytes", "aat_gemm_modp",
-    "aat_gemm_modp_noalloc",
+    "aat_modp", "aat_modp_ex", "aat_syrk_modp", "aat_modp_host", "aat_modp_host_d2h_bytes", "aat_gemm_modp",
+    "aat_gemm_modp_noalloc", "aat_tune_modp", "aat_tune_lookup", "aat_tune_save", "aat_tune_load",
+    "aat_tune_clear",
     "aat_workspace_size",
     "aat_last_error", "aat_device_status", "aat_shutdown", "aat_version",
     "aat_profile_begin", "aat_profile_end", "aah_complex", "aah_complex_ex", "aat_complex_2m",
@@ -69,6 +70,22 @@ class Problem(ctypes.Structure):
         ("p", ctypes.c_uint32),
         ("flags", ctypes.c_uint32),
     ]
+
+
+class Tune(ctypes.Structure):
+    _fields_ = [
+        ("levels", ctypes.c_int32),
+        ("form", ctypes.c_int32),
+        ("plain_digits", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("ms", ctypes.c_double),
+        ("ms_default", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return dict(levels=int(self.levels), form=int(self.form),
+                    plain_digits=int(self.plain_digits), ms=float(self.ms),
+                    ms_default=float(self.ms_default))
 
 
 class AatError(RuntimeError):
@@ -133,10 +150,16 @@ def lib():
         L.aat_modp.argtypes = [vp, i64, i64, u32, vp, vp]
         L.aat_modp_ex.argtypes = [vp, i64, i64, i64, u32, vp, i64, u32, vp]
         L.aat_modp_host.argtypes = [vp, i64, i64, u32, vp, u32]
+        L.aat_syrk_modp.argtypes = [u32, vp, i64, i64, i64, u32, vp, i64, u32, u32, vp]
         L.aat_modp_host_d2h_bytes.argtypes = [i64, u32]
         L.aat_modp_host_d2h_bytes.restype = i64
         L.aat_gemm_modp.argtypes = [vp, i64, vp, i64, i64, i64, i64, u32, vp, i64, u32, vp]
         L.aat_gemm_modp_noalloc.argtypes = [vp, i64, vp, i64, i64, i64, i64, u32, vp, i64, vp]
+        L.aat_tune_modp.argtypes = [i64, i64, u32, u32, i32, vp, ctypes.POINTER(Tune)]
+        L.aat_tune_lookup.argtypes = [i64, i64, u32, ctypes.POINTER(Tune)]
+        L.aat_tune_save.argtypes = [ctypes.c_char_p]
+        L.aat_tune_load.argtypes = [ctypes.c_char_p]
+        L.aat_tune_clear.restype = None
         L.aat_workspace_size.argtypes = [i64, i64, u32, u32]
         L.aat_workspace_size.restype = ctypes.c_size_t
         L.aat_last_error.restype = ctypes.c_char_p

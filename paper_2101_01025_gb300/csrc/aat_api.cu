@@ -361,6 +361,8 @@ struct Ctx {
   cudaEvent_t split_ev = nullptr;
   int top_levels = -1;
   int64_t split_row = 0;
+  int form = 0;  // leaf kernel form (TcLeafArgs::form)
+  uint32_t alpha = 1;  // scale of every product (the SYRK update's alpha)
 };
 
 static Planes planes_for(const DigitSpec &ds, int64_t rows, int64_t cols) {
@@ -403,9 +405,11 @@ static bool check(Ctx &c, cudaError_t e, const char *where) {
   return c.err == AAT_OK;
 }
 
-// out = X Y^T (M x N, inner K) mod p; lower: only i >= j; accumulate: out += .
+// out <- alpha X Y^T + beta out (M x N, inner K) mod p, alpha = c.alpha;
+// lower: only i >= j.  beta 0 stores the product, 1 accumulates.
 static void leaf(Ctx &c, Operand X, Operand Y, bool same, int64_t M, int64_t N, int64_t K,
-                 int32_t *out, int64_t ldo, int lower, int accumulate) {
+                 int32_t *out, int64_t ldo, int lower, uint32_t beta) {
+  const Lin lin = lin_of(c.alpha, beta, c.m.p);
   if (c.stats) {
     if (lower) {
       c.stats->syrk_leaves++;
@@ -417,7 +421,7 @@ static void leaf(Ctx &c, Operand X, Operand Y, bool same, int64_t M, int64_t N, 
   }
   if (c.leaf == AAT_LEAF_SIMT) {
     if (!c.ar.dry)
-      check(c, launch_leaf_simt(X.x, X.ld, Y.x, Y.ld, M, N, K, out, ldo, lower, accumulate, c.m,
+      check(c, launch_leaf_simt(X.x, X.ld, Y.x, Y.ld, M, N, K, out, ldo, lower, lin, c.m,
                                 c.st),
             "leaf (CUDA cores)");
     return;
@@ -426,7 +430,7 @@ static void leaf(Ctx &c, Operand X, Operand Y, bool same, int64_t M, int64_t N, 
     const size_t mark = c.ar.used;
     void *ws = c.ar.get(leaf_i8_workspace(M, N, K, c.m.p));
     if (!c.ar.dry)
-      check(c, launch_leaf_i8(X.x, X.ld, Y.x, Y.ld, M, N, K, out, ldo, lower, accumulate, c.m, ws,
+      check(c, launch_leaf_i8(X.x, X.ld, Y.x, Y.ld, M, N, K, out, ldo, lower, lin, c.m, ws,
                               c.st),
             "leaf (INT8 mma.sync)");
     c.ar.used = mark;
@@ -434,7 +438,7 @@ static void leaf(Ctx &c, Operand X, Operand Y, bool same, int64_t M, int64_t N, 
   }
   if (c.leaf == AAT_LEAF_F64) {
     if (!c.ar.dry)
-      check(c, launch_leaf_f64(X.x, X.ld, Y.x, Y.ld, M, N, K, out, ldo, lower, accumulate, c.m,
+      check(c, launch_leaf_f64(X.x, X.ld, Y.x, Y.ld, M, N, K, out, ldo, lower, lin, c.m,
                                c.st),
             "leaf (FP64 mma.sync)");
     return;
@@ -462,16 +466,75 @@ static void leaf(Ctx &c, Operand X, Operand Y, bool same, int64_t M, int64_t N, 
     a.out = out;
     a.ldo = ldo;
     a.lower = lower;
-    a.accumulate = accumulate;
+    a.lin = lin;
     a.exact_bits = c.exact_bits;
+    a.form = c.form;
     check(c, launch_leaf_tc(a, c.m, c.st), "leaf (tensor cores)");
   }
   c.ar.used = mark;
 }
 
-// Low(A A^T) mod p -> Low(C) by Algorithm 1 with `levels` levels.
-// n must be divisible by 2^levels and k by 2^levels (2^(levels+1) for a
-// kind-2 Y).  `ap` optionally holds the digit planes of A (tensor-core leaf).
+// The operands of one level's products after the S-block step (K1).
+struct LevelOps {
+  Operand oS1, oS2, oS4, oA22;
+  Planes pA11, pA12, pS3;  // planes of A11, A12, S3 (last level, tensor-core leaf)
+};
+
+// Step 1 of a level: S1..S4 (4 additions, 2 products by Y) in one pass over
+// A.  S3 is written as int32 to S3 (row stride ldS3) unless it is needed
+// only as digit planes (last level, tensor-core leaf; S3 may be null then).
+static LevelOps sblocks_step(Ctx &c, const int32_t *A, int64_t lda, int64_t h, int64_t kap,
+                             int32_t *S3, int64_t ldS3, bool last) {
+  const bool tc = (c.leaf == AAT_LEAF_TC);
+  const int32_t *A22 = A + h * lda + kap;
+  SKernelOut o;
+  std::memset(&o, 0, sizeof(o));
+  o.s[2] = (tc && last) ? nullptr : S3;
+  o.lds[2] = ldS3;
+  LevelOps L;
+  L.oS1 = Operand{nullptr, 0, no_planes()};
+  L.oS2 = L.oS1;
+  L.oS4 = L.oS1;
+  L.oA22 = Operand{A22, lda, no_planes()};
+  L.pA11 = L.pA12 = L.pS3 = no_planes();
+  if (tc) {
+    o.sp[0] = L.oS1.pl = planes_alloc(c, h, kap);
+    o.sp[1] = L.oS2.pl = planes_alloc(c, h, kap);
+    o.sp[3] = L.oS4.pl = planes_alloc(c, h, kap);
+    o.a22 = L.oA22.pl = planes_alloc(c, h, kap);
+    if (last) {
+      o.a11 = L.pA11 = planes_alloc(c, h, kap);
+      o.a12 = L.pA12 = planes_alloc(c, h, kap);
+      o.sp[2] = L.pS3 = planes_alloc(c, h, kap);
+    }
+  } else {
+    for (int q : {0, 1, 3}) {
+      o.s[q] = (int32_t *)c.ar.get((size_t)h * kap * 4);
+      o.lds[q] = kap;
+    }
+    L.oS1.x = o.s[0];
+    L.oS1.ld = kap;
+    L.oS2.x = o.s[1];
+    L.oS2.ld = kap;
+    L.oS4.x = o.s[3];
+    L.oS4.ld = kap;
+  }
+  if (!c.ar.dry) check(c, launch_sblocks(A, lda, h, kap, c.m, c.y, c.ds.b, o, c.st), "sblocks");
+  return L;
+}
+
+static void count_level(Ctx &c) {
+  if (c.stats) {
+    c.stats->recursive_products += 3;
+    c.stats->block_additions += 9;
+    c.stats->half_additions += 3;
+  }
+}
+
+// Low(A A^T) mod p -> Low(C) by Algorithm 1 with `levels` levels (times
+// c.alpha).  n must be divisible by 2^levels and k by 2^levels (2^(levels+1)
+// for a kind-2 Y).  `ap` optionally holds the digit planes of A
+// (tensor-core leaf).  Memory placement of Table 3 (Sec. 7).
 static void rec(Ctx &c, const int32_t *A, int64_t lda, int64_t n, int64_t k, int32_t *C,
                 int64_t ldc, int levels, Planes ap) {
   if (c.err != AAT_OK) return;
@@ -482,18 +545,10 @@ static void rec(Ctx &c, const int32_t *A, int64_t lda, int64_t n, int64_t k, int
   }
   const int64_t h = n / 2, kap = k / 2;
   int32_t *C11 = C, *C12 = C + h, *C21 = C + h * ldc, *C22 = C + h * ldc + h;
-  const int32_t *A11 = A, *A12 = A + kap, *A22 = A + h * lda + kap;
-  const bool tc = (c.leaf == AAT_LEAF_TC);
+  const int32_t *A11 = A, *A12 = A + kap;
   const bool last = (levels == 1);
   const size_t mark = c.ar.used;
-  if (c.stats) {
-    c.stats->recursive_products += 3;
-    c.stats->block_additions += 9;
-    c.stats->half_additions += 3;
-  }
-
-  SKernelOut o;
-  std::memset(&o, 0, sizeof(o));
+  count_level(c);
   // S3: the input of the recursive product P5.  Table 3 keeps it in C21
   // (needs kappa <= h, i.e. k <= n); otherwise it takes workspace.
   int32_t *S3;
@@ -505,57 +560,111 @@ static void rec(Ctx &c, const int32_t *A, int64_t lda, int64_t n, int64_t k, int
     S3 = (int32_t *)c.ar.get((size_t)h * kap * 4);
     ldS3 = kap;
   }
-  // with tensor-core leaves the last level needs S3 only as digit planes
-  o.s[2] = (tc && last) ? nullptr : S3;
-  o.lds[2] = ldS3;
-  Operand oS1{nullptr, 0, no_planes()}, oS2 = oS1, oS4 = oS1, oA22{A22, lda, no_planes()};
-  Planes pA11 = no_planes(), pA12 = no_planes(), pS3 = no_planes();
-  if (tc) {
-    o.sp[0] = oS1.pl = planes_alloc(c, h, kap);
-    o.sp[1] = oS2.pl = planes_alloc(c, h, kap);
-    o.sp[3] = oS4.pl = planes_alloc(c, h, kap);
-    o.a22 = oA22.pl = planes_alloc(c, h, kap);
-    if (last) {
-      o.a11 = pA11 = planes_alloc(c, h, kap);
-      o.a12 = pA12 = planes_alloc(c, h, kap);
-      o.sp[2] = pS3 = planes_alloc(c, h, kap);
-    }
-  } else {
-    for (int q : {0, 1, 3}) {
-      o.s[q] = (int32_t *)c.ar.get((size_t)h * kap * 4);
-      o.lds[q] = kap;
-    }
-    oS1.x = o.s[0];
-    oS1.ld = kap;
-    oS2.x = o.s[1];
-    oS2.ld = kap;
-    oS4.x = o.s[3];
-    oS4.ld = kap;
-  }
   // 1. S1..S4 (4 additions, 2 products by Y) in one pass over A
-  if (!c.ar.dry) check(c, launch_sblocks(A, lda, h, kap, c.m, c.y, c.ds.b, o, c.st), "sblocks");
+  const LevelOps L = sblocks_step(c, A, lda, h, kap, S3, ldS3, last);
   // 2. P4^T = S2 S1^T -> C22
-  leaf(c, oS2, oS1, false, h, h, kap, C22, ldc, 0, 0);
+  leaf(c, L.oS2, L.oS1, false, h, h, kap, C22, ldc, 0, 0);
   // 3. P5 = Low(S3 S3^T) -> C12
-  rec(c, S3, ldS3, h, kap, C12, ldc, levels - 1, pS3);
+  rec(c, S3, ldS3, h, kap, C12, ldc, levels - 1, L.pS3);
   // 4. P3 = A22 S4^T -> C21 (S3 is no longer needed)
-  leaf(c, oA22, oS4, false, h, h, kap, C21, ldc, 0, 0);
+  leaf(c, L.oA22, L.oS4, false, h, h, kap, C21, ldc, 0, 0);
   // 5. P1 = Low(A11 A11^T) -> C11
-  rec(c, A11, lda, h, kap, C11, ldc, levels - 1, pA11);
+  rec(c, A11, lda, h, kap, C11, ldc, levels - 1, L.pA11);
   // 6. U1 = P1 + P5, U2 = U1 + P4, U4 = U2 + P3 -> C21, U5 = Low(U2 + P4^T) -> C22
-  if (!c.ar.dry) check(c, launch_postadd(C11, C12, C21, C22, ldc, h, c.m, c.st), "postadd");
+  if (!c.ar.dry) check(c, launch_postadd(C11, ldc, C12, C21, C22, ldc, h, c.m, c.st), "postadd");
   // rows [h, n) of the top level (C21 = U4, Low(C22) = Low(U5)) are final
   if (c.split_ev && levels == c.top_levels && !c.ar.dry && c.err == AAT_OK)
     cudaEventRecord(c.split_ev, c.st);
   // 7-8. P2 = Low(A12 A12^T), U3 = P1 + P2 -> C11
   if (last) {
-    Operand X{A12, lda, pA12};
+    Operand X{A12, lda, L.pA12};
     leaf(c, X, X, true, h, h, kap, C11, ldc, 1, 1);  // accumulates onto P1
   } else {
     rec(c, A12, lda, h, kap, C12, ldc, levels - 1, no_planes());
-    if (!c.ar.dry) check(c, launch_add_low(C11, C12, ldc, h, c.m, c.st), "add_low");
+    if (!c.ar.dry) check(c, launch_add_low(C11, ldc, C12, ldc, h, c.m, c.st), "add_low");
   }
   c.ar.used = mark;
+}
+
+// Low(C) <- alpha Low(A A^T) + beta Low(C) mod p, alpha = c.alpha (the SYRK
+// form, Sec. 7, Table 4).  The schedule of Table 4: C12 and one h x h
+// temporary (tmp) hold intermediate blocks, the strictly lower part of C22
+// is saved transposed in the upper triangle of C11 (its diagonal in an
+// h-vector: Up(C11) includes the diagonal, which C11 itself still needs), P3
+// and P2 take beta C21 and beta C11 in their epilogues, U5 takes beta C22.
+// P5 and P1 are plain products (beta = 0) by `rec`; P2 is this update,
+// recursively, on (A12, C11).
+static void syrk_rec(Ctx &c, const int32_t *A, int64_t lda, int64_t n, int64_t k, int32_t *C,
+                     int64_t ldc, int levels, const MulConst &beta) {
+  if (c.err != AAT_OK) return;
+  if (levels == 0 || n < 2 || k < 2) {
+    Operand X{A, lda, no_planes()};
+    leaf(c, X, X, true, n, n, k, C, ldc, 1, beta.w);
+    return;
+  }
+  const int64_t h = n / 2, kap = k / 2;
+  int32_t *C11 = C, *C12 = C + h, *C21 = C + h * ldc, *C22 = C + h * ldc + h;
+  const int32_t *A11 = A, *A12 = A + kap;
+  const bool last = (levels == 1);
+  const size_t mark = c.ar.used;
+  count_level(c);
+  int32_t *tmp = (int32_t *)c.ar.get((size_t)h * h * 4);
+  int32_t *dg = (int32_t *)c.ar.get((size_t)h * 4);
+  // S3 (when needed as int32) lives in tmp until P1 takes it (k <= n)
+  int32_t *S3;
+  int64_t ldS3;
+  if (kap <= h) {
+    S3 = tmp;
+    ldS3 = h;
+  } else {
+    S3 = (int32_t *)c.ar.get((size_t)h * kap * 4);
+    ldS3 = kap;
+  }
+  const LevelOps L = sblocks_step(c, A, lda, h, kap, S3, ldS3, last);
+  // Up(C11) <- Low(C22)^T (strictly), diag(C22) -> dg
+  if (!c.ar.dry) check(c, launch_save_c22(C11, C22, ldc, h, dg, c.st), "save C22");
+  // P4^T = alpha S2 S1^T -> C22
+  leaf(c, L.oS2, L.oS1, false, h, h, kap, C22, ldc, 0, 0);
+  // P5 = alpha Low(S3 S3^T) -> C12
+  rec(c, S3, ldS3, h, kap, C12, ldc, levels - 1, L.pS3);
+  // P3 = alpha A22 S4^T + beta C21 -> C21
+  leaf(c, L.oA22, L.oS4, false, h, h, kap, C21, ldc, 0, beta.w);
+  // P1 = alpha Low(A11 A11^T) -> tmp (S3 is no longer needed)
+  rec(c, A11, lda, h, kap, tmp, h, levels - 1, L.pA11);
+  // U1 = P1 + P5, U2 = U1 + P4, U4 = U2 + P3 -> C21,
+  // U5 = Low(U2 + P4^T) + beta Low(C22 before) -> C22
+  const SyrkSave sv{C11, dg, beta};
+  if (!c.ar.dry) check(c, launch_postadd(tmp, h, C12, C21, C22, ldc, h, c.m, c.st, &sv), "postadd");
+  // P2 = alpha A12 A12^T + beta C11 -> C11, then U3 = P1 + P2 -> C11
+  if (last) {
+    Operand X{A12, lda, L.pA12};
+    leaf(c, X, X, true, h, h, kap, C11, ldc, 1, beta.w);
+  } else {
+    syrk_rec(c, A12, lda, h, kap, C11, ldc, levels - 1, beta);
+  }
+  if (!c.ar.dry) check(c, launch_add_low(C11, ldc, tmp, h, h, c.m, c.st), "add_low");
+  c.ar.used = mark;
+}
+
+// ------------------------------------------------------------ tuning table
+
+// Tuned choices for Low(A A^T) mod p on the tensor-core leaf, per (n, k, p):
+// recursion levels, leaf kernel form (TcLeafArgs::form) and digit-product
+// form.  Filled by aat_tune_modp or aat_tune_load; consulted whenever the
+// flags leave these choices open.
+struct TuneVal {
+  int levels, form, plain;
+  double ms, ms_default;
+};
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int64_t, int64_t, uint32_t>, TuneVal> g_tune;
+
+static bool tune_find(int64_t n, int64_t k, uint32_t p, TuneVal *v) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tune.find(std::make_tuple(n, k, p));
+  if (it == g_tune.end()) return false;
+  *v = it->second;
+  return true;
 }
 
 // Recursion depth chosen from measurements on GB300: a level pays off while
@@ -572,6 +681,13 @@ struct Prepared {
   int64_t n_pad, k_pad;
   bool padded;
 };
+
+// Recursion depth of the untuned choice for (n, k) (no AAT_LEVELS in flags).
+static int prepare_levels(int64_t n, int64_t k, uint32_t p, uint32_t flags) {
+  (void)p;
+  const uint32_t lv = (flags & AAT_LEVELS_MASK) >> 8;
+  return lv ? (int)lv - 1 : auto_levels(n, k);
+}
 
 static Prepared prepare(int64_t n, int64_t k, const YParams &y, uint32_t flags) {
   Prepared r;
@@ -618,8 +734,17 @@ static int setup(Ctx &c, uint32_t p, uint32_t flags, cudaStream_t st) {
 }
 
 // Runs (or, with dry, measures) the whole product; returns workspace bytes.
+// beta: null for Low(A A^T) (Table 3), else the SYRK update's beta (Table 4).
 static size_t run_plan(Ctx &c, const int32_t *A, int64_t n, int64_t k, int64_t lda, int32_t *C,
-                       int64_t ldc, uint32_t flags, bool dry, char *ws) {
+                       int64_t ldc, uint32_t flags, bool dry, char *ws,
+                       const MulConst *beta = nullptr) {
+  // choices the flags leave open come from the tuning table, if it has the shape
+  TuneVal tv;
+  if (c.leaf == AAT_LEAF_TC && !(flags & AAT_LEVELS_MASK) && tune_find(n, k, c.m.p, &tv)) {
+    flags |= AAT_LEVELS(tv.levels);
+    c.form = tv.form;
+    if (tv.plain) c.ds.nsum = 0;
+  }
   Prepared pr = prepare(n, k, c.y, flags);
   c.ar = Arena();
   c.ar.dry = dry;
@@ -633,6 +758,9 @@ static size_t run_plan(Ctx &c, const int32_t *A, int64_t n, int64_t k, int64_t l
     int32_t *Cp = (int32_t *)c.ar.get((size_t)pr.n_pad * pr.n_pad * 4);
     if (!dry)
       check(c, launch_pad_copy(A, lda, n, k, Ap, pr.k_pad, pr.n_pad, pr.k_pad, c.st), "pad");
+    // the SYRK update reads C: it goes into the padded copy too
+    if (!dry && beta)
+      check(c, launch_pad_copy(C, ldc, n, n, Cp, pr.n_pad, pr.n_pad, pr.n_pad, c.st), "pad C");
     Aw = Ap;
     ldaw = pr.k_pad;
     Cw = Cp;
@@ -643,10 +771,13 @@ static size_t run_plan(Ctx &c, const int32_t *A, int64_t n, int64_t k, int64_t l
     c.stats->n_pad = pr.n_pad;
     c.stats->k_pad = pr.k_pad;
   }
-  const bool early = !pr.padded && pr.levels >= 1;
+  const bool early = !pr.padded && pr.levels >= 1 && !beta;
   c.top_levels = early ? pr.levels : -1;
   c.split_row = early ? pr.n_pad / 2 : n;
-  rec(c, Aw, ldaw, pr.n_pad, pr.k_pad, Cw, ldcw, pr.levels, no_planes());
+  if (beta)
+    syrk_rec(c, Aw, ldaw, pr.n_pad, pr.k_pad, Cw, ldcw, pr.levels, *beta);
+  else
+    rec(c, Aw, ldaw, pr.n_pad, pr.k_pad, Cw, ldcw, pr.levels, no_planes());
   if (pr.padded && !dry) check(c, launch_copy_low(Cw, ldcw, C, ldc, n, c.st), "unpad");
   if (!dry && (flags & AAT_ZERO_UPPER)) check(c, launch_zero_upper(C, ldc, n, c.st), "zero upper");
   if (!dry && !early && c.split_ev && c.err == AAT_OK) cudaEventRecord(c.split_ev, c.st);
@@ -672,18 +803,25 @@ static int check_device() {
 }
 
 // Used by the batched plans (aat_plan.cu).
-int modp_levels(int64_t n, int64_t k, uint32_t flags) {
+int modp_levels(int64_t n, int64_t k, uint32_t p, uint32_t flags) {
   const uint32_t lv = (flags & AAT_LEVELS_MASK) >> 8;
-  return lv ? (int)lv - 1 : auto_levels(n, k);
+  if (lv) return (int)lv - 1;
+  TuneVal tv;
+  if ((flags & AAT_LEAF_MASK) == AAT_LEAF_TC && tune_find(n, k, p, &tv)) return tv.levels;
+  return auto_levels(n, k);
 }
 
 Planes planes_layout(const DigitSpec &ds, int64_t rows, int64_t cols) {
   return planes_for(ds, rows, cols);
 }
 
-DigitSpec digits_for_flags(uint32_t p, uint32_t flags) {
+DigitSpec digits_for_problem(int64_t n, int64_t k, uint32_t p, uint32_t flags) {
   DigitSpec d = make_digits(p);
+  TuneVal tv;
   if (flags & AAT_DIGITS_PLAIN) d.nsum = 0;
+  else if (!(flags & AAT_LEVELS_MASK) && (flags & AAT_LEAF_MASK) == AAT_LEAF_TC &&
+           tune_find(n, k, p, &tv) && tv.plain)
+    d.nsum = 0;
   return d;
 }
 
@@ -719,7 +857,7 @@ const char *aat_last_error(void) { return g_last_error.c_str(); }
 // aat_modp_ex with the optional early-rows event (aat_modp_host).
 static int modp_device(const int32_t *A, int64_t n, int64_t k, int64_t lda, uint32_t p, int32_t *C,
                        int64_t ldc, uint32_t flags, cudaStream_t stream, cudaEvent_t split_ev,
-                       int64_t *split_row) {
+                       int64_t *split_row, int form = 0) {
   if (split_row) *split_row = n;
   if (n < 0 || k < 0) return fail(AAT_EINVAL, "negative size");
   if (n > (1 << 30) || k > (1 << 30)) return fail(AAT_EINVAL, "size too large");
@@ -737,6 +875,7 @@ static int modp_device(const int32_t *A, int64_t n, int64_t k, int64_t lda, uint
     cudaError_t ce = cudaMemset2DAsync(C, (size_t)ldc * 4, 0, (size_t)n * 4, (size_t)n, c.st);
     return ce == cudaSuccess ? AAT_OK : cuda_fail(ce, "memset");
   }
+  c.form = form;
   const size_t need = run_plan(c, A, n, k, lda, C, ldc, flags, true, nullptr);
   void *ws = nullptr;
   if ((e = ensure_workspace(need, &ws))) return e;
@@ -777,6 +916,44 @@ int aat_modp_ex(const int32_t *A, int64_t n, int64_t k, int64_t lda, uint32_t p,
                 int64_t ldc, uint32_t flags, void *stream) {
   g_last_error.clear();
   return modp_device(A, n, k, lda, p, C, ldc, flags, (cudaStream_t)stream, nullptr, nullptr);
+}
+
+int aat_syrk_modp(uint32_t alpha, const int32_t *A, int64_t n, int64_t k, int64_t lda,
+                  uint32_t beta, int32_t *C, int64_t ldc, uint32_t p, uint32_t flags,
+                  void *stream) {
+  g_last_error.clear();
+  if (n < 0 || k < 0) return fail(AAT_EINVAL, "negative size");
+  if (n > (1 << 30) || k > (1 << 30)) return fail(AAT_EINVAL, "size too large");
+  if (lda < std::max<int64_t>(k, 1) || ldc < std::max<int64_t>(n, 1))
+    return fail(AAT_EINVAL, "stride smaller than the row length");
+  if (n > 0 && (!C || (k > 0 && !A))) return fail(AAT_EINVAL, "null pointer");
+  int e;
+  Ctx c;
+  if ((e = setup(c, p, flags, (cudaStream_t)stream))) return e;
+  if (n == 0) return AAT_OK;
+  if (k > 0 && overlaps(A, (size_t)((n - 1) * lda + k) * 4, C, (size_t)((n - 1) * ldc + n) * 4))
+    return fail(AAT_EINVAL, "C overlaps A");
+  if ((e = check_device())) return e;
+  const MulConst b = mul_const(beta, p);
+  c.alpha = mul_const(alpha, p).w;
+  cudaError_t ce = cudaSuccess;
+  if (k == 0 || c.alpha == 0) {
+    // Low(C) <- beta Low(C)
+    if (b.w == 0)
+      ce = cudaMemset2DAsync(C, (size_t)ldc * 4, 0, (size_t)n * 4, (size_t)n, c.st);
+    else
+      ce = launch_scale_low(C, ldc, n, b, c.m, c.st);
+    if (ce == cudaSuccess && (flags & AAT_ZERO_UPPER)) ce = launch_zero_upper(C, ldc, n, c.st);
+    return ce == cudaSuccess ? AAT_OK : cuda_fail(ce, "scale C");
+  }
+  // beta = 0: the product itself (Table 3 placement), scaled by alpha
+  const MulConst *pb = b.w ? &b : nullptr;
+  const size_t need = run_plan(c, A, n, k, lda, C, ldc, flags, true, nullptr, pb);
+  void *ws = nullptr;
+  if ((e = ensure_workspace(need, &ws))) return e;
+  c.err = AAT_OK;
+  run_plan(c, A, n, k, lda, C, ldc, flags, false, (char *)ws, pb);
+  return c.err;
 }
 
 int aat_modp(const int32_t *A, int64_t n, int64_t k, uint32_t p, int32_t *C, void *stream) {
@@ -849,6 +1026,201 @@ int aat_modp_host(const int32_t *A_host, int64_t n, int64_t k, uint32_t p, int32
   }
   if ((ce = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(ce, "synchronize");
   return AAT_OK;
+}
+
+int aat_tune_modp(int64_t n, int64_t k, uint32_t p, uint32_t flags, int reps, void *stream,
+                  aat_tune_t *out) {
+  g_last_error.clear();
+  if (!out) return fail(AAT_EINVAL, "null pointer");
+  if (n <= 0 || k <= 0 || n > (1 << 30) || k > (1 << 30)) return fail(AAT_EINVAL, "bad size");
+  if ((flags & AAT_LEAF_MASK) != AAT_LEAF_TC)
+    return fail(AAT_EUNSUPPORTED, "tuning covers the tensor-core leaf");
+  // the tuned choices themselves are not flags of the candidates
+  flags &= ~(AAT_LEVELS_MASK | AAT_DIGITS_PLAIN | AAT_ZERO_UPPER);
+  cudaStream_t st = (cudaStream_t)stream;
+  int e;
+  {
+    Ctx c0;
+    if ((e = setup(c0, p, flags, st))) return e;
+  }
+  if ((e = check_device())) return e;
+  reps = std::min(std::max(reps, 1), 50);
+  int32_t *A = nullptr, *C = nullptr;
+  if (cudaMalloc(&A, (size_t)n * k * 4) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(AAT_ENOMEM, "tuning input");
+  }
+  if (cudaMalloc(&C, (size_t)n * n * 4) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(A);
+    return fail(AAT_ENOMEM, "tuning output");
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaError_t ce = launch_fill_residues(A, n * k, p, 0x2101010250ull, st);
+  // candidates: the untuned choice first, then every (levels, form, digits)
+  struct Cand {
+    uint32_t flags;
+    int levels, form, plain;
+    double ms;
+  };
+  std::vector<Cand> cands;
+  cands.push_back({flags, -1, 0, 0, 1e300});
+  int maxl = 0;
+  while (maxl < 3 && (n >> (maxl + 1)) >= 512 && (k >> (maxl + 1)) >= 128) ++maxl;
+  const bool sums = make_digits(p).nsum > 0;
+  for (int l = 0; l <= maxl; ++l)
+    for (int form = 1; form <= 2; ++form) {
+      if (form == 2 && (n >> l) < 256) continue;  // no leaf tall enough for a pair
+      for (int plain = 0; plain <= (sums ? 1 : 0); ++plain)
+        cands.push_back({flags | AAT_LEVELS(l) | (plain ? AAT_DIGITS_PLAIN : 0u), l, form, plain,
+                         1e300});
+    }
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune.erase(std::make_tuple(n, k, p));
+  }
+  if (ce != cudaSuccess) e = cuda_fail(ce, "tuning input");
+  // one untimed run of each, then `reps` rounds that time every candidate
+  // once, round robin (clock and power drift spread evenly); best of rounds
+  for (size_t i = 0; i < cands.size() && !e; ++i)
+    e = modp_device(A, n, k, k, p, C, n, cands[i].flags, st, nullptr, nullptr, cands[i].form);
+  for (int r = 0; r < reps && !e; ++r)
+    for (size_t i = 0; i < cands.size() && !e; ++i) {
+      cudaEventRecord(e0, st);
+      e = modp_device(A, n, k, k, p, C, n, cands[i].flags, st, nullptr, nullptr, cands[i].form);
+      cudaEventRecord(e1, st);
+      cudaError_t se = cudaEventSynchronize(e1);
+      if (!e && se != cudaSuccess) e = cuda_fail(se, "tuning run");
+      float t = 0.f;
+      if (!e) cudaEventElapsedTime(&t, e0, e1);
+      cands[i].ms = std::min(cands[i].ms, (double)t);
+    }
+  // the fastest, unless it beats the untuned choice by less than 2 %
+  size_t bi = 1;
+  for (size_t i = 1; i < cands.size(); ++i)
+    if (cands[i].ms < cands[bi].ms) bi = i;
+  const double ms_default = cands[0].ms;
+  TuneVal best;
+  if (cands.size() < 2 || cands[bi].ms > 0.98 * ms_default)
+    best = TuneVal{prepare_levels(n, k, p, flags), 0, 0, ms_default, 0.0};
+  else
+    best = TuneVal{cands[bi].levels, cands[bi].form, cands[bi].plain, cands[bi].ms, 0.0};
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(st);
+  cudaFree(A);
+  cudaFree(C);
+  if (e) return e;
+  best.ms_default = ms_default;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune[std::make_tuple(n, k, p)] = best;
+  }
+  out->levels = best.levels;
+  out->form = best.form;
+  out->plain_digits = best.plain;
+  out->reserved = 0;
+  out->ms = best.ms;
+  out->ms_default = best.ms_default;
+  return AAT_OK;
+}
+
+int aat_tune_lookup(int64_t n, int64_t k, uint32_t p, aat_tune_t *out) {
+  TuneVal v;
+  if (!tune_find(n, k, p, &v)) return 0;
+  if (out) {
+    out->levels = v.levels;
+    out->form = v.form;
+    out->plain_digits = v.plain;
+    out->reserved = 0;
+    out->ms = v.ms;
+    out->ms_default = v.ms_default;
+  }
+  return 1;
+}
+
+void aat_tune_clear(void) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune.clear();
+}
+
+static std::string device_name() {
+  int dev = 0;
+  cudaDeviceProp prop;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return std::string();
+  }
+  std::string name(prop.name);
+  for (char &ch : name)
+    if (ch == '"' || ch == '\\' || ch < 32) ch = ' ';
+  return name;
+}
+
+int aat_tune_save(const char *path) {
+  g_last_error.clear();
+  if (!path) return fail(AAT_EINVAL, "null path");
+  FILE *f = fopen(path, "w");
+  if (!f) return fail(AAT_EINVAL, std::string("cannot write ") + path);
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  fprintf(f, "{\"gpu\": \"%s\", \"entries\": [\n", device_name().c_str());
+  size_t i = 0;
+  for (const auto &kv : g_tune) {
+    const TuneVal &v = kv.second;
+    fprintf(f,
+            "  {\"n\": %lld, \"k\": %lld, \"p\": %u, \"levels\": %d, \"form\": %d, "
+            "\"plain_digits\": %d, \"ms\": %.6f, \"ms_default\": %.6f}%s\n",
+            (long long)std::get<0>(kv.first), (long long)std::get<1>(kv.first),
+            (unsigned)std::get<2>(kv.first), v.levels, v.form, v.plain, v.ms, v.ms_default,
+            ++i < g_tune.size() ? "," : "");
+  }
+  fprintf(f, "]}\n");
+  const bool ok = (fclose(f) == 0);
+  if (!ok) return fail(AAT_EINVAL, std::string("cannot write ") + path);
+  return (int)g_tune.size();
+}
+
+int aat_tune_load(const char *path) {
+  g_last_error.clear();
+  if (!path) return fail(AAT_EINVAL, "null path");
+  FILE *f = fopen(path, "r");
+  if (!f) return fail(AAT_EINVAL, std::string("cannot read ") + path);
+  std::string text;
+  char buf[4096];
+  size_t got;
+  while ((got = fread(buf, 1, sizeof(buf), f)) > 0) text.append(buf, got);
+  fclose(f);
+  // entries tuned on another kind of GPU do not apply here
+  const std::string here = device_name();
+  const size_t g = text.find("\"gpu\": \"");
+  if (g != std::string::npos && !here.empty()) {
+    const size_t b = g + 8, q = text.find('"', b);
+    if (q == std::string::npos || text.compare(b, q - b, here) != 0) return 0;
+  }
+  int count = 0;
+  size_t pos = 0;
+  while ((pos = text.find("{\"n\":", pos)) != std::string::npos) {
+    long long n = 0, k = 0;
+    unsigned p = 0;
+    int levels = -1, form = -1, plain = -1;
+    double ms = 0.0, msd = 0.0;
+    const int m = sscanf(text.c_str() + pos,
+                         "{\"n\": %lld, \"k\": %lld, \"p\": %u, \"levels\": %d, \"form\": %d, "
+                         "\"plain_digits\": %d, \"ms\": %lf, \"ms_default\": %lf}",
+                         &n, &k, &p, &levels, &form, &plain, &ms, &msd);
+    ++pos;
+    if (m != 8 || n <= 0 || k <= 0 || n > (1 << 30) || k > (1 << 30) || levels < 0 ||
+        levels > 14 || form < 0 || form > 2 || (plain != 0 && plain != 1) || validate(p) != AAT_OK)
+      continue;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune[std::make_tuple((int64_t)n, (int64_t)k, (uint32_t)p)] =
+        TuneVal{levels, form, plain, ms, msd};
+    ++count;
+  }
+  g_last_error.clear();
+  return count;
 }
 
 int64_t aat_modp_host_d2h_bytes(int64_t n, uint32_t flags) {
@@ -1072,7 +1444,7 @@ int aatx_postadd(int32_t *C, int64_t ldc, int64_t h, uint32_t p, void *stream) {
   if (e) return e;
   if ((e = check_device())) return e;
   cudaError_t ce =
-      launch_postadd(C, C + h, C + h * ldc, C + h * ldc + h, ldc, h, c.m, (cudaStream_t)stream);
+      launch_postadd(C, ldc, C + h, C + h * ldc, C + h * ldc + h, ldc, h, c.m, (cudaStream_t)stream);
   return ce == cudaSuccess ? AAT_OK : cuda_fail(ce, "postadd");
 }
 

@@ -138,8 +138,8 @@ static int create(const aat_problem_t *probs, int count, Plan **out) {
       }
       const bool tc = (q.flags & AAT_LEAF_MASK) == AAT_LEAF_TC;
       const bool extra = (q.flags & AAT_ZERO_UPPER) != 0;
-      if (tc && !extra && modp_levels(q.n, q.k, q.flags) == 0) {
-        const DigitSpec ds = digits_for_flags(q.p, q.flags);
+      if (tc && !extra && modp_levels(q.n, q.k, q.p, q.flags) == 0) {
+        const DigitSpec ds = digits_for_problem(q.n, q.k, q.p, q.flags);
         const Planes pl = planes_layout(ds, q.n, q.k);
         plane_off[i] = batch_bytes;
         batch_bytes += r256((size_t)pl.L * pl.rows * pl.kstride * 2);
@@ -196,7 +196,7 @@ static int create(const aat_problem_t *probs, int count, Plan **out) {
     std::vector<SplitDesc> sd;
     for (int i : P->batched) {
       const aat_problem_t &q = P->probs[i];
-      const DigitSpec ds = digits_for_flags(q.p, q.flags);
+      const DigitSpec ds = digits_for_problem(q.n, q.k, q.p, q.flags);
       Planes pl = planes_layout(ds, q.n, q.k);
       pl.ptr = (__nv_bfloat16 *)((char *)P->ws + plane_off[i]);
       SplitDesc d;
@@ -219,7 +219,7 @@ static int create(const aat_problem_t *probs, int count, Plan **out) {
       a.out = (int32_t *)q.C;
       a.ldo = q.ldc;
       a.lower = 1;
-      a.accumulate = 0;
+      a.lin = lin_of(1, 0, q.p);
       a.exact_bits = 24;
       P->leaf_args.push_back(a);
       P->leaf_mods.push_back(d.m);

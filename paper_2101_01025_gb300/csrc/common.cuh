@@ -91,6 +91,60 @@ __host__ __device__ __forceinline__ uint32_t bal_to_canon(int32_t x, const ModP 
   return x < 0 ? (uint32_t)(x + (int32_t)m.p) : (uint32_t)x;
 }
 
+// a * w mod p, balanced, for any int32 a and a fixed w in [0, p) with
+// wsh = floor(w 2^32 / p) (Shoup's modular multiplication): with |a| < 2^32,
+// |a| w - floor(|a| wsh / 2^32) p lies in [0, 2p), so 32-bit arithmetic and
+// one conditional subtraction give the residue.
+__host__ __device__ __forceinline__ int32_t mulmod_shoup(int32_t a, uint32_t w, uint32_t wsh,
+                                                         const ModP &m) {
+  const uint32_t ax = a < 0 ? 0u - (uint32_t)a : (uint32_t)a;
+#ifdef __CUDA_ARCH__
+  const uint32_t q = __umulhi(ax, wsh);
+#else
+  const uint32_t q = (uint32_t)(((uint64_t)ax * wsh) >> 32);
+#endif
+  uint32_t r = ax * w - q * m.p;
+  if (r >= m.p) r -= m.p;
+  const int32_t b = r > m.half ? (int32_t)r - (int32_t)m.p : (int32_t)r;
+  return a < 0 ? -b : b;
+}
+
+// Shoup's quotient of a fixed multiplier w (reduced mod p first).
+struct MulConst {
+  uint32_t w, wsh;
+};
+inline MulConst mul_const(uint64_t w, uint32_t p) {
+  MulConst c;
+  c.w = (uint32_t)(w % p);
+  c.wsh = (uint32_t)(((uint64_t)c.w << 32) / p);
+  return c;
+}
+
+// The epilogue of a leaf product: out <- alpha * product + beta * out (mod p)
+// (the SYRK update C <- alpha A A^T + beta C, Sec. 7; alpha = 1, beta = 0
+// stores the product, beta = 1 accumulates).  Inputs in out must satisfy
+// |x| < p; the stored value is canonical.
+struct Lin {
+  MulConst alpha, beta;
+};
+inline Lin lin_of(uint64_t alpha, uint64_t beta, uint32_t p) {
+  Lin l;
+  l.alpha = mul_const(alpha, p);
+  l.beta = mul_const(beta, p);
+  return l;
+}
+
+__host__ __device__ __forceinline__ uint32_t lin_apply(int32_t v, int32_t old, const Lin &L,
+                                                       const ModP &m) {
+  if (L.alpha.w != 1u) v = mulmod_shoup(v, L.alpha.w, L.alpha.wsh, m);
+  if (L.beta.w != 0u) {
+    int32_t o = bal(old, m);
+    if (L.beta.w != 1u) o = mulmod_shoup(o, L.beta.w, L.beta.wsh, m);
+    v = add_bal(v, o, m);
+  }
+  return bal_to_canon(v, m);
+}
+
 // ------------------------------------------------------ skew-unitary Y
 
 // ykind 1: Y = i I, i^2 = -1 (Sec. 4.2).
@@ -222,13 +276,32 @@ cudaError_t launch_sblocks(const int32_t *A, int64_t lda, int64_t h, int64_t kap
 cudaError_t launch_split(const int32_t *X, int64_t ldx, int64_t rows, int64_t cols,
                          const ModP &m, int b, const Planes &P, cudaStream_t st);
 
-// K6: U4 and U5 of Algorithm 1 from P1 (Low, in C11), P5 (Low, in C12),
-// P3 (in C21) and P4^T (in C22); writes U4 over C21 and Low(U5) over C22.
-cudaError_t launch_postadd(int32_t *C11, int32_t *C12, int32_t *C21, int32_t *C22,
-                           int64_t ldc, int64_t h, const ModP &m, cudaStream_t st);
+// What the SYRK schedule (Table 4) saved of C22 before it received P4^T:
+// its strictly lower part transposed into the upper triangle `up` of C11
+// (row stride ldc), its diagonal in dg; U5 gains beta times it.
+struct SyrkSave {
+  const int32_t *up;
+  const int32_t *dg;
+  MulConst beta;
+};
 
-// Low(C11) <- Low(C11 + C12)   (U3 = P1 + P2)
-cudaError_t launch_add_low(int32_t *C11, const int32_t *C12, int64_t ldc, int64_t h,
+// K6: U4 and U5 of Algorithm 1 from P1 (Low, at P1 with row stride ldp: C11
+// in Table 3), P5 (Low, in C12), P3 (in C21) and P4^T (in C22); writes U4
+// over C21 and Low(U5) (+ beta Low(C22 before), SYRK) over C22.
+cudaError_t launch_postadd(const int32_t *P1, int64_t ldp, int32_t *C12, int32_t *C21,
+                           int32_t *C22, int64_t ldc, int64_t h, const ModP &m, cudaStream_t st,
+                           const SyrkSave *sv = nullptr);
+
+// Up(C11) <- Low(C22)^T strictly, dg <- diag(C22) (SYRK, Table 4).
+cudaError_t launch_save_c22(int32_t *C11, const int32_t *C22, int64_t ldc, int64_t h, int32_t *dg,
+                            cudaStream_t st);
+
+// Low(C) <- beta Low(C).
+cudaError_t launch_scale_low(int32_t *C, int64_t ldc, int64_t n, MulConst beta, const ModP &m,
+                             cudaStream_t st);
+
+// Low(C11) <- Low(C11 + S)   (U3 = P1 + P2)
+cudaError_t launch_add_low(int32_t *C11, int64_t ldc, const int32_t *S, int64_t lds, int64_t h,
                            const ModP &m, cudaStream_t st);
 
 // Copy / pad: dst (rows_d x cols_d) <- src (rows x cols) with zeros outside.
@@ -239,12 +312,16 @@ cudaError_t launch_pad_copy(const int32_t *src, int64_t lds, int64_t rows, int64
 cudaError_t launch_copy_low(const int32_t *src, int64_t lds, int32_t *dst, int64_t ldd,
                             int64_t n, cudaStream_t st);
 cudaError_t launch_zero_upper(int32_t *C, int64_t ldc, int64_t n, cudaStream_t st);
+// count balanced residues mod p, element t = SplitMix64 output t of stream
+// `seed` mapped to [0, p) by (z >> 32) p >> 32 (synthetic tuning inputs).
+cudaError_t launch_fill_residues(int32_t *A, int64_t count, uint32_t p, uint64_t seed,
+                                 cudaStream_t st);
 
-// Plain CUDA-core leaf: out = X Y^T mod p (lower triangle only if `lower`;
-// out = out + X Y^T if `accumulate`).  Exact int64 arithmetic.
+// Plain CUDA-core leaf: out <- alpha X Y^T + beta out mod p (lin; lower
+// triangle only if `lower`).  Exact int64 arithmetic.
 cudaError_t launch_leaf_simt(const int32_t *X, int64_t ldx, const int32_t *Y, int64_t ldy,
                              int64_t M, int64_t N, int64_t K, int32_t *out, int64_t ldo,
-                             int lower, int accumulate, const ModP &m, cudaStream_t st);
+                             int lower, const Lin &lin, const ModP &m, cudaStream_t st);
 
 // Warp-level mma.sync leaves (k_leaf_mma.cu): INT8 digits with exact INT32
 // accumulation (workspace: leaf_i8_workspace bytes), and FP64 (exact while
@@ -253,10 +330,10 @@ int i8_digits(uint32_t p);
 size_t leaf_i8_workspace(int64_t M, int64_t N, int64_t K, uint32_t p);
 cudaError_t launch_leaf_i8(const int32_t *X, int64_t ldx, const int32_t *Y, int64_t ldy,
                            int64_t M, int64_t N, int64_t K, int32_t *out, int64_t ldo, int lower,
-                           int accumulate, const ModP &m, void *ws, cudaStream_t st);
+                           const Lin &lin, const ModP &m, void *ws, cudaStream_t st);
 cudaError_t launch_leaf_f64(const int32_t *X, int64_t ldx, const int32_t *Y, int64_t ldy,
                             int64_t M, int64_t N, int64_t K, int32_t *out, int64_t ldo, int lower,
-                            int accumulate, const ModP &m, cudaStream_t st);
+                            const Lin &lin, const ModP &m, cudaStream_t st);
 
 // Tensor-core leaf: out = sum over digit pairs (i, j) of 2^(b (i + j))
 // X_i Y_j^T mod p on tcgen05 (BF16 digits, FP32 accumulation drained to
@@ -268,8 +345,9 @@ struct TcLeafArgs {
   int32_t *out;
   int64_t ldo;
   int lower;              // only tiles/entries with i >= j
-  int accumulate;         // out <- out + product
+  Lin lin;                // out <- alpha product + beta out
   int exact_bits;         // |partial FP32 sums| kept <= 2^exact_bits
+  int form;               // kernel form: 0 chosen from the shape, 1 one CTA, 2 CTA pairs
 };
 cudaError_t launch_leaf_tc(const TcLeafArgs &a, const ModP &m, cudaStream_t st);
 void leaf_tc_release();
@@ -298,9 +376,9 @@ cudaError_t launch_split_batch(const SplitDesc *descs_dev, int count, int64_t ma
 void leaf_f32_release();
 
 // Host helpers of the batched plans.
-int modp_levels(int64_t n, int64_t k, uint32_t flags);
+int modp_levels(int64_t n, int64_t k, uint32_t p, uint32_t flags);
 Planes planes_layout(const DigitSpec &ds, int64_t rows, int64_t cols);
-DigitSpec digits_for_flags(uint32_t p, uint32_t flags);
+DigitSpec digits_for_problem(int64_t n, int64_t k, uint32_t p, uint32_t flags);
 // One Low(A A^T) mod p with an explicit workspace (dry: only *need).
 int modp_run(const int32_t *A, int64_t n, int64_t k, int64_t lda, uint32_t p, int32_t *C,
              int64_t ldc, uint32_t flags, cudaStream_t st, char *ws, bool dry, size_t *need);

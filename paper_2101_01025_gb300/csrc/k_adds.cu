@@ -180,11 +180,22 @@ __global__ void split_batch_kernel(const SplitDesc *__restrict__ descs) {
 // and no other block touches them, so the in-place update is safe.
 constexpr int T = 32;
 
-__global__ void postadd_kernel(const int32_t *__restrict__ C11, const int32_t *__restrict__ C12,
-                               int32_t *C21, int32_t *C22, int64_t ldc, int64_t h, ModP m) {
+// U1 = Sym(P1 + P5), U2 = U1 + P4, U4 = U2 + P3 -> C21 and
+// Low(U5) = Low(U2 + P4^T) (+ beta Low(C22 before)) -> C22, one tile pair
+// {(I, J), (J, I)} of the h x h blocks per CTA.  P1 is read from `P1` (C11
+// in the Table 3 schedule, the temporary in the SYRK one); in the SYRK
+// schedule (beta != 0) the strictly lower part of the original C22 is read
+// back transposed from `up` (the upper triangle of C11) and its diagonal
+// from `dg`.
+template <bool SYRK>
+__global__ void postadd_kernel(const int32_t *__restrict__ P1, int64_t ldp,
+                               const int32_t *__restrict__ C12, int32_t *C21, int32_t *C22,
+                               int64_t ldc, int64_t h, ModP m, const int32_t *__restrict__ up,
+                               const int32_t *__restrict__ dg, uint32_t beta, uint32_t beta_sh) {
   __shared__ int32_t p4t_ij[T][T + 1];  // C22 tile (I, J) = P4^T block
   __shared__ int32_t p4t_ji[T][T + 1];  // C22 tile (J, I)
   __shared__ int32_t u1_ij[T][T + 1];   // U1 tile (I, J) (lower part source)
+  __shared__ int32_t up_ji[SYRK ? T : 1][T + 1];  // saved C22, transposed (tile (J, I) of C11)
   const int64_t ntiles = (h + T - 1) / T;
   // map blockIdx.x to (I, J) with I >= J
   int64_t pid = blockIdx.x;
@@ -202,10 +213,14 @@ __global__ void postadd_kernel(const int32_t *__restrict__ C11, const int32_t *_
       p4t_ij[yy][tx] = bal(C22[r * ldc + c], m);
       // U1(r, c): lower entries from P1 + P5, upper ones by symmetry
       int64_t lr = r >= c ? r : c, lc = r >= c ? c : r;
-      u1_ij[yy][tx] = add_bal(bal(C11[lr * ldc + lc], m), bal(C12[lr * ldc + lc], m), m);
+      u1_ij[yy][tx] = add_bal(bal(P1[lr * ldp + lc], m), bal(C12[lr * ldc + lc], m), m);
     }
     int64_t r2 = c0 + yy, c2 = r0 + tx;  // tile (J, I)
-    if (r2 < h && c2 < h) p4t_ji[yy][tx] = bal(C22[r2 * ldc + c2], m);
+    if (r2 < h && c2 < h) {
+      p4t_ji[yy][tx] = bal(C22[r2 * ldc + c2], m);
+      if constexpr (SYRK)
+        if (r2 < c2) up_ji[yy][tx] = bal(up[r2 * ldc + c2], m);
+    }
   }
   __syncthreads();
   // tile (I, J): U4 and U5
@@ -219,6 +234,12 @@ __global__ void postadd_kernel(const int32_t *__restrict__ C11, const int32_t *_
       C21[r * ldc + c] = (int32_t)bal_to_canon(u4, m);
       if (r >= c) {
         int32_t u5 = add_bal(u2, p4t_ij[yy][tx], m);
+        if constexpr (SYRK) {
+          // C22 before the update: (r, c) was saved at (c, r) of C11
+          int32_t old = r == c ? bal(dg[r], m) : up_ji[tx][yy];
+          if (beta != 1u) old = mulmod_shoup(old, beta, beta_sh, m);
+          u5 = add_bal(u5, old, m);
+        }
         C22[r * ldc + c] = (int32_t)bal_to_canon(u5, m);
       }
     }
@@ -237,14 +258,57 @@ __global__ void postadd_kernel(const int32_t *__restrict__ C11, const int32_t *_
   }
 }
 
-__global__ void add_low_kernel(int32_t *C11, const int32_t *__restrict__ C12, int64_t ldc,
-                               int64_t h, ModP m) {
+// The SYRK schedule's first step (Table 4): Up(C11) <- Low(C22)^T on the
+// strictly triangular parts (C11[c][r] = C22[r][c], r > c) and dg[r] =
+// C22[r][r], so that C22 can receive P4^T.  One T x T tile of Low(C22) per
+// CTA, transposed through shared memory.
+__global__ void save_c22_kernel(int32_t *C11, const int32_t *__restrict__ C22, int64_t ldc,
+                                int64_t h, int32_t *dg) {
+  __shared__ int32_t t[T][T + 1];
+  const int64_t ntiles = (h + T - 1) / T;
+  int64_t pid = blockIdx.x;
+  int64_t I = (int64_t)((sqrt(8.0 * (double)pid + 1.0) - 1.0) * 0.5);
+  while (I * (I + 1) / 2 > pid) --I;
+  while ((I + 1) * (I + 2) / 2 <= pid) ++I;
+  const int64_t J = pid - I * (I + 1) / 2;
+  if (I >= ntiles) return;
+  const int tx = threadIdx.x % T, ty = threadIdx.x / T;
+  const int64_t r0 = I * T, c0 = J * T;
+  for (int yy = ty; yy < T; yy += 8) {
+    const int64_t r = r0 + yy, c = c0 + tx;
+    if (r < h && c < h && r >= c) {
+      const int32_t v = C22[r * ldc + c];
+      t[yy][tx] = v;
+      if (r == c) dg[r] = v;
+    }
+  }
+  __syncthreads();
+  for (int yy = ty; yy < T; yy += 8) {
+    const int64_t rr = c0 + yy, cc = r0 + tx;  // C11 (rr, cc) <- C22 (cc, rr)
+    if (rr < h && cc < h && cc > rr) C11[rr * ldc + cc] = t[tx][yy];
+  }
+}
+
+// Low(C) <- beta Low(C) (the SYRK update with k = 0).
+__global__ void scale_low_kernel(int32_t *C, int64_t ldc, int64_t n, uint32_t beta,
+                                 uint32_t beta_sh, ModP m) {
+  const int64_t total = n * n;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / n, c = t - (t / n) * n;
+    if (c > r) continue;
+    C[r * ldc + c] = (int32_t)bal_to_canon(mulmod_shoup(bal(C[r * ldc + c], m), beta, beta_sh, m), m);
+  }
+}
+
+__global__ void add_low_kernel(int32_t *C11, int64_t ldc, const int32_t *__restrict__ S,
+                               int64_t lds, int64_t h, ModP m) {
   const int64_t total = h * h;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = t / h, c = t - (t / h) * h;
     if (c > r) continue;
-    int32_t v = add_bal(bal(C11[r * ldc + c], m), bal(C12[r * ldc + c], m), m);
+    int32_t v = add_bal(bal(C11[r * ldc + c], m), bal(S[r * lds + c], m), m);
     C11[r * ldc + c] = (int32_t)bal_to_canon(v, m);
   }
 }
@@ -378,22 +442,47 @@ cudaError_t launch_split_batch(const SplitDesc *descs_dev, int count, int64_t ma
   return cudaGetLastError();
 }
 
-cudaError_t launch_postadd(int32_t *C11, int32_t *C12, int32_t *C21, int32_t *C22,
-                           int64_t ldc, int64_t h, const ModP &m, cudaStream_t st) {
+cudaError_t launch_postadd(const int32_t *P1, int64_t ldp, int32_t *C12, int32_t *C21,
+                           int32_t *C22, int64_t ldc, int64_t h, const ModP &m, cudaStream_t st,
+                           const SyrkSave *sv) {
   if (h <= 0) return cudaSuccess;
   const int64_t nt = (h + T - 1) / T;
   const int64_t pairs = nt * (nt + 1) / 2;
   const double tri = 0.5 * (double)h * (double)(h + 1), sq = (double)h * h;
-  ProfScope prof(AAT_K_POSTADD, st, 4.0 * (3.0 * tri + 3.0 * sq));
-  postadd_kernel<<<(unsigned)pairs, T * 8, 0, st>>>(C11, C12, C21, C22, ldc, h, m);
+  const bool b = sv && sv->beta.w;
+  ProfScope prof(AAT_K_POSTADD, st, 4.0 * ((b ? 4.0 : 3.0) * tri + 3.0 * sq));
+  if (b)
+    postadd_kernel<true><<<(unsigned)pairs, T * 8, 0, st>>>(P1, ldp, C12, C21, C22, ldc, h, m,
+                                                           sv->up, sv->dg, sv->beta.w,
+                                                           sv->beta.wsh);
+  else
+    postadd_kernel<false><<<(unsigned)pairs, T * 8, 0, st>>>(P1, ldp, C12, C21, C22, ldc, h, m,
+                                                            nullptr, nullptr, 0u, 0u);
   return cudaGetLastError();
 }
 
-cudaError_t launch_add_low(int32_t *C11, const int32_t *C12, int64_t ldc, int64_t h,
+cudaError_t launch_save_c22(int32_t *C11, const int32_t *C22, int64_t ldc, int64_t h, int32_t *dg,
+                            cudaStream_t st) {
+  if (h <= 0) return cudaSuccess;
+  const int64_t nt = (h + T - 1) / T;
+  ProfScope prof(AAT_K_COPY, st, 8.0 * 0.5 * (double)h * (double)(h + 1));
+  save_c22_kernel<<<(unsigned)(nt * (nt + 1) / 2), T * 8, 0, st>>>(C11, C22, ldc, h, dg);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_low(int32_t *C, int64_t ldc, int64_t n, MulConst beta, const ModP &m,
+                             cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  ProfScope prof(AAT_K_COPY, st, 8.0 * 0.5 * (double)n * (double)(n + 1));
+  scale_low_kernel<<<grid_for(n * n), kThreads, 0, st>>>(C, ldc, n, beta.w, beta.wsh, m);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add_low(int32_t *C11, int64_t ldc, const int32_t *S, int64_t lds, int64_t h,
                            const ModP &m, cudaStream_t st) {
   if (h <= 0) return cudaSuccess;
   ProfScope prof(AAT_K_ADD_LOW, st, 4.0 * 3.0 * 0.5 * (double)h * (double)(h + 1));
-  add_low_kernel<<<grid_for(h * h), kThreads, 0, st>>>(C11, C12, ldc, h, m);
+  add_low_kernel<<<grid_for(h * h), kThreads, 0, st>>>(C11, ldc, S, lds, h, m);
   return cudaGetLastError();
 }
 
@@ -412,6 +501,25 @@ cudaError_t launch_copy_low(const int32_t *src, int64_t lds, int32_t *dst, int64
   if (n <= 0) return cudaSuccess;
   ProfScope prof(AAT_K_COPY, st, 8.0 * 0.5 * (double)n * (double)(n + 1));
   copy_low_kernel<<<grid_for(n * n), kThreads, 0, st>>>(src, lds, dst, ldd, n);
+  return cudaGetLastError();
+}
+
+__global__ void fill_residues_kernel(int32_t *A, int64_t count, uint32_t p, uint64_t seed) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += stride) {
+    uint64_t z = seed + (uint64_t)(t + 1) * 0x9E3779B97F4A7C15ull;  // SplitMix64
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    const uint32_t r = (uint32_t)(((z >> 32) * (uint64_t)p) >> 32);
+    A[t] = r > (p - 1) / 2 ? (int32_t)r - (int32_t)p : (int32_t)r;
+  }
+}
+
+cudaError_t launch_fill_residues(int32_t *A, int64_t count, uint32_t p, uint64_t seed,
+                                 cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  fill_residues_kernel<<<grid_for(count), kThreads, 0, st>>>(A, count, p, seed);
   return cudaGetLastError();
 }
 

@@ -68,7 +68,8 @@ struct I8Args {
   uint32_t w2;            // 2^8 mod p (Horner base)
   int32_t *out;
   int64_t ldo;
-  int lower, accumulate;
+  int lower;
+  Lin lin;
   ModP m;
 };
 
@@ -187,9 +188,9 @@ __global__ void __launch_bounds__(I8_THREADS) leaf_i8_kernel(I8Args a) {
         const int64_t r = r0 + wm * 64 + i * 16 + g + (q >> 1) * 8;
         const int64_t c = c0 + wn * 32 + j * 8 + 2 * tq + (q & 1);
         if (r >= a.M || c >= a.N || (a.lower && c > r)) continue;
-        int32_t v = red_s64((int64_t)acc[i][j][q], m);
-        if (a.accumulate) v = add_bal(v, bal(a.out[r * a.ldo + c], m), m);
-        a.out[r * a.ldo + c] = (int32_t)bal_to_canon(v, m);
+        const int32_t v = red_s64((int64_t)acc[i][j][q], m);
+        const int32_t old = a.lin.beta.w ? a.out[r * a.ldo + c] : 0;
+        a.out[r * a.ldo + c] = (int32_t)lin_apply(v, old, a.lin, m);
       }
 }
 
@@ -204,7 +205,8 @@ struct F64Args {
   int64_t kchunk;  // K steps per exact FP64 chunk (a multiple of F_BK)
   int32_t *out;
   int64_t ldo;
-  int lower, accumulate;
+  int lower;
+  Lin lin;
   ModP m;
 };
 
@@ -277,9 +279,9 @@ __global__ void __launch_bounds__(F_THREADS) leaf_f64_kernel(F64Args a) {
         const int64_t r = r0 + wm * 32 + i * 8 + g;
         const int64_t c = c0 + wn * 32 + j * 8 + 2 * tq + q;
         if (r >= a.M || c >= a.N || (a.lower && c > r)) continue;
-        int32_t v = red_s64((int64_t)reduce_f64(acc[i][j][q], pd), m);
-        if (a.accumulate) v = add_bal(v, bal(a.out[r * a.ldo + c], m), m);
-        a.out[r * a.ldo + c] = (int32_t)bal_to_canon(v, m);
+        const int32_t v = red_s64((int64_t)reduce_f64(acc[i][j][q], pd), m);
+        const int32_t old = a.lin.beta.w ? a.out[r * a.ldo + c] : 0;
+        a.out[r * a.ldo + c] = (int32_t)lin_apply(v, old, a.lin, m);
       }
 }
 
@@ -310,7 +312,7 @@ size_t leaf_i8_workspace(int64_t M, int64_t N, int64_t K, uint32_t p) {
 
 cudaError_t launch_leaf_i8(const int32_t *X, int64_t ldx, const int32_t *Y, int64_t ldy,
                            int64_t M, int64_t N, int64_t K, int32_t *out, int64_t ldo, int lower,
-                           int accumulate, const ModP &m, void *ws, cudaStream_t st) {
+                           const Lin &lin, const ModP &m, void *ws, cudaStream_t st) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   const int L = i8_digits(m.p);
   // int32 accumulation of one digit pair: (p-1)/2 + K 127^2 < 2^31
@@ -338,7 +340,7 @@ cudaError_t launch_leaf_i8(const int32_t *X, int64_t ldx, const int32_t *Y, int6
   a.out = out;
   a.ldo = ldo;
   a.lower = lower;
-  a.accumulate = accumulate;
+  a.lin = lin;
   a.m = m;
   dim3 grid((unsigned)((N + I8_BN - 1) / I8_BN), (unsigned)((M + I8_BM - 1) / I8_BM));
   const double macs = lower ? 0.5 * (double)M * (double)(M + 1) * K : (double)M * N * K;
@@ -349,7 +351,7 @@ cudaError_t launch_leaf_i8(const int32_t *X, int64_t ldx, const int32_t *Y, int6
 
 cudaError_t launch_leaf_f64(const int32_t *X, int64_t ldx, const int32_t *Y, int64_t ldy,
                             int64_t M, int64_t N, int64_t K, int32_t *out, int64_t ldo, int lower,
-                            int accumulate, const ModP &m, cudaStream_t st) {
+                            const Lin &lin, const ModP &m, cudaStream_t st) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   // partial sums: p (after a reduction) + kchunk ((p-1)/2)^2 < 2^53
   const double h = (double)m.half;
@@ -369,7 +371,7 @@ cudaError_t launch_leaf_f64(const int32_t *X, int64_t ldx, const int32_t *Y, int
   a.out = out;
   a.ldo = ldo;
   a.lower = lower;
-  a.accumulate = accumulate;
+  a.lin = lin;
   a.m = m;
   dim3 grid((unsigned)((N + F_BN - 1) / F_BN), (unsigned)((M + F_BM - 1) / F_BM));
   const double macs = lower ? 0.5 * (double)M * (double)(M + 1) * K : (double)M * N * K;

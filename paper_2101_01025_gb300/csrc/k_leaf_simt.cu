@@ -13,7 +13,7 @@ constexpr int TK = 32;
 __global__ void leaf_simt_kernel(const int32_t *__restrict__ X, int64_t ldx,
                                  const int32_t *__restrict__ Y, int64_t ldy, int64_t M,
                                  int64_t N, int64_t K, int32_t *out, int64_t ldo, int lower,
-                                 int accumulate, ModP m) {
+                                 Lin lin, ModP m) {
   __shared__ int32_t xs[TS][TK + 1];
   __shared__ int32_t ys[TS][TK + 1];
   const int64_t r0 = (int64_t)blockIdx.y * TS, c0 = (int64_t)blockIdx.x * TS;
@@ -41,9 +41,8 @@ __global__ void leaf_simt_kernel(const int32_t *__restrict__ X, int64_t ldx,
     int64_t r = r0 + ty + 8 * q, c = c0 + tx;
     if (r >= M || c >= N) continue;
     if (lower && c > r) continue;
-    int32_t v = acc[q];
-    if (accumulate) v = add_bal(v, bal(out[r * ldo + c], m), m);
-    out[r * ldo + c] = (int32_t)bal_to_canon(v, m);
+    const int32_t old = lin.beta.w ? out[r * ldo + c] : 0;
+    out[r * ldo + c] = (int32_t)lin_apply(acc[q], old, lin, m);
   }
 }
 
@@ -51,13 +50,12 @@ __global__ void leaf_simt_kernel(const int32_t *__restrict__ X, int64_t ldx,
 
 cudaError_t launch_leaf_simt(const int32_t *X, int64_t ldx, const int32_t *Y, int64_t ldy,
                              int64_t M, int64_t N, int64_t K, int32_t *out, int64_t ldo,
-                             int lower, int accumulate, const ModP &m, cudaStream_t st) {
+                             int lower, const Lin &lin, const ModP &m, cudaStream_t st) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   dim3 grid((unsigned)((N + TS - 1) / TS), (unsigned)((M + TS - 1) / TS));
   const double macs = lower ? 0.5 * (double)M * (double)(M + 1) * K : (double)M * N * K;
   ProfScope prof(AAT_K_LEAF_SIMT, st, 2.0 * macs);
-  leaf_simt_kernel<<<grid, 256, 0, st>>>(X, ldx, Y, ldy, M, N, K, out, ldo, lower,
-                                         accumulate, m);
+  leaf_simt_kernel<<<grid, 256, 0, st>>>(X, ldx, Y, ldy, M, N, K, out, ldo, lower, lin, m);
   return cudaGetLastError();
 }
 

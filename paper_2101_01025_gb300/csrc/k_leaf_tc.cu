@@ -71,7 +71,8 @@ struct alignas(64) BatchProb {
   int32_t *out;
   int64_t ldo, M, N;
   int goff, ng;  // its groups: gtab[goff .. goff + ng)
-  int lower, accumulate;
+  int lower, accumulate;  // accumulate: out <- product + beta out
+  uint32_t beta, beta_sh;
   ModP m;
 };
 
@@ -84,7 +85,8 @@ struct Params {
   int64_t ldo, M, N;
   const int2 *tiles;
   int ntiles;
-  int lower, accumulate;
+  int lower, accumulate;  // accumulate: out <- product + beta out
+  uint32_t beta, beta_sh;
   ModP m;
   int32_t *status;
   // batched launches: tiles are (problem, I, J) and every problem carries
@@ -168,6 +170,7 @@ struct OutView {
   int32_t *out;
   int64_t ldo, M, N;
   int lower, accumulate;
+  uint32_t beta, beta_sh;
 };
 
 template <bool BATCH>
@@ -181,6 +184,8 @@ __device__ __forceinline__ OutView tile_out(const Params &P, int t) {
     o.N = b.N;
     o.lower = b.lower;
     o.accumulate = b.accumulate;
+    o.beta = b.beta;
+    o.beta_sh = b.beta_sh;
   } else {
     o.out = P.out;
     o.ldo = P.ldo;
@@ -188,21 +193,10 @@ __device__ __forceinline__ OutView tile_out(const Params &P, int t) {
     o.N = P.N;
     o.lower = P.lower;
     o.accumulate = P.accumulate;
+    o.beta = P.beta;
+    o.beta_sh = P.beta_sh;
   }
   return o;
-}
-
-// a * w mod p, balanced, for any int32 a and a fixed w in [0, p) with
-// wsh = floor(w 2^32 / p) (Shoup's modular multiplication): with |a| < 2^32,
-// |a| w - floor(|a| wsh / 2^32) p lies in [0, 2p), so 32-bit arithmetic and
-// one conditional subtraction give the residue.
-__device__ __forceinline__ int32_t mulmod_shoup(int32_t a, uint32_t w, uint32_t wsh, const ModP &m) {
-  const uint32_t ax = a < 0 ? 0u - (uint32_t)a : (uint32_t)a;
-  const uint32_t q = __umulhi(ax, wsh);
-  uint32_t r = ax * w - q * m.p;
-  if (r >= m.p) r -= m.p;
-  const int32_t b = r > m.half ? (int32_t)r - (int32_t)m.p : (int32_t)r;
-  return a < 0 ? -b : b;
 }
 
 // ------------------------------------------------------------------ kernel
@@ -496,7 +490,11 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_tc_kernel(const __grid_consta
             for (int j = 0; j < 4; ++j) {
               if (c + j < lim) {
                 int32_t x = acc[c + j];
-                if (o.accumulate) x = (int32_t)bal_to_canon(add_bal(to_bal((uint32_t)x, m), bal(orow[c + j], m), m), m);
+                if (o.accumulate) {
+                  int32_t old = bal(orow[c + j], m);
+                  if (o.beta != 1u) old = mulmod_shoup(old, o.beta, o.beta_sh, m);
+                  x = (int32_t)bal_to_canon(add_bal(to_bal((uint32_t)x, m), old, m), m);
+                }
                 orow[c + j] = x;
               }
             }
@@ -691,12 +689,16 @@ bool build_groups(const TcLeafArgs &a, const ModP &m, Group *out, int *ng_out, i
       }
     }
   }
-  if (ng > 0 && wprev != 1u) {  // final multiplier: a group without K blocks
+  // final multiplier (a group without K blocks): the last weight times the
+  // product's scale alpha (the SYRK update's alpha, 1 otherwise)
+  const uint32_t wfinal = mulm(wprev, a.lin.alpha.w % m.p);
+  if (ng > 0 && wfinal != 1u) {
+    if (ng >= MAX_GROUPS) return false;
     Group &g = out[ng++];
     g.xp = g.yp = 0;
     g.kb0 = g.kb1 = 0;
     g.kchunk = 1;
-    g.ratio = wprev;
+    g.ratio = wfinal;
   }
   set_shoup(out, ng, m.p);
   int nprod = 0;
@@ -733,9 +735,10 @@ int pair_units(int dev) {
   return units;
 }
 
-// AAT_LEAF_PAIR=0 keeps every leaf on the one-CTA form, =1 puts every leaf
-// with at least 256 rows on the CTA-pair form; unset: the pair form when its
-// tiles fill every co-resident pair at least once.
+// The form of a leaf: the caller's (TcLeafArgs::form, set by the tuning
+// table), else AAT_LEAF_PAIR=0 (every leaf on the one-CTA form) or =1 (every
+// leaf with at least 256 rows on the CTA-pair form), else the pair form when
+// its tiles fill every co-resident pair at least once.
 int pair_override() {
   static const int v = [] {
     const char *e = getenv("AAT_LEAF_PAIR");
@@ -766,7 +769,7 @@ cudaError_t launch_leaf_tc(const TcLeafArgs &a, const ModP &m, cudaStream_t st) 
   bool pair = false;
   if (units > 0 && a.M >= 256) {
     const int64_t pt = ((a.M + 255) / 256) * ((a.N + BN - 1) / BN);
-    const int ov = pair_override();
+    const int ov = a.form > 0 ? a.form - 1 : pair_override();
     pair = ov >= 0 ? ov > 0 : (a.lower ? pt / 2 : pt) >= units;
   }
   const int tm = pair ? Shape<true>::TM : Shape<false>::TM;
@@ -790,7 +793,9 @@ cudaError_t launch_leaf_tc(const TcLeafArgs &a, const ModP &m, cudaStream_t st) 
   P->M = a.M;
   P->N = a.N;
   P->lower = a.lower;
-  P->accumulate = a.accumulate;
+  P->accumulate = a.lin.beta.w != 0u;
+  P->beta = a.lin.beta.w;
+  P->beta_sh = a.lin.beta.wsh;
   P->m = m;
   P->status = device_status_ptr();
   int2 *tiles = nullptr;
@@ -876,7 +881,9 @@ cudaError_t leaf_tc_batch_build(const TcLeafArgs *args, const ModP *mods, int co
     b.M = a.M;
     b.N = a.N;
     b.lower = a.lower;
-    b.accumulate = a.accumulate;
+    b.accumulate = a.lin.beta.w != 0u;
+    b.beta = a.lin.beta.w;
+    b.beta_sh = a.lin.beta.wsh;
     b.m = mods[i];
     const double kb = (double)((a.K + BK - 1) / BK);
     const double cost = kb * nprod;  // K blocks x plane products per tile
@@ -1137,6 +1144,7 @@ extern "C" AAT_API int aat_gemm_modp_noalloc(const int32_t *X, int64_t ldx, cons
   P.N = n;
   P.lower = 0;
   P.accumulate = 0;
+  P.beta = P.beta_sh = 0;
   P.m = mp;
   P.status = nd.status;
   P.tiles = tiles_dev;
@@ -1174,6 +1182,7 @@ extern "C" AAT_API int aatx_leaf_groups(uint32_t p, int64_t K, uint32_t flags, i
   a.M = a.N = 1;
   a.K = K;
   a.exact_bits = exact_bits > 0 ? exact_bits : 24;
+  a.lin = lin_of(1, 0, p);
   std::vector<Group> g(MAX_GROUPS);
   int ng = 0;
   if (!build_groups(a, make_modp(p), g.data(), &ng, nprod))

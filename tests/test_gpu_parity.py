@@ -277,6 +277,30 @@ def test_aat_modp_host_early_rows_overlap(lib, levels):
     assert np.array_equal(got[ij[:, 0], ij[:, 1]].astype(np.int64), np.asarray(ref, dtype=np.int64))
 
 
+def test_autotune_choice_is_used_and_exact(lib):
+    """aat_tune_modp times every candidate (levels, leaf form, digit form)
+    for one shape; later calls of that shape take the choice from the table
+    and stay bit-exact."""
+    p = 2**31 - 1
+    n, k = 2048, 1024
+    lib.tune_clear()
+    t = lib.tune_modp(n, k, p, reps=1)
+    assert t["form"] in (0, 1, 2) and 0 <= t["levels"] <= 4 and t["plain_digits"] in (0, 1)
+    assert t["ms"] > 0 and t["ms_default"] > 0
+    assert lib.tune_lookup(n, k, p) == t
+    from paper_2101_01025_gb300 import testing as T
+    assert T.plan_stats(n, k, p).levels == t["levels"]
+    A = synth.residues(93, (n, k), p, balanced=True)
+    C = host(lib.aat_modp(dev(A), p))
+    ref = host(lib.aat_modp(dev(A), p, levels=1))
+    assert low_equal(C, ref)
+    ij = np.array([(i, j) for i in (0, 1, 1023, 1024, 2047) for j in (0, i // 3, i)],
+                  dtype=np.int64)
+    want = np.asarray(oracle.aat_modp_entries(A, p, ij), dtype=np.int64)
+    assert np.array_equal(C[ij[:, 0], ij[:, 1]].astype(np.int64), want)
+    lib.tune_clear()
+
+
 def test_aat_modp_host_zero_upper_copies_everything(lib):
     p = 131071
     A = synth.residues(92, (600, 400), p)
@@ -338,3 +362,53 @@ def test_full_size_n16384_p2_31m1(lib):
 def test_full_size_config2(lib, n, k, p):
     A = synth.residues(synth.SEED_BASE + 1, (n, k), p)
     _full_check(lib, A, p, levels_expected_min=0, nsample=1500, nvec=1)
+
+
+# ------------------------------------------------------- SYRK form (Sec. 7)
+
+@pytest.mark.parametrize("p", PRIMES)
+@pytest.mark.parametrize("n,k,levels", [(512, 384, 1), (600, 400, 2), (333, 250, 1),
+                                        (256, 640, 1), (700, 350, 0)])
+def test_syrk_update_matches_oracle(lib, p, n, k, levels):
+    """Low(C) <- alpha Low(A A^T) + beta Low(C) by the Table 4 schedule:
+    ragged and padded shapes, k > n (S3 in workspace), 0-2 levels."""
+    A = synth.residues(51, (n, k), p, balanced=(p == 2**31 - 1))
+    C0 = synth.residues(52, (n, n), p).astype(np.int32)
+    for alpha, beta in [(1, 1), (7, p - 3), (p - 1, 2**32 - 5)]:
+        C = dev(C0)
+        lib.aat_syrk_modp(alpha, dev(A), beta, C, p, levels=levels)
+        want = oracle.syrk_modp_low(alpha, A, beta % p, C0, p)
+        assert low_equal(host(C), want), (alpha, beta)
+
+
+@pytest.mark.parametrize("leaf", ["AAT_LEAF_SIMT", "AAT_LEAF_I8"])
+def test_syrk_update_other_leaves(lib, leaf):
+    p = 131071
+    A = synth.residues(53, (384, 256), p)
+    C0 = synth.residues(54, (384, 384), p).astype(np.int32)
+    C = dev(C0)
+    lib.aat_syrk_modp(5, dev(A), 9, C, p, flags=getattr(lib, leaf), levels=2)
+    assert low_equal(host(C), oracle.syrk_modp_low(5, A, 9, C0, p))
+
+
+def test_syrk_update_degenerate(lib):
+    p = 65521
+    A = synth.residues(55, (300, 200), p)
+    C0 = synth.residues(56, (300, 300), p).astype(np.int32)
+    # beta = 0: alpha times the product; alpha = 0: beta C; k = 0: beta C
+    C = dev(C0)
+    lib.aat_syrk_modp(3, dev(A), 0, C, p)
+    assert low_equal(host(C), oracle.syrk_modp_low(3, A, 0, C0, p))
+    C = dev(C0)
+    lib.aat_syrk_modp(0, dev(A), 4, C, p)
+    assert low_equal(host(C), oracle.syrk_modp_low(0, A, 4, C0, p))
+    C = dev(C0)
+    lib.aat_syrk_modp(2, torch.empty((300, 0), dtype=torch.int32, device="cuda"), 6, C, p)
+    assert low_equal(host(C), (6 * C0.astype(np.int64)) % p)
+    # balanced C entries on input, zeroed upper triangle on request
+    Cb = np.where(C0 > p // 2, C0 - p, C0).astype(np.int32)
+    C = dev(Cb)
+    lib.aat_syrk_modp(1, dev(A), 1, C, p, flags=lib.AAT_ZERO_UPPER, levels=1)
+    got = host(C)
+    assert low_equal(got, oracle.syrk_modp_low(1, A, 1, C0, p))
+    assert not np.triu(got, 1).any()

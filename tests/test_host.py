@@ -227,3 +227,50 @@ def test_host_copy_volume_is_the_lower_triangle_in_bands():
         assert 4 * n * (n + 1) // 2 <= got <= 4 * n * n
         assert aat.aat_modp_host_d2h_bytes(n, aat.AAT_ZERO_UPPER) == 4 * n * n
     assert aat.aat_modp_host_d2h_bytes(0) == 0
+
+
+def test_tuning_table_save_load_and_lookup(tmp_path):
+    """The autotuning table (no GPU needed for the table itself): entries
+    loaded from JSON are looked up by (n, k, p), invalid ones are skipped, a
+    saved table loads back to the same entries, and the plan of a tuned shape
+    takes its recursion depth from the table unless the flags fix it."""
+    import json
+    import paper_2101_01025_gb300 as aat
+    aat.tune_clear()
+    assert aat.tune_lookup(4096, 2048, 2**31 - 1) is None
+    src = tmp_path / "tune.json"
+    entries = [
+        {"n": 4096, "k": 2048, "p": 2**31 - 1, "levels": 3, "form": 1, "plain_digits": 0,
+         "ms": 1.5, "ms_default": 2.0},
+        {"n": 2048, "k": 2048, "p": 65521, "levels": 0, "form": 2, "plain_digits": 1,
+         "ms": 0.5, "ms_default": 0.6},
+        # invalid: not a prime, bad form
+        {"n": 100, "k": 100, "p": 65535, "levels": 1, "form": 1, "plain_digits": 0,
+         "ms": 1.0, "ms_default": 1.0},
+        {"n": 100, "k": 100, "p": 65521, "levels": 1, "form": 7, "plain_digits": 0,
+         "ms": 1.0, "ms_default": 1.0},
+    ]
+    lines = ['{"gpu": "", "entries": [']
+    lines += ["  " + json.dumps(e) + ("," if i + 1 < len(entries) else "")
+              for i, e in enumerate(entries)]
+    lines.append("]}")
+    src.write_text("\n".join(lines) + "\n")
+    assert aat.tune_load(str(src)) == 2
+    t = aat.tune_lookup(4096, 2048, 2**31 - 1)
+    assert t["levels"] == 3 and t["form"] == 1 and t["plain_digits"] == 0
+    assert aat.tune_lookup(2048, 2048, 65521)["plain_digits"] == 1
+    assert aat.tune_lookup(100, 100, 65521) is None
+    # the recursion plan follows the table; explicit levels win
+    assert T.plan_stats(4096, 2048, 2**31 - 1).levels == 3
+    assert T.plan_stats(4096, 2048, 2**31 - 1, flags=aat.AAT_LEVELS(1)).levels == 1
+    out = tmp_path / "saved.json"
+    assert aat.tune_save(str(out)) == 2
+    saved = json.loads(out.read_text())
+    assert sorted((e["n"], e["k"], e["p"], e["levels"]) for e in saved["entries"]) == \
+        [(2048, 2048, 65521, 0), (4096, 2048, 2**31 - 1, 3)]
+    aat.tune_clear()
+    assert aat.tune_lookup(4096, 2048, 2**31 - 1) is None
+    assert aat.tune_load(str(out)) == 2
+    aat.tune_clear()
+    with pytest.raises(aat.AatError):
+        aat.tune_load(str(tmp_path / "missing.json"))
