@@ -114,6 +114,40 @@ def syrk_modp_low(alpha: int, A, beta: int, C, p: int, threads: int = 0) -> np.n
     return np.tril(out).astype(np.uint32)
 
 
+def quat_aah_modp_low(A, B, C, D, p: int, threads: int = 0):
+    """M M^H mod p for the quaternion matrix M = A + B i + C j + D k (n x k
+    over F_p, i^2 = j^2 = k^2 = ijk = -1), M^H the conjugate transpose
+    (Sec. 6.2): returns Low(H1), Low(H2), Low(H3), Low(H4) of
+    H = H1 + H2 i + H3 j + H4 k as n x n uint32 arrays.  Written out from the
+    definition: H[r, c] = sum_l M[r, l] conj(M[c, l]) with the Hamilton
+    product (a1 + b1 i + c1 j + d1 k)(a2 - b2 i - c2 j - d2 k) =
+        (a1 a2 + b1 b2 + c1 c2 + d1 d2)
+      + (-a1 b2 + b1 a2 - c1 d2 + d1 c2) i
+      + (-a1 c2 + b1 d2 + c1 a2 - d1 b2) j
+      + (-a1 d2 - b1 c2 + c1 b2 + d1 a2) k,
+    each sum of products over l one exact product X Y^T mod p (gemm_modp)."""
+    Ms = [_i32(X) for X in (A, B, C, D)]
+    prod = {}
+
+    def g(x, y):
+        if (x, y) not in prod:
+            prod[(x, y)] = gemm_modp(Ms[x], Ms[y], p, threads).astype(np.int64)
+        return prod[(x, y)]
+
+    # (sign, index of the left factor's part, index of the right one's)
+    terms = [
+        [(1, 0, 0), (1, 1, 1), (1, 2, 2), (1, 3, 3)],
+        [(-1, 0, 1), (1, 1, 0), (-1, 2, 3), (1, 3, 2)],
+        [(-1, 0, 2), (1, 1, 3), (1, 2, 0), (-1, 3, 1)],
+        [(-1, 0, 3), (-1, 1, 2), (1, 2, 1), (1, 3, 0)],
+    ]
+    out = []
+    for comp in terms:
+        H = sum(s * g(x, y) for s, x, y in comp) % p
+        out.append(np.tril(H).astype(np.uint32))
+    return tuple(out)
+
+
 def aat_modp_entries(A, p: int, ij, threads: int = 0) -> np.ndarray:
     """(A A^T)[i, j] mod p at the given (i, j) pairs (array of shape (t, 2))."""
     A = _i32(A)

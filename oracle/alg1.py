@@ -14,6 +14,9 @@ blocks as well, so that tests can check the proof identities of Theorem 3.1.
 ``syrk_table4`` takes the steps of the SYRK schedule of Table 4 (Sec. 7),
 one level, on the locations the table names.
 
+``quat_6m`` takes the steps of the 6-multiplication quaternion algorithm of
+Sec. 6.2 over F_p.
+
 ``two_m`` takes the steps of Algorithm 2 (Sec. 6.1) with K = R, E = C.
 """
 from __future__ import annotations
@@ -167,6 +170,31 @@ def syrk_table4(alpha, A, beta, C, p, ykind, ya, yb, save_diagonal=True):
     C11()[:, :] = low((al * (A12 @ A12.T) + be * C11()) % p)  # P2 -> C11
     C11()[:, :] = low((tmp + C11()) % p)              # U3 = P1 + P2 -> C11
     return low(M)
+
+
+def quat_6m(A, B, C, D, p):
+    """The 6-multiplication algorithm of Sec. 6.2 for M M^H, M = A + B i +
+    C j + D k a quaternion matrix (Q6 a product by its own transpose), in the
+    paper's order and notation (U1, U2, Q1..Q6, T1..T3, H1..H4), on exact
+    integers mod p.
+    Returns Low(H1), Low(H2), Low(H3), Low(H4)."""
+    A, B, C, D = (_obj(X) % p for X in (A, B, C, D))
+    U1 = (A + B) % p
+    U2 = (C + D) % p
+    Q1 = (C @ A.T) % p
+    Q2 = (D @ B.T) % p
+    Q3 = (U2 @ U1.T) % p
+    Q4 = (A @ B.T) % p
+    Q5 = (C @ D.T) % p
+    Q6 = ((U1 + U2) @ (U1 + U2).T) % p
+    T1 = (Q1 - Q2) % p
+    T2 = (Q4 + Q5) % p
+    T3 = ((Q1 + Q2) - Q3) % p
+    H1 = low((Q6 - (Q3.T + Q3) - (T2.T + T2)) % p)
+    H2 = low((T2.T - T2) % p)
+    H3 = low((T1 - T1.T) % p)
+    H4 = low((T3.T - T3) % p)
+    return H1, H2, H3, H4
 
 
 def two_m(Are, Aim, conj=True):

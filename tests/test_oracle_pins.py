@@ -531,3 +531,81 @@ def test_syrk_table4_literal_reading_loses_the_diagonal():
     assert not np.array_equal(np.diag(got)[:4], np.diag(want)[:4])
     assert np.array_equal(np.diag(got)[4:], np.diag(want)[4:])
     assert np.array_equal(np.tril(got, -1), np.tril(want, -1))
+
+
+# ------------------------------------------------ quaternions (Sec. 6.2)
+
+def _qmul(x, y, p):
+    """Hamilton product of (a, b, c, d) = a + b i + c j + d k, mod p."""
+    a1, b1, c1, d1 = x
+    a2, b2, c2, d2 = y
+    return ((a1 * a2 - b1 * b2 - c1 * c2 - d1 * d2) % p,
+            (a1 * b2 + b1 * a2 + c1 * d2 - d1 * c2) % p,
+            (a1 * c2 - b1 * d2 + c1 * a2 + d1 * b2) % p,
+            (a1 * d2 + b1 * c2 - c1 * b2 + d1 * a2) % p)
+
+
+def _brute_quat_aah(A, B, C, D, p):
+    n, k = A.shape
+    H = np.zeros((4, n, n), dtype=np.int64)
+    for r in range(n):
+        for c in range(n):
+            acc = (0, 0, 0, 0)
+            for l in range(k):
+                x = (int(A[r, l]), int(B[r, l]), int(C[r, l]), int(D[r, l]))
+                y = (int(A[c, l]), -int(B[c, l]), -int(C[c, l]), -int(D[c, l]))
+                t = _qmul(x, y, p)
+                acc = tuple((u + v) % p for u, v in zip(acc, t))
+            H[:, r, c] = acc
+    return H
+
+
+def test_hamilton_units():
+    """i^2 = j^2 = k^2 = ijk = -1, ij = k, ji = -k (the product used below)."""
+    p = 101
+    one, i, j, k = (1, 0, 0, 0), (0, 1, 0, 0), (0, 0, 1, 0), (0, 0, 0, 1)
+    m1 = (p - 1, 0, 0, 0)
+    assert _qmul(i, i, p) == m1 and _qmul(j, j, p) == m1 and _qmul(k, k, p) == m1
+    assert _qmul(_qmul(i, j, p), k, p) == m1
+    assert _qmul(i, j, p) == k and _qmul(j, i, p) == (0, 0, 0, p - 1)
+    assert _qmul(one, j, p) == j
+
+
+@pytest.mark.parametrize("p", [3, 7, 13, 131071])
+def test_quat_oracle_against_hamilton_brute_force(p):
+    n, k = 5, 4
+    A, B, C, D = (synth.residues(70 + q, (n, k), p) for q in range(4))
+    H = _brute_quat_aah(A, B, C, D, p)
+    got = oracle.quat_aah_modp_low(A, B, C, D, p)
+    for q in range(4):
+        assert np.array_equal(got[q].astype(np.int64), np.tril(H[q]))
+    # M M^H is quaternion-Hermitian: H1 symmetric, H2..H4 skew-symmetric
+    assert np.array_equal(H[0], H[0].T)
+    for q in (1, 2, 3):
+        assert np.array_equal((H[q] + H[q].T) % p, np.zeros((n, n), dtype=np.int64))
+
+
+def test_quat_oracle_special_cases():
+    p = 65521
+    A = synth.residues(81, (6, 9), p)
+    Z = np.zeros_like(A)
+    low = oracle.aat_modp_low(A, p).astype(np.int64)
+    # a real matrix: H = A A^T, no imaginary parts
+    got = oracle.quat_aah_modp_low(A, Z, Z, Z, p)
+    assert np.array_equal(got[0].astype(np.int64), low) and not any(g.any() for g in got[1:])
+    # A times a unit (i, j or k): (A u)(A u)^H = A A^T u conj(u) = A A^T
+    for q in (1, 2, 3):
+        parts = [Z, Z, Z, Z]
+        parts[q] = A
+        got = oracle.quat_aah_modp_low(*parts, p)
+        assert np.array_equal(got[0].astype(np.int64), low) and not any(g.any() for g in got[1:])
+
+
+@pytest.mark.parametrize("p", [5, 131071, 2**31 - 1])
+def test_quat_6m_algorithm_equals_definition(p):
+    """The 6-multiplication algorithm of Sec. 6.2 gives M M^H."""
+    A, B, C, D = (synth.residues(90 + q, (7, 6), p) for q in range(4))
+    want = oracle.quat_aah_modp_low(A, B, C, D, p)
+    got = alg1.quat_6m(A, B, C, D, p)
+    for q in range(4):
+        assert np.array_equal(np.asarray(got[q], dtype=np.int64), want[q].astype(np.int64)), q
