@@ -99,6 +99,23 @@ AAT_API int aat_syrk_modp(uint32_t alpha, const int32_t *A, int64_t n, int64_t k
                   void *stream);
 
 /*
+ * Quaternion M M^H mod p (Sec. 6.2): M = A + B i + C j + D k with A, B, C, D
+ * n x k over F_p (row stride lda, residues |x| < p), i^2 = j^2 = k^2 = ijk =
+ * -1, M^H the conjugate transpose.  Writes H = M M^H = H1 + H2 i + H3 j + H4 k
+ * as the lower triangles (diagonal included, canonical) of H1..H4 (n x n,
+ * row stride ldh, four distinct buffers not overlapping the inputs); H1 is
+ * symmetric and H2..H4 skew-symmetric, so Low(H) determines H.  By the
+ * paper's 6-multiplication algorithm: five general products on the exact
+ * leaf and one product by its own transpose by Algorithm 1.  The strict
+ * upper triangles are unspecified (zeroed with AAT_ZERO_UPPER); other flags
+ * as for aat_modp_ex.  Asynchronous on `stream`; uses library workspace of
+ * about (3 n k + 5 n^2) int32 plus the leaves' digit planes.
+ */
+AAT_API int aah_quat_modp(const int32_t *A, const int32_t *B, const int32_t *C, const int32_t *D,
+                  int64_t n, int64_t k, int64_t lda, uint32_t p, int32_t *H1, int32_t *H2,
+                  int32_t *H3, int32_t *H4, int64_t ldh, uint32_t flags, void *stream);
+
+/*
  * End-to-end form: A_host (n x k, row stride k) and C_host (n x n, row
  * stride n) are HOST buffers (pinned or pageable; pinned buffers let the
  * copies overlap the computation).  The call copies A to the device, runs

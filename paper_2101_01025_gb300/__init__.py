@@ -20,7 +20,7 @@ from ._native import (AAT_C_BF16, AAT_C_BF16X3, AAT_C_FP32, AAT_DIGITS_PLAIN,  #
                       AAT_IN_BALANCED, AAT_LEAF_F64, AAT_LEAF_I8, AAT_LEAF_SIMT, AAT_LEAF_TC, AAT_LEVELS, AAT_ZERO_UPPER, AatError, PlanStats, check, last_error, lib)
 
 __all__ = [
-    "aat_modp", "aat_syrk_modp", "aat_gemm_modp", "aat_modp_host", "aat_modp_host_d2h_bytes", "aat_workspace_size",
+    "aat_modp", "aat_syrk_modp", "aah_quat_modp", "aat_gemm_modp", "aat_modp_host", "aat_modp_host_d2h_bytes", "aat_workspace_size",
     "aat_device_status", "tune_modp", "tune_lookup", "tune_save", "tune_load", "tune_clear",
     "aat_shutdown", "aat_version", "aah_complex", "aat_complex_2m", "aat_complex", "Plan", "AAT_LEVELS", "AAT_LEAF_TC", "AAT_LEAF_SIMT",
     "AAT_ZERO_UPPER", "AAT_IN_BALANCED", "AatError",
@@ -94,6 +94,31 @@ def aat_syrk_modp(alpha: int, A, beta: int, C, p: int, flags: int = 0,
     check(lib().aat_syrk_modp(alpha % 2**32, A.data_ptr(), n, k, lda, beta % 2**32,
                               C.data_ptr(), ldc, p, flags, _stream(stream)))
     return C
+
+
+def aah_quat_modp(A, B, C, D, p: int, H=None, flags: int = 0, levels: int | None = None,
+                  stream=None):
+    """Quaternion M M^H mod p for M = A + B i + C j + D k (four n x k int32
+    CUDA tensors with the same row stride): returns (H1, H2, H3, H4), n x n
+    int32 CUDA tensors holding Low of each part (H may pass four of them)."""
+    import torch
+    if levels is not None:
+        flags |= AAT_LEVELS(levels)
+    lda = _check_mat(A, "A")
+    n, k = A.shape
+    for X, nm in ((B, "B"), (C, "C"), (D, "D")):
+        if _check_mat(X, nm) != lda or tuple(X.shape) != (n, k):
+            raise ValueError("A, B, C, D must have the same shape and row stride")
+    if H is None:
+        H = tuple(torch.empty((n, n), dtype=torch.int32, device=A.device) for _ in range(4))
+    ldh = _check_mat(H[0], "H1")
+    for X in H[1:]:
+        if _check_mat(X, "H") != ldh or tuple(X.shape) != (n, n):
+            raise ValueError("H1..H4 must be n x n with the same row stride")
+    check(lib().aah_quat_modp(A.data_ptr(), B.data_ptr(), C.data_ptr(), D.data_ptr(), n, k, lda,
+                              p, H[0].data_ptr(), H[1].data_ptr(), H[2].data_ptr(),
+                              H[3].data_ptr(), ldh, flags, _stream(stream)))
+    return tuple(H)
 
 
 def aat_modp_host(A, p: int, C=None, flags: int = 0, levels: int | None = None):

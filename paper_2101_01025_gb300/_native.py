@@ -40,7 +40,7 @@ def AAT_LEVELS(l: int) -> int:
 
 #: every symbol include/aat.h and include/aat_testing.h declare
 EXPORTS = [
-    "aat_modp", "aat_modp_ex", "aat_syrk_modp", "aat_modp_host", "aat_modp_host_d2h_bytes", "aat_gemm_modp",
+    "aat_modp", "aat_modp_ex", "aat_syrk_modp", "aah_quat_modp", "aat_modp_host", "aat_modp_host_d2h_bytes", "aat_gemm_modp",
     "aat_gemm_modp_noalloc", "aat_tune_modp", "aat_tune_lookup", "aat_tune_save", "aat_tune_load",
     "aat_tune_clear",
     "aat_workspace_size",
@@ -151,6 +151,8 @@ def lib():
         L.aat_modp_ex.argtypes = [vp, i64, i64, i64, u32, vp, i64, u32, vp]
         L.aat_modp_host.argtypes = [vp, i64, i64, u32, vp, u32]
         L.aat_syrk_modp.argtypes = [u32, vp, i64, i64, i64, u32, vp, i64, u32, u32, vp]
+        L.aah_quat_modp.argtypes = [vp, vp, vp, vp, i64, i64, i64, u32, vp, vp, vp, vp, i64, u32,
+                                    vp]
         L.aat_modp_host_d2h_bytes.argtypes = [i64, u32]
         L.aat_modp_host_d2h_bytes.restype = i64
         L.aat_gemm_modp.argtypes = [vp, i64, vp, i64, i64, i64, i64, u32, vp, i64, u32, vp]

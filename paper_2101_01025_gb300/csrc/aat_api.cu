@@ -178,6 +178,18 @@ static bool make_y(uint32_t p, YParams *y) {
     y->b = 0;
     return true;
   }
+  // p = 3 mod 8: -2 is a square (Lemma 4.3), so a = 1, b = sqrt(-2) give
+  // a^2 + b^2 = -1 and Y costs 2 multiplications per column pair instead of
+  // 3 (the examples closing Sec. 3)
+  if (p % 8 == 3) {
+    uint64_t r;
+    if (sqrt_mod(p - 2, p, &r) && (1 + mulmod64(r, r, p)) % p == p - 1) {
+      y->kind = 2;
+      y->a = 1;
+      y->b = bal_host(r, p);
+      return true;
+    }
+  }
   uint64_t a, b;
   if (!sos(p - 1, p, &a, &b)) return false;
   if ((mulmod64(a, a, p) + mulmod64(b, b, p)) % p != p - 1) return false;
@@ -735,9 +747,10 @@ static int setup(Ctx &c, uint32_t p, uint32_t flags, cudaStream_t st) {
 
 // Runs (or, with dry, measures) the whole product; returns workspace bytes.
 // beta: null for Low(A A^T) (Table 3), else the SYRK update's beta (Table 4).
-static size_t run_plan(Ctx &c, const int32_t *A, int64_t n, int64_t k, int64_t lda, int32_t *C,
-                       int64_t ldc, uint32_t flags, bool dry, char *ws,
-                       const MulConst *beta = nullptr) {
+// The product (or update) on the arena as it stands (c.ar): allocations
+// continue after what the caller already holds.
+static size_t run_plan_in(Ctx &c, const int32_t *A, int64_t n, int64_t k, int64_t lda, int32_t *C,
+                          int64_t ldc, uint32_t flags, bool dry, const MulConst *beta) {
   // choices the flags leave open come from the tuning table, if it has the shape
   TuneVal tv;
   if (c.leaf == AAT_LEAF_TC && !(flags & AAT_LEVELS_MASK) && tune_find(n, k, c.m.p, &tv)) {
@@ -746,9 +759,6 @@ static size_t run_plan(Ctx &c, const int32_t *A, int64_t n, int64_t k, int64_t l
     if (tv.plain) c.ds.nsum = 0;
   }
   Prepared pr = prepare(n, k, c.y, flags);
-  c.ar = Arena();
-  c.ar.dry = dry;
-  c.ar.base = ws;
   const int32_t *Aw = A;
   int64_t ldaw = lda;
   int32_t *Cw = C;
@@ -781,6 +791,62 @@ static size_t run_plan(Ctx &c, const int32_t *A, int64_t n, int64_t k, int64_t l
   if (pr.padded && !dry) check(c, launch_copy_low(Cw, ldcw, C, ldc, n, c.st), "unpad");
   if (!dry && (flags & AAT_ZERO_UPPER)) check(c, launch_zero_upper(C, ldc, n, c.st), "zero upper");
   if (!dry && !early && c.split_ev && c.err == AAT_OK) cudaEventRecord(c.split_ev, c.st);
+  return c.ar.peak;
+}
+
+static size_t run_plan(Ctx &c, const int32_t *A, int64_t n, int64_t k, int64_t lda, int32_t *C,
+                       int64_t ldc, uint32_t flags, bool dry, char *ws,
+                       const MulConst *beta = nullptr) {
+  c.ar = Arena();
+  c.ar.dry = dry;
+  c.ar.base = ws;
+  return run_plan_in(c, A, n, k, lda, C, ldc, flags, dry, beta);
+}
+
+// M M^H mod p for the quaternion matrix M = A + B i + C j + D k (Sec. 6.2,
+// the 6-multiplication algorithm): U1 = A + B, U2 = C + D; five general
+// products Q1 = C A^T, Q2 = D B^T, Q3 = U2 U1^T, Q4 = A B^T, Q5 = C D^T on the
+// exact leaf (digit planes of A, B, C, D, U1, U2 split once and shared);
+// Q6 = Low((U1 + U2)(U1 + U2)^T) by Algorithm 1 into H1; then the closing
+// additions into Low(H1..H4).
+static size_t quat_plan(Ctx &c, const int32_t *const M[4], int64_t n, int64_t k, int64_t lda,
+                        int32_t *const H[4], int64_t ldh, uint32_t flags, bool dry, char *ws) {
+  c.ar = Arena();
+  c.ar.dry = dry;
+  c.ar.base = ws;
+  const bool tc = (c.leaf == AAT_LEAF_TC);
+  int32_t *U = (int32_t *)c.ar.get((size_t)3 * n * k * 4);
+  int32_t *U1 = U, *U2 = U + n * k, *U12 = U + 2 * n * k;
+  int32_t *Q = (int32_t *)c.ar.get((size_t)5 * n * n * 4);
+  if (!dry)
+    check(c, launch_quat_sums(M[0], M[1], M[2], M[3], lda, n, k, U1, U2, U12, k, c.m, c.st),
+          "quaternion sums");
+  Operand o[6] = {{M[0], lda, no_planes()}, {M[1], lda, no_planes()}, {M[2], lda, no_planes()},
+                  {M[3], lda, no_planes()}, {U1, k, no_planes()},   {U2, k, no_planes()}};
+  if (tc)
+    for (Operand &x : o) {
+      x.pl = planes_alloc(c, n, k);
+      if (!dry) check(c, launch_split(x.x, x.ld, n, k, c.m, c.ds.b, x.pl, c.st), "split");
+    }
+  const Operand &oA = o[0], &oB = o[1], &oC = o[2], &oD = o[3], &oU1 = o[4], &oU2 = o[5];
+  leaf(c, oC, oA, false, n, n, k, Q + 0 * n * n, n, 0, 0);   // Q1 = C A^T
+  leaf(c, oD, oB, false, n, n, k, Q + 1 * n * n, n, 0, 0);   // Q2 = D B^T
+  leaf(c, oU2, oU1, false, n, n, k, Q + 2 * n * n, n, 0, 0); // Q3 = U2 U1^T
+  leaf(c, oA, oB, false, n, n, k, Q + 3 * n * n, n, 0, 0);   // Q4 = A B^T
+  leaf(c, oC, oD, false, n, n, k, Q + 4 * n * n, n, 0, 0);   // Q5 = C D^T
+  // Q6 = Low((U1 + U2)(U1 + U2)^T) -> H1 (the tuning table may change the
+  // digit form for it; the five products above keep theirs)
+  const DigitSpec ds = c.ds;
+  const int form = c.form;
+  run_plan_in(c, U12, n, k, k, H[0], ldh, flags & ~(uint32_t)AAT_ZERO_UPPER, dry, nullptr);
+  c.ds = ds;
+  c.form = form;
+  if (!dry) {
+    check(c, launch_quat_combine(Q, n, n * n, H[0], H[1], H[2], H[3], ldh, n, c.m, c.st),
+          "quaternion combine");
+    if (flags & AAT_ZERO_UPPER)
+      for (int q = 0; q < 4; ++q) check(c, launch_zero_upper(H[q], ldh, n, c.st), "zero upper");
+  }
   return c.ar.peak;
 }
 
@@ -953,6 +1019,46 @@ int aat_syrk_modp(uint32_t alpha, const int32_t *A, int64_t n, int64_t k, int64_
   if ((e = ensure_workspace(need, &ws))) return e;
   c.err = AAT_OK;
   run_plan(c, A, n, k, lda, C, ldc, flags, false, (char *)ws, pb);
+  return c.err;
+}
+
+int aah_quat_modp(const int32_t *A, const int32_t *B, const int32_t *C, const int32_t *D,
+                  int64_t n, int64_t k, int64_t lda, uint32_t p, int32_t *H1, int32_t *H2,
+                  int32_t *H3, int32_t *H4, int64_t ldh, uint32_t flags, void *stream) {
+  g_last_error.clear();
+  if (n < 0 || k < 0) return fail(AAT_EINVAL, "negative size");
+  if (n > (1 << 30) || k > (1 << 30)) return fail(AAT_EINVAL, "size too large");
+  if (lda < std::max<int64_t>(k, 1) || ldh < std::max<int64_t>(n, 1))
+    return fail(AAT_EINVAL, "stride smaller than the row length");
+  const int32_t *const M[4] = {A, B, C, D};
+  int32_t *const H[4] = {H1, H2, H3, H4};
+  if (n > 0) {
+    for (int q = 0; q < 4; ++q)
+      if (!H[q] || (k > 0 && !M[q])) return fail(AAT_EINVAL, "null pointer");
+    const size_t hb = (size_t)((n - 1) * ldh + n) * 4, mb = (size_t)((n - 1) * lda + k) * 4;
+    for (int q = 0; q < 4; ++q)
+      for (int r = 0; r < 4; ++r) {
+        if (r != q && overlaps(H[q], hb, H[r], hb)) return fail(AAT_EINVAL, "outputs overlap");
+        if (k > 0 && overlaps(H[q], hb, M[r], mb)) return fail(AAT_EINVAL, "an output overlaps an input");
+      }
+  }
+  int e;
+  Ctx c;
+  if ((e = setup(c, p, flags, (cudaStream_t)stream))) return e;
+  if (n == 0) return AAT_OK;
+  if ((e = check_device())) return e;
+  if (k == 0) {
+    for (int q = 0; q < 4; ++q) {
+      cudaError_t ce = cudaMemset2DAsync(H[q], (size_t)ldh * 4, 0, (size_t)n * 4, (size_t)n, c.st);
+      if (ce != cudaSuccess) return cuda_fail(ce, "memset");
+    }
+    return AAT_OK;
+  }
+  const size_t need = quat_plan(c, M, n, k, lda, H, ldh, flags, true, nullptr);
+  void *ws = nullptr;
+  if ((e = ensure_workspace(need, &ws))) return e;
+  c.err = AAT_OK;
+  quat_plan(c, M, n, k, lda, H, ldh, flags, false, (char *)ws);
   return c.err;
 }
 

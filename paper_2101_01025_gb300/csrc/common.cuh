@@ -312,6 +312,17 @@ cudaError_t launch_pad_copy(const int32_t *src, int64_t lds, int64_t rows, int64
 cudaError_t launch_copy_low(const int32_t *src, int64_t lds, int32_t *dst, int64_t ldd,
                             int64_t n, cudaStream_t st);
 cudaError_t launch_zero_upper(int32_t *C, int64_t ldc, int64_t n, cudaStream_t st);
+// Quaternion M M^H (Sec. 6.2): the sums U1 = A + B, U2 = C + D, U12 = U1 + U2
+// (row stride ldu), and the closing additions from Q1..Q5 (Q_i at
+// Q + i qstride, row stride ldq) and Low(Q6) (in H1) to Low(H1..H4).
+cudaError_t launch_quat_sums(const int32_t *A, const int32_t *B, const int32_t *C,
+                             const int32_t *D, int64_t lda, int64_t n, int64_t k, int32_t *U1,
+                             int32_t *U2, int32_t *U12, int64_t ldu, const ModP &m,
+                             cudaStream_t st);
+cudaError_t launch_quat_combine(const int32_t *Q, int64_t ldq, int64_t qstride, int32_t *H1,
+                                int32_t *H2, int32_t *H3, int32_t *H4, int64_t ldh, int64_t n,
+                                const ModP &m, cudaStream_t st);
+
 // count balanced residues mod p, element t = SplitMix64 output t of stream
 // `seed` mapped to [0, p) by (z >> 32) p >> 32 (synthetic tuning inputs).
 cudaError_t launch_fill_residues(int32_t *A, int64_t count, uint32_t p, uint64_t seed,

@@ -22,9 +22,15 @@ __device__ __forceinline__ bool has(const Planes &P) { return P.ptr != nullptr; 
 // Y applied to the pair (x_j, x_{j+kappa/2}) for kind 2, or to x_j for kind 1.
 __device__ __forceinline__ void apply_y2(int32_t x0, int32_t x1, const YParams &y,
                                          const ModP &m, int32_t &o0, int32_t &o1) {
-  // [x0 x1] [[a, b], [-b, a]] = [a x0 - b x1, b x0 + a x1]
-  o0 = red_s64((int64_t)y.a * x0 - (int64_t)y.b * x1, m);
-  o1 = red_s64((int64_t)y.b * x0 + (int64_t)y.a * x1, m);
+  // [x0 x1] [[a, b], [-b, a]] = [a x0 - b x1, b x0 + a x1]; a = 1 when
+  // p = 3 mod 8 (two multiplications instead of three)
+  if (y.a == 1) {
+    o0 = red_s64((int64_t)x0 - (int64_t)y.b * x1, m);
+    o1 = red_s64((int64_t)y.b * x0 + (int64_t)x1, m);
+  } else {
+    o0 = red_s64((int64_t)y.a * x0 - (int64_t)y.b * x1, m);
+    o1 = red_s64((int64_t)y.b * x0 + (int64_t)y.a * x1, m);
+  }
 }
 
 __device__ __forceinline__ void ld4_bal(const int32_t *p, const ModP &m, int32_t (&v)[4]) {
@@ -504,6 +510,72 @@ cudaError_t launch_copy_low(const int32_t *src, int64_t lds, int32_t *dst, int64
   return cudaGetLastError();
 }
 
+// U1 = A + B, U2 = C + D, U12 = U1 + U2 (balanced), the sums of the
+// quaternion algorithm of Sec. 6.2 (M = A + B i + C j + D k).
+__global__ void quat_sums_kernel(const int32_t *__restrict__ A, const int32_t *__restrict__ B,
+                                 const int32_t *__restrict__ C, const int32_t *__restrict__ D,
+                                 int64_t lda, int64_t n, int64_t k, int32_t *U1, int32_t *U2,
+                                 int32_t *U12, int64_t ldu, ModP m) {
+  const int64_t total = n * k;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / k, c = t - r * k;
+    const int64_t s = r * lda + c;
+    const int32_t u1 = add_bal(bal(A[s], m), bal(B[s], m), m);
+    const int32_t u2 = add_bal(bal(C[s], m), bal(D[s], m), m);
+    U1[r * ldu + c] = u1;
+    U2[r * ldu + c] = u2;
+    U12[r * ldu + c] = add_bal(u1, u2, m);
+  }
+}
+
+// The additions closing the quaternion algorithm of Sec. 6.2, on the lower
+// triangle: T1 = Q1 - Q2, T2 = Q4 + Q5, T3 = (Q1 + Q2) - Q3,
+// H1 = Q6 - (Q3^T + Q3) - (T2^T + T2), H2 = T2^T - T2, H3 = T1 - T1^T,
+// H4 = T3^T - T3.  Low(Q6) arrives in H1.  One T x T tile (I, J), I >= J,
+// per CTA, with tile (J, I) of every Q for the transposed terms.
+__global__ void quat_combine_kernel(const int32_t *__restrict__ Q, int64_t ldq, int64_t qstride,
+                                    int32_t *H1, int32_t *H2, int32_t *H3, int32_t *H4,
+                                    int64_t ldh, int64_t n, ModP m) {
+  __shared__ int32_t qt[5][T][T + 1];  // tile (J, I) of Q1..Q5
+  const int64_t ntiles = (n + T - 1) / T;
+  int64_t pid = blockIdx.x;
+  int64_t I = (int64_t)((sqrt(8.0 * (double)pid + 1.0) - 1.0) * 0.5);
+  while (I * (I + 1) / 2 > pid) --I;
+  while ((I + 1) * (I + 2) / 2 <= pid) ++I;
+  const int64_t J = pid - I * (I + 1) / 2;
+  if (I >= ntiles) return;
+  const int tx = threadIdx.x % T, ty = threadIdx.x / T;
+  const int64_t r0 = I * T, c0 = J * T;
+  for (int yy = ty; yy < T; yy += 8) {
+    const int64_t r2 = c0 + yy, c2 = r0 + tx;
+    if (r2 < n && c2 < n)
+#pragma unroll
+      for (int q = 0; q < 5; ++q) qt[q][yy][tx] = bal(Q[q * qstride + r2 * ldq + c2], m);
+  }
+  __syncthreads();
+  for (int yy = ty; yy < T; yy += 8) {
+    const int64_t r = r0 + yy, c = c0 + tx;
+    if (r >= n || c >= n || c > r) continue;
+    int32_t q[5], qT[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      q[i] = bal(Q[i * qstride + r * ldq + c], m);
+      qT[i] = qt[i][tx][yy];  // Q_i(c, r)
+    }
+    const int32_t t1 = sub_bal(q[0], q[1], m), t1T = sub_bal(qT[0], qT[1], m);
+    const int32_t t2 = add_bal(q[3], q[4], m), t2T = add_bal(qT[3], qT[4], m);
+    const int32_t t3 = sub_bal(add_bal(q[0], q[1], m), q[2], m);
+    const int32_t t3T = sub_bal(add_bal(qT[0], qT[1], m), qT[2], m);
+    int32_t h1 = sub_bal(bal(H1[r * ldh + c], m), add_bal(qT[2], q[2], m), m);
+    h1 = sub_bal(h1, add_bal(t2T, t2, m), m);
+    H1[r * ldh + c] = (int32_t)bal_to_canon(h1, m);
+    H2[r * ldh + c] = (int32_t)bal_to_canon(sub_bal(t2T, t2, m), m);
+    H3[r * ldh + c] = (int32_t)bal_to_canon(sub_bal(t1, t1T, m), m);
+    H4[r * ldh + c] = (int32_t)bal_to_canon(sub_bal(t3T, t3, m), m);
+  }
+}
+
 __global__ void fill_residues_kernel(int32_t *A, int64_t count, uint32_t p, uint64_t seed) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += stride) {
@@ -514,6 +586,29 @@ __global__ void fill_residues_kernel(int32_t *A, int64_t count, uint32_t p, uint
     const uint32_t r = (uint32_t)(((z >> 32) * (uint64_t)p) >> 32);
     A[t] = r > (p - 1) / 2 ? (int32_t)r - (int32_t)p : (int32_t)r;
   }
+}
+
+cudaError_t launch_quat_sums(const int32_t *A, const int32_t *B, const int32_t *C,
+                             const int32_t *D, int64_t lda, int64_t n, int64_t k, int32_t *U1,
+                             int32_t *U2, int32_t *U12, int64_t ldu, const ModP &m,
+                             cudaStream_t st) {
+  if (n * k <= 0) return cudaSuccess;
+  ProfScope prof(AAT_K_COPY, st, 4.0 * 7.0 * (double)n * k);
+  quat_sums_kernel<<<grid_for(n * k), kThreads, 0, st>>>(A, B, C, D, lda, n, k, U1, U2, U12, ldu,
+                                                          m);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_quat_combine(const int32_t *Q, int64_t ldq, int64_t qstride, int32_t *H1,
+                                int32_t *H2, int32_t *H3, int32_t *H4, int64_t ldh, int64_t n,
+                                const ModP &m, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t nt = (n + T - 1) / T;
+  const double tri = 0.5 * (double)n * (double)(n + 1);
+  ProfScope prof(AAT_K_POSTADD, st, 4.0 * (10.0 * tri + 4.0 * tri + tri));
+  quat_combine_kernel<<<(unsigned)(nt * (nt + 1) / 2), T * 8, 0, st>>>(Q, ldq, qstride, H1, H2,
+                                                                       H3, H4, ldh, n, m);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_fill_residues(int32_t *A, int64_t count, uint32_t p, uint64_t seed,

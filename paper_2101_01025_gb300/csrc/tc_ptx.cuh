@@ -354,6 +354,37 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 }
 
 
+// Add 16 consecutive FP32 TMEM columns of this thread's lane into the FP32
+// registers acc[B .. B+15] (round to nearest): load, wait and add in one
+// statement (half the temporaries of the 32-column form).
+template <int B>
+__device__ __forceinline__ void tmem_accum16f(uint32_t taddr, float (&acc)[128]) {
+  asm volatile(
+      "{\n\t.reg .f32 t0, t1, t2, t3, t4, t5, t6, t7, t8, t9, t10, t11, t12, t13, t14, t15;\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {t0, t1, t2, t3, t4, t5, t6, t7, t8, t9, t10, t11, t12, t13, t14, t15}, [%16];\n\t"
+      "tcgen05.wait::ld.sync.aligned;\n\t"
+      "add.f32 %0, %0, t0;\n\t"
+      "add.f32 %1, %1, t1;\n\t"
+      "add.f32 %2, %2, t2;\n\t"
+      "add.f32 %3, %3, t3;\n\t"
+      "add.f32 %4, %4, t4;\n\t"
+      "add.f32 %5, %5, t5;\n\t"
+      "add.f32 %6, %6, t6;\n\t"
+      "add.f32 %7, %7, t7;\n\t"
+      "add.f32 %8, %8, t8;\n\t"
+      "add.f32 %9, %9, t9;\n\t"
+      "add.f32 %10, %10, t10;\n\t"
+      "add.f32 %11, %11, t11;\n\t"
+      "add.f32 %12, %12, t12;\n\t"
+      "add.f32 %13, %13, t13;\n\t"
+      "add.f32 %14, %14, t14;\n\t"
+      "add.f32 %15, %15, t15;\n\t"
+      "}"
+      : "+f"(acc[B + 0]), "+f"(acc[B + 1]), "+f"(acc[B + 2]), "+f"(acc[B + 3]), "+f"(acc[B + 4]), "+f"(acc[B + 5]), "+f"(acc[B + 6]), "+f"(acc[B + 7]), "+f"(acc[B + 8]), "+f"(acc[B + 9]), "+f"(acc[B + 10]), "+f"(acc[B + 11]), "+f"(acc[B + 12]), "+f"(acc[B + 13]), "+f"(acc[B + 14]), "+f"(acc[B + 15])
+      : "r"(taddr)
+      : "memory");
+}
+
 // Add 32 consecutive FP32 TMEM columns of this thread's lane into the FP32
 // registers acc[B .. B+31] (round to nearest), load, wait and add in one
 // statement.

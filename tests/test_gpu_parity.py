@@ -412,3 +412,38 @@ def test_syrk_update_degenerate(lib):
     got = host(C)
     assert low_equal(got, oracle.syrk_modp_low(1, A, 1, C0, p))
     assert not np.triu(got, 1).any()
+
+
+@pytest.mark.parametrize("p", [1000003, 2147483587])
+@pytest.mark.parametrize("levels", [1, 2])
+def test_p_3_mod_8_y_with_a_equal_one(lib, p, levels):
+    """p = 3 mod 8 takes Y = [[1, sqrt(-2)], [-sqrt(-2), 1]] (x) I (Lemma 4.3):
+    the result is the same Low(A A^T) mod p."""
+    A = synth.residues(61, (520, 456), p, balanced=True)
+    C = host(lib.aat_modp(dev(A), p, levels=levels))
+    assert low_equal(C, oracle.aat_modp_low(A, p))
+
+
+# --------------------------------------------------- quaternions (Sec. 6.2)
+
+@pytest.mark.parametrize("p", PRIMES)
+@pytest.mark.parametrize("n,k,levels", [(300, 257, 1), (512, 384, 2), (129, 70, 0)])
+def test_quaternion_aah_matches_oracle(lib, p, n, k, levels):
+    """M M^H for M = A + B i + C j + D k by the 6-multiplication algorithm:
+    the four lower triangles, bit-exact, ragged and padded shapes."""
+    parts = [synth.residues(100 + q, (n, k), p, balanced=(q % 2 == 1)) for q in range(4)]
+    H = lib.aah_quat_modp(*[dev(X) for X in parts], p, levels=levels)
+    want = oracle.quat_aah_modp_low(*parts, p)
+    for q in range(4):
+        assert low_equal(host(H[q]), want[q]), q
+
+
+def test_quaternion_aah_other_leaf_and_zero_upper(lib):
+    p = 131071
+    parts = [synth.residues(110 + q, (200, 160), p) for q in range(4)]
+    H = lib.aah_quat_modp(*[dev(X) for X in parts], p, flags=lib.AAT_LEAF_SIMT | lib.AAT_ZERO_UPPER,
+                          levels=1)
+    want = oracle.quat_aah_modp_low(*parts, p)
+    for q in range(4):
+        got = host(H[q])
+        assert low_equal(got, want[q]) and not np.triu(got, 1).any()

@@ -69,6 +69,16 @@ def test_y_is_skew_unitary(p):
     assert np.array_equal((Y @ Y.T) % p, (np.eye(6, dtype=object) * (p - 1)) % p)
 
 
+@pytest.mark.parametrize("p", [3, 11, 19, 43, 59, 83, 1000003, 2147483587])
+def test_y_has_a_equal_one_when_p_is_3_mod_8(p):
+    """p = 3 mod 8: Lemma 4.3 makes -2 a square, so the library takes a = 1,
+    b = sqrt(-2) (two multiplications by Y entries per column pair instead
+    of three, the examples closing Sec. 3)."""
+    assert p % 8 == 3 and oracle.is_prime(p)
+    kind, a, b = T.y_params(p)
+    assert kind == 2 and a == 1 and (1 + b * b) % p == p - 1
+
+
 def test_sos_all_residues():
     for p in [3, 7, 11, 19, 23, 131071]:
         for k in list(range(min(p, 200))) + [p - 1]:
