@@ -15,7 +15,7 @@
 // x0y1, x1y0, x0y2, x1y1, x2y0 (close to FP32), P = 2 gives x0y0, x0y1, x1y0,
 // P = 1 is plain BF16.  The piece products of a tile accumulate in FP32 in
 // TMEM (sign per product from the instruction's negate bit), drained every
-// 2 K blocks into FP32 registers (round to nearest) while the next chunk
+// 8 K blocks into FP32 registers (round to nearest) while the next chunk
 // accumulates in the other TMEM buffer.  The Hermitian diagonal sum_l |a_il|^2 is
 // computed in FP64 (real and >= 0).
 #include <cuda.h>
@@ -40,20 +40,13 @@ namespace {
 
 using namespace tc;
 
-constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
-constexpr int A_BYTES = BM * BK * 2;
-constexpr int B_BYTES = BN * BK * 2;
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int BM = 128, BN = 256, BK = 64;
 constexpr int EPI_WARPS = 8;
 constexpr int THREADS = 64 + EPI_WARPS * 32;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t ACC_COLS = 256;
 constexpr int MAX_FGROUPS = 48;
-constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + 256;
-// kind::f16, FP32 accumulator, BF16 A and B, K-major, N = 256, M = 128;
-// bit 13 negates A.
-constexpr uint32_t IDESC_F = (1u << 4) | (1u << 7) | (1u << 10) |
-                             ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+// bit 13 of the instruction descriptor negates A
 constexpr uint32_t NEG_A = 1u << 13;
 
 struct FGroup {
@@ -63,7 +56,7 @@ struct FGroup {
 
 struct FParams {
   CUtensorMap tmx;  // 3D {K, rows, plane}, box {64, 128, 1}
-  CUtensorMap tmy;  // 3D {K, rows, plane}, box {64, 256, 1}
+  CUtensorMap tmy;  // 3D {K, rows, plane}, box {64, 256, 1} (CTA pair: {64, 128, 1})
   FGroup g[MAX_FGROUPS];
   int ng;
   int kblocks;
@@ -77,12 +70,35 @@ struct FParams {
 };
 
 // out = sum_g (+-) X_{xp(g)} Y_{yp(g)}^T in FP32, one TMEM accumulation per
-// output tile.  Same CTA organisation as the modular leaf kernel.
+// output tile.  Same CTA organisation as the modular leaf kernel, in the
+// same two forms: one CTA per 128 x 256 tile (4 stages of 48 KB), or a CTA
+// pair per 256 x 256 tile (tcgen05 cta_group::2; each CTA holds 128 rows of
+// X and 128 rows of Y per stage, 6 stages of 32 KB; the leader issues the
+// M=256 MMAs, both CTAs' copies complete on its barrier, its commits
+// multicast to both, and the epilogues of both release a buffer on its
+// barrier).
+template <bool PAIR>
+struct FShape {
+  static constexpr int TM = PAIR ? 256 : 128;
+  static constexpr int YROWS = PAIR ? 128 : 256;
+  static constexpr int STAGES = PAIR ? 6 : 4;
+  static constexpr int A_BYTES = BM * BK * 2;
+  static constexpr int B_BYTES = YROWS * BK * 2;
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + 256;
+  // kind::f16, FP32 accumulator, BF16 A and B, K-major, N = 256, M = TM
+  static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) |
+                                    ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+};
+
+template <bool PAIR>
 __global__ void __launch_bounds__(THREADS, 1) leaf_f32_kernel(const __grid_constant__ FParams P) {
+  using S = FShape<PAIR>;
+  constexpr int STAGES = S::STAGES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   const uint32_t sbase = smem_u32(smem);
-  uint64_t *bars = (uint64_t *)(smem + (size_t)STAGES * STAGE_BYTES);
+  uint64_t *bars = (uint64_t *)(smem + (size_t)STAGES * S::STAGE_BYTES);
   const uint32_t bar0 = smem_u32(bars);
 #define FULL(s) (bar0 + 8u * (uint32_t)(s))
 #define EMPTY(s) (bar0 + 8u * (uint32_t)(STAGES + (s)))
@@ -92,6 +108,14 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_f32_kernel(const __grid_const
   uint32_t *tmem_slot = (uint32_t *)(bars + 2 * STAGES + 5);
   volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
 
+  uint32_t rank = 0, unit0 = blockIdx.x, nunits = gridDim.x;
+  if constexpr (PAIR) {
+    rank = cluster_ctarank();
+    unit0 = cluster_id_x();
+    nunits = ncluster_x();
+  }
+  const bool leader = (rank == 0);
+
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -100,7 +124,7 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_f32_kernel(const __grid_const
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(AFULL(b), 1);
-      mbar_init(AEMPTY(b), EPI_WARPS);
+      mbar_init(AEMPTY(b), PAIR ? 2 * EPI_WARPS : EPI_WARPS);
     }
     mbar_init(DONE, 1);
     *abort_flag = 0;
@@ -108,14 +132,23 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_f32_kernel(const __grid_const
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(tmem_slot)),
-                 "r"(TMEM_COLS)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    if constexpr (PAIR) {
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       smem_u32(tmem_slot)),
+                   "r"(TMEM_COLS)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    } else {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       smem_u32(tmem_slot)),
+                   "r"(TMEM_COLS)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
     tc_fence_before();
   }
   __syncthreads();
+  if constexpr (PAIR) cluster_sync();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
@@ -124,19 +157,29 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_f32_kernel(const __grid_const
       int stage = 0, issued = 0;
       uint32_t ph = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
+      const uint32_t full0 = PAIR ? map_to_rank(FULL(0), 0) : FULL(0);
+      for (int t = (int)unit0; t < P.ntiles && ok; t += (int)nunits) {
         const int2 tile = P.tiles[t];
+        const int rowx = tile.x * S::TM + (int)rank * BM;
+        const int rowy = tile.y * BN + (int)rank * S::YROWS;
         for (int gi = 0; gi < P.ng && ok; ++gi) {
           const FGroup g = P.g[gi];
           for (int kb = 0; kb < P.kblocks; ++kb) {
-            if (!wait_bounded(EMPTY(stage), ph ^ 1u, abort_flag, P.status)) {
+            if (!wait_bounded<PAIR>(EMPTY(stage), ph ^ 1u, abort_flag, P.status)) {
               ok = false;
               break;
             }
-            mbar_expect_tx(FULL(stage), (uint32_t)STAGE_BYTES);
-            const uint32_t sa = sbase + (uint32_t)(stage * STAGE_BYTES);
-            tma_load_3d(sa, &P.tmx, FULL(stage), kb * BK, tile.x * BM, g.xp);
-            tma_load_3d(sa + A_BYTES, &P.tmy, FULL(stage), kb * BK, tile.y * BN, g.yp);
+            const uint32_t sa = sbase + (uint32_t)(stage * S::STAGE_BYTES);
+            const uint32_t fb = full0 + 8u * (uint32_t)stage;
+            if constexpr (PAIR) {
+              if (leader) mbar_expect_tx(FULL(stage), (uint32_t)(2 * S::STAGE_BYTES));
+              tma_load_3d_pair(sa, &P.tmx, fb, kb * BK, rowx, g.xp);
+              tma_load_3d_pair(sa + S::A_BYTES, &P.tmy, fb, kb * BK, rowy, g.yp);
+            } else {
+              mbar_expect_tx(FULL(stage), (uint32_t)S::STAGE_BYTES);
+              tma_load_3d(sa, &P.tmx, fb, kb * BK, rowx, g.xp);
+              tma_load_3d(sa + S::A_BYTES, &P.tmy, fb, kb * BK, rowy, g.yp);
+            }
             ++issued;
             if (++stage == STAGES) {
               stage = 0;
@@ -146,57 +189,74 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_f32_kernel(const __grid_const
         }
       }
       if (!ok) {
-        int s = stage;
-        uint32_t q = ph;
-        for (int i = 0; i < STAGES && i < issued; ++i) {
-          if (--s < 0) {
-            s = STAGES - 1;
-            q ^= 1u;
+        if (!PAIR || leader) {
+          int s = stage;
+          uint32_t q = ph;
+          for (int i = 0; i < STAGES && i < issued; ++i) {
+            if (--s < 0) {
+              s = STAGES - 1;
+              q ^= 1u;
+            }
+            wait_quiet(FULL(s), q);
           }
-          wait_quiet(FULL(s), q);
+        } else {
+          // the peer's copies complete on the leader's barriers: give them
+          // a fixed 20 ms to land
+          const unsigned long long t0 = gtimer();
+          while (gtimer() - t0 < 20000000ull) {
+          }
         }
       }
     }
   } else if (warp == 1) {
-    if (lane == 0) {  // MMA issuer: chunks of kchunk K blocks over (group, K block)
+    if (lane == 0 && leader) {  // MMA issuer: chunks of kchunk K blocks over (group, K block)
       int stage = 0;
       uint32_t ph = 0, chunk = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
+      for (int t = (int)unit0; t < P.ntiles && ok; t += (int)nunits) {
         int inchunk = 0;
         uint32_t dt = 0;
         for (int gi = 0; gi < P.ng && ok; ++gi) {
-          const uint32_t idesc = IDESC_F | (P.g[gi].neg ? NEG_A : 0u);
+          const uint32_t idesc = S::IDESC | (P.g[gi].neg ? NEG_A : 0u);
           for (int kb = 0; kb < P.kblocks; ++kb) {
             if (inchunk == 0) {
               const uint32_t buf = chunk & 1u, use = chunk >> 1;
-              if (!wait_bounded(AEMPTY(buf), (use & 1u) ^ 1u, abort_flag, P.status)) {
+              if (!wait_bounded<PAIR>(AEMPTY(buf), (use & 1u) ^ 1u, abort_flag, P.status)) {
                 ok = false;
                 break;
               }
               tc_fence_after();
               dt = tmem + buf * ACC_COLS;
             }
-            if (!wait_bounded(FULL(stage), ph, abort_flag, P.status)) {
+            if (!wait_bounded<PAIR>(FULL(stage), ph, abort_flag, P.status)) {
               ok = false;
               break;
             }
             tc_fence_after();
-            const uint32_t sa = sbase + (uint32_t)(stage * STAGE_BYTES);
-            const uint32_t sb = sa + A_BYTES;
+            const uint32_t sa = sbase + (uint32_t)(stage * S::STAGE_BYTES);
+            const uint32_t sb = sa + S::A_BYTES;
 #pragma unroll
             for (int s = 0; s < BK / 16; ++s) {
-              tc_mma(dt, sw128_desc(sa + 32u * s), sw128_desc(sb + 32u * s), idesc,
-                     (inchunk == 0 && s == 0) ? 0u : 1u);
+              const uint32_t acc = (inchunk == 0 && s == 0) ? 0u : 1u;
+              if constexpr (PAIR)
+                tc_mma_pair(dt, sw128_desc(sa + 32u * s), sw128_desc(sb + 32u * s), idesc, acc);
+              else
+                tc_mma(dt, sw128_desc(sa + 32u * s), sw128_desc(sb + 32u * s), idesc, acc);
             }
-            tc_commit(EMPTY(stage));
+            if constexpr (PAIR)
+              tc_commit_pair(EMPTY(stage), 3);
+            else
+              tc_commit(EMPTY(stage));
             if (++stage == STAGES) {
               stage = 0;
               ph ^= 1u;
             }
             const bool last = (gi == P.ng - 1) && (kb == P.kblocks - 1);
             if (++inchunk == P.kchunk || last) {
-              tc_commit(AFULL(chunk & 1u));
+              if constexpr (PAIR)
+                tc_commit_pair(AFULL(chunk & 1u), 3);
+              else
+                tc_commit(AFULL(chunk & 1u));
               ++chunk;
               inchunk = 0;
             }
@@ -204,7 +264,10 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_f32_kernel(const __grid_const
         }
       }
       if (!ok) {
-        tc_commit(DONE);
+        if constexpr (PAIR)
+          tc_commit_pair(DONE, 1);
+        else
+          tc_commit(DONE);
         wait_quiet(DONE, 0);
       }
     }
@@ -215,32 +278,42 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_f32_kernel(const __grid_const
     const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
     const int total_kb = P.ng * P.kblocks;
     const int nchunks = (total_kb + P.kchunk - 1) / P.kchunk;
+    const uint32_t aempty0 = PAIR ? map_to_rank(AEMPTY(0), 0) : AEMPTY(0);
     uint32_t chunk = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
+    for (int t = (int)unit0; t < P.ntiles && ok; t += (int)nunits) {
       const int2 tile = P.tiles[t];
       float acc[128];
 #pragma unroll
       for (int i = 0; i < 128; ++i) acc[i] = 0.0f;
       for (int c = 0; c < nchunks; ++c) {
         const uint32_t buf = chunk & 1u, use = chunk >> 1;
-        if (!wait_bounded(AFULL(buf), use & 1u, abort_flag, P.status)) {
+        if (!wait_bounded<PAIR>(AFULL(buf), use & 1u, abort_flag, P.status)) {
           ok = false;
           break;
         }
         tc_fence_after();
         const uint32_t ta = tmem + lane_base + buf * ACC_COLS + (uint32_t)(chalf * 128);
-        tmem_accum32f<0>(ta, acc);
-        tmem_accum32f<32>(ta + 32u, acc);
-        tmem_accum32f<64>(ta + 64u, acc);
-        tmem_accum32f<96>(ta + 96u, acc);
+        tmem_accum16f<0>(ta, acc);
+        tmem_accum16f<16>(ta + 16u, acc);
+        tmem_accum16f<32>(ta + 32u, acc);
+        tmem_accum16f<48>(ta + 48u, acc);
+        tmem_accum16f<64>(ta + 64u, acc);
+        tmem_accum16f<80>(ta + 80u, acc);
+        tmem_accum16f<96>(ta + 96u, acc);
+        tmem_accum16f<112>(ta + 112u, acc);
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(AEMPTY(buf));
+        if (lane == 0) {
+          if constexpr (PAIR)
+            mbar_arrive_cluster(aempty0 + 8u * buf);
+          else
+            mbar_arrive(AEMPTY(buf));
+        }
         ++chunk;
       }
       if (!ok) break;
-      const int64_t row = (int64_t)tile.x * BM + quarter * 32 + lane;
+      const int64_t row = (int64_t)tile.x * S::TM + (int64_t)rank * BM + quarter * 32 + lane;
       const int64_t col0 = (int64_t)tile.y * BN + chalf * 128;
       int64_t lim = P.N - col0;
       if (P.lower) lim = min(lim, row - col0 + 1);
@@ -265,11 +338,17 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_f32_kernel(const __grid_const
   }
 
   __syncthreads();
+  if constexpr (PAIR) cluster_sync();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(TMEM_COLS)
-                 : "memory");
+    if constexpr (PAIR)
+      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                   "r"(TMEM_COLS)
+                   : "memory");
+    else
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                   "r"(TMEM_COLS)
+                   : "memory");
   }
 #undef FULL
 #undef EMPTY
@@ -297,23 +376,51 @@ struct CSplitOut {
   Planes re, im, s, d;  // pieces of Re, Im, Re + Im, Re - Im (each optional)
 };
 
+// One thread per 4 consecutive columns of a row (rows over blockIdx.y, a
+// grid-stride loop over column quads): the pieces of 4 values go out as one
+// 8-byte store per plane (kstride is a multiple of 8); a ragged last quad
+// stores element by element.
 __global__ void csplit_kernel(const float2 *__restrict__ A, int64_t lda, int64_t rows, int64_t cols,
                               int np, CSplitOut o) {
-  const int64_t total = rows * cols;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = t / cols, c = t - (t / cols) * cols;
-    const float2 a = A[r * lda + c];
-    const float vals[4] = {a.x, a.y, a.x + a.y, a.x - a.y};
-    const Planes *outs[4] = {&o.re, &o.im, &o.s, &o.d};
+  const int64_t cq = (cols + 3) / 4;
+  const Planes *outs[4] = {&o.re, &o.im, &o.s, &o.d};
+  for (int64_t r = blockIdx.y; r < rows; r += gridDim.y) {
+    const float2 *a_row = A + r * lda;
+    for (int64_t q4 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q4 < cq;
+         q4 += (int64_t)gridDim.x * blockDim.x) {
+      const int64_t c0 = 4 * q4;
+      const int nv = (int)min((int64_t)4, cols - c0);
+      float2 a[4];
 #pragma unroll
-    for (int w = 0; w < 4; ++w) {
-      const Planes &P = *outs[w];
-      if (!P.ptr) continue;
-      __nv_bfloat16 pc[3];
-      pieces(vals[w], np, pc);
-      const int64_t plane = P.rows * P.kstride;
-      for (int q = 0; q < np; ++q) P.ptr[q * plane + r * P.kstride + c] = pc[q];
+      for (int v = 0; v < 4; ++v) a[v] = v < nv ? a_row[c0 + v] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        const Planes &P = *outs[w];
+        if (!P.ptr) continue;
+        __nv_bfloat16 pc[4][3];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const float x = w == 0 ? a[v].x : w == 1 ? a[v].y : w == 2 ? a[v].x + a[v].y : a[v].x - a[v].y;
+          pieces(x, np, pc[v]);
+        }
+        const int64_t plane = P.rows * P.kstride;
+        __nv_bfloat16 *dst = P.ptr + r * P.kstride + c0;
+        for (int q = 0; q < np; ++q) {
+          if (nv == 4) {
+            __nv_bfloat162 lo, hi;
+            lo.x = pc[0][q];
+            lo.y = pc[1][q];
+            hi.x = pc[2][q];
+            hi.y = pc[3][q];
+            uint2 u;
+            u.x = *reinterpret_cast<uint32_t *>(&lo);
+            u.y = *reinterpret_cast<uint32_t *>(&hi);
+            *reinterpret_cast<uint2 *>(dst + q * plane) = u;
+          } else {
+            for (int v = 0; v < nv; ++v) dst[q * plane + v] = pc[v][q];
+          }
+        }
+      }
     }
   }
 }
@@ -365,11 +472,23 @@ __global__ void herm_diag_kernel(const float2 *__restrict__ A, int64_t lda, int6
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
-  double s = 0.0;
-  for (int64_t l = lane; l < k; l += 32) {
-    const float2 a = A[row * lda + l];
-    s += (double)a.x * a.x + (double)a.y * a.y;
+  // four independent FP64 sums per lane (the FP64 pipe is narrow: keep
+  // several fused multiply-adds in flight)
+  const float2 *a_row = A + row * lda;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int64_t l = lane;
+  for (; l + 96 < k; l += 128) {
+    const float2 a0 = a_row[l], a1 = a_row[l + 32], a2 = a_row[l + 64], a3 = a_row[l + 96];
+    s0 = fma((double)a0.x, (double)a0.x, fma((double)a0.y, (double)a0.y, s0));
+    s1 = fma((double)a1.x, (double)a1.x, fma((double)a1.y, (double)a1.y, s1));
+    s2 = fma((double)a2.x, (double)a2.x, fma((double)a2.y, (double)a2.y, s2));
+    s3 = fma((double)a3.x, (double)a3.x, fma((double)a3.y, (double)a3.y, s3));
   }
+  for (; l < k; l += 32) {
+    const float2 a = a_row[l];
+    s0 = fma((double)a.x, (double)a.x, fma((double)a.y, (double)a.y, s0));
+  }
+  double s = (s0 + s1) + (s2 + s3);
   for (int off = 16; off; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
   if (lane == 0) C[row * ldc + row] = make_float2((float)s, 0.0f);
 }
@@ -378,8 +497,9 @@ __global__ void herm_diag_kernel(const float2 *__restrict__ A, int64_t lda, int6
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode_c = nullptr;
 std::mutex g_mu_c;
-std::map<std::tuple<int, int64_t, int64_t, int>, std::pair<int2 *, int>> g_tiles_c;
+std::map<std::tuple<int, int64_t, int64_t, int, int>, std::pair<int2 *, int>> g_tiles_c;
 std::map<int, bool> g_attr_c;
+std::map<int, int> g_pair_units_c;
 
 cudaError_t encode_c(CUtensorMap *tm, const Planes &P, int box_rows) {
   if (!g_encode_c) {
@@ -401,21 +521,23 @@ cudaError_t encode_c(CUtensorMap *tm, const Planes &P, int box_rows) {
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-cudaError_t tiles_c(int dev, int64_t M, int64_t N, int lower, int2 **out, int *count) {
-  auto key = std::make_tuple(dev, M, N, lower);
+// tm: tile height (128, or 256 for CTA pairs); super-blocks of 2048 x 2048
+cudaError_t tiles_c(int dev, int64_t M, int64_t N, int lower, int tm, int2 **out, int *count) {
+  auto key = std::make_tuple(dev, M, N, lower, tm);
   auto it = g_tiles_c.find(key);
   if (it != g_tiles_c.end()) {
     *out = it->second.first;
     *count = it->second.second;
     return cudaSuccess;
   }
-  const int64_t TI = (M + BM - 1) / BM, TJ = (N + BN - 1) / BN;
+  const int64_t TI = (M + tm - 1) / tm, TJ = (N + BN - 1) / BN;
+  const int64_t SI = 2048 / tm;
   std::vector<int2> v;
-  for (int64_t bi = 0; bi < TI; bi += 16)
+  for (int64_t bi = 0; bi < TI; bi += SI)
     for (int64_t bj = 0; bj < TJ; bj += 8)
-      for (int64_t i = bi; i < std::min(TI, bi + 16); ++i)
+      for (int64_t i = bi; i < std::min(TI, bi + SI); ++i)
         for (int64_t j = bj; j < std::min(TJ, bj + 8); ++j) {
-          if (lower && j * BN > i * BM + BM - 1) continue;
+          if (lower && j * BN > i * tm + tm - 1) continue;
           v.push_back(make_int2((int)i, (int)j));
         }
   int2 *d = nullptr;
@@ -439,6 +561,32 @@ int grid_c(int64_t total, int threads) {
   int64_t want = (total + threads - 1) / threads;
   want = std::min<int64_t>(want, (int64_t)sms * 16);
   return (int)std::max<int64_t>(want, 1);
+}
+
+// Co-resident CTA pairs of the pair kernel on this device (0: none).
+int pair_units_c(int dev) {
+  auto it = g_pair_units_c.find(dev);
+  if (it != g_pair_units_c.end()) return it->second;
+  int units = 0;
+  if (cudaFuncSetAttribute(leaf_f32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)FShape<true>::SMEM) == cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(2, 1, 1);
+    cfg.blockDim = dim3(THREADS, 1, 1);
+    cfg.dynamicSmemBytes = FShape<true>::SMEM;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaOccupancyMaxActiveClusters(&units, leaf_f32_kernel<true>, &cfg) != cudaSuccess)
+      units = 0;
+  }
+  cudaGetLastError();
+  g_pair_units_c[dev] = units;
+  return units;
 }
 
 }  // namespace
@@ -468,11 +616,24 @@ static cudaError_t launch_leaf_f32(const std::vector<FTerm> &terms, int np, int6
   // every term must use the same two plane buffers: X planes in one
   // tensor map, Y planes in the other (plane index = set * np + piece)
   std::lock_guard<std::mutex> lock(g_mu_c);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  // the form: CTA pairs when the 256 x 256 tiles keep every co-resident pair
+  // busy (AAT_LEAF_PAIR=0/1 forces one form, as for the modular leaf)
+  const int units = pair_units_c(dev);
+  bool pair = false;
+  if (units > 0 && M >= 256) {
+    const int64_t pt = ((M + 255) / 256) * ((N + BN - 1) / BN);
+    const char *ev = getenv("AAT_LEAF_PAIR");
+    pair = ev ? atoi(ev) > 0 : (lower ? pt / 2 : pt) >= units;
+  }
   FParams *P = new FParams;
   std::memset(P, 0, sizeof(FParams));
   cudaError_t e;
   const Planes &X = *terms[0].x, &Y = *terms[0].y;
-  if ((e = encode_c(&P->tmx, X, BM)) != cudaSuccess || (e = encode_c(&P->tmy, Y, BN)) != cudaSuccess) {
+  if ((e = encode_c(&P->tmx, X, BM)) != cudaSuccess ||
+      (e = encode_c(&P->tmy, Y, pair ? FShape<true>::YROWS : FShape<false>::YROWS)) !=
+          cudaSuccess) {
     delete P;
     return e;
   }
@@ -495,29 +656,30 @@ static cudaError_t launch_leaf_f32(const std::vector<FTerm> &terms, int np, int6
   }
   P->ng = ng;
   P->kblocks = (int)((K + BK - 1) / BK);
-  // FP32 accumulation in the tensor core drifts over long K loops (its
-  // rounding is not to nearest); draining every 2 K blocks into FP32
-  // registers keeps the error of a K = 8192 product near FP32 rounding.
-  P->kchunk = 2;
+  // The tensor core's FP32 accumulation is drained into round-to-nearest
+  // FP32 registers every 8 K blocks (512 products).  Measured at n = k =
+  // 8192 (A A^H, 3 pieces, N(0,1) entries, 3000 sampled entries against the
+  // FP64 oracle): relative error 6.9e-7 / 5.2e-7 / 5.9e-7 / 1.0e-6 draining
+  // every 2 / 4 / 8 / 16 K blocks, time 9.23 / 8.41 / 8.01 / 7.82 ms.
+  P->kchunk = 8;
   P->out = out;
   P->ldo = ldo;
   P->M = M;
   P->N = N;
   P->lower = lower;
   P->status = device_status_ptr();
-  int dev = 0;
-  cudaGetDevice(&dev);
   int2 *tiles = nullptr;
   int nt = 0;
-  if ((e = tiles_c(dev, M, N, lower, &tiles, &nt)) != cudaSuccess) {
+  if ((e = tiles_c(dev, M, N, lower, pair ? 256 : 128, &tiles, &nt)) != cudaSuccess) {
     delete P;
     return e;
   }
   P->tiles = tiles;
   P->ntiles = nt;
   if (!g_attr_c[dev]) {
-    if ((e = cudaFuncSetAttribute(leaf_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)SMEM_BYTES)) != cudaSuccess) {
+    if ((e = cudaFuncSetAttribute(leaf_f32_kernel<false>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)FShape<false>::SMEM)) != cudaSuccess) {
       delete P;
       return e;
     }
@@ -528,7 +690,27 @@ static cudaError_t launch_leaf_f32(const std::vector<FTerm> &terms, int np, int6
   if (nt > 0) {
     const double macs = lower ? 0.5 * (double)M * (double)(M + 1) * K : (double)M * N * K;
     ProfScope prof(AAT_K_LEAF_F32, st, 2.0 * ng * macs);
-    leaf_f32_kernel<<<std::max(1, std::min(nt, sms)), THREADS, SMEM_BYTES, st>>>(*P);
+    if (pair) {
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = 2;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3(2 * std::max(1, std::min(nt, units)), 1, 1);
+      cfg.blockDim = dim3(THREADS, 1, 1);
+      cfg.dynamicSmemBytes = FShape<true>::SMEM;
+      cfg.stream = st;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      e = cudaLaunchKernelEx(&cfg, leaf_f32_kernel<true>, *P);
+      if (e != cudaSuccess) {
+        delete P;
+        return e;
+      }
+    } else {
+      leaf_f32_kernel<false><<<std::max(1, std::min(nt, sms)), THREADS, FShape<false>::SMEM, st>>>(*P);
+    }
   }
   delete P;
   return cudaGetLastError();
@@ -540,6 +722,7 @@ void leaf_f32_release() {
     if (kv.second.first) cudaFree(kv.second.first);
   g_tiles_c.clear();
   g_attr_c.clear();
+  g_pair_units_c.clear();
 }
 
 static int pieces_for(uint32_t flags) {
@@ -727,7 +910,10 @@ static void csplit(CCtx &c, const float2 *A, int64_t lda, int64_t rows, int64_t 
   int nsets = (o.re.ptr != nullptr) + (o.im.ptr != nullptr) + (o.s.ptr != nullptr) +
               (o.d.ptr != nullptr);
   ProfScope prof(AAT_K_SPLIT, c.st, (double)rows * cols * (8.0 + 2.0 * c.np * nsets));
-  csplit_kernel<<<grid_c(rows * cols, 256), 256, 0, c.st>>>(A, lda, rows, cols, c.np, o);
+  const int64_t cq = (cols + 3) / 4;
+  const dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((cq + 255) / 256, 64)),
+                  (unsigned)std::max<int64_t>(1, std::min<int64_t>(rows, 65535)));
+  csplit_kernel<<<grid, 256, 0, c.st>>>(A, lda, rows, cols, c.np, o);
   cchk(c, cudaGetLastError(), "complex split");
 }
 
