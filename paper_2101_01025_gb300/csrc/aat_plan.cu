@@ -45,7 +45,7 @@ struct Plan {
   std::vector<ModP> leaf_mods;
   SplitDesc *split_dev = nullptr;
   int nsplit = 0;
-  int64_t split_max = 0;
+  int split_blocks = 0;
   double split_bytes = 0.0;
   LeafBatch leaf;
   size_t solo_off = 0;            // workspace offset of the shared region
@@ -77,7 +77,7 @@ static int enqueue(Plan &P, cudaStream_t st) {
     if (e) return e;
   }
   if (P.nsplit > 0) {
-    if ((ce = launch_split_batch(P.split_dev, P.nsplit, P.split_max, P.split_bytes, st)) !=
+    if ((ce = launch_split_batch(P.split_dev, P.nsplit, P.split_blocks, P.split_bytes, st)) !=
         cudaSuccess)
       return report_error(AAT_ECUDA, cudaGetErrorString(ce));
     if ((ce = leaf_tc_batch_launch(P.leaf, st)) != cudaSuccess)
@@ -208,7 +208,6 @@ static int create(const aat_problem_t *probs, int count, Plan **out) {
       d.b = ds.b;
       d.P = pl;
       sd.push_back(d);
-      P->split_max = std::max<int64_t>(P->split_max, q.n * q.k);
       P->split_bytes += (double)q.n * q.k * (4.0 + 2.0 * pl.L);
       TcLeafArgs a;
       std::memset(&a, 0, sizeof(a));
@@ -225,6 +224,11 @@ static int create(const aat_problem_t *probs, int count, Plan **out) {
       P->leaf_mods.push_back(d.m);
     }
     P->nsplit = (int)sd.size();
+    P->split_blocks = split_batch_blocks(sd.data(), P->nsplit);
+    if (P->split_blocks < 0) {
+      destroy(P);
+      return report_error(AAT_ERANGE, "batch too large for one split launch");
+    }
     if ((ce = cudaMalloc(&P->split_dev, sizeof(SplitDesc) * sd.size())) != cudaSuccess ||
         (ce = cudaMemcpy(P->split_dev, sd.data(), sizeof(SplitDesc) * sd.size(),
                          cudaMemcpyHostToDevice)) != cudaSuccess ||

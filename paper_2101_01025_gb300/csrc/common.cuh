@@ -381,9 +381,13 @@ struct SplitDesc {
   ModP m;
   int b;
   Planes P;
+  int first_block;  // first block of this problem in the launch (split_batch_blocks)
+  int vec;          // rows start 16-byte aligned and cols % 4 == 0: 4-wide path
 };
-cudaError_t launch_split_batch(const SplitDesc *descs_dev, int count, int64_t max_elems,
-                               double bytes, cudaStream_t st);
+// Fills first_block / vec of descs (host) and returns the launch's block count.
+int split_batch_blocks(SplitDesc *descs, int count);
+cudaError_t launch_split_batch(const SplitDesc *descs_dev, int count, int nblocks, double bytes,
+                               cudaStream_t st);
 void leaf_f32_release();
 
 // Host helpers of the batched plans.

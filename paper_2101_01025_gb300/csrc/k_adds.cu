@@ -157,22 +157,49 @@ __global__ void split_kernel(const int32_t *__restrict__ X, int64_t ldx, int64_t
   }
 }
 
-// Batched split: problem blockIdx.y, elements strided over blockIdx.x.
-__global__ void split_batch_kernel(const SplitDesc *__restrict__ descs) {
-  const SplitDesc &d = descs[blockIdx.y];
-  const int64_t total = d.rows * d.cols;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = t / d.cols, c = t - (t / d.cols) * d.cols;
-    const int32_t x[1] = {bal(d.X[r * d.ldx + c], d.m)};
-    switch (d.P.nbase) {
-      case 1: store_digits_t<1, 1>(d.P, r, c, x, d.b); break;
-      case 2: store_digits_t<2, 1>(d.P, r, c, x, d.b); break;
-      case 3: store_digits_t<3, 1>(d.P, r, c, x, d.b); break;
-      case 4: store_digits_t<4, 1>(d.P, r, c, x, d.b); break;
-      case 5: store_digits_t<5, 1>(d.P, r, c, x, d.b); break;
-      default: break;
+// Batched split: every problem owns ceil(rows / kSplitRows) consecutive
+// blocks (first_block ascending), so the work of a block does not depend on
+// how large its problem is; a block finds its problem by binary search and
+// splits its kSplitRows rows, 4 columns per thread where rows are aligned.
+constexpr int kSplitRows = 8;
+
+template <int NB>
+__device__ __forceinline__ void split_rows(const SplitDesc &d, int64_t r0) {
+  const int64_t r1 = min(r0 + kSplitRows, d.rows);
+  for (int64_t r = r0; r < r1; ++r) {
+    const int32_t *xr = d.X + r * d.ldx;
+    if (d.vec) {
+      for (int64_t c4 = threadIdx.x; c4 < d.cols / 4; c4 += blockDim.x) {
+        int32_t v[4];
+        ldv_bal<4>(xr + 4 * c4, d.m, v);
+        store_digits_t<NB, 4>(d.P, r, 4 * c4, v, d.b);
+      }
+    } else {
+      for (int64_t c = threadIdx.x; c < d.cols; c += blockDim.x) {
+        const int32_t x[1] = {bal(xr[c], d.m)};
+        store_digits_t<NB, 1>(d.P, r, c, x, d.b);
+      }
     }
+  }
+}
+
+__global__ void split_batch_kernel(const SplitDesc *__restrict__ descs, int count) {
+  const int b = blockIdx.x;
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (descs[mid].first_block <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  const SplitDesc &d = descs[lo];
+  const int64_t r0 = (int64_t)(b - d.first_block) * kSplitRows;
+  switch (d.P.nbase) {
+    case 1: split_rows<1>(d, r0); break;
+    case 2: split_rows<2>(d, r0); break;
+    case 3: split_rows<3>(d, r0); break;
+    case 4: split_rows<4>(d, r0); break;
+    case 5: split_rows<5>(d, r0); break;
+    default: break;
   }
 }
 
@@ -433,18 +460,22 @@ cudaError_t launch_split(const int32_t *X, int64_t ldx, int64_t rows, int64_t co
   return cudaGetLastError();
 }
 
-cudaError_t launch_split_batch(const SplitDesc *descs_dev, int count, int64_t max_elems,
-                               double bytes, cudaStream_t st) {
-  if (count <= 0 || max_elems <= 0) return cudaSuccess;
-  if (count > 65535) return cudaErrorInvalidValue;
-  int dev = 0, sms = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // enough blocks per problem for the largest one, capped by the GPU's width
-  int64_t bx = (max_elems + kThreads - 1) / kThreads;
-  bx = std::min<int64_t>(bx, std::max<int64_t>(1, (int64_t)sms * 16 / count + 1));
+int split_batch_blocks(SplitDesc *descs, int count) {
+  int64_t nb = 0;
+  for (int i = 0; i < count; ++i) {
+    SplitDesc &d = descs[i];
+    d.first_block = (int)nb;
+    d.vec = (d.cols % 4 == 0) && (d.ldx % 4 == 0) && ((reinterpret_cast<uintptr_t>(d.X) & 15) == 0);
+    nb += (d.rows + kSplitRows - 1) / kSplitRows;
+  }
+  return nb > INT32_MAX ? -1 : (int)nb;
+}
+
+cudaError_t launch_split_batch(const SplitDesc *descs_dev, int count, int nblocks, double bytes,
+                               cudaStream_t st) {
+  if (count <= 0 || nblocks <= 0) return cudaSuccess;
   ProfScope prof(AAT_K_SPLIT, st, bytes);
-  split_batch_kernel<<<dim3((unsigned)bx, (unsigned)count), kThreads, 0, st>>>(descs_dev);
+  split_batch_kernel<<<(unsigned)nblocks, kThreads, 0, st>>>(descs_dev, count);
   return cudaGetLastError();
 }
 
