@@ -357,9 +357,10 @@ def run_ours(args):
                "ms_per_step": 1e3 * t_e2e,
                "h2d_bytes_per_step": N * K * 4,
                "d2h_bytes_per_step": aat.aat_modp_host_d2h_bytes(N),
-               "api": "aat_modp_host (pinned host A and C; copies inside the call; the "
-                      "lower triangle of C comes back in row bands, the rows below n/2 "
-                      "while the last product runs)"}
+               "api": "aat_modp_host (pinned host A and C; copies inside the call: A11 "
+                      "first so that P1 runs while the rest of A arrives; the lower "
+                      "triangle of C back in row bands, the rows below n/2 while the last "
+                      "product runs)"}
 
     cpu = None
     if not args.no_extras and rank == 0 and world == 1:

@@ -122,10 +122,12 @@ AAT_API int aah_quat_modp(const int32_t *A, const int32_t *B, const int32_t *C, 
  * aat_modp_ex with `flags`, copies the result back and synchronises.  The
  * device buffers are owned by the library.  Only the lower triangle of C is
  * defined (its strict upper triangle is unspecified, as for aat_modp): it is
- * copied back in bands of 512 rows, band [a, b) carrying columns [0, b), and
- * when a recursion level runs, the rows below n/2 go back while the last
- * product still computes.  With AAT_ZERO_UPPER the whole of C is copied
- * (upper triangle zero) after the computation.
+ * copied back in bands of 512 rows, band [a, b) carrying columns [0, b).
+ * When a recursion level runs, A's top-left block A11 is copied first and
+ * the product P1 = Low(A11 A11^T) runs while the rest of A arrives, and the
+ * rows below n/2 of C go back while the last product still computes.  With
+ * AAT_ZERO_UPPER, A is copied whole first and the whole of C (upper
+ * triangle zero) after the computation.
  */
 AAT_API int aat_modp_host(const int32_t *A_host, int64_t n, int64_t k, uint32_t p,
                   int32_t *C_host, uint32_t flags);

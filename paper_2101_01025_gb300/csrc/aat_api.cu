@@ -256,6 +256,7 @@ struct DeviceState {
   cudaStream_t e2e_stream = nullptr;
   cudaStream_t e2e_stream2 = nullptr;  // copies rows that are final early
   cudaEvent_t e2e_split = nullptr;
+  cudaEvent_t e2e_a11 = nullptr, e2e_rest = nullptr;  // copies of A in
 };
 
 static std::mutex g_state_mu;
@@ -374,6 +375,9 @@ struct Ctx {
   int top_levels = -1;
   int64_t split_row = 0;
   int form = 0;  // leaf kernel form (TcLeafArgs::form)
+  // optional (end-to-end path): A11's and the rest of A's copies to the
+  // device complete at these events; the stream waits for them
+  cudaEvent_t in_a11 = nullptr, in_rest = nullptr;
   uint32_t alpha = 1;  // scale of every product (the SYRK update's alpha)
 };
 
@@ -495,8 +499,10 @@ struct LevelOps {
 // Step 1 of a level: S1..S4 (4 additions, 2 products by Y) in one pass over
 // A.  S3 is written as int32 to S3 (row stride ldS3) unless it is needed
 // only as digit planes (last level, tensor-core leaf; S3 may be null then).
+// pA11: digit planes of A11 already split (the end-to-end path computes P1
+// before the rest of A arrives), or none.
 static LevelOps sblocks_step(Ctx &c, const int32_t *A, int64_t lda, int64_t h, int64_t kap,
-                             int32_t *S3, int64_t ldS3, bool last) {
+                             int32_t *S3, int64_t ldS3, bool last, Planes pA11 = Planes{}) {
   const bool tc = (c.leaf == AAT_LEAF_TC);
   const int32_t *A22 = A + h * lda + kap;
   SKernelOut o;
@@ -515,7 +521,10 @@ static LevelOps sblocks_step(Ctx &c, const int32_t *A, int64_t lda, int64_t h, i
     o.sp[3] = L.oS4.pl = planes_alloc(c, h, kap);
     o.a22 = L.oA22.pl = planes_alloc(c, h, kap);
     if (last) {
-      o.a11 = L.pA11 = planes_alloc(c, h, kap);
+      if (pA11.L)
+        L.pA11 = pA11;
+      else
+        o.a11 = L.pA11 = planes_alloc(c, h, kap);
       o.a12 = L.pA12 = planes_alloc(c, h, kap);
       o.sp[2] = L.pS3 = planes_alloc(c, h, kap);
     }
@@ -561,6 +570,21 @@ static void rec(Ctx &c, const int32_t *A, int64_t lda, int64_t n, int64_t k, int
   const bool last = (levels == 1);
   const size_t mark = c.ar.used;
   count_level(c);
+  // End-to-end path: A11 arrives first, so P1 = Low(A11 A11^T) runs while
+  // the rest of A is copied in (step 5 moved ahead; C11 is not touched by
+  // steps 1-4, and the post-additions read P1 from it as before).
+  const bool p1_first = c.in_rest && levels == c.top_levels;
+  Planes pA11_early = no_planes();
+  if (p1_first) {
+    if (!c.ar.dry) cudaStreamWaitEvent(c.st, c.in_a11, 0);
+    if (c.leaf == AAT_LEAF_TC && last) {
+      pA11_early = planes_alloc(c, h, kap);
+      if (!c.ar.dry)
+        check(c, launch_split(A11, lda, h, kap, c.m, c.ds.b, pA11_early, c.st), "split");
+    }
+    rec(c, A11, lda, h, kap, C11, ldc, levels - 1, pA11_early);
+    if (!c.ar.dry) cudaStreamWaitEvent(c.st, c.in_rest, 0);
+  }
   // S3: the input of the recursive product P5.  Table 3 keeps it in C21
   // (needs kappa <= h, i.e. k <= n); otherwise it takes workspace.
   int32_t *S3;
@@ -573,7 +597,7 @@ static void rec(Ctx &c, const int32_t *A, int64_t lda, int64_t n, int64_t k, int
     ldS3 = kap;
   }
   // 1. S1..S4 (4 additions, 2 products by Y) in one pass over A
-  const LevelOps L = sblocks_step(c, A, lda, h, kap, S3, ldS3, last);
+  const LevelOps L = sblocks_step(c, A, lda, h, kap, S3, ldS3, last, pA11_early);
   // 2. P4^T = S2 S1^T -> C22
   leaf(c, L.oS2, L.oS1, false, h, h, kap, C22, ldc, 0, 0);
   // 3. P5 = Low(S3 S3^T) -> C12
@@ -581,7 +605,7 @@ static void rec(Ctx &c, const int32_t *A, int64_t lda, int64_t n, int64_t k, int
   // 4. P3 = A22 S4^T -> C21 (S3 is no longer needed)
   leaf(c, L.oA22, L.oS4, false, h, h, kap, C21, ldc, 0, 0);
   // 5. P1 = Low(A11 A11^T) -> C11
-  rec(c, A11, lda, h, kap, C11, ldc, levels - 1, L.pA11);
+  if (!p1_first) rec(c, A11, lda, h, kap, C11, ldc, levels - 1, L.pA11);
   // 6. U1 = P1 + P5, U2 = U1 + P4, U4 = U2 + P3 -> C21, U5 = Low(U2 + P4^T) -> C22
   if (!c.ar.dry) check(c, launch_postadd(C11, ldc, C12, C21, C22, ldc, h, c.m, c.st), "postadd");
   // rows [h, n) of the top level (C21 = U4, Low(C22) = Low(U5)) are final
@@ -759,6 +783,17 @@ static size_t run_plan_in(Ctx &c, const int32_t *A, int64_t n, int64_t k, int64_
     if (tv.plain) c.ds.nsum = 0;
   }
   Prepared pr = prepare(n, k, c.y, flags);
+  const bool early = !pr.padded && pr.levels >= 1 && !beta;
+  // end-to-end path: with no top level to overlap, wait for all of A
+  // before anything reads it
+  const cudaEvent_t in_a11 = c.in_a11, in_rest = c.in_rest;
+  if (in_rest && !early) {
+    if (!dry) {
+      cudaStreamWaitEvent(c.st, in_a11, 0);
+      cudaStreamWaitEvent(c.st, in_rest, 0);
+    }
+    c.in_a11 = c.in_rest = nullptr;
+  }
   const int32_t *Aw = A;
   int64_t ldaw = lda;
   int32_t *Cw = C;
@@ -781,9 +816,9 @@ static size_t run_plan_in(Ctx &c, const int32_t *A, int64_t n, int64_t k, int64_
     c.stats->n_pad = pr.n_pad;
     c.stats->k_pad = pr.k_pad;
   }
-  const bool early = !pr.padded && pr.levels >= 1 && !beta;
   c.top_levels = early ? pr.levels : -1;
   c.split_row = early ? pr.n_pad / 2 : n;
+
   if (beta)
     syrk_rec(c, Aw, ldaw, pr.n_pad, pr.k_pad, Cw, ldcw, pr.levels, *beta);
   else
@@ -791,6 +826,8 @@ static size_t run_plan_in(Ctx &c, const int32_t *A, int64_t n, int64_t k, int64_
   if (pr.padded && !dry) check(c, launch_copy_low(Cw, ldcw, C, ldc, n, c.st), "unpad");
   if (!dry && (flags & AAT_ZERO_UPPER)) check(c, launch_zero_upper(C, ldc, n, c.st), "zero upper");
   if (!dry && !early && c.split_ev && c.err == AAT_OK) cudaEventRecord(c.split_ev, c.st);
+  c.in_a11 = in_a11;
+  c.in_rest = in_rest;
   return c.ar.peak;
 }
 
@@ -923,7 +960,8 @@ const char *aat_last_error(void) { return g_last_error.c_str(); }
 // aat_modp_ex with the optional early-rows event (aat_modp_host).
 static int modp_device(const int32_t *A, int64_t n, int64_t k, int64_t lda, uint32_t p, int32_t *C,
                        int64_t ldc, uint32_t flags, cudaStream_t stream, cudaEvent_t split_ev,
-                       int64_t *split_row, int form = 0) {
+                       int64_t *split_row, int form = 0, cudaEvent_t in_a11 = nullptr,
+                       cudaEvent_t in_rest = nullptr) {
   if (split_row) *split_row = n;
   if (n < 0 || k < 0) return fail(AAT_EINVAL, "negative size");
   if (n > (1 << 30) || k > (1 << 30)) return fail(AAT_EINVAL, "size too large");
@@ -942,6 +980,8 @@ static int modp_device(const int32_t *A, int64_t n, int64_t k, int64_t lda, uint
     return ce == cudaSuccess ? AAT_OK : cuda_fail(ce, "memset");
   }
   c.form = form;
+  c.in_a11 = in_a11;
+  c.in_rest = in_rest;
   const size_t need = run_plan(c, A, n, k, lda, C, ldc, flags, true, nullptr);
   void *ws = nullptr;
   if ((e = ensure_workspace(need, &ws))) return e;
@@ -1082,7 +1122,9 @@ int aat_modp_host(const int32_t *A_host, int64_t n, int64_t k, uint32_t p, int32
     if (!s->e2e_stream) cudaStreamCreateWithFlags(&s->e2e_stream, cudaStreamNonBlocking);
     if (!s->e2e_stream2) cudaStreamCreateWithFlags(&s->e2e_stream2, cudaStreamNonBlocking);
     if (!s->e2e_split) cudaEventCreateWithFlags(&s->e2e_split, cudaEventDisableTiming);
-    if (!s->e2e_stream || !s->e2e_stream2 || !s->e2e_split)
+    if (!s->e2e_a11) cudaEventCreateWithFlags(&s->e2e_a11, cudaEventDisableTiming);
+    if (!s->e2e_rest) cudaEventCreateWithFlags(&s->e2e_rest, cudaEventDisableTiming);
+    if (!s->e2e_stream || !s->e2e_stream2 || !s->e2e_split || !s->e2e_a11 || !s->e2e_rest)
       return fail(AAT_ECUDA, "e2e streams");
     if (s->e2e_a_size < abytes) {
       if (s->e2e_a) cudaFree(s->e2e_a);
@@ -1101,10 +1143,45 @@ int aat_modp_host(const int32_t *A_host, int64_t n, int64_t k, uint32_t p, int32
   }
   cudaStream_t st = s->e2e_stream;
   cudaError_t ce;
+  const int32_t *Cd = (const int32_t *)s->e2e_c;
+  if (!(flags & AAT_ZERO_UPPER) && n >= 2 && k >= 2) {
+    // A comes in on the second stream, its top-left block A11 (rows and
+    // columns below n/2, k/2) first: when a recursion level runs, the
+    // product P1 = Low(A11 A11^T) starts while the rest of A is in flight
+    int32_t *Ad = (int32_t *)s->e2e_a;
+    const int64_t h = n / 2, kap = k / 2;
+    cudaStream_t s2 = s->e2e_stream2;
+    if ((ce = cudaMemcpy2DAsync(Ad, (size_t)k * 4, A_host, (size_t)k * 4, (size_t)kap * 4,
+                                (size_t)h, cudaMemcpyHostToDevice, s2)) != cudaSuccess ||
+        (ce = cudaEventRecord(s->e2e_a11, s2)) != cudaSuccess ||
+        (ce = cudaMemcpy2DAsync(Ad + kap, (size_t)k * 4, A_host + kap, (size_t)k * 4,
+                                (size_t)(k - kap) * 4, (size_t)h, cudaMemcpyHostToDevice, s2)) !=
+            cudaSuccess ||
+        (ce = cudaMemcpyAsync(Ad + h * k, A_host + h * k, (size_t)(n - h) * k * 4,
+                              cudaMemcpyHostToDevice, s2)) != cudaSuccess ||
+        (ce = cudaEventRecord(s->e2e_rest, s2)) != cudaSuccess)
+      return cuda_fail(ce, "copy A to the device");
+    // only the lower triangle is defined: copy it in row bands; the rows
+    // below the top-level split are final before the last product P2 runs
+    // and go back on the second stream meanwhile
+    int64_t split = n;
+    e = modp_device(Ad, n, k, k, p, (int32_t *)Cd, n, flags, st, s->e2e_split, &split, 0,
+                    s->e2e_a11, s->e2e_rest);
+    if (e) return e;
+    if (split < n) {
+      if ((ce = cudaStreamWaitEvent(s2, s->e2e_split, 0)) != cudaSuccess ||
+          (ce = copy_low_bands(C_host, Cd, n, split, n, s2)) != cudaSuccess)
+        return cuda_fail(ce, "copy C to the host");
+    }
+    if ((ce = copy_low_bands(C_host, Cd, n, 0, split, st)) != cudaSuccess)
+      return cuda_fail(ce, "copy C to the host");
+    if ((ce = cudaStreamSynchronize(s2)) != cudaSuccess) return cuda_fail(ce, "synchronize");
+    if ((ce = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(ce, "synchronize");
+    return AAT_OK;
+  }
   if (k > 0 && (ce = cudaMemcpyAsync(s->e2e_a, A_host, (size_t)n * k * 4, cudaMemcpyHostToDevice,
                                      st)) != cudaSuccess)
     return cuda_fail(ce, "copy A to the device");
-  const int32_t *Cd = (const int32_t *)s->e2e_c;
   if (flags & AAT_ZERO_UPPER) {
     // the caller asked for the whole matrix: one copy at the end
     e = modp_device((const int32_t *)s->e2e_a, n, k, std::max<int64_t>(k, 1), p, (int32_t *)Cd, n,
@@ -1404,6 +1481,8 @@ void aat_shutdown(void) {
     if (s.e2e_stream) cudaStreamDestroy(s.e2e_stream);
     if (s.e2e_stream2) cudaStreamDestroy(s.e2e_stream2);
     if (s.e2e_split) cudaEventDestroy(s.e2e_split);
+    if (s.e2e_a11) cudaEventDestroy(s.e2e_a11);
+    if (s.e2e_rest) cudaEventDestroy(s.e2e_rest);
     cudaSetDevice(cur);
   }
   g_states.clear();
