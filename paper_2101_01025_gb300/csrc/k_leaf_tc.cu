@@ -65,6 +65,7 @@ struct Group {
   uint32_t ratio_sh;  // floor(ratio 2^32 / p), Shoup's precomputed quotient
 };
 
+
 // One problem of a batched launch; its tensor maps live in global memory.
 struct alignas(64) BatchProb {
   CUtensorMap tmx, tmy;
@@ -96,6 +97,11 @@ struct Params {
   const Group *gtab;
 };
 
+// Batched tile entries are (problem, I, J, goff | ng << 16): the tile's
+// group table is one hop away instead of two.
+__device__ __forceinline__ int tile_goff(int w) { return w & 0xFFFF; }
+__device__ __forceinline__ int tile_ngrp(int w) { return w >> 16; }
+
 // What one tile of the launch reads.
 struct TileView {
   const CUtensorMap *tmx, *tmy;
@@ -111,8 +117,8 @@ __device__ __forceinline__ TileView tile_view(const Params &P, int t) {
     const BatchProb &b = P.probs[tl.x];
     v.tmx = &b.tmx;
     v.tmy = &b.tmy;
-    v.g = P.gtab + b.goff;
-    v.ng = b.ng;
+    v.g = P.gtab + tile_goff(tl.w);
+    v.ng = tile_ngrp(tl.w);
     v.I = tl.y;
     v.J = tl.z;
   } else {
@@ -131,7 +137,7 @@ __device__ __forceinline__ TileView tile_view(const Params &P, int t) {
 template <bool BATCH>
 __device__ __forceinline__ Group tile_group(const Params &P, int t, int gi) {
   if constexpr (BATCH) {
-    return P.gtab[P.probs[P.btiles[t].x].goff + gi];
+    return P.gtab[tile_goff(P.btiles[t].w) + gi];
   } else {
     return P.g[gi];
   }
@@ -140,7 +146,7 @@ __device__ __forceinline__ Group tile_group(const Params &P, int t, int gi) {
 template <bool BATCH>
 __device__ __forceinline__ int tile_ng(const Params &P, int t) {
   if constexpr (BATCH) {
-    return P.probs[P.btiles[t].x].ng;
+    return tile_ngrp(P.btiles[t].w);
   } else {
     return P.ng;
   }
@@ -218,7 +224,13 @@ struct Shape {
   static constexpr int A_BYTES = BM * BK * 2;
   static constexpr int B_BYTES = YROWS * BK * 2;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-  static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + 256;
+  // + 256 bytes of barriers + a per-warp cache of the tile's groups
+  // (batched launches: 8 epilogue warps x 32 groups) + a per-warp 32 x 17
+  // int32 staging area of the output stores
+  static constexpr size_t GCACHE_BYTES = (size_t)EPI_WARPS * 32 * sizeof(Group);
+  static constexpr size_t XS_BYTES = (size_t)EPI_WARPS * 32 * 17 * 4;
+  static constexpr size_t SMEM =
+      1024 + (size_t)STAGES * STAGE_BYTES + 256 + GCACHE_BYTES + XS_BYTES;
   // Instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator
   // (bit 4), A and B BF16 (bits 7, 10), both K-major, N >> 3 at bit 17,
   // M >> 4 at bit 24.
@@ -422,17 +434,33 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_tc_kernel(const __grid_consta
     const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
     // the leader's MMA waits until the epilogues of both CTAs drained a buffer
     const uint32_t aempty0 = PAIR ? map_to_rank(AEMPTY(0), 0) : AEMPTY(0);
+    Group *gcache = reinterpret_cast<Group *>(smem + (size_t)STAGES * S::STAGE_BYTES + 256) + e * 32;
+    int32_t *xs = reinterpret_cast<int32_t *>(smem + (size_t)STAGES * S::STAGE_BYTES + 256 +
+                                              S::GCACHE_BYTES) + e * 32 * 17;
     uint32_t chunk = 0;
     bool ok = true;
     ModP m = P.m;
     for (int t = (int)unit0; t < P.ntiles && ok; t += (int)nunits) {
-      if constexpr (BATCH) m = tile_modp<BATCH>(P, t);
-      const int ng = tile_ng<BATCH>(P, t);
+      int ng;
+      // batched launches: the tile's groups come from global memory; lane i
+      // of each warp loads group i into the warp's shared-memory cache at
+      // the start of the tile (all loads in flight together) and the group
+      // loop reads them from there
+      if constexpr (BATCH) {
+        const int4 tl = P.btiles[t];
+        ng = tile_ngrp(tl.w);
+        __syncwarp();
+        if (lane < ng) gcache[lane] = P.gtab[tile_goff(tl.w) + lane];
+        __syncwarp();
+        m = P.probs[tl.x].m;
+      } else {
+        ng = tile_ng<BATCH>(P, t);
+      }
       int32_t acc[128];
 #pragma unroll
       for (int i = 0; i < 128; ++i) acc[i] = 0;
       for (int gi = 0; gi < ng && ok; ++gi) {
-        const Group g = tile_group<BATCH>(P, t, gi);
+        const Group g = (BATCH && gi < 32) ? gcache[gi] : tile_group<BATCH>(P, t, gi);
         if (gi > 0) {
 #pragma unroll
           for (int i = 0; i < 128; ++i) acc[i] = mulmod_shoup(acc[i], g.ratio, g.ratio_sh, m);
@@ -473,33 +501,64 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_tc_kernel(const __grid_consta
       // final value, canonical, in place (the last digit pair has weight 1)
 #pragma unroll
       for (int i = 0; i < 128; ++i) acc[i] = (int32_t)red_i32_canon(acc[i], m);
-      // columns [0, lim) of this thread's 128 are written
       const OutView o = tile_out<BATCH>(P, t);
-      int64_t lim = o.N - col0;
-      if (o.lower) lim = min(lim, row - col0 + 1);
-      if (row < o.M && lim > 0) {
-        int32_t *orow = o.out + row * o.ldo + col0;
-        const bool vec = ((reinterpret_cast<uintptr_t>(orow) & 15) == 0) && !o.accumulate;
+      const int64_t row0 = row - lane;
+      // rows 16-byte aligned and nothing to read back: each thread stores its
+      // row segment with 16-byte stores
+      if (!o.accumulate && ((reinterpret_cast<uintptr_t>(o.out) | (uintptr_t)(o.ldo * 4)) & 15) == 0) {
+        int64_t lim = o.N - col0;
+        if (o.lower) lim = min(lim, row - col0 + 1);
+        if (row < o.M && lim > 0) {
+          int32_t *orow = o.out + row * o.ldo + col0;
 #pragma unroll
-        for (int q = 0; q < 32; ++q) {
-          const int c = 4 * q;
-          if (vec && c + 4 <= lim) {
-            *reinterpret_cast<int4 *>(orow + c) = make_int4(acc[c], acc[c + 1], acc[c + 2], acc[c + 3]);
-          } else {
+          for (int q = 0; q < 32; ++q) {
+            const int c = 4 * q;
+            if (c + 4 <= lim) {
+              *reinterpret_cast<int4 *>(orow + c) = make_int4(acc[c], acc[c + 1], acc[c + 2], acc[c + 3]);
+            } else {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              if (c + j < lim) {
-                int32_t x = acc[c + j];
-                if (o.accumulate) {
-                  int32_t old = bal(orow[c + j], m);
-                  if (o.beta != 1u) old = mulmod_shoup(old, o.beta, o.beta_sh, m);
-                  x = (int32_t)bal_to_canon(add_bal(to_bal((uint32_t)x, m), old, m), m);
-                }
-                orow[c + j] = x;
-              }
+              for (int j = 0; j < 4; ++j)
+                if (c + j < lim) orow[c + j] = acc[c + j];
             }
+            asm volatile("" ::: "memory");
           }
-          asm volatile("" ::: "memory");
+        }
+        continue;
+      }
+      // Otherwise coalesced through shared memory: each thread owns one row
+      // of the tile (its TMEM lane), so the warp writes 16 columns of its 32
+      // rows at a time into shared memory and reads them back two rows per
+      // instruction, every store instruction covering two contiguous 64-byte
+      // row segments (ragged rows, and the read-modify-write of an
+      // accumulating product).
+      // the warp's 32 x 128 block: rows below mlim, columns below nlim, and
+      // for a lower product only column - row <= dl (tile coordinates)
+      const int mlim = (int)max((int64_t)0, min((int64_t)32, o.M - row0));
+      const int nlim = (int)max((int64_t)0, min((int64_t)128, o.N - col0));
+      const int dl = o.lower ? (int)max((int64_t)-256, min((int64_t)256, row0 - col0)) : 1 << 20;
+      int32_t *const base = o.out + row0 * o.ldo + col0;
+      const int64_t ldo = o.ldo;
+      const int accum = o.accumulate;
+      const uint32_t beta = o.beta, beta_sh = o.beta_sh;
+#pragma unroll
+      for (int cb = 0; cb < 128; cb += 16) {
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) xs[lane * 17 + j] = acc[cb + j];
+        __syncwarp();
+#pragma unroll 1
+        for (int i = 0; i < 16; ++i) {
+          const int rr = 2 * i + (lane >> 4), cl = cb + (lane & 15);
+          if (rr < mlim && cl < nlim && cl - rr <= dl) {
+            int32_t x = xs[rr * 17 + (lane & 15)];
+            int32_t *dst = base + (int64_t)rr * ldo + cl;
+            if (accum) {
+              int32_t old = bal(*dst, m);
+              if (beta != 1u) old = mulmod_shoup(old, beta, beta_sh, m);
+              x = (int32_t)bal_to_canon(add_bal(to_bal((uint32_t)x, m), old, m), m);
+            }
+            *dst = x;
+          }
         }
       }
     }
@@ -875,6 +934,7 @@ cudaError_t leaf_tc_batch_build(const TcLeafArgs *args, const ModP *mods, int co
     if (!build_groups(a, mods[i], tmp.data(), &ng, &nprod)) return cudaErrorInvalidValue;
     b.goff = (int)gtab.size();
     b.ng = ng;
+    if (b.goff + ng > 0xFFFF) return cudaErrorInvalidValue;  // tile entries pack goff in 16 bits
     gtab.insert(gtab.end(), tmp.begin(), tmp.begin() + ng);
     b.out = a.out;
     b.ldo = a.ldo;
@@ -891,7 +951,7 @@ cudaError_t leaf_tc_batch_build(const TcLeafArgs *args, const ModP *mods, int co
     for (int64_t I = 0; I < TI; ++I)
       for (int64_t J = 0; J < TJ; ++J) {
         if (a.lower && J * BN > I * BM + BM - 1) continue;
-        tiles.push_back({make_int4(i, (int)I, (int)J, 0), cost});
+        tiles.push_back({make_int4(i, (int)I, (int)J, b.goff | (ng << 16)), cost});
       }
     const double macs =
         a.lower ? 0.5 * (double)a.M * (double)(a.M + 1) * a.K : (double)a.M * a.N * a.K;
