@@ -28,7 +28,7 @@
 
 namespace aat {
 
-constexpr int kBranches = 8;
+constexpr int kBranches = 16;
 
 struct Plan {
   int dev = 0;
