@@ -254,9 +254,12 @@ AAT_API int aat_complex_ex(const void *A, int64_t n, int64_t k, int64_t lda, voi
  * list of problems (their pointers, sizes and flags) and executed any number
  * of times; each execution recomputes every C from the current contents of
  * every A.  F_p problems whose recursion depth is 0 share ONE persistent
- * tensor-core leaf launch over all their tiles; the others run their own
- * launches.  Execution is one CUDA graph launch on the given stream (no
- * allocation, no host synchronisation).  The plan owns its workspace.
+ * tensor-core leaf launch over all their tiles; complex A A^H problems (2M)
+ * share one split, ONE persistent FP32 leaf launch over the tiles of all
+ * their products, one combine and one diagonal launch (beside the F_p
+ * batch, on a stream of their own); the others run their own launches.
+ * Execution is one CUDA graph launch on the given stream (no allocation, no
+ * host synchronisation).  The plan owns its workspace.
  */
 #define AAT_KIND_MODP 0   /* Low(A A^T) mod p: int32 A and C, field p */
 #define AAT_KIND_AAH 1    /* Low(A A^H): complex64 A and C, 2M        */
@@ -272,7 +275,8 @@ typedef struct {
 typedef struct aat_plan aat_plan_t;
 AAT_API int aat_plan_create(const aat_problem_t *probs, int count, aat_plan_t **plan);
 AAT_API int aat_plan_execute(aat_plan_t *plan, void *stream);
-/* problems in the shared leaf launch, problems run on their own, workspace */
+/* problems in the shared (F_p or complex) leaf launches, problems run on
+ * their own, workspace bytes */
 AAT_API int aat_plan_info(const aat_plan_t *plan, int *batched, int *solo, size_t *workspace);
 AAT_API void aat_plan_destroy(aat_plan_t *plan);
 

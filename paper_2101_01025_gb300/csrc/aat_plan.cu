@@ -7,8 +7,12 @@
 //     plane set, and ONE persistent tensor-core leaf launch walks a single
 //     tile list spanning all of them (per-problem tensor maps, group tables
 //     and outputs live in device tables), heaviest tiles first;
-//   * every other problem (recursive F_p products, complex products) runs
-//     its own sequence of launches.
+//   * complex A A^H problems (Algorithm 2, 2M) join a second batch: one
+//     split, ONE persistent FP32 leaf launch over the H and G tiles of all
+//     of them, one combine and one diagonal launch, on a side stream beside
+//     the F_p batch;
+//   * every other problem (recursive F_p products, complex A A^T) runs its
+//     own sequence of launches.
 // The other problems are spread round robin over up to kBranches side
 // streams, each with its own workspace region, so that the small launches of
 // different problems share the SMs; the batch runs on the main stream beside
@@ -41,6 +45,10 @@ struct Plan {
   std::vector<aat_problem_t> probs;
   std::vector<int> solo;          // problems run on their own
   std::vector<int> batched;       // F_p problems in the batched leaf launch
+  std::vector<int> cbatched;      // complex A A^H problems in the complex batch
+  CBatch cb;
+  cudaStream_t cb_st = nullptr;   // the complex batch's stream
+  cudaEvent_t cb_ev[2] = {nullptr, nullptr};  // its fork and join
   std::vector<TcLeafArgs> leaf_args;
   std::vector<ModP> leaf_mods;
   SplitDesc *split_dev = nullptr;
@@ -55,6 +63,13 @@ struct Plan {
 
 static int enqueue(Plan &P, cudaStream_t st) {
   cudaError_t ce;
+  if (!P.cbatched.empty()) {  // the complex batch on its own stream
+    if ((ce = cudaEventRecord(P.cb_ev[0], st)) != cudaSuccess ||
+        (ce = cudaStreamWaitEvent(P.cb_st, P.cb_ev[0], 0)) != cudaSuccess ||
+        (ce = cbatch_launch(P.cb, P.cb_st)) != cudaSuccess ||
+        (ce = cudaEventRecord(P.cb_ev[1], P.cb_st)) != cudaSuccess)
+      return report_error(AAT_ECUDA, cudaGetErrorString(ce));
+  }
   const int nb = (int)P.side.size();
   if (nb > 0) {  // fork the side branches off the main stream
     if ((ce = cudaEventRecord(P.ev[0], st)) != cudaSuccess)
@@ -88,6 +103,8 @@ static int enqueue(Plan &P, cudaStream_t st) {
         (ce = cudaStreamWaitEvent(st, P.ev[1 + b], 0)) != cudaSuccess)
       return report_error(AAT_ECUDA, cudaGetErrorString(ce));
   }
+  if (!P.cbatched.empty() && (ce = cudaStreamWaitEvent(st, P.cb_ev[1], 0)) != cudaSuccess)
+    return report_error(AAT_ECUDA, cudaGetErrorString(ce));
   return AAT_OK;
 }
 
@@ -99,6 +116,10 @@ static void destroy(Plan *P) {
   if (P->exec) cudaGraphExecDestroy(P->exec);
   if (P->graph) cudaGraphDestroy(P->graph);
   leaf_tc_batch_free(&P->leaf);
+  cbatch_free(&P->cb);
+  for (cudaEvent_t e : P->cb_ev)
+    if (e) cudaEventDestroy(e);
+  if (P->cb_st) cudaStreamDestroy(P->cb_st);
   if (P->split_dev) cudaFree(P->split_dev);
   if (P->ws) cudaFree(P->ws);
   for (cudaEvent_t e : P->ev) cudaEventDestroy(e);
@@ -147,6 +168,15 @@ static int create(const aat_problem_t *probs, int count, Plan **out) {
         continue;
       }
     }
+    if (q.kind == AAT_KIND_AAH) {
+      const uint32_t prec = q.flags & AAT_C_PREC_MASK;
+      if (prec != AAT_C_FP32 && prec != AAT_C_BF16X3 && prec != AAT_C_BF16) {
+        destroy(P);
+        return report_error(AAT_EUNSUPPORTED, "unknown precision");
+      }
+      P->cbatched.push_back(i);
+      continue;
+    }
     size_t need = 0;
     if (fp)
       e = modp_run((const int32_t *)q.A, q.n, q.k, q.lda, q.p, (int32_t *)q.C, q.ldc, q.flags,
@@ -162,8 +192,15 @@ static int create(const aat_problem_t *probs, int count, Plan **out) {
     P->solo.push_back(i);
   }
   const int nb = std::min<int>(kBranches, (int)P->solo.size());
+  std::vector<CBInput> cb_in;
+  for (int i : P->cbatched) {
+    const aat_problem_t &q = P->probs[i];
+    cb_in.push_back(CBInput{(const float2 *)q.A, q.lda, q.n, q.k, (float2 *)q.C, q.ldc, q.flags, 1});
+  }
+  const size_t cb_off = r256(batch_bytes);
+  const size_t cb_bytes = r256(cbatch_workspace(cb_in.data(), (int)cb_in.size()));
   P->region = r256(solo_bytes);
-  P->solo_off = r256(batch_bytes);
+  P->solo_off = cb_off + cb_bytes;
   P->ws_size = P->solo_off + (size_t)nb * P->region + 256;
   cudaError_t ce;
   if ((ce = cudaMalloc(&P->ws, P->ws_size)) != cudaSuccess) {
@@ -190,6 +227,17 @@ static int create(const aat_problem_t *probs, int count, Plan **out) {
       return report_error(AAT_ECUDA, cudaGetErrorString(ce));
     }
     P->ev.push_back(ev);
+  }
+  // the complex batch
+  if (!P->cbatched.empty()) {
+    if ((ce = cudaStreamCreateWithFlags(&P->cb_st, cudaStreamNonBlocking)) != cudaSuccess ||
+        (ce = cudaEventCreateWithFlags(&P->cb_ev[0], cudaEventDisableTiming)) != cudaSuccess ||
+        (ce = cudaEventCreateWithFlags(&P->cb_ev[1], cudaEventDisableTiming)) != cudaSuccess ||
+        (ce = cbatch_build(cb_in.data(), (int)cb_in.size(), (char *)P->ws + cb_off, &P->cb)) !=
+            cudaSuccess) {
+      destroy(P);
+      return report_error(AAT_ECUDA, cudaGetErrorString(ce));
+    }
   }
   // the batch: split descriptors and leaf tables
   if (!P->batched.empty()) {
@@ -296,7 +344,7 @@ AAT_API int aat_plan_execute(aat_plan_t *plan, void *stream) {
 
 AAT_API int aat_plan_info(const aat_plan_t *plan, int *batched, int *solo, size_t *workspace) {
   if (!plan || !plan->p) return report_error(AAT_EINVAL, "null plan");
-  if (batched) *batched = (int)plan->p->batched.size();
+  if (batched) *batched = (int)(plan->p->batched.size() + plan->p->cbatched.size());
   if (solo) *solo = (int)plan->p->solo.size();
   if (workspace) *workspace = plan->p->ws_size;
   return AAT_OK;

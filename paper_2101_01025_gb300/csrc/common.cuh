@@ -402,6 +402,27 @@ int modp_run(const int32_t *A, int64_t n, int64_t k, int64_t lda, uint32_t p, in
 int complex_run(int method, const void *A, int64_t n, int64_t k, int64_t lda, void *C,
                 int64_t ldc, uint32_t flags, cudaStream_t st, char *ws, bool dry, size_t *need);
 
+// A batch of complex products by Algorithm 2 (2M, A A^H when herm, A A^T
+// otherwise) as four launches: one split of every problem, ONE persistent
+// FP32 leaf launch over the H and G tiles of all problems, one combine and
+// one Hermitian diagonal.  The workspace (cbatch_workspace bytes, caller's)
+// holds every problem's planes and products.
+struct CBInput {
+  const float2 *A;
+  int64_t lda, n, k;
+  float2 *C;
+  int64_t ldc;
+  uint32_t flags;  // precision (AAT_C_*)
+  int herm;
+};
+struct CBatch {
+  void *impl = nullptr;
+};
+size_t cbatch_workspace(const CBInput *in, int count);
+cudaError_t cbatch_build(const CBInput *in, int count, char *ws, CBatch *out);
+cudaError_t cbatch_launch(const CBatch &b, cudaStream_t st);
+void cbatch_free(CBatch *b);
+
 // Host helpers shared with the allocation-free entry point (aat_api.cu).
 DigitSpec digits_for_prime(uint32_t p);
 int check_prime_arg(uint32_t p);

@@ -54,6 +54,14 @@ struct FGroup {
   int32_t neg;     // subtract this product
 };
 
+// One product of a batched launch (its maps live in global memory).
+struct alignas(64) FJobDesc {
+  CUtensorMap tmx, tmy;
+  float *out;
+  int64_t ldo, M, N;
+  int lower, kblocks, goff, ng;  // its groups: gtab[goff .. goff + ng)
+};
+
 struct FParams {
   CUtensorMap tmx;  // 3D {K, rows, plane}, box {64, 128, 1}
   CUtensorMap tmy;  // 3D {K, rows, plane}, box {64, 256, 1} (CTA pair: {64, 128, 1})
@@ -67,7 +75,57 @@ struct FParams {
   int ntiles;
   int lower;
   int32_t *status;
+  // batched launches: tiles are (job, I, J) and every job carries its own
+  // maps, groups, K and output
+  const FJobDesc *jobs;
+  const int4 *btiles;
+  const FGroup *gtab;
 };
+
+// What one tile of a launch works on.
+struct FJob {
+  const CUtensorMap *tmx, *tmy;
+  const FGroup *g;
+  int ng, kblocks, lower, I, J;
+  float *out;
+  int64_t ldo, M, N;
+};
+
+template <bool BATCH>
+__device__ __forceinline__ FJob fjob(const FParams &P, int t) {
+  FJob j;
+  if constexpr (BATCH) {
+    const int4 tl = P.btiles[t];
+    const FJobDesc &d = P.jobs[tl.x];
+    j.tmx = &d.tmx;
+    j.tmy = &d.tmy;
+    j.g = P.gtab + d.goff;
+    j.ng = d.ng;
+    j.kblocks = d.kblocks;
+    j.lower = d.lower;
+    j.out = d.out;
+    j.ldo = d.ldo;
+    j.M = d.M;
+    j.N = d.N;
+    j.I = tl.y;
+    j.J = tl.z;
+  } else {
+    const int2 tl = P.tiles[t];
+    j.tmx = &P.tmx;
+    j.tmy = &P.tmy;
+    j.g = P.g;
+    j.ng = P.ng;
+    j.kblocks = P.kblocks;
+    j.lower = P.lower;
+    j.out = P.out;
+    j.ldo = P.ldo;
+    j.M = P.M;
+    j.N = P.N;
+    j.I = tl.x;
+    j.J = tl.y;
+  }
+  return j;
+}
 
 // out = sum_g (+-) X_{xp(g)} Y_{yp(g)}^T in FP32, one TMEM accumulation per
 // output tile.  Same CTA organisation as the modular leaf kernel, in the
@@ -85,13 +143,16 @@ struct FShape {
   static constexpr int A_BYTES = BM * BK * 2;
   static constexpr int B_BYTES = YROWS * BK * 2;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-  static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + 256;
+  // + 256 bytes of barriers + a per-warp 32 x 17 FP32 staging area of the
+  // output stores
+  static constexpr size_t XS_BYTES = (size_t)EPI_WARPS * 32 * 17 * 4;
+  static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + 256 + XS_BYTES;
   // kind::f16, FP32 accumulator, BF16 A and B, K-major, N = 256, M = TM
   static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) |
                                     ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 };
 
-template <bool PAIR>
+template <bool PAIR, bool BATCH>
 __global__ void __launch_bounds__(THREADS, 1) leaf_f32_kernel(const __grid_constant__ FParams P) {
   using S = FShape<PAIR>;
   constexpr int STAGES = S::STAGES;
@@ -159,12 +220,12 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_f32_kernel(const __grid_const
       bool ok = true;
       const uint32_t full0 = PAIR ? map_to_rank(FULL(0), 0) : FULL(0);
       for (int t = (int)unit0; t < P.ntiles && ok; t += (int)nunits) {
-        const int2 tile = P.tiles[t];
-        const int rowx = tile.x * S::TM + (int)rank * BM;
-        const int rowy = tile.y * BN + (int)rank * S::YROWS;
-        for (int gi = 0; gi < P.ng && ok; ++gi) {
-          const FGroup g = P.g[gi];
-          for (int kb = 0; kb < P.kblocks; ++kb) {
+        const FJob jb = fjob<BATCH>(P, t);
+        const int rowx = jb.I * S::TM + (int)rank * BM;
+        const int rowy = jb.J * BN + (int)rank * S::YROWS;
+        for (int gi = 0; gi < jb.ng && ok; ++gi) {
+          const FGroup g = jb.g[gi];
+          for (int kb = 0; kb < jb.kblocks; ++kb) {
             if (!wait_bounded<PAIR>(EMPTY(stage), ph ^ 1u, abort_flag, P.status)) {
               ok = false;
               break;
@@ -173,12 +234,12 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_f32_kernel(const __grid_const
             const uint32_t fb = full0 + 8u * (uint32_t)stage;
             if constexpr (PAIR) {
               if (leader) mbar_expect_tx(FULL(stage), (uint32_t)(2 * S::STAGE_BYTES));
-              tma_load_3d_pair(sa, &P.tmx, fb, kb * BK, rowx, g.xp);
-              tma_load_3d_pair(sa + S::A_BYTES, &P.tmy, fb, kb * BK, rowy, g.yp);
+              tma_load_3d_pair(sa, jb.tmx, fb, kb * BK, rowx, g.xp);
+              tma_load_3d_pair(sa + S::A_BYTES, jb.tmy, fb, kb * BK, rowy, g.yp);
             } else {
               mbar_expect_tx(FULL(stage), (uint32_t)S::STAGE_BYTES);
-              tma_load_3d(sa, &P.tmx, fb, kb * BK, rowx, g.xp);
-              tma_load_3d(sa + S::A_BYTES, &P.tmy, fb, kb * BK, rowy, g.yp);
+              tma_load_3d(sa, jb.tmx, fb, kb * BK, rowx, g.xp);
+              tma_load_3d(sa + S::A_BYTES, jb.tmy, fb, kb * BK, rowy, g.yp);
             }
             ++issued;
             if (++stage == STAGES) {
@@ -214,11 +275,12 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_f32_kernel(const __grid_const
       uint32_t ph = 0, chunk = 0;
       bool ok = true;
       for (int t = (int)unit0; t < P.ntiles && ok; t += (int)nunits) {
+        const FJob jb = fjob<BATCH>(P, t);
         int inchunk = 0;
         uint32_t dt = 0;
-        for (int gi = 0; gi < P.ng && ok; ++gi) {
-          const uint32_t idesc = S::IDESC | (P.g[gi].neg ? NEG_A : 0u);
-          for (int kb = 0; kb < P.kblocks; ++kb) {
+        for (int gi = 0; gi < jb.ng && ok; ++gi) {
+          const uint32_t idesc = S::IDESC | (jb.g[gi].neg ? NEG_A : 0u);
+          for (int kb = 0; kb < jb.kblocks; ++kb) {
             if (inchunk == 0) {
               const uint32_t buf = chunk & 1u, use = chunk >> 1;
               if (!wait_bounded<PAIR>(AEMPTY(buf), (use & 1u) ^ 1u, abort_flag, P.status)) {
@@ -251,7 +313,7 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_f32_kernel(const __grid_const
               stage = 0;
               ph ^= 1u;
             }
-            const bool last = (gi == P.ng - 1) && (kb == P.kblocks - 1);
+            const bool last = (gi == jb.ng - 1) && (kb == jb.kblocks - 1);
             if (++inchunk == P.kchunk || last) {
               if constexpr (PAIR)
                 tc_commit_pair(AFULL(chunk & 1u), 3);
@@ -276,13 +338,14 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_f32_kernel(const __grid_const
     const int quarter = warp & 3;
     const int chalf = e >> 2;
     const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
-    const int total_kb = P.ng * P.kblocks;
-    const int nchunks = (total_kb + P.kchunk - 1) / P.kchunk;
+
     const uint32_t aempty0 = PAIR ? map_to_rank(AEMPTY(0), 0) : AEMPTY(0);
+    float *xs = reinterpret_cast<float *>(smem + (size_t)STAGES * S::STAGE_BYTES + 256) + e * 32 * 17;
     uint32_t chunk = 0;
     bool ok = true;
     for (int t = (int)unit0; t < P.ntiles && ok; t += (int)nunits) {
-      const int2 tile = P.tiles[t];
+      const FJob jb = fjob<BATCH>(P, t);
+      const int nchunks = (jb.ng * jb.kblocks + P.kchunk - 1) / P.kchunk;
       float acc[128];
 #pragma unroll
       for (int i = 0; i < 128; ++i) acc[i] = 0.0f;
@@ -313,25 +376,49 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_f32_kernel(const __grid_const
         ++chunk;
       }
       if (!ok) break;
-      const int64_t row = (int64_t)tile.x * S::TM + (int64_t)rank * BM + quarter * 32 + lane;
-      const int64_t col0 = (int64_t)tile.y * BN + chalf * 128;
-      int64_t lim = P.N - col0;
-      if (P.lower) lim = min(lim, row - col0 + 1);
-      if (row < P.M && lim > 0) {
-        float *orow = P.out + row * P.ldo + col0;
-        const bool vec = ((reinterpret_cast<uintptr_t>(orow) & 15) == 0);
+      const int64_t row = (int64_t)jb.I * S::TM + (int64_t)rank * BM + quarter * 32 + lane;
+      const int64_t col0 = (int64_t)jb.J * BN + chalf * 128;
+      // rows 16-byte aligned: each thread stores its row segment with
+      // 16-byte stores
+      if (((reinterpret_cast<uintptr_t>(jb.out) | (uintptr_t)(jb.ldo * 4)) & 15) == 0) {
+        int64_t lim = jb.N - col0;
+        if (jb.lower) lim = min(lim, row - col0 + 1);
+        if (row < jb.M && lim > 0) {
+          float *orow = jb.out + row * jb.ldo + col0;
 #pragma unroll
-        for (int q = 0; q < 32; ++q) {
-          const int cc = 4 * q;
-          if (vec && cc + 4 <= lim) {
-            *reinterpret_cast<float4 *>(orow + cc) =
-                make_float4(acc[cc], acc[cc + 1], acc[cc + 2], acc[cc + 3]);
-          } else {
+          for (int q = 0; q < 32; ++q) {
+            const int cc = 4 * q;
+            if (cc + 4 <= lim) {
+              *reinterpret_cast<float4 *>(orow + cc) =
+                  make_float4(acc[cc], acc[cc + 1], acc[cc + 2], acc[cc + 3]);
+            } else {
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-              if (cc + j < lim) orow[cc + j] = acc[cc + j];
+              for (int j = 0; j < 4; ++j)
+                if (cc + j < lim) orow[cc + j] = acc[cc + j];
+            }
+            asm volatile("" ::: "memory");
           }
-          asm volatile("" ::: "memory");
+        }
+        continue;
+      }
+      // otherwise coalesced through shared memory: 16 columns of the warp's
+      // 32 rows at a time, two contiguous 64-byte row segments per store
+      const int64_t row0 = row - lane;
+      const int mlim = (int)max((int64_t)0, min((int64_t)32, jb.M - row0));
+      const int nlim = (int)max((int64_t)0, min((int64_t)128, jb.N - col0));
+      const int dl = jb.lower ? (int)max((int64_t)-256, min((int64_t)256, row0 - col0)) : 1 << 20;
+      float *const base = jb.out + row0 * jb.ldo + col0;
+      const int64_t ldo = jb.ldo;
+#pragma unroll
+      for (int cb = 0; cb < 128; cb += 16) {
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) xs[lane * 17 + j] = acc[cb + j];
+        __syncwarp();
+#pragma unroll 1
+        for (int i = 0; i < 16; ++i) {
+          const int rr = 2 * i + (lane >> 4), cl = cb + (lane & 15);
+          if (rr < mlim && cl < nlim && cl - rr <= dl) base[(int64_t)rr * ldo + cl] = xs[rr * 17 + (lane & 15)];
         }
       }
     }
@@ -380,14 +467,11 @@ struct CSplitOut {
 // grid-stride loop over column quads): the pieces of 4 values go out as one
 // 8-byte store per plane (kstride is a multiple of 8); a ragged last quad
 // stores element by element.
-__global__ void csplit_kernel(const float2 *__restrict__ A, int64_t lda, int64_t rows, int64_t cols,
-                              int np, CSplitOut o) {
-  const int64_t cq = (cols + 3) / 4;
+__device__ __forceinline__ void csplit_quad(const float2 *__restrict__ a_row, int64_t r,
+                                            int64_t q4, int64_t cols, int np, const CSplitOut &o) {
   const Planes *outs[4] = {&o.re, &o.im, &o.s, &o.d};
-  for (int64_t r = blockIdx.y; r < rows; r += gridDim.y) {
-    const float2 *a_row = A + r * lda;
-    for (int64_t q4 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q4 < cq;
-         q4 += (int64_t)gridDim.x * blockDim.x) {
+  {
+    {
       const int64_t c0 = 4 * q4;
       const int nv = (int)min((int64_t)4, cols - c0);
       float2 a[4];
@@ -425,16 +509,68 @@ __global__ void csplit_kernel(const float2 *__restrict__ A, int64_t lda, int64_t
   }
 }
 
+__global__ void csplit_kernel(const float2 *__restrict__ A, int64_t lda, int64_t rows, int64_t cols,
+                              int np, CSplitOut o) {
+  const int64_t cq = (cols + 3) / 4;
+  for (int64_t r = blockIdx.y; r < rows; r += gridDim.y)
+    for (int64_t q4 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q4 < cq;
+         q4 += (int64_t)gridDim.x * blockDim.x)
+      csplit_quad(A + r * lda, r, q4, cols, np, o);
+}
+
+// ------------------------------------------------ batched A A^H / A A^T (2M)
+
+// One problem of the batched 2M sequence: its input, pieces, plane sets,
+// the products H and G and the output, and the first block it owns in each
+// of the batched element-wise launches.
+struct CBProb {
+  const float2 *A;
+  int64_t lda, n, k;
+  int np, herm;
+  CSplitOut ox, oy;
+  float *H, *G;
+  float2 *C;
+  int64_t ldc;
+  int split_first, comb_first, diag_first;
+};
+
+constexpr int kCSplitRows = 8, kDiagRows = 8;
+
+__device__ __forceinline__ int cb_find(const CBProb *pr, int count, int b, int which) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    const int f = which == 0 ? pr[mid].split_first : which == 1 ? pr[mid].comb_first
+                                                                : pr[mid].diag_first;
+    if (f <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// both plane sets of kCSplitRows rows of one problem per block
+__global__ void csplit_batch_kernel(const CBProb *__restrict__ pr, int count) {
+  const CBProb &q = pr[cb_find(pr, count, blockIdx.x, 0)];
+  const int64_t r0 = (int64_t)(blockIdx.x - q.split_first) * kCSplitRows;
+  const int64_t r1 = min(r0 + kCSplitRows, q.n);
+  const int64_t cq = (q.k + 3) / 4;
+  for (int64_t r = r0; r < r1; ++r)
+    for (int64_t q4 = threadIdx.x; q4 < cq; q4 += blockDim.x) {
+      csplit_quad(q.A + r * q.lda, r, q4, q.k, q.np, q.ox);
+      csplit_quad(q.A + r * q.lda, r, q4, q.k, q.np, q.oy);
+    }
+}
+
 // The combination of Algorithm 2 for one tile pair {(I, J), (J, I)}, I >= J,
 // writing Low(C) (complex64):  herm: Re = G - H - H^T, Im = H^T - H;
 // otherwise Re = G + H - H^T, Im = H + H^T.
 constexpr int T = 32;
-__global__ void combine2m_kernel(const float *__restrict__ G, const float *__restrict__ H,
-                                 int64_t ldw, int64_t n, float2 *C, int64_t ldc, int herm) {
-  __shared__ float hij[T][T + 1];
-  __shared__ float hji[T][T + 1];
+__device__ __forceinline__ void combine2m_tile(const float *__restrict__ G,
+                                               const float *__restrict__ H, int64_t ldw,
+                                               int64_t n, float2 *C, int64_t ldc, int herm,
+                                               int64_t pid, float (&hij)[T][T + 1],
+                                               float (&hji)[T][T + 1]) {
   const int64_t ntiles = (n + T - 1) / T;
-  int64_t pid = blockIdx.x;
   int64_t I = (int64_t)((sqrt(8.0 * (double)pid + 1.0) - 1.0) * 0.5);
   while (I * (I + 1) / 2 > pid) --I;
   while ((I + 1) * (I + 2) / 2 <= pid) ++I;
@@ -466,10 +602,24 @@ __global__ void combine2m_kernel(const float *__restrict__ G, const float *__res
   }
 }
 
-// C[i,i] = sum_l |a_il|^2 in FP64 (A A^H: real and >= 0), one warp per row.
-__global__ void herm_diag_kernel(const float2 *__restrict__ A, int64_t lda, int64_t n, int64_t k,
-                                 float2 *C, int64_t ldc) {
-  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+__global__ void combine2m_kernel(const float *__restrict__ G, const float *__restrict__ H,
+                                 int64_t ldw, int64_t n, float2 *C, int64_t ldc, int herm) {
+  __shared__ float hij[T][T + 1];
+  __shared__ float hji[T][T + 1];
+  combine2m_tile(G, H, ldw, n, C, ldc, herm, blockIdx.x, hij, hji);
+}
+
+__global__ void combine2m_batch_kernel(const CBProb *__restrict__ pr, int count) {
+  __shared__ float hij[T][T + 1];
+  __shared__ float hji[T][T + 1];
+  const CBProb &q = pr[cb_find(pr, count, blockIdx.x, 1)];
+  combine2m_tile(q.G, q.H, q.n, q.n, q.C, q.ldc, q.herm, (int64_t)(blockIdx.x - q.comb_first),
+                 hij, hji);
+}
+
+__device__ __forceinline__ void herm_diag_row(const float2 *__restrict__ A, int64_t lda,
+                                              int64_t n, int64_t k, float2 *C, int64_t ldc,
+                                              int64_t row) {
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
   // four independent FP64 sums per lane (the FP64 pipe is narrow: keep
@@ -491,6 +641,18 @@ __global__ void herm_diag_kernel(const float2 *__restrict__ A, int64_t lda, int6
   double s = (s0 + s1) + (s2 + s3);
   for (int off = 16; off; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
   if (lane == 0) C[row * ldc + row] = make_float2((float)s, 0.0f);
+}
+
+__global__ void herm_diag_kernel(const float2 *__restrict__ A, int64_t lda, int64_t n, int64_t k,
+                                 float2 *C, int64_t ldc) {
+  herm_diag_row(A, lda, n, k, C, ldc, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32);
+}
+
+// one warp per row, kDiagRows rows of one Hermitian problem per block
+__global__ void herm_diag_batch_kernel(const CBProb *__restrict__ pr, int count) {
+  const CBProb &q = pr[cb_find(pr, count, blockIdx.x, 2)];
+  const int64_t row = (int64_t)(blockIdx.x - q.diag_first) * kDiagRows + threadIdx.x / 32;
+  herm_diag_row(q.A, q.lda, q.n, q.k, q.C, q.ldc, row);
 }
 
 // ------------------------------------------------------------------ host
@@ -568,7 +730,7 @@ int pair_units_c(int dev) {
   auto it = g_pair_units_c.find(dev);
   if (it != g_pair_units_c.end()) return it->second;
   int units = 0;
-  if (cudaFuncSetAttribute(leaf_f32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (cudaFuncSetAttribute(leaf_f32_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)FShape<true>::SMEM) == cudaSuccess) {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
@@ -581,7 +743,7 @@ int pair_units_c(int dev) {
     cfg.dynamicSmemBytes = FShape<true>::SMEM;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (cudaOccupancyMaxActiveClusters(&units, leaf_f32_kernel<true>, &cfg) != cudaSuccess)
+    if (cudaOccupancyMaxActiveClusters(&units, leaf_f32_kernel<true, false>, &cfg) != cudaSuccess)
       units = 0;
   }
   cudaGetLastError();
@@ -677,7 +839,7 @@ static cudaError_t launch_leaf_f32(const std::vector<FTerm> &terms, int np, int6
   P->tiles = tiles;
   P->ntiles = nt;
   if (!g_attr_c[dev]) {
-    if ((e = cudaFuncSetAttribute(leaf_f32_kernel<false>,
+    if ((e = cudaFuncSetAttribute(leaf_f32_kernel<false, false>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)FShape<false>::SMEM)) != cudaSuccess) {
       delete P;
@@ -703,13 +865,13 @@ static cudaError_t launch_leaf_f32(const std::vector<FTerm> &terms, int np, int6
       cfg.stream = st;
       cfg.attrs = attr;
       cfg.numAttrs = 1;
-      e = cudaLaunchKernelEx(&cfg, leaf_f32_kernel<true>, *P);
+      e = cudaLaunchKernelEx(&cfg, leaf_f32_kernel<true, false>, *P);
       if (e != cudaSuccess) {
         delete P;
         return e;
       }
     } else {
-      leaf_f32_kernel<false><<<std::max(1, std::min(nt, sms)), THREADS, FShape<false>::SMEM, st>>>(*P);
+      leaf_f32_kernel<false, false><<<std::max(1, std::min(nt, sms)), THREADS, FShape<false>::SMEM, st>>>(*P);
     }
   }
   delete P;
@@ -1093,6 +1255,219 @@ static int complex_levels(int64_t n, int64_t k, uint32_t flags) {
   int levels = 0;  // one level pays off once the leaves stay large
   while (levels < 4 && (n >> (levels + 1)) >= 4096 && (k >> (levels + 1)) >= 2048) ++levels;
   return levels;
+}
+
+// ----------------------------------------------- batched A A^H (2M), host
+
+struct CBatchImpl {
+  CBProb *probs = nullptr;
+  FJobDesc *jobs = nullptr;
+  FGroup *gtab = nullptr;
+  int4 *tiles = nullptr;
+  int count = 0, ntiles = 0;
+  int split_blocks = 0, comb_blocks = 0, diag_blocks = 0;
+  double leaf_work = 0.0, split_bytes = 0.0, comb_bytes = 0.0, diag_bytes = 0.0;
+};
+
+static size_t r256c(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static size_t cb_planes_bytes(int64_t n, int64_t k, int np) {
+  return r256c((size_t)2 * np * n * ((k + 7) / 8 * 8) * 2);
+}
+
+size_t cbatch_workspace(const CBInput *in, int count) {
+  size_t total = 0;
+  for (int i = 0; i < count; ++i) {
+    const int np = pieces_for(in[i].flags);
+    total += 2 * cb_planes_bytes(in[i].n, in[i].k, np) + 2 * r256c((size_t)in[i].n * in[i].n * 4);
+  }
+  return total;
+}
+
+void cbatch_free(CBatch *b) {
+  CBatchImpl *L = (CBatchImpl *)b->impl;
+  if (!L) return;
+  if (L->probs) cudaFree(L->probs);
+  if (L->jobs) cudaFree(L->jobs);
+  if (L->gtab) cudaFree(L->gtab);
+  if (L->tiles) cudaFree(L->tiles);
+  delete L;
+  b->impl = nullptr;
+}
+
+cudaError_t cbatch_build(const CBInput *in, int count, char *ws, CBatch *out) {
+  std::lock_guard<std::mutex> lock(g_mu_c);
+  std::vector<CBProb> probs(count);
+  std::vector<FJobDesc> jobs;
+  std::vector<FGroup> gtab;
+  struct T4 { int4 t; double cost; };
+  std::vector<T4> tiles;
+  CBatchImpl *L = new CBatchImpl;
+  L->count = count;
+  char *w = ws;
+  int sb = 0, cbk = 0, db = 0;
+  for (int i = 0; i < count; ++i) {
+    const CBInput &q = in[i];
+    CBProb &b = probs[i];
+    std::memset(&b, 0, sizeof(b));
+    const int np = pieces_for(q.flags);
+    Planes X, Y;
+    std::memset(&X, 0, sizeof(X));
+    X.rows = q.n;
+    X.cols = q.k;
+    X.kstride = (q.k + 7) / 8 * 8;
+    X.L = X.nbase = 2 * np;
+    Y = X;
+    X.ptr = (__nv_bfloat16 *)w;
+    w += cb_planes_bytes(q.n, q.k, np);
+    Y.ptr = (__nv_bfloat16 *)w;
+    w += cb_planes_bytes(q.n, q.k, np);
+    b.H = (float *)w;
+    w += r256c((size_t)q.n * q.n * 4);
+    b.G = (float *)w;
+    w += r256c((size_t)q.n * q.n * 4);
+    b.A = q.A;
+    b.lda = q.lda;
+    b.n = q.n;
+    b.k = q.k;
+    b.np = np;
+    b.herm = q.herm;
+    b.ox.re = subset(X, 0, np);
+    b.ox.s = subset(X, 1, np);
+    b.oy.im = subset(Y, 0, np);
+    if (q.herm)
+      b.oy.s = subset(Y, 1, np);
+    else
+      b.oy.d = subset(Y, 1, np);
+    b.C = q.C;
+    b.ldc = q.ldc;
+    b.split_first = sb;
+    sb += (int)((q.n + kCSplitRows - 1) / kCSplitRows);
+    const int64_t nt = (q.n + T - 1) / T;
+    b.comb_first = cbk;
+    cbk += (int)(nt * (nt + 1) / 2);
+    b.diag_first = db;
+    if (q.herm) db += (int)((q.n + kDiagRows - 1) / kDiagRows);
+    L->split_bytes += (double)q.n * q.k * (8.0 + 2.0 * np * 4);
+    L->comb_bytes += (double)q.n * q.n * (4.0 * 1.5 + 8.0 * 0.5);
+    if (q.herm) L->diag_bytes += (double)q.n * q.k * 8.0;
+    // two jobs: H = Ar Ai^T (all entries) from plane sets 0, G (lower) from sets 1
+    int pairs[6][2];
+    const int npairs = piece_pairs(np, pairs);
+    for (int jb = 0; jb < 2; ++jb) {
+      FJobDesc d;
+      std::memset(&d, 0, sizeof(d));
+      cudaError_t e;
+      if ((e = encode_c(&d.tmx, X, BM)) != cudaSuccess ||
+          (e = encode_c(&d.tmy, Y, FShape<false>::YROWS)) != cudaSuccess) {
+        CBatch tmp;
+        tmp.impl = L;
+        cbatch_free(&tmp);
+        return e;
+      }
+      d.out = jb == 0 ? b.H : b.G;
+      d.ldo = q.n;
+      d.M = d.N = q.n;
+      d.lower = jb;
+      d.kblocks = (int)((q.k + BK - 1) / BK);
+      d.goff = (int)gtab.size();
+      d.ng = npairs;
+      for (int qq = 0; qq < npairs; ++qq) {
+        FGroup g;
+        g.xp = (int16_t)(jb * np + pairs[qq][0]);
+        g.yp = (int16_t)(jb * np + pairs[qq][1]);
+        g.neg = 0;
+        gtab.push_back(g);
+      }
+      const int jobi = (int)jobs.size();
+      jobs.push_back(d);
+      const double cost = (double)d.kblocks * npairs;
+      const int64_t TI = (q.n + BM - 1) / BM, TJ = (q.n + BN - 1) / BN;
+      for (int64_t I = 0; I < TI; ++I)
+        for (int64_t J = 0; J < TJ; ++J) {
+          if (jb == 1 && J * BN > I * BM + BM - 1) continue;
+          tiles.push_back({make_int4(jobi, (int)I, (int)J, 0), cost});
+        }
+      const double macs = jb == 1 ? 0.5 * (double)q.n * (q.n + 1) * q.k : (double)q.n * q.n * q.k;
+      L->leaf_work += 2.0 * npairs * macs;
+    }
+  }
+  std::stable_sort(tiles.begin(), tiles.end(),
+                   [](const T4 &u, const T4 &v) { return u.cost > v.cost; });
+  std::vector<int4> tl(tiles.size());
+  for (size_t i = 0; i < tiles.size(); ++i) tl[i] = tiles[i].t;
+  L->ntiles = (int)tl.size();
+  L->split_blocks = sb;
+  L->comb_blocks = cbk;
+  L->diag_blocks = db;
+  cudaError_t e;
+  if ((e = cudaMalloc(&L->probs, sizeof(CBProb) * std::max(count, 1))) != cudaSuccess ||
+      (e = cudaMalloc(&L->jobs, sizeof(FJobDesc) * std::max<size_t>(jobs.size(), 1))) != cudaSuccess ||
+      (e = cudaMalloc(&L->gtab, sizeof(FGroup) * std::max<size_t>(gtab.size(), 1))) != cudaSuccess ||
+      (e = cudaMalloc(&L->tiles, sizeof(int4) * std::max<size_t>(tl.size(), 1))) != cudaSuccess ||
+      (e = cudaMemcpy(L->probs, probs.data(), sizeof(CBProb) * count, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(L->jobs, jobs.data(), sizeof(FJobDesc) * jobs.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(L->gtab, gtab.data(), sizeof(FGroup) * gtab.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (tl.size() && (e = cudaMemcpy(L->tiles, tl.data(), sizeof(int4) * tl.size(), cudaMemcpyHostToDevice)) != cudaSuccess)) {
+    CBatch tmp;
+    tmp.impl = L;
+    cbatch_free(&tmp);
+    return e;
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if ((e = cudaFuncSetAttribute(leaf_f32_kernel<false, true>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)FShape<false>::SMEM)) != cudaSuccess) {
+    CBatch tmp;
+    tmp.impl = L;
+    cbatch_free(&tmp);
+    return e;
+  }
+  out->impl = L;
+  return cudaSuccess;
+}
+
+cudaError_t cbatch_launch(const CBatch &b, cudaStream_t st) {
+  const CBatchImpl *L = (const CBatchImpl *)b.impl;
+  if (!L || L->count == 0) return cudaSuccess;
+  cudaError_t e;
+  if (L->split_blocks > 0) {
+    ProfScope prof(AAT_K_SPLIT, st, L->split_bytes);
+    csplit_batch_kernel<<<(unsigned)L->split_blocks, 256, 0, st>>>(L->probs, L->count);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (L->ntiles > 0) {
+    FParams *P = new FParams;
+    std::memset(P, 0, sizeof(FParams));
+    P->kchunk = 8;  // as launch_leaf_f32
+    P->ntiles = L->ntiles;
+    P->status = device_status_ptr();
+    P->jobs = L->jobs;
+    P->btiles = L->tiles;
+    P->gtab = L->gtab;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    {
+      ProfScope prof(AAT_K_LEAF_F32, st, L->leaf_work);
+      leaf_f32_kernel<false, true><<<std::max(1, std::min(L->ntiles, sms)), THREADS,
+                                     FShape<false>::SMEM, st>>>(*P);
+    }
+    delete P;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (L->comb_blocks > 0) {
+    ProfScope prof(AAT_K_POSTADD, st, L->comb_bytes);
+    combine2m_batch_kernel<<<(unsigned)L->comb_blocks, T * 8, 0, st>>>(L->probs, L->count);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (L->diag_blocks > 0) {
+    ProfScope prof(AAT_K_COPY, st, L->diag_bytes);
+    herm_diag_batch_kernel<<<(unsigned)L->diag_blocks, 256, 0, st>>>(L->probs, L->count);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 int complex_run(int method, const void *A, int64_t n, int64_t k, int64_t lda, void *C,

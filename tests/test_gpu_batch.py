@@ -69,7 +69,9 @@ def test_plan_mixed_batch_twice(lib):
         hosts.append((kind, Z, Zd, Cz, None))
     plan = lib.Plan(problems)
     info = plan.info()
-    assert info["batched"] == 30 and info["solo"] == 4
+    # 30 depth-0 F_p problems and the two A A^H ones are batched; the
+    # recursive product and the complex A A^T run on their own
+    assert info["batched"] == 32 and info["solo"] == 2
     for rnd in range(2):
         if rnd == 1:   # new inputs: the plan must read them
             for idx, (kind, A, Ad, Cd, p) in enumerate(hosts):
@@ -124,12 +126,43 @@ def test_plan_config5_batch(lib):
     for A, Cd in hosts:
         _fp_check(A, Cd.cpu().numpy(), p, full=A.shape[0] * A.shape[0] * A.shape[1] < 2e8)
     rng = np.random.default_rng(3)
-    for Z, Cz in chosts[::4]:
+    for Z, Cz in chosts:
         n = Z.shape[0]
         i = rng.integers(0, n, 200)
         j = rng.integers(0, n, 200)
-        ij = np.stack([np.maximum(i, j), np.minimum(i, j)], 1)
+        d = rng.integers(0, n, 20)   # diagonal entries (the FP64 sums)
+        ij = np.concatenate([np.stack([np.maximum(i, j), np.minimum(i, j)], 1),
+                             np.stack([d, d], 1)])
         ref = oracle.complex_entries(Z.astype(np.complex128), ij, conj=True)
         got = Cz.cpu().numpy()[ij[:, 0], ij[:, 1]]
         assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-5
+    plan.close()
+
+
+@pytest.mark.parametrize("flags", [1 << 16, 2 << 16])
+def test_plan_complex_batch_precisions(lib, flags):
+    """The batched complex path with 2 and 1 BF16 pieces per value, ragged
+    sizes, against the FP64 oracle (the tolerances of the single calls)."""
+    problems, hosts = [], []
+    for q, (n, k) in enumerate([(33, 70), (300, 257), (129, 1000), (700, 64)]):
+        Z = synth.complex_normal(300 + q, (n, k))
+        Zd = torch.from_numpy(Z).cuda()
+        Cz = torch.zeros((n, n), dtype=torch.complex64, device="cuda")
+        problems.append(("aah", Zd, Cz, 0, flags))
+        hosts.append((Z, Cz))
+    plan = lib.Plan(problems)
+    assert plan.info()["batched"] == 4 and plan.info()["solo"] == 0
+    plan.execute()
+    torch.cuda.synchronize()
+    # plain BF16 (1 piece): Re C = G - H - H^T sums the input-rounding errors
+    # of three products of the result's size; with n >> k (700 x 64 here) the
+    # exact FP64 diagonal carries little of the norm and the error reaches
+    # ~3.1e-3, so this shape gets 3.5e-3
+    tol = 1e-4 if flags == 1 << 16 else 3.5e-3
+    for Z, Cz in hosts:
+        ref = oracle.complex_low(Z.astype(np.complex128), conj=True)
+        C = Cz.cpu().numpy()
+        err = np.linalg.norm(np.tril(C - ref)) / np.linalg.norm(np.tril(ref))
+        assert err <= tol, err
+        assert np.all(np.abs(np.diag(C).imag) == 0) and np.all(np.diag(C).real >= 0)
     plan.close()
