@@ -30,6 +30,9 @@ def main(argv=None):
                     help="leaf kind of the F_p cases")
     ap.add_argument("--plain-digits", action="store_true",
                     help="one product per digit pair instead of the pair-sum form")
+    ap.add_argument("--profile", action="store_true",
+                    help="per kernel class: launches, ms per repetition and the rate of "
+                         "its algorithmic work (bytes or FLOPs) over the timed repetitions")
     a = ap.parse_args(argv)
 
     import torch
@@ -67,6 +70,11 @@ def main(argv=None):
     else:
         fn = lambda: aat.aat_gemm_modp(X, X, p, C=C, flags=flags)  # noqa: E731
     times = []
+    if a.profile:
+        fn()
+        torch.cuda.synchronize()
+        from paper_2101_01025_gb300 import _native
+        _native.lib().aat_profile_begin()
     for _ in range(a.reps):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -75,9 +83,28 @@ def main(argv=None):
         e1.record()
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
-    print(json.dumps({"case": a.case, "n": n, "k": k, "p": p, "levels": a.levels,
-                      "plain_digits": a.plain_digits, "prec": a.prec, "leaf": a.leaf,
-                      "ms": times, "status": aat.aat_device_status()}))
+    out = {"case": a.case, "n": n, "k": k, "p": p, "levels": a.levels,
+           "plain_digits": a.plain_digits, "prec": a.prec, "leaf": a.leaf,
+           "ms": times, "status": aat.aat_device_status()}
+    if a.profile:
+        out["kernels"] = profile_end(a.reps)
+    print(json.dumps(out))
+
+
+def profile_end(reps):
+    """Per kernel class over the profiled repetitions: launches and ms per
+    repetition, and GB/s (element-wise classes) or TFLOP/s (leaf classes) of
+    the algorithmic work the library counts for each launch."""
+    from paper_2101_01025_gb300 import _native
+    prof = _native.Profile()
+    _native.check(_native.lib().aat_profile_end(prof))
+    out = {}
+    for name, v in prof.as_dict().items():
+        per_s = v["work"] / max(v["ms"] * 1e-3, 1e-12)
+        leafy = name.startswith("leaf")
+        out[name] = {"launches": v["launches"] / reps, "ms": v["ms"] / reps,
+                     ("tflops" if leafy else "gbs"): per_s / 1e12 if leafy else per_s / 1e9}
+    return out
 
 
 def batch_case(a):

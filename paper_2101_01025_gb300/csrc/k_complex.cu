@@ -22,6 +22,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -475,8 +476,17 @@ __device__ __forceinline__ void csplit_quad(const float2 *__restrict__ a_row, in
       const int64_t c0 = 4 * q4;
       const int nv = (int)min((int64_t)4, cols - c0);
       float2 a[4];
+      if (nv == 4 && (reinterpret_cast<uintptr_t>(a_row) & 15) == 0) {
+        const float4 u0 = reinterpret_cast<const float4 *>(a_row + c0)[0];
+        const float4 u1 = reinterpret_cast<const float4 *>(a_row + c0)[1];
+        a[0] = make_float2(u0.x, u0.y);
+        a[1] = make_float2(u0.z, u0.w);
+        a[2] = make_float2(u1.x, u1.y);
+        a[3] = make_float2(u1.z, u1.w);
+      } else {
 #pragma unroll
-      for (int v = 0; v < 4; ++v) a[v] = v < nv ? a_row[c0 + v] : make_float2(0.f, 0.f);
+        for (int v = 0; v < 4; ++v) a[v] = v < nv ? a_row[c0 + v] : make_float2(0.f, 0.f);
+      }
 #pragma unroll
       for (int w = 0; w < 4; ++w) {
         const Planes &P = *outs[w];
@@ -552,13 +562,15 @@ __device__ __forceinline__ int cb_find(const CBProb *pr, int count, int b, int w
 __global__ void csplit_batch_kernel(const CBProb *__restrict__ pr, int count) {
   const CBProb &q = pr[cb_find(pr, count, blockIdx.x, 0)];
   const int64_t r0 = (int64_t)(blockIdx.x - q.split_first) * kCSplitRows;
-  const int64_t r1 = min(r0 + kCSplitRows, q.n);
+  const int64_t nr = min((int64_t)kCSplitRows, q.n - r0);
   const int64_t cq = (q.k + 3) / 4;
-  for (int64_t r = r0; r < r1; ++r)
-    for (int64_t q4 = threadIdx.x; q4 < cq; q4 += blockDim.x) {
-      csplit_quad(q.A + r * q.lda, r, q4, q.k, q.np, q.ox);
-      csplit_quad(q.A + r * q.lda, r, q4, q.k, q.np, q.oy);
-    }
+  // the block's rows x column quads as one index: every thread has work
+  // when the rows are short
+  for (int64_t t = threadIdx.x; t < nr * cq; t += blockDim.x) {
+    const int64_t r = r0 + t / cq, q4 = t - (t / cq) * cq;
+    csplit_quad(q.A + r * q.lda, r, q4, q.k, q.np, q.ox);
+    csplit_quad(q.A + r * q.lda, r, q4, q.k, q.np, q.oy);
+  }
 }
 
 // The combination of Algorithm 2 for one tile pair {(I, J), (J, I)}, I >= J,
@@ -617,28 +629,59 @@ __global__ void combine2m_batch_kernel(const CBProb *__restrict__ pr, int count)
                  hij, hji);
 }
 
+// x·x added to the unevaluated float pair hi + lo without rounding error:
+// the product by its FMA residual (x·x = p + e exactly) and the sum by
+// Knuth's TwoSum (hi + p = s + err exactly).  The _rn intrinsics keep the
+// compiler from contracting any of these steps into an FMA.
+__device__ __forceinline__ void sq_acc(float x, float &hi, float &lo) {
+  const float p = __fmul_rn(x, x);
+  const float e = fmaf(x, x, -p);
+  const float s = __fadd_rn(hi, p);
+  const float bp = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(err, e));
+}
+
+// Re C[row][row] = Σ_l |a_l|², one warp per row.  Each lane sums its
+// columns' squares as a float pair (about 48 significant bits: the only
+// rounding is in lo, whose terms are each below ulp(hi)), two pairs per lane
+// for the real and imaginary parts so the two dependency chains overlap;
+// the lanes' pairs are added in FP64.  This part's FP64 pipe is a small
+// fraction of its FP32 pipe: an FP64 multiply-add per square (and two
+// conversions) held the kernel far below the memory rate.
 __device__ __forceinline__ void herm_diag_row(const float2 *__restrict__ A, int64_t lda,
                                               int64_t n, int64_t k, float2 *C, int64_t ldc,
                                               int64_t row) {
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
-  // four independent FP64 sums per lane (the FP64 pipe is narrow: keep
-  // several fused multiply-adds in flight)
   const float2 *a_row = A + row * lda;
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-  int64_t l = lane;
-  for (; l + 96 < k; l += 128) {
-    const float2 a0 = a_row[l], a1 = a_row[l + 32], a2 = a_row[l + 64], a3 = a_row[l + 96];
-    s0 = fma((double)a0.x, (double)a0.x, fma((double)a0.y, (double)a0.y, s0));
-    s1 = fma((double)a1.x, (double)a1.x, fma((double)a1.y, (double)a1.y, s1));
-    s2 = fma((double)a2.x, (double)a2.x, fma((double)a2.y, (double)a2.y, s2));
-    s3 = fma((double)a3.x, (double)a3.x, fma((double)a3.y, (double)a3.y, s3));
+  float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+  int64_t l = 0;
+  if ((reinterpret_cast<uintptr_t>(a_row) & 15) == 0) {
+    // two complex values per lane per 16-byte load, four loads in flight
+    const float4 *a4 = reinterpret_cast<const float4 *>(a_row);
+    const int64_t k2 = k / 2;
+    int64_t q = lane;
+    for (; q + 96 < k2; q += 128) {
+      const float4 v0 = a4[q], v1 = a4[q + 32], v2 = a4[q + 64], v3 = a4[q + 96];
+      sq_acc(v0.x, h0, l0); sq_acc(v0.y, h1, l1); sq_acc(v0.z, h0, l0); sq_acc(v0.w, h1, l1);
+      sq_acc(v1.x, h0, l0); sq_acc(v1.y, h1, l1); sq_acc(v1.z, h0, l0); sq_acc(v1.w, h1, l1);
+      sq_acc(v2.x, h0, l0); sq_acc(v2.y, h1, l1); sq_acc(v2.z, h0, l0); sq_acc(v2.w, h1, l1);
+      sq_acc(v3.x, h0, l0); sq_acc(v3.y, h1, l1); sq_acc(v3.z, h0, l0); sq_acc(v3.w, h1, l1);
+    }
+    for (; q < k2; q += 32) {
+      const float4 v = a4[q];
+      sq_acc(v.x, h0, l0); sq_acc(v.y, h1, l1); sq_acc(v.z, h0, l0); sq_acc(v.w, h1, l1);
+    }
+    l = 2 * k2;  // an odd last column is left to the loop below
   }
-  for (; l < k; l += 32) {
+  for (l += lane; l < k; l += 32) {
     const float2 a = a_row[l];
-    s0 = fma((double)a.x, (double)a.x, fma((double)a.y, (double)a.y, s0));
+    sq_acc(a.x, h0, l0);
+    sq_acc(a.y, h1, l1);
   }
-  double s = (s0 + s1) + (s2 + s3);
+  double s = ((double)h0 + (double)l0) + ((double)h1 + (double)l1);
   for (int off = 16; off; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
   if (lane == 0) C[row * ldc + row] = make_float2((float)s, 0.0f);
 }
@@ -1084,9 +1127,10 @@ static void c_two_m(CCtx &c, const float2 *A, int64_t lda, int64_t n, int64_t k,
                     int64_t ldc, int herm) {
   if (c.err) return;
   const size_t mark = c.ar.used;
-  Planes X = cplanes(c, n, k, 2), Y = cplanes(c, n, k, 2);
+  // A A^H: G's two operands are both Ar + Ai, so its pieces are split once
+  Planes X = cplanes(c, n, k, 2), Y = cplanes(c, n, k, herm ? 1 : 2);
   Planes Xr = subset(X, 0, c.np), Xs = subset(X, 1, c.np);
-  Planes Yi = subset(Y, 0, c.np), Ysd = subset(Y, 1, c.np);
+  Planes Yi = subset(Y, 0, c.np), Ysd = herm ? Xs : subset(Y, 1, c.np);
   float *H = (float *)c.ar.get((size_t)n * n * 4);
   float *G = (float *)c.ar.get((size_t)n * n * 4);
   if (!c.ar.dry) {
@@ -1096,10 +1140,7 @@ static void c_two_m(CCtx &c, const float2 *A, int64_t lda, int64_t n, int64_t k,
     ox.re = Xr;
     ox.s = Xs;
     oy.im = Yi;
-    if (herm)
-      oy.s = Ysd;
-    else
-      oy.d = Ysd;
+    if (!herm) oy.d = Ysd;
     csplit(c, A, lda, n, k, ox);
     csplit(c, A, lda, n, k, oy);
     // H = Ar Ai^T (all entries), G = (Ar + Ai)(Ar +- Ai)^T (lower tiles)
@@ -1335,10 +1376,7 @@ cudaError_t cbatch_build(const CBInput *in, int count, char *ws, CBatch *out) {
     b.ox.re = subset(X, 0, np);
     b.ox.s = subset(X, 1, np);
     b.oy.im = subset(Y, 0, np);
-    if (q.herm)
-      b.oy.s = subset(Y, 1, np);
-    else
-      b.oy.d = subset(Y, 1, np);
+    if (!q.herm) b.oy.d = subset(Y, 1, np);  // A A^H: G reads Ar + Ai from X twice
     b.C = q.C;
     b.ldc = q.ldc;
     b.split_first = sb;
@@ -1348,7 +1386,7 @@ cudaError_t cbatch_build(const CBInput *in, int count, char *ws, CBatch *out) {
     cbk += (int)(nt * (nt + 1) / 2);
     b.diag_first = db;
     if (q.herm) db += (int)((q.n + kDiagRows - 1) / kDiagRows);
-    L->split_bytes += (double)q.n * q.k * (8.0 + 2.0 * np * 4);
+    L->split_bytes += (double)q.n * q.k * (8.0 + 2.0 * np * (q.herm ? 3 : 4));
     L->comb_bytes += (double)q.n * q.n * (4.0 * 1.5 + 8.0 * 0.5);
     if (q.herm) L->diag_bytes += (double)q.n * q.k * 8.0;
     // two jobs: H = Ar Ai^T (all entries) from plane sets 0, G (lower) from sets 1
@@ -1358,8 +1396,11 @@ cudaError_t cbatch_build(const CBInput *in, int count, char *ws, CBatch *out) {
       FJobDesc d;
       std::memset(&d, 0, sizeof(d));
       cudaError_t e;
+      // A A^H's G job (jb 1): both operands are X's Ar + Ai pieces, which
+      // sit at the same plane indices in X as Ar - Ai would in Y
+      const Planes &ysrc = (jb == 1 && q.herm) ? X : Y;
       if ((e = encode_c(&d.tmx, X, BM)) != cudaSuccess ||
-          (e = encode_c(&d.tmy, Y, FShape<false>::YROWS)) != cudaSuccess) {
+          (e = encode_c(&d.tmy, ysrc, FShape<false>::YROWS)) != cudaSuccess) {
         CBatch tmp;
         tmp.impl = L;
         cbatch_free(&tmp);
