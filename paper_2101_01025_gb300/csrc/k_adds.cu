@@ -165,21 +165,24 @@ constexpr int kSplitRows = 8;
 
 template <int NB>
 __device__ __forceinline__ void split_rows(const SplitDesc &d, int64_t r0) {
-  const int64_t r1 = min(r0 + kSplitRows, d.rows);
-  for (int64_t r = r0; r < r1; ++r) {
-    const int32_t *xr = d.X + r * d.ldx;
+  // the block's rows x column quads as one index, so that every thread has
+  // work when the rows are short; plane rows are 16-byte aligned (kstride is
+  // a multiple of 8), so each quad leaves as one 8-byte store per plane,
+  // the columns past the last one written as zeros into the row padding
+  const int64_t nr = min((int64_t)kSplitRows, d.rows - r0);
+  const int64_t nq = (d.cols + 3) / 4;
+  for (int64_t t = threadIdx.x; t < nr * nq; t += blockDim.x) {
+    const int64_t ri = t / nq;
+    const int64_t c = 4 * (t - ri * nq);
+    const int32_t *xr = d.X + (r0 + ri) * d.ldx;
+    int32_t v[4];
     if (d.vec) {
-      for (int64_t c4 = threadIdx.x; c4 < d.cols / 4; c4 += blockDim.x) {
-        int32_t v[4];
-        ldv_bal<4>(xr + 4 * c4, d.m, v);
-        store_digits_t<NB, 4>(d.P, r, 4 * c4, v, d.b);
-      }
+      ldv_bal<4>(xr + c, d.m, v);
     } else {
-      for (int64_t c = threadIdx.x; c < d.cols; c += blockDim.x) {
-        const int32_t x[1] = {bal(xr[c], d.m)};
-        store_digits_t<NB, 1>(d.P, r, c, x, d.b);
-      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v[j] = c + j < d.cols ? ld_bal(xr + c + j, d.m) : 0;
     }
+    store_digits_t<NB, 4>(d.P, r0 + ri, c, v, d.b);
   }
 }
 

@@ -51,8 +51,6 @@ namespace {
 using namespace tc;
 
 constexpr int BM = 128, BN = 256, BK = 64;
-constexpr int EPI_WARPS = 8;
-constexpr int THREADS = 64 + EPI_WARPS * 32;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t ACC_COLS = 256;
 constexpr int MAX_GROUPS = 160;
@@ -216,8 +214,19 @@ __device__ __forceinline__ OutView tile_out(const Params &P, int t) {
 //            flight cover more of the DRAM latency; the leader CTA (rank 0)
 //            issues M=256 N=256 MMAs that read both CTAs' shared memory and
 //            write 128 TMEM lanes in each CTA.
-template <bool PAIR>
+//   EW: epilogue warps, 8 or 16.  Each owns 32 TMEM lanes (its warp index
+//   mod 4 picks them) and 1024 / EW of the 256 columns, so it holds 128 or
+//   64 int32 accumulators per thread.  16 warps run the drains, Horner steps
+//   and stores of a tile with twice the threads (the epilogue's per-entry
+//   work is latency-bound at 2 warps per scheduler: the 128 live
+//   accumulators leave few registers for independent temporaries); the
+//   price is 112 registers per thread.
+template <bool PAIR, int EW = 8>
 struct Shape {
+  static constexpr int EPI_WARPS = EW;
+  static constexpr int THREADS = 64 + EW * 32;
+  static constexpr int VALS = 1024 / EW;          // accumulators per thread
+  static constexpr int XB = EW == 8 ? 16 : 8;     // staged store block width
   static constexpr int TM = PAIR ? 256 : 128;     // output tile rows
   static constexpr int YROWS = PAIR ? 128 : 256;  // rows of Y per CTA and stage
   static constexpr int STAGES = PAIR ? 6 : 4;
@@ -225,10 +234,10 @@ struct Shape {
   static constexpr int B_BYTES = YROWS * BK * 2;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
   // + 256 bytes of barriers + a per-warp cache of the tile's groups
-  // (batched launches: 8 epilogue warps x 32 groups) + a per-warp 32 x 17
-  // int32 staging area of the output stores
-  static constexpr size_t GCACHE_BYTES = (size_t)EPI_WARPS * 32 * sizeof(Group);
-  static constexpr size_t XS_BYTES = (size_t)EPI_WARPS * 32 * 17 * 4;
+  // (batched launches: 32 groups per epilogue warp) + a per-warp
+  // 32 x (XB + 1) int32 staging area of the output stores
+  static constexpr size_t GCACHE_BYTES = (size_t)EW * 32 * sizeof(Group);
+  static constexpr size_t XS_BYTES = (size_t)EW * 32 * (XB + 1) * 4;
   static constexpr size_t SMEM =
       1024 + (size_t)STAGES * STAGE_BYTES + 256 + GCACHE_BYTES + XS_BYTES;
   // Instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator
@@ -238,9 +247,15 @@ struct Shape {
                                     ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 };
 
-template <bool BATCH, bool PAIR>
-__global__ void __launch_bounds__(THREADS, 1) leaf_tc_kernel(const __grid_constant__ Params P) {
-  using S = Shape<PAIR>;
+// Epilogue warps of the single-problem launches and of the batched launch
+// (whose tiles are mostly short in K, so the per-tile epilogue dominates).
+constexpr int kEwLeaf = 8, kEwBatch = 16;
+
+template <bool BATCH, bool PAIR, int EW>
+__global__ void __launch_bounds__(Shape<PAIR, EW>::THREADS, 1)
+    leaf_tc_kernel(const __grid_constant__ Params P) {
+  using S = Shape<PAIR, EW>;
+  constexpr int EPI_WARPS = S::EPI_WARPS, VALS = S::VALS, XB = S::XB;
   constexpr int STAGES = S::STAGES;
   extern __shared__ uint8_t smem_raw[];
   // 1024-byte alignment of the shared-window address (128B-swizzle atoms);
@@ -430,13 +445,13 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_tc_kernel(const __grid_consta
     // ---------------------------------------------------------- epilogue
     const int e = warp - 2;
     const int quarter = warp & 3;  // TMEM lanes [32 quarter, 32 quarter + 32)
-    const int chalf = e >> 2;      // columns [128 chalf, 128 chalf + 128)
+    const int cpart = e >> 2;      // columns [VALS cpart, VALS cpart + VALS)
     const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
     // the leader's MMA waits until the epilogues of both CTAs drained a buffer
     const uint32_t aempty0 = PAIR ? map_to_rank(AEMPTY(0), 0) : AEMPTY(0);
     Group *gcache = reinterpret_cast<Group *>(smem + (size_t)STAGES * S::STAGE_BYTES + 256) + e * 32;
     int32_t *xs = reinterpret_cast<int32_t *>(smem + (size_t)STAGES * S::STAGE_BYTES + 256 +
-                                              S::GCACHE_BYTES) + e * 32 * 17;
+                                              S::GCACHE_BYTES) + e * 32 * (XB + 1);
     uint32_t chunk = 0;
     bool ok = true;
     ModP m = P.m;
@@ -456,14 +471,14 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_tc_kernel(const __grid_consta
       } else {
         ng = tile_ng<BATCH>(P, t);
       }
-      int32_t acc[128];
+      int32_t acc[VALS];
 #pragma unroll
-      for (int i = 0; i < 128; ++i) acc[i] = 0;
+      for (int i = 0; i < VALS; ++i) acc[i] = 0;
       for (int gi = 0; gi < ng && ok; ++gi) {
         const Group g = (BATCH && gi < 32) ? gcache[gi] : tile_group<BATCH>(P, t, gi);
         if (gi > 0) {
 #pragma unroll
-          for (int i = 0; i < 128; ++i) acc[i] = mulmod_shoup(acc[i], g.ratio, g.ratio_sh, m);
+          for (int i = 0; i < VALS; ++i) acc[i] = mulmod_shoup(acc[i], g.ratio, g.ratio_sh, m);
         }
         for (int kb = g.kb0; kb < g.kb1;) {
           const int kend = min(kb + g.kchunk, g.kb1);
@@ -473,15 +488,17 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_tc_kernel(const __grid_consta
             break;
           }
           tc_fence_after();
-          const uint32_t ta = tmem + lane_base + buf * ACC_COLS + (uint32_t)(chalf * 128);
+          const uint32_t ta = tmem + lane_base + buf * ACC_COLS + (uint32_t)(cpart * VALS);
           tmem_drain16<0>(ta, acc);
           tmem_drain16<16>(ta + 16u, acc);
           tmem_drain16<32>(ta + 32u, acc);
           tmem_drain16<48>(ta + 48u, acc);
-          tmem_drain16<64>(ta + 64u, acc);
-          tmem_drain16<80>(ta + 80u, acc);
-          tmem_drain16<96>(ta + 96u, acc);
-          tmem_drain16<112>(ta + 112u, acc);
+          if constexpr (VALS == 128) {
+            tmem_drain16<64>(ta + 64u, acc);
+            tmem_drain16<80>(ta + 80u, acc);
+            tmem_drain16<96>(ta + 96u, acc);
+            tmem_drain16<112>(ta + 112u, acc);
+          }
           tc_fence_before();
           __syncwarp();
           if (lane == 0) {
@@ -497,10 +514,11 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_tc_kernel(const __grid_consta
       if (!ok) break;
       const int2 ij = tile_ij<BATCH>(P, t);
       const int64_t row = (int64_t)ij.x * S::TM + (int64_t)rank * BM + quarter * 32 + lane;
-      const int64_t col0 = (int64_t)ij.y * BN + chalf * 128;
-      // final value, canonical, in place (the last digit pair has weight 1)
+      const int64_t col0 = (int64_t)ij.y * BN + cpart * VALS;
+      // final value, canonical, in place: the last group is the final
+      // multiplier, whose Horner step left every entry balanced
 #pragma unroll
-      for (int i = 0; i < 128; ++i) acc[i] = (int32_t)red_i32_canon(acc[i], m);
+      for (int i = 0; i < VALS; ++i) acc[i] = (int32_t)bal_to_canon(acc[i], m);
       const OutView o = tile_out<BATCH>(P, t);
       const int64_t row0 = row - lane;
       // rows 16-byte aligned and nothing to read back: each thread stores its
@@ -511,7 +529,7 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_tc_kernel(const __grid_consta
         if (row < o.M && lim > 0) {
           int32_t *orow = o.out + row * o.ldo + col0;
 #pragma unroll
-          for (int q = 0; q < 32; ++q) {
+          for (int q = 0; q < VALS / 4; ++q) {
             const int c = 4 * q;
             if (c + 4 <= lim) {
               *reinterpret_cast<int4 *>(orow + c) = make_int4(acc[c], acc[c + 1], acc[c + 2], acc[c + 3]);
@@ -526,31 +544,33 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_tc_kernel(const __grid_consta
         continue;
       }
       // Otherwise coalesced through shared memory: each thread owns one row
-      // of the tile (its TMEM lane), so the warp writes 16 columns of its 32
-      // rows at a time into shared memory and reads them back two rows per
-      // instruction, every store instruction covering two contiguous 64-byte
-      // row segments (ragged rows, and the read-modify-write of an
-      // accumulating product).
-      // the warp's 32 x 128 block: rows below mlim, columns below nlim, and
+      // of the tile (its TMEM lane), so the warp writes XB columns of its 32
+      // rows at a time into shared memory and reads them back 32 / XB rows
+      // per instruction, every store instruction covering 32 / XB contiguous
+      // row segments of 4 XB bytes (ragged rows, and the read-modify-write of
+      // an accumulating product).
+      // the warp's 32 x VALS block: rows below mlim, columns below nlim, and
       // for a lower product only column - row <= dl (tile coordinates)
+      constexpr int RPI = 32 / XB;  // rows per store instruction
       const int mlim = (int)max((int64_t)0, min((int64_t)32, o.M - row0));
-      const int nlim = (int)max((int64_t)0, min((int64_t)128, o.N - col0));
+      const int nlim = (int)max((int64_t)0, min((int64_t)VALS, o.N - col0));
       const int dl = o.lower ? (int)max((int64_t)-256, min((int64_t)256, row0 - col0)) : 1 << 20;
       int32_t *const base = o.out + row0 * o.ldo + col0;
       const int64_t ldo = o.ldo;
       const int accum = o.accumulate;
       const uint32_t beta = o.beta, beta_sh = o.beta_sh;
+      const int lr = lane / XB, lc = lane % XB;
 #pragma unroll
-      for (int cb = 0; cb < 128; cb += 16) {
+      for (int cb = 0; cb < VALS; cb += XB) {
         __syncwarp();
 #pragma unroll
-        for (int j = 0; j < 16; ++j) xs[lane * 17 + j] = acc[cb + j];
+        for (int j = 0; j < XB; ++j) xs[lane * (XB + 1) + j] = acc[cb + j];
         __syncwarp();
 #pragma unroll 1
-        for (int i = 0; i < 16; ++i) {
-          const int rr = 2 * i + (lane >> 4), cl = cb + (lane & 15);
+        for (int i = 0; i < XB; ++i) {
+          const int rr = RPI * i + lr, cl = cb + lc;
           if (rr < mlim && cl < nlim && cl - rr <= dl) {
-            int32_t x = xs[rr * 17 + (lane & 15)];
+            int32_t x = xs[rr * (XB + 1) + lc];
             int32_t *dst = base + (int64_t)rr * ldo + cl;
             if (accum) {
               int32_t old = bal(*dst, m);
@@ -749,9 +769,11 @@ bool build_groups(const TcLeafArgs &a, const ModP &m, Group *out, int *ng_out, i
     }
   }
   // final multiplier (a group without K blocks): the last weight times the
-  // product's scale alpha (the SYRK update's alpha, 1 otherwise)
+  // product's scale alpha (the SYRK update's alpha, 1 otherwise).  It is
+  // there even when it is 1: its Horner step leaves every entry balanced,
+  // which the kernel's final canonicalisation relies on.
   const uint32_t wfinal = mulm(wprev, a.lin.alpha.w % m.p);
-  if (ng > 0 && wfinal != 1u) {
+  if (ng > 0) {
     if (ng >= MAX_GROUPS) return false;
     Group &g = out[ng++];
     g.xp = g.yp = 0;
@@ -773,8 +795,8 @@ int pair_units(int dev) {
   auto it = g_pair_units.find(dev);
   if (it != g_pair_units.end()) return it->second;
   int units = 0;
-  if (cudaFuncSetAttribute(leaf_tc_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)Shape<true>::SMEM) == cudaSuccess) {
+  if (cudaFuncSetAttribute(leaf_tc_kernel<false, true, kEwLeaf>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)Shape<true, kEwLeaf>::SMEM) == cudaSuccess) {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -782,11 +804,11 @@ int pair_units(int dev) {
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(2, 1, 1);
-    cfg.blockDim = dim3(THREADS, 1, 1);
-    cfg.dynamicSmemBytes = Shape<true>::SMEM;
+    cfg.blockDim = dim3(Shape<true, kEwLeaf>::THREADS, 1, 1);
+    cfg.dynamicSmemBytes = Shape<true, kEwLeaf>::SMEM;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (cudaOccupancyMaxActiveClusters(&units, leaf_tc_kernel<false, true>, &cfg) != cudaSuccess)
+    if (cudaOccupancyMaxActiveClusters(&units, leaf_tc_kernel<false, true, kEwLeaf>, &cfg) != cudaSuccess)
       units = 0;
   }
   cudaGetLastError();
@@ -866,8 +888,9 @@ cudaError_t launch_leaf_tc(const TcLeafArgs &a, const ModP &m, cudaStream_t st) 
   P->tiles = tiles;
   P->ntiles = nt;
   if (!g_attr_set[dev]) {
-    e = cudaFuncSetAttribute(leaf_tc_kernel<false, false>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Shape<false>::SMEM);
+    e = cudaFuncSetAttribute(leaf_tc_kernel<false, false, kEwLeaf>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Shape<false, kEwLeaf>::SMEM);
     if (e != cudaSuccess) { delete P; return e; }
     g_attr_set[dev] = true;
   }
@@ -887,15 +910,17 @@ cudaError_t launch_leaf_tc(const TcLeafArgs &a, const ModP &m, cudaStream_t st) 
       attr[0].val.clusterDim.y = 1;
       attr[0].val.clusterDim.z = 1;
       cfg.gridDim = dim3(2 * std::max(1, std::min(nt, units)), 1, 1);
-      cfg.blockDim = dim3(THREADS, 1, 1);
-      cfg.dynamicSmemBytes = Shape<true>::SMEM;
+      cfg.blockDim = dim3(Shape<true, kEwLeaf>::THREADS, 1, 1);
+      cfg.dynamicSmemBytes = Shape<true, kEwLeaf>::SMEM;
       cfg.stream = st;
       cfg.attrs = attr;
       cfg.numAttrs = 1;
-      e = cudaLaunchKernelEx(&cfg, leaf_tc_kernel<false, true>, *P);
+      e = cudaLaunchKernelEx(&cfg, leaf_tc_kernel<false, true, kEwLeaf>, *P);
       if (e != cudaSuccess) { delete P; return e; }
     } else {
-      leaf_tc_kernel<false, false><<<std::max(1, std::min(nt, sms)), THREADS, Shape<false>::SMEM, st>>>(*P);
+      leaf_tc_kernel<false, false, kEwLeaf>
+          <<<std::max(1, std::min(nt, sms)), Shape<false, kEwLeaf>::THREADS,
+             Shape<false, kEwLeaf>::SMEM, st>>>(*P);
     }
   }
   delete P;
@@ -991,9 +1016,9 @@ cudaError_t leaf_tc_batch_launch(const LeafBatch &lb, cudaStream_t st) {
     std::lock_guard<std::mutex> lock(g_mu);
     static std::map<int, bool> attr;
     if (!attr[dev]) {
-      cudaError_t e = cudaFuncSetAttribute(leaf_tc_kernel<true, false>,
+      cudaError_t e = cudaFuncSetAttribute(leaf_tc_kernel<true, false, kEwBatch>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)Shape<false>::SMEM);
+                                           (int)Shape<false, kEwBatch>::SMEM);
       if (e != cudaSuccess) return e;
       attr[dev] = true;
     }
@@ -1009,7 +1034,9 @@ cudaError_t leaf_tc_batch_launch(const LeafBatch &lb, cudaStream_t st) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   {
     ProfScope prof(AAT_K_LEAF_TC, st, L->work);
-    leaf_tc_kernel<true, false><<<std::max(1, std::min(L->ntiles, sms)), THREADS, Shape<false>::SMEM, st>>>(*P);
+    leaf_tc_kernel<true, false, kEwBatch>
+        <<<std::max(1, std::min(L->ntiles, sms)), Shape<false, kEwBatch>::THREADS,
+           Shape<false, kEwBatch>::SMEM, st>>>(*P);
   }
   delete P;
   return cudaGetLastError();
@@ -1210,15 +1237,16 @@ extern "C" AAT_API int aat_gemm_modp_noalloc(const int32_t *X, int64_t ldx, cons
   P.tiles = tiles_dev;
   P.ntiles = (int)(TI * TJ);
   if (!g_attr_set[dev]) {
-    ce = cudaFuncSetAttribute(leaf_tc_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)Shape<false>::SMEM);
+    ce = cudaFuncSetAttribute(leaf_tc_kernel<false, false, kEwLeaf>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)Shape<false, kEwLeaf>::SMEM);
     if (ce != cudaSuccess) return report_error(AAT_ECUDA, cudaGetErrorString(ce));
     g_attr_set[dev] = true;
   }
   int sms = 148;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = std::max(1, std::min(P.ntiles, sms));
-  leaf_tc_kernel<false, false><<<grid, THREADS, Shape<false>::SMEM, st>>>(P);
+  leaf_tc_kernel<false, false, kEwLeaf>
+      <<<grid, Shape<false, kEwLeaf>::THREADS, Shape<false, kEwLeaf>::SMEM, st>>>(P);
   ce = cudaGetLastError();
   return ce == cudaSuccess ? AAT_OK : report_error(AAT_ECUDA, cudaGetErrorString(ce));
 }

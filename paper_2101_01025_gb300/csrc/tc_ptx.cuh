@@ -298,8 +298,8 @@ __device__ __forceinline__ void tmem_drain32(uint32_t taddr, int32_t (&acc)[128]
 // int32 accumulators acc[B .. B+15] (load, wait, convert, add in one
 // statement); half the temporaries of the 32-column form, so that the
 // 128 accumulators and the temporaries fit the epilogue's registers.
-template <int B>
-__device__ __forceinline__ void tmem_drain16(uint32_t taddr, int32_t (&acc)[128]) {
+template <int B, int N>
+__device__ __forceinline__ void tmem_drain16(uint32_t taddr, int32_t (&acc)[N]) {
   asm volatile(
       "{\n\t.reg .b32 t0, t1, t2, t3, t4, t5, t6, t7, t8, t9, t10, t11, t12, t13, t14, t15;\n\t"
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {t0, t1, t2, t3, t4, t5, t6, t7, t8, t9, t10, t11, t12, t13, t14, t15}, [%16];\n\t"
