@@ -706,7 +706,15 @@ static bool tune_find(int64_t n, int64_t k, uint32_t p, TuneVal *v) {
 // Recursion depth chosen from measurements on GB300: a level pays off while
 // the leaf products stay large enough to keep every SM busy at full tensor
 // rate (leaf n >= 8192 at the sizes measured so far).
-static int auto_levels(int64_t n, int64_t k) {
+// Recursion depth of the untuned choice.  A level saves 1/8 of the leaves'
+// ring MACs (Table 1) and costs the block additions at the HBM rate plus
+// leaves with half the K, whose per-tile epilogue weighs more.  Measured with
+// the BF16-digit leaf: with 3 or 4 plane products per ring MAC (p = 65521,
+// 131071) no depth beats the plain lower product at n = 8192..16384,
+// k = 4096..8192; with 10 (p = 2^31 - 1) one level wins at n = k = 16384.
+static int auto_levels(int64_t n, int64_t k, uint32_t p) {
+  const DigitSpec d = make_digits(p);
+  if ((d.nsum ? d.L + d.nsum : d.L * d.L) < 6) return 0;
   int l = 0;
   while (l < 6 && (n >> (l + 1)) >= 8192 && (k >> (l + 1)) >= 2048) ++l;
   return l;
@@ -722,13 +730,13 @@ struct Prepared {
 static int prepare_levels(int64_t n, int64_t k, uint32_t p, uint32_t flags) {
   (void)p;
   const uint32_t lv = (flags & AAT_LEVELS_MASK) >> 8;
-  return lv ? (int)lv - 1 : auto_levels(n, k);
+  return lv ? (int)lv - 1 : auto_levels(n, k, p);
 }
 
-static Prepared prepare(int64_t n, int64_t k, const YParams &y, uint32_t flags) {
+static Prepared prepare(int64_t n, int64_t k, uint32_t p, const YParams &y, uint32_t flags) {
   Prepared r;
   const uint32_t lv = (flags & AAT_LEVELS_MASK) >> 8;
-  r.levels = lv ? (int)lv - 1 : auto_levels(n, k);
+  r.levels = lv ? (int)lv - 1 : auto_levels(n, k, p);
   // each level halves n and k; k/2 must be even at every level for kind 2
   const int64_t mn = (int64_t)1 << r.levels;
   const int64_t mk = (int64_t)1 << (r.levels + (y.kind == 2 ? 1 : 0));
@@ -782,7 +790,7 @@ static size_t run_plan_in(Ctx &c, const int32_t *A, int64_t n, int64_t k, int64_
     c.form = tv.form;
     if (tv.plain) c.ds.nsum = 0;
   }
-  Prepared pr = prepare(n, k, c.y, flags);
+  Prepared pr = prepare(n, k, c.m.p, c.y, flags);
   const bool early = !pr.padded && pr.levels >= 1 && !beta;
   // end-to-end path: with no top level to overlap, wait for all of A
   // before anything reads it
@@ -911,7 +919,7 @@ int modp_levels(int64_t n, int64_t k, uint32_t p, uint32_t flags) {
   if (lv) return (int)lv - 1;
   TuneVal tv;
   if ((flags & AAT_LEAF_MASK) == AAT_LEAF_TC && tune_find(n, k, p, &tv)) return tv.levels;
-  return auto_levels(n, k);
+  return auto_levels(n, k, p);
 }
 
 Planes planes_layout(const DigitSpec &ds, int64_t rows, int64_t cols) {

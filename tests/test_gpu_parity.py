@@ -5,6 +5,8 @@ output tiles with ragged tails; full-size cases compare sampled entries (at
 every recursion block boundary) one by one with the oracle and check the
 whole result with Freivalds' test.
 """
+import functools
+
 import numpy as np
 import pytest
 
@@ -334,12 +336,14 @@ def _sample_pairs(n, levels, count, seed):
     return np.array(pairs, dtype=np.int64)
 
 
-def _full_check(lib, A, p, levels_expected_min=1, nsample=3000, nvec=2):
+def _full_check(lib, A, p, levels_expected_min=1, nsample=3000, nvec=2, levels=None):
+    """levels None: the default launch configuration (as bench.py)."""
+    from paper_2101_01025_gb300 import _native
     from paper_2101_01025_gb300 import testing as T
     n, k = A.shape
-    st = T.plan_stats(n, k, p)
+    st = T.plan_stats(n, k, p) if levels is None else T.plan_stats(n, k, p, _native.AAT_LEVELS(levels))
     assert st.levels >= levels_expected_min
-    C = lib.aat_modp(dev(A), p)          # default launch configuration (as bench.py)
+    C = lib.aat_modp(dev(A), p, levels=levels)
     Ch = host(C)
     del C
     ij = _sample_pairs(n, st.levels, nsample, seed=n + k)
@@ -358,10 +362,21 @@ def test_full_size_n16384_p2_31m1(lib):
     assert st.n_pad == 16384
 
 
-@pytest.mark.parametrize("n,k,p", [(8192, 8192, 65521), (16384, 4096, 131071)])
-def test_full_size_config2(lib, n, k, p):
-    A = synth.residues(synth.SEED_BASE + 1, (n, k), p)
-    _full_check(lib, A, p, levels_expected_min=0, nsample=1500, nvec=1)
+@functools.lru_cache(maxsize=4)
+def _config2_input(n, k, p):
+    return synth.residues(synth.SEED_BASE + 1, (n, k), p)
+
+
+@pytest.mark.parametrize("levels", [None, 2, 3])
+@pytest.mark.parametrize("n,k,p", [(8192, 8192, 65521), (8192, 8192, 131071),
+                                   (16384, 4096, 65521), (16384, 4096, 131071)])
+def test_full_size_config2(lib, n, k, p, levels):
+    """8192 x 8192 and 16384 x 4096 over F_65521 and F_131071 with the default
+    depth and with 2 and 3 recursion levels: sampled entries and Freivalds."""
+    A = _config2_input(n, k, p)
+    st = _full_check(lib, A, p, levels_expected_min=0, nsample=1500, nvec=1, levels=levels)
+    if levels is not None:
+        assert st.levels == levels
 
 
 # ------------------------------------------------------- SYRK form (Sec. 7)
