@@ -46,12 +46,12 @@ N = K = 16384
 P = 2**31 - 1
 SEED_OFFSET = 2
 # DRAM traffic of the dominant kernel from one ncu capture of an 8192^3 leaf
-# product (dram__bytes_read.sum + dram__bytes_write.sum = 30.28 GB for
+# product (dram__bytes_read.sum + dram__bytes_write.sum = 14.60 GB for
 # 10.995 TFLOP of algorithmic work, CTA-pair form,
 # profiles/leaf_tc_kernel_gemm8192_p2p31m1.md), scaled to the average launch
 # of the step by its algorithmic work.  None whenever the kernel has changed
 # since the counters were taken.
-LEAF_TC_BYTES_PER_FLOP = 30.28e9 / 10.995e12
+LEAF_TC_BYTES_PER_FLOP = 14.60e9 / 10.995e12
 
 
 def parse():
