@@ -220,7 +220,7 @@ __device__ __forceinline__ OutView tile_out(const Params &P, int t) {
 //   and stores of a tile with twice the threads (the epilogue's per-entry
 //   work is latency-bound at 2 warps per scheduler: the 128 live
 //   accumulators leave few registers for independent temporaries); the
-//   price is 112 registers per thread.
+//   price is 96 registers per thread (and some spills).
 template <bool PAIR, int EW = 8>
 struct Shape {
   static constexpr int EPI_WARPS = EW;
@@ -240,6 +240,7 @@ struct Shape {
   static constexpr size_t XS_BYTES = (size_t)EW * 32 * (XB + 1) * 4;
   static constexpr size_t SMEM =
       1024 + (size_t)STAGES * STAGE_BYTES + 256 + GCACHE_BYTES + XS_BYTES;
+  static_assert(SMEM <= 227 * 1024, "shared memory per CTA");
   // Instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator
   // (bit 4), A and B BF16 (bits 7, 10), both K-major, N >> 3 at bit 17,
   // M >> 4 at bit 24.
