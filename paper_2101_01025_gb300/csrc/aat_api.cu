@@ -168,7 +168,7 @@ static int32_t bal_host(uint64_t r, uint32_t p) {
 }
 
 // Y for the transposition over F_p (Sec. 4.2 / Prop. 4.2 with Algorithm 3).
-static bool make_y(uint32_t p, YParams *y) {
+static bool make_y_uncached(uint32_t p, YParams *y) {
   if (p % 4 == 1) {
     uint64_t i;
     if (!sqrt_mod(p - 1, p, &i)) return false;
@@ -196,6 +196,28 @@ static bool make_y(uint32_t p, YParams *y) {
   y->kind = 2;
   y->a = bal_host(a, p);
   y->b = bal_host(b, p);
+  return true;
+}
+
+// Y per prime, computed once.  The remark after Algorithm 3 (Sec. 4.3)
+// reuses the quadratic non-residue for several sums of squares modulo one
+// prime; calls with the same p here reuse the whole Y, so the square roots
+// and the two-squares search run on the first call with p only.
+static std::mutex g_y_mu;
+static std::map<uint32_t, YParams> g_y_cache;
+
+static bool make_y(uint32_t p, YParams *y) {
+  {
+    std::lock_guard<std::mutex> lock(g_y_mu);
+    auto it = g_y_cache.find(p);
+    if (it != g_y_cache.end()) {
+      *y = it->second;
+      return true;
+    }
+  }
+  if (!make_y_uncached(p, y)) return false;
+  std::lock_guard<std::mutex> lock(g_y_mu);
+  if (g_y_cache.size() < 4096) g_y_cache[p] = *y;
   return true;
 }
 

@@ -169,11 +169,12 @@ __device__ __forceinline__ void split_rows(const SplitDesc &d, int64_t r0) {
   // work when the rows are short; plane rows are 16-byte aligned (kstride is
   // a multiple of 8), so each quad leaves as one 8-byte store per plane,
   // the columns past the last one written as zeros into the row padding
-  const int64_t nr = min((int64_t)kSplitRows, d.rows - r0);
-  const int64_t nq = (d.cols + 3) / 4;
-  for (int64_t t = threadIdx.x; t < nr * nq; t += blockDim.x) {
-    const int64_t ri = t / nq;
-    const int64_t c = 4 * (t - ri * nq);
+  // (32-bit index arithmetic: nr * nq < 8 * 2^28)
+  const uint32_t nr = (uint32_t)min((int64_t)kSplitRows, d.rows - r0);
+  const uint32_t nq = (uint32_t)((d.cols + 3) / 4);
+  for (uint32_t t = threadIdx.x; t < nr * nq; t += blockDim.x) {
+    const uint32_t ri = t / nq;
+    const int64_t c = 4 * (int64_t)(t - ri * nq);
     const int32_t *xr = d.X + (r0 + ri) * d.ldx;
     int32_t v[4];
     if (d.vec) {

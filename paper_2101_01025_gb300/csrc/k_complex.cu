@@ -562,12 +562,13 @@ __device__ __forceinline__ int cb_find(const CBProb *pr, int count, int b, int w
 __global__ void csplit_batch_kernel(const CBProb *__restrict__ pr, int count) {
   const CBProb &q = pr[cb_find(pr, count, blockIdx.x, 0)];
   const int64_t r0 = (int64_t)(blockIdx.x - q.split_first) * kCSplitRows;
-  const int64_t nr = min((int64_t)kCSplitRows, q.n - r0);
-  const int64_t cq = (q.k + 3) / 4;
+  const uint32_t nr = (uint32_t)min((int64_t)kCSplitRows, q.n - r0);
+  const uint32_t cq = (uint32_t)((q.k + 3) / 4);
   // the block's rows x column quads as one index: every thread has work
-  // when the rows are short
-  for (int64_t t = threadIdx.x; t < nr * cq; t += blockDim.x) {
-    const int64_t r = r0 + t / cq, q4 = t - (t / cq) * cq;
+  // when the rows are short (32-bit index arithmetic: nr * cq < 8 * 2^28)
+  for (uint32_t t = threadIdx.x; t < nr * cq; t += blockDim.x) {
+    const uint32_t ri = t / cq;
+    const int64_t r = r0 + ri, q4 = t - ri * cq;
     csplit_quad(q.A + r * q.lda, r, q4, q.k, q.np, q.ox);
     csplit_quad(q.A + r * q.lda, r, q4, q.k, q.np, q.oy);
   }

@@ -79,6 +79,22 @@ def test_y_has_a_equal_one_when_p_is_3_mod_8(p):
     assert kind == 2 and a == 1 and (1 + b * b) % p == p - 1
 
 
+def test_y_cache_many_primes():
+    """Y is kept per prime after its first computation: for 300 primes (all
+    three kinds of Y), a second request returns the first answer, and every
+    answer is skew-unitary."""
+    primes = [q for q in range(3, 200000) if oracle.is_prime(q)][-300:]
+    first = {q: T.y_params(q) for q in primes}
+    for q in primes:
+        kind, a, b = T.y_params(q)
+        assert (kind, a, b) == first[q]
+        if q % 4 == 1:
+            assert kind == 1 and (a * a + 1) % q == 0
+        else:
+            assert kind == 2 and (a * a + b * b + 1) % q == 0
+    assert {q % 8 for q in primes} >= {1, 3, 5, 7}
+
+
 def test_sos_all_residues():
     for p in [3, 7, 11, 19, 23, 131071]:
         for k in list(range(min(p, 200))) + [p - 1]:
