@@ -445,9 +445,7 @@ static bool check(Ctx &c, cudaError_t e, const char *where) {
 
 // out <- alpha X Y^T + beta out (M x N, inner K) mod p, alpha = c.alpha;
 // lower: only i >= j.  beta 0 stores the product, 1 accumulates.
-static void leaf(Ctx &c, Operand X, Operand Y, bool same, int64_t M, int64_t N, int64_t K,
-                 int32_t *out, int64_t ldo, int lower, uint32_t beta) {
-  const Lin lin = lin_of(c.alpha, beta, c.m.p);
+static void count_leaf(Ctx &c, int64_t M, int64_t N, int64_t K, int lower) {
   if (c.stats) {
     if (lower) {
       c.stats->syrk_leaves++;
@@ -457,6 +455,33 @@ static void leaf(Ctx &c, Operand X, Operand Y, bool same, int64_t M, int64_t N, 
       c.stats->ring_macs += (double)M * (double)N * (double)K;
     }
   }
+}
+
+// The tensor-core leaf's arguments for out <- alpha X Y^T + beta out from
+// the digit planes of X (M x K) and Y (N x K).
+static TcLeafArgs tc_args(const Ctx &c, const Planes &x, const Planes &y, int64_t M, int64_t N,
+                          int64_t K, int32_t *out, int64_t ldo, int lower, uint32_t beta) {
+  TcLeafArgs a;
+  a.x = x;
+  a.y = y;
+  a.dx = c.ds;
+  a.dy = c.ds;
+  a.M = M;
+  a.N = N;
+  a.K = K;
+  a.out = out;
+  a.ldo = ldo;
+  a.lower = lower;
+  a.lin = lin_of(c.alpha, beta, c.m.p);
+  a.exact_bits = c.exact_bits;
+  a.form = c.form;
+  return a;
+}
+
+static void leaf(Ctx &c, Operand X, Operand Y, bool same, int64_t M, int64_t N, int64_t K,
+                 int32_t *out, int64_t ldo, int lower, uint32_t beta) {
+  const Lin lin = lin_of(c.alpha, beta, c.m.p);
+  count_leaf(c, M, N, K, lower);
   if (c.leaf == AAT_LEAF_SIMT) {
     if (!c.ar.dry)
       check(c, launch_leaf_simt(X.x, X.ld, Y.x, Y.ld, M, N, K, out, ldo, lower, lin, c.m,
@@ -492,23 +517,9 @@ static void leaf(Ctx &c, Operand X, Operand Y, bool same, int64_t M, int64_t N, 
     Y.pl = planes_alloc(c, N, K);
     if (!c.ar.dry) check(c, launch_split(Y.x, Y.ld, N, K, c.m, c.ds.b, Y.pl, c.st), "split");
   }
-  if (!c.ar.dry && c.err == AAT_OK) {
-    TcLeafArgs a;
-    a.x = X.pl;
-    a.y = Y.pl;
-    a.dx = c.ds;
-    a.dy = c.ds;
-    a.M = M;
-    a.N = N;
-    a.K = K;
-    a.out = out;
-    a.ldo = ldo;
-    a.lower = lower;
-    a.lin = lin;
-    a.exact_bits = c.exact_bits;
-    a.form = c.form;
-    check(c, launch_leaf_tc(a, c.m, c.st), "leaf (tensor cores)");
-  }
+  if (!c.ar.dry && c.err == AAT_OK)
+    check(c, launch_leaf_tc(tc_args(c, X.pl, Y.pl, M, N, K, out, ldo, lower, beta), c.m, c.st),
+          "leaf (tensor cores)");
   c.ar.used = mark;
 }
 
@@ -574,6 +585,16 @@ static void count_level(Ctx &c) {
   }
 }
 
+// The independent leaf products of a last level in one launch (default), or
+// one launch per product with AAT_LEAF_FUSE=0.
+static bool fuse_leaves() {
+  static const bool v = [] {
+    const char *e = getenv("AAT_LEAF_FUSE");
+    return !(e && atoi(e) == 0);
+  }();
+  return v;
+}
+
 // Low(A A^T) mod p -> Low(C) by Algorithm 1 with `levels` levels (times
 // c.alpha).  n must be divisible by 2^levels and k by 2^levels (2^(levels+1)
 // for a kind-2 Y).  `ap` optionally holds the digit planes of A
@@ -620,14 +641,34 @@ static void rec(Ctx &c, const int32_t *A, int64_t lda, int64_t n, int64_t k, int
   }
   // 1. S1..S4 (4 additions, 2 products by Y) in one pass over A
   const LevelOps L = sblocks_step(c, A, lda, h, kap, S3, ldS3, last, pA11_early);
-  // 2. P4^T = S2 S1^T -> C22
-  leaf(c, L.oS2, L.oS1, false, h, h, kap, C22, ldc, 0, 0);
-  // 3. P5 = Low(S3 S3^T) -> C12
-  rec(c, S3, ldS3, h, kap, C12, ldc, levels - 1, L.pS3);
-  // 4. P3 = A22 S4^T -> C21 (S3 is no longer needed)
-  leaf(c, L.oA22, L.oS4, false, h, h, kap, C21, ldc, 0, 0);
-  // 5. P1 = Low(A11 A11^T) -> C11
-  if (!p1_first) rec(c, A11, lda, h, kap, C11, ldc, levels - 1, L.pA11);
+  if (last && c.leaf == AAT_LEAF_TC && fuse_leaves()) {
+    // 2-5 at the last level: P4^T, P5, P3 and P1 read only digit planes
+    // written by step 1 and write four different blocks of C, so they run
+    // as one persistent launch over the tiles of all four
+    TcLeafArgs a[4];
+    int np = 0;
+    count_leaf(c, h, h, kap, 0);
+    a[np++] = tc_args(c, L.oS2.pl, L.oS1.pl, h, h, kap, C22, ldc, 0, 0);
+    count_leaf(c, h, h, kap, 1);
+    a[np++] = tc_args(c, L.pS3, L.pS3, h, h, kap, C12, ldc, 1, 0);
+    count_leaf(c, h, h, kap, 0);
+    a[np++] = tc_args(c, L.oA22.pl, L.oS4.pl, h, h, kap, C21, ldc, 0, 0);
+    if (!p1_first) {
+      count_leaf(c, h, h, kap, 1);
+      a[np++] = tc_args(c, L.pA11, L.pA11, h, h, kap, C11, ldc, 1, 0);
+    }
+    if (!c.ar.dry && c.err == AAT_OK)
+      check(c, launch_leaf_tc_multi(a, np, c.m, c.st), "leaf (tensor cores, P1 P3 P4 P5)");
+  } else {
+    // 2. P4^T = S2 S1^T -> C22
+    leaf(c, L.oS2, L.oS1, false, h, h, kap, C22, ldc, 0, 0);
+    // 3. P5 = Low(S3 S3^T) -> C12
+    rec(c, S3, ldS3, h, kap, C12, ldc, levels - 1, L.pS3);
+    // 4. P3 = A22 S4^T -> C21 (S3 is no longer needed)
+    leaf(c, L.oA22, L.oS4, false, h, h, kap, C21, ldc, 0, 0);
+    // 5. P1 = Low(A11 A11^T) -> C11
+    if (!p1_first) rec(c, A11, lda, h, kap, C11, ldc, levels - 1, L.pA11);
+  }
   // 6. U1 = P1 + P5, U2 = U1 + P4, U4 = U2 + P3 -> C21, U5 = Low(U2 + P4^T) -> C22
   if (!c.ar.dry) check(c, launch_postadd(C11, ldc, C12, C21, C22, ldc, h, c.m, c.st), "postadd");
   // rows [h, n) of the top level (C21 = U4, Low(C22) = Low(U5)) are final

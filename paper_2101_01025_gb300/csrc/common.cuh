@@ -361,6 +361,10 @@ struct TcLeafArgs {
   int form;               // kernel form: 0 chosen from the shape, 1 one CTA, 2 CTA pairs
 };
 cudaError_t launch_leaf_tc(const TcLeafArgs &a, const ModP &m, cudaStream_t st);
+// Up to 16 independent leaf products of one modulus and digit base in one
+// persistent launch (one tile list over all of them).
+cudaError_t launch_leaf_tc_multi(const TcLeafArgs *as, int count, const ModP &m,
+                                 cudaStream_t st);
 void leaf_tc_release();
 
 // A batched tensor-core leaf launch: device tables (per-problem tensor maps,

@@ -75,6 +75,25 @@ struct alignas(64) BatchProb {
   ModP m;
 };
 
+// One problem of a multi-problem launch (up to MAX_MULTI independent
+// products that share one digit spec and modulus); its tensor maps live in
+// the kernel parameters like the single-problem maps.
+constexpr int MAX_MULTI = 16;
+struct alignas(64) MultiProb {
+  CUtensorMap tmx, tmy;
+  int32_t *out;
+  int64_t ldo, M, N;
+  int goff, ng;  // its groups: Params::g[goff .. goff + ng)
+  int lower, accumulate;
+  uint32_t beta, beta_sh;
+};
+
+// Launch modes of the kernel: one problem (maps and groups in the
+// parameters), a batch (per-problem maps and groups in global memory, many
+// moduli), several problems of one modulus (maps and groups in the
+// parameters, tile entries (problem, I, J) in global memory).
+constexpr int kSingle = 0, kBatch = 1, kMulti = 2;
+
 struct Params {
   CUtensorMap tmx;  // 3D {K, rows, plane}, box {64, 128, 1}
   CUtensorMap tmy;  // 3D {K, rows, plane}, box {64, 256, 1} (CTA pair: {64, 128, 1})
@@ -93,6 +112,9 @@ struct Params {
   const BatchProb *probs;
   const int4 *btiles;
   const Group *gtab;
+  // multi-problem launches: tile entries (problem, I, J, 0)
+  const int4 *mtiles;
+  MultiProb mp[MAX_MULTI];
 };
 
 // Batched tile entries are (problem, I, J, goff | ng << 16): the tile's
@@ -107,16 +129,25 @@ struct TileView {
   int ng, I, J;
 };
 
-template <bool BATCH>
+template <int MODE>
 __device__ __forceinline__ TileView tile_view(const Params &P, int t) {
   TileView v;
-  if constexpr (BATCH) {
+  if constexpr (MODE == kBatch) {
     const int4 tl = P.btiles[t];
     const BatchProb &b = P.probs[tl.x];
     v.tmx = &b.tmx;
     v.tmy = &b.tmy;
     v.g = P.gtab + tile_goff(tl.w);
     v.ng = tile_ngrp(tl.w);
+    v.I = tl.y;
+    v.J = tl.z;
+  } else if constexpr (MODE == kMulti) {
+    const int4 tl = P.mtiles[t];
+    const MultiProb &b = P.mp[tl.x];
+    v.tmx = &b.tmx;
+    v.tmy = &b.tmy;
+    v.g = P.g + b.goff;
+    v.ng = b.ng;
     v.I = tl.y;
     v.J = tl.z;
   } else {
@@ -132,37 +163,44 @@ __device__ __forceinline__ TileView tile_view(const Params &P, int t) {
 }
 
 // Group gi of tile t, and the group count (parameter loads when not batched).
-template <bool BATCH>
+template <int MODE>
 __device__ __forceinline__ Group tile_group(const Params &P, int t, int gi) {
-  if constexpr (BATCH) {
+  if constexpr (MODE == kBatch) {
     return P.gtab[tile_goff(P.btiles[t].w) + gi];
+  } else if constexpr (MODE == kMulti) {
+    return P.g[P.mp[P.mtiles[t].x].goff + gi];
   } else {
     return P.g[gi];
   }
 }
 
-template <bool BATCH>
+template <int MODE>
 __device__ __forceinline__ int tile_ng(const Params &P, int t) {
-  if constexpr (BATCH) {
+  if constexpr (MODE == kBatch) {
     return tile_ngrp(P.btiles[t].w);
+  } else if constexpr (MODE == kMulti) {
+    return P.mp[P.mtiles[t].x].ng;
   } else {
     return P.ng;
   }
 }
 
-template <bool BATCH>
+template <int MODE>
 __device__ __forceinline__ int2 tile_ij(const Params &P, int t) {
-  if constexpr (BATCH) {
+  if constexpr (MODE == kBatch) {
     const int4 tl = P.btiles[t];
+    return make_int2(tl.y, tl.z);
+  } else if constexpr (MODE == kMulti) {
+    const int4 tl = P.mtiles[t];
     return make_int2(tl.y, tl.z);
   } else {
     return P.tiles[t];
   }
 }
 
-template <bool BATCH>
+template <int MODE>
 __device__ __forceinline__ const ModP &tile_modp(const Params &P, int t) {
-  if constexpr (BATCH) {
+  if constexpr (MODE == kBatch) {
     return P.probs[P.btiles[t].x].m;
   } else {
     return P.m;
@@ -177,30 +215,29 @@ struct OutView {
   uint32_t beta, beta_sh;
 };
 
-template <bool BATCH>
-__device__ __forceinline__ OutView tile_out(const Params &P, int t) {
+template <class B>
+__device__ __forceinline__ OutView out_view(const B &b) {
   OutView o;
-  if constexpr (BATCH) {
-    const BatchProb &b = P.probs[P.btiles[t].x];
-    o.out = b.out;
-    o.ldo = b.ldo;
-    o.M = b.M;
-    o.N = b.N;
-    o.lower = b.lower;
-    o.accumulate = b.accumulate;
-    o.beta = b.beta;
-    o.beta_sh = b.beta_sh;
-  } else {
-    o.out = P.out;
-    o.ldo = P.ldo;
-    o.M = P.M;
-    o.N = P.N;
-    o.lower = P.lower;
-    o.accumulate = P.accumulate;
-    o.beta = P.beta;
-    o.beta_sh = P.beta_sh;
-  }
+  o.out = b.out;
+  o.ldo = b.ldo;
+  o.M = b.M;
+  o.N = b.N;
+  o.lower = b.lower;
+  o.accumulate = b.accumulate;
+  o.beta = b.beta;
+  o.beta_sh = b.beta_sh;
   return o;
+}
+
+template <int MODE>
+__device__ __forceinline__ OutView tile_out(const Params &P, int t) {
+  if constexpr (MODE == kBatch) {
+    return out_view(P.probs[P.btiles[t].x]);
+  } else if constexpr (MODE == kMulti) {
+    return out_view(P.mp[P.mtiles[t].x]);
+  } else {
+    return out_view(P);
+  }
 }
 
 // ------------------------------------------------------------------ kernel
@@ -252,7 +289,7 @@ struct Shape {
 // (whose tiles are mostly short in K, so the per-tile epilogue dominates).
 constexpr int kEwLeaf = 8, kEwBatch = 16;
 
-template <bool BATCH, bool PAIR, int EW>
+template <int MODE, bool PAIR, int EW>
 __global__ void __launch_bounds__(Shape<PAIR, EW>::THREADS, 1)
     leaf_tc_kernel(const __grid_constant__ Params P) {
   using S = Shape<PAIR, EW>;
@@ -330,7 +367,7 @@ __global__ void __launch_bounds__(Shape<PAIR, EW>::THREADS, 1)
       // both CTAs' copies of a stage complete on the leader's FULL barrier
       const uint32_t full0 = PAIR ? map_to_rank(FULL(0), 0) : FULL(0);
       for (int t = (int)unit0; t < P.ntiles && ok; t += (int)nunits) {
-        const TileView v = tile_view<BATCH>(P, t);
+        const TileView v = tile_view<MODE>(P, t);
         const int rowx = v.I * S::TM + (int)rank * BM;
         const int rowy = v.J * BN + (int)rank * S::YROWS;
         for (int gi = 0; gi < v.ng && ok; ++gi) {
@@ -387,9 +424,9 @@ __global__ void __launch_bounds__(Shape<PAIR, EW>::THREADS, 1)
       uint32_t ph = 0, chunk = 0;
       bool ok = true;
       for (int t = (int)unit0; t < P.ntiles && ok; t += (int)nunits) {
-        const int ng = tile_ng<BATCH>(P, t);
+        const int ng = tile_ng<MODE>(P, t);
         for (int gi = 0; gi < ng && ok; ++gi) {
-          const Group g = tile_group<BATCH>(P, t, gi);
+          const Group g = tile_group<MODE>(P, t, gi);
           for (int kb = g.kb0; kb < g.kb1 && ok;) {
             const int kend = min(kb + g.kchunk, g.kb1);
             const uint32_t buf = chunk & 1u, use = chunk >> 1;
@@ -462,7 +499,7 @@ __global__ void __launch_bounds__(Shape<PAIR, EW>::THREADS, 1)
       // of each warp loads group i into the warp's shared-memory cache at
       // the start of the tile (all loads in flight together) and the group
       // loop reads them from there
-      if constexpr (BATCH) {
+      if constexpr (MODE == kBatch) {
         const int4 tl = P.btiles[t];
         ng = tile_ngrp(tl.w);
         __syncwarp();
@@ -470,13 +507,13 @@ __global__ void __launch_bounds__(Shape<PAIR, EW>::THREADS, 1)
         __syncwarp();
         m = P.probs[tl.x].m;
       } else {
-        ng = tile_ng<BATCH>(P, t);
+        ng = tile_ng<MODE>(P, t);
       }
       int32_t acc[VALS];
 #pragma unroll
       for (int i = 0; i < VALS; ++i) acc[i] = 0;
       for (int gi = 0; gi < ng && ok; ++gi) {
-        const Group g = (BATCH && gi < 32) ? gcache[gi] : tile_group<BATCH>(P, t, gi);
+        const Group g = (MODE == kBatch && gi < 32) ? gcache[gi] : tile_group<MODE>(P, t, gi);
         if (gi > 0) {
 #pragma unroll
           for (int i = 0; i < VALS; ++i) acc[i] = mulmod_shoup(acc[i], g.ratio, g.ratio_sh, m);
@@ -513,14 +550,14 @@ __global__ void __launch_bounds__(Shape<PAIR, EW>::THREADS, 1)
         }
       }
       if (!ok) break;
-      const int2 ij = tile_ij<BATCH>(P, t);
+      const int2 ij = tile_ij<MODE>(P, t);
       const int64_t row = (int64_t)ij.x * S::TM + (int64_t)rank * BM + quarter * 32 + lane;
       const int64_t col0 = (int64_t)ij.y * BN + cpart * VALS;
       // final value, canonical, in place: the last group is the final
       // multiplier, whose Horner step left every entry balanced
 #pragma unroll
       for (int i = 0; i < VALS; ++i) acc[i] = (int32_t)bal_to_canon(acc[i], m);
-      const OutView o = tile_out<BATCH>(P, t);
+      const OutView o = tile_out<MODE>(P, t);
       const int64_t row0 = row - lane;
       // rows 16-byte aligned and nothing to read back: each thread stores its
       // row segment with 16-byte stores
@@ -638,20 +675,31 @@ cudaError_t encode_planes(CUtensorMap *tm, const Planes &P, int box_rows) {
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-uint32_t pow2mod(uint64_t e, uint32_t p) {
-  uint64_t r = 1 % p, b = 2 % p;
-  while (e) {
-    if (e & 1) r = (r * b) % p;
-    b = (b * b) % p;
-    e >>= 1;
-  }
-  return (uint32_t)r;
-}
-
 // Tile order: super-blocks of 2048 x 2048 outputs (16 x 8 tiles of 128 x 256,
 // or 8 x 8 of 256 x 256) swept row-major, tiles inside a super-block
 // row-major, so that the CTAs running at the same time share rows of X and
 // columns of Y in L2.  `tm` is the tile height (128 or 256).
+void tile_order(int64_t M, int64_t N, int lower, int tm, std::vector<int2> &v) {
+  const int64_t TI = (M + tm - 1) / tm, TJ = (N + BN - 1) / BN;
+  const int64_t SI = 2048 / tm, SJ = 8;
+  for (int64_t bi = 0; bi < TI; bi += SI)
+    for (int64_t bj = 0; bj < TJ; bj += SJ)
+      for (int64_t i = bi; i < std::min(TI, bi + SI); ++i)
+        for (int64_t j = bj; j < std::min(TJ, bj + SJ); ++j) {
+          if (lower && j * BN > i * tm + tm - 1) continue;
+          v.push_back(make_int2((int)i, (int)j));
+        }
+}
+
+template <class T>
+cudaError_t upload(const std::vector<T> &v, T **out) {
+  *out = nullptr;
+  if (v.empty()) return cudaSuccess;
+  cudaError_t e = cudaMalloc(out, v.size() * sizeof(T));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*out, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
 cudaError_t get_tiles(int dev, int64_t M, int64_t N, int lower, int tm, int2 **out, int *count) {
   auto key = std::make_tuple(dev, M, N, lower, tm);
   auto it = g_tiles.find(key);
@@ -660,26 +708,49 @@ cudaError_t get_tiles(int dev, int64_t M, int64_t N, int lower, int tm, int2 **o
     *count = it->second.second;
     return cudaSuccess;
   }
-  const int64_t TI = (M + tm - 1) / tm, TJ = (N + BN - 1) / BN;
-  const int64_t SI = 2048 / tm, SJ = 8;
   std::vector<int2> v;
-  for (int64_t bi = 0; bi < TI; bi += SI)
-    for (int64_t bj = 0; bj < TJ; bj += SJ)
-      for (int64_t i = bi; i < std::min(TI, bi + SI); ++i)
-        for (int64_t j = bj; j < std::min(TJ, bj + SJ); ++j) {
-          if (lower && j * BN > i * tm + tm - 1) continue;
-          v.push_back(make_int2((int)i, (int)j));
-        }
+  tile_order(M, N, lower, tm, v);
   int2 *d = nullptr;
-  if (!v.empty()) {
-    cudaError_t e = cudaMalloc(&d, v.size() * sizeof(int2));
-    if (e != cudaSuccess) return e;
-    e = cudaMemcpy(d, v.data(), v.size() * sizeof(int2), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return e;
-  }
+  cudaError_t e = upload(v, &d);
+  if (e != cudaSuccess) return e;
   g_tiles[key] = std::make_pair(d, (int)v.size());
   *out = d;
   *count = (int)v.size();
+  return cudaSuccess;
+}
+
+// Tile list of a multi-problem launch: the problems in launch order, each in
+// its own super-block order, entries (problem, I, J, 0).  Cached per device,
+// tile height and list of shapes.
+std::map<std::vector<int64_t>, std::pair<int4 *, int>> g_mtiles;
+
+cudaError_t get_multi_tiles(int dev, const TcLeafArgs *as, const int *order, int count, int tm,
+                            int4 **out, int *ntiles) {
+  std::vector<int64_t> key = {dev, tm};
+  for (int q = 0; q < count; ++q) {
+    const TcLeafArgs &a = as[order[q]];
+    key.insert(key.end(), {(int64_t)order[q], a.M, a.N, (int64_t)a.lower});
+  }
+  auto it = g_mtiles.find(key);
+  if (it != g_mtiles.end()) {
+    *out = it->second.first;
+    *ntiles = it->second.second;
+    return cudaSuccess;
+  }
+  std::vector<int4> v;
+  std::vector<int2> one;
+  for (int q = 0; q < count; ++q) {
+    const TcLeafArgs &a = as[order[q]];
+    one.clear();
+    tile_order(a.M, a.N, a.lower, tm, one);
+    for (const int2 &t : one) v.push_back(make_int4(order[q], t.x, t.y, 0));
+  }
+  int4 *d = nullptr;
+  cudaError_t e = upload(v, &d);
+  if (e != cudaSuccess) return e;
+  g_mtiles[key] = std::make_pair(d, (int)v.size());
+  *out = d;
+  *ntiles = (int)v.size();
   return cudaSuccess;
 }
 
@@ -796,7 +867,7 @@ int pair_units(int dev) {
   auto it = g_pair_units.find(dev);
   if (it != g_pair_units.end()) return it->second;
   int units = 0;
-  if (cudaFuncSetAttribute(leaf_tc_kernel<false, true, kEwLeaf>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (cudaFuncSetAttribute(leaf_tc_kernel<kSingle, true, kEwLeaf>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)Shape<true, kEwLeaf>::SMEM) == cudaSuccess) {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
@@ -809,7 +880,7 @@ int pair_units(int dev) {
     cfg.dynamicSmemBytes = Shape<true, kEwLeaf>::SMEM;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (cudaOccupancyMaxActiveClusters(&units, leaf_tc_kernel<false, true, kEwLeaf>, &cfg) != cudaSuccess)
+    if (cudaOccupancyMaxActiveClusters(&units, leaf_tc_kernel<kSingle, true, kEwLeaf>, &cfg) != cudaSuccess)
       units = 0;
   }
   cudaGetLastError();
@@ -889,7 +960,7 @@ cudaError_t launch_leaf_tc(const TcLeafArgs &a, const ModP &m, cudaStream_t st) 
   P->tiles = tiles;
   P->ntiles = nt;
   if (!g_attr_set[dev]) {
-    e = cudaFuncSetAttribute(leaf_tc_kernel<false, false, kEwLeaf>,
+    e = cudaFuncSetAttribute(leaf_tc_kernel<kSingle, false, kEwLeaf>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)Shape<false, kEwLeaf>::SMEM);
     if (e != cudaSuccess) { delete P; return e; }
@@ -916,10 +987,159 @@ cudaError_t launch_leaf_tc(const TcLeafArgs &a, const ModP &m, cudaStream_t st) 
       cfg.stream = st;
       cfg.attrs = attr;
       cfg.numAttrs = 1;
-      e = cudaLaunchKernelEx(&cfg, leaf_tc_kernel<false, true, kEwLeaf>, *P);
+      e = cudaLaunchKernelEx(&cfg, leaf_tc_kernel<kSingle, true, kEwLeaf>, *P);
       if (e != cudaSuccess) { delete P; return e; }
     } else {
-      leaf_tc_kernel<false, false, kEwLeaf>
+      leaf_tc_kernel<kSingle, false, kEwLeaf>
+          <<<std::max(1, std::min(nt, sms)), Shape<false, kEwLeaf>::THREADS,
+             Shape<false, kEwLeaf>::SMEM, st>>>(*P);
+    }
+  }
+  delete P;
+  return cudaGetLastError();
+}
+
+// Several independent products of one modulus and digit base in one
+// persistent launch: the tiles of all of them form one list taken round
+// robin, so the last wave of one product is filled by the tiles of the next
+// instead of leaving SMs idle between launches.
+cudaError_t launch_leaf_tc_multi(const TcLeafArgs *as, int count, const ModP &m,
+                                 cudaStream_t st) {
+  if (count < 1 || count > MAX_MULTI) return cudaErrorInvalidValue;
+  for (int i = 0; i < count; ++i) {
+    const TcLeafArgs &a = as[i];
+    if (a.M <= 0 || a.N <= 0) return cudaErrorInvalidValue;
+    if (a.dx.b != as[0].dx.b || a.dx.b != a.dy.b || a.x.nbase != a.dx.L ||
+        a.y.nbase != a.dy.L || a.x.L != a.x.nbase + a.x.nsum || a.y.L != a.y.nbase + a.y.nsum)
+      return cudaErrorInvalidValue;
+    if (a.x.kstride % 8 || a.y.kstride % 8 || a.x.cols != a.K || a.y.cols != a.K)
+      return cudaErrorInvalidValue;
+    if (((uintptr_t)a.x.ptr | (uintptr_t)a.y.ptr) & 15) return cudaErrorInvalidValue;
+  }
+  std::lock_guard<std::mutex> lock(g_mu);
+  cudaError_t e = get_encode();
+  if (e != cudaSuccess) return e;
+  int dev = 0;
+  cudaGetDevice(&dev);
+
+  // the form, as for one product, over the tiles of all of them
+  const int units = pair_units(dev);
+  bool pair = false;
+  if (units > 0) {
+    bool big = true;
+    int64_t pt = 0;
+    for (int i = 0; i < count; ++i) {
+      big = big && as[i].M >= 256;
+      const int64_t t = ((as[i].M + 255) / 256) * ((as[i].N + BN - 1) / BN);
+      pt += as[i].lower ? t / 2 : t;
+    }
+    const int ov = as[0].form > 0 ? as[0].form - 1 : pair_override();
+    pair = big && (ov >= 0 ? ov > 0 : pt >= units);
+  }
+  const int tm = pair ? Shape<true>::TM : Shape<false>::TM;
+
+  Params *P = new Params;
+  std::memset(P, 0, sizeof(Params));
+  std::vector<Group> tmp(MAX_GROUPS);
+  std::vector<double> cost(count);
+  int gused = 0;
+  double work = 0.0;
+  for (int i = 0; i < count; ++i) {
+    const TcLeafArgs &a = as[i];
+    MultiProb &b = P->mp[i];
+    if ((e = encode_planes(&b.tmx, a.x, BM)) != cudaSuccess ||
+        (e = encode_planes(&b.tmy, a.y, pair ? Shape<true>::YROWS : Shape<false>::YROWS)) !=
+            cudaSuccess) {
+      delete P;
+      return e;
+    }
+    int ng = 0, nprod = 0;
+    if (!build_groups(a, m, tmp.data(), &ng, &nprod)) {
+      delete P;
+      return cudaErrorInvalidValue;
+    }
+    // problems with the same K, scale and digit form share one group list
+    int goff = -1;
+    for (int j = 0; j < i && goff < 0; ++j)
+      if (P->mp[j].ng == ng &&
+          std::memcmp(P->g + P->mp[j].goff, tmp.data(), sizeof(Group) * ng) == 0)
+        goff = P->mp[j].goff;
+    if (goff < 0) {
+      if (gused + ng > MAX_GROUPS) {
+        delete P;
+        return cudaErrorInvalidValue;
+      }
+      std::memcpy(P->g + gused, tmp.data(), sizeof(Group) * ng);
+      goff = gused;
+      gused += ng;
+    }
+    b.goff = goff;
+    b.ng = ng;
+    b.out = a.out;
+    b.ldo = a.ldo;
+    b.M = a.M;
+    b.N = a.N;
+    b.lower = a.lower;
+    b.accumulate = a.lin.beta.w != 0u;
+    b.beta = a.lin.beta.w;
+    b.beta_sh = a.lin.beta.wsh;
+    cost[i] = (double)((a.K + BK - 1) / BK) * nprod;
+    const double macs =
+        a.lower ? 0.5 * (double)a.M * (double)(a.M + 1) * a.K : (double)a.M * a.N * a.K;
+    work += 2.0 * nprod * macs;
+  }
+  P->ng = gused;
+  // the problems with the most expensive tiles first
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int u, int v) { return cost[u] > cost[v]; });
+  int4 *tiles = nullptr;
+  int nt = 0;
+  if ((e = get_multi_tiles(dev, as, order.data(), count, tm, &tiles, &nt)) != cudaSuccess) {
+    delete P;
+    return e;
+  }
+  P->mtiles = tiles;
+  P->ntiles = nt;
+  P->m = m;
+  P->status = device_status_ptr();
+  static std::map<int, bool> attr;
+  if (!attr[dev]) {
+    if ((e = cudaFuncSetAttribute(leaf_tc_kernel<kMulti, false, kEwLeaf>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)Shape<false, kEwLeaf>::SMEM)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(leaf_tc_kernel<kMulti, true, kEwLeaf>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)Shape<true, kEwLeaf>::SMEM)) != cudaSuccess) {
+      delete P;
+      return e;
+    }
+    attr[dev] = true;
+  }
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (nt > 0) {
+    ProfScope prof(AAT_K_LEAF_TC, st, work);
+    if (pair) {
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute attr1[1];
+      attr1[0].id = cudaLaunchAttributeClusterDimension;
+      attr1[0].val.clusterDim.x = 2;
+      attr1[0].val.clusterDim.y = 1;
+      attr1[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3(2 * std::max(1, std::min(nt, units)), 1, 1);
+      cfg.blockDim = dim3(Shape<true, kEwLeaf>::THREADS, 1, 1);
+      cfg.dynamicSmemBytes = Shape<true, kEwLeaf>::SMEM;
+      cfg.stream = st;
+      cfg.attrs = attr1;
+      cfg.numAttrs = 1;
+      e = cudaLaunchKernelEx(&cfg, leaf_tc_kernel<kMulti, true, kEwLeaf>, *P);
+      if (e != cudaSuccess) {
+        delete P;
+        return e;
+      }
+    } else {
+      leaf_tc_kernel<kMulti, false, kEwLeaf>
           <<<std::max(1, std::min(nt, sms)), Shape<false, kEwLeaf>::THREADS,
              Shape<false, kEwLeaf>::SMEM, st>>>(*P);
     }
@@ -1017,7 +1237,7 @@ cudaError_t leaf_tc_batch_launch(const LeafBatch &lb, cudaStream_t st) {
     std::lock_guard<std::mutex> lock(g_mu);
     static std::map<int, bool> attr;
     if (!attr[dev]) {
-      cudaError_t e = cudaFuncSetAttribute(leaf_tc_kernel<true, false, kEwBatch>,
+      cudaError_t e = cudaFuncSetAttribute(leaf_tc_kernel<kBatch, false, kEwBatch>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)Shape<false, kEwBatch>::SMEM);
       if (e != cudaSuccess) return e;
@@ -1035,7 +1255,7 @@ cudaError_t leaf_tc_batch_launch(const LeafBatch &lb, cudaStream_t st) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   {
     ProfScope prof(AAT_K_LEAF_TC, st, L->work);
-    leaf_tc_kernel<true, false, kEwBatch>
+    leaf_tc_kernel<kBatch, false, kEwBatch>
         <<<std::max(1, std::min(L->ntiles, sms)), Shape<false, kEwBatch>::THREADS,
            Shape<false, kEwBatch>::SMEM, st>>>(*P);
   }
@@ -1058,6 +1278,9 @@ void leaf_tc_release() {
   for (auto &kv : g_tiles)
     if (kv.second.first) cudaFree(kv.second.first);
   g_tiles.clear();
+  for (auto &kv : g_mtiles)
+    if (kv.second.first) cudaFree(kv.second.first);
+  g_mtiles.clear();
   g_attr_set.clear();
   g_pair_units.clear();
 }
@@ -1201,30 +1424,22 @@ extern "C" AAT_API int aat_gemm_modp_noalloc(const int32_t *X, int64_t ldx, cons
   std::memset(&P, 0, sizeof(P));
   if (encode_planes(&P.tmx, px, BM) != cudaSuccess || encode_planes(&P.tmy, py, BN) != cudaSuccess)
     return report_error(AAT_ECUDA, "tensor map encoding failed");
-  // digit pairs in decreasing weight 2^(b (i + j)); Horner ratios between them
-  const int kblocks = (int)((k + BK - 1) / BK);
-  const int64_t room = ((int64_t)1 << 31) - 1 - (int64_t)mp.half;
-  int ng = 0, prev_s = -1;
-  for (int s = 2 * (ds.L - 1); s >= 0; --s)
-    for (int i = 0; i < ds.L; ++i) {
-      const int j = s - i;
-      if (j < 0 || j >= ds.L) continue;
-      const int64_t prod = std::max<int64_t>((int64_t)ds.dmax[i] * ds.dmax[j], 1);
-      const int64_t kc = std::max<int64_t>(((int64_t)1 << 23) / prod / BK, 1);
-      const int64_t kr = std::max<int64_t>(room / prod / BK, 1);
-      for (int kb = 0; kb < kblocks; kb += (int)kr) {
-        if (ng >= MAX_GROUPS) return report_error(AAT_ERANGE, "too many digit groups");
-        Group &g = P.g[ng++];
-        g.xp = (int16_t)i;
-        g.yp = (int16_t)j;
-        g.kb0 = kb;
-        g.kb1 = (int)std::min<int64_t>(kblocks, kb + kr);
-        g.kchunk = (int)std::min<int64_t>(kc, 1 << 20);
-        g.ratio = (prev_s < 0) ? 1u : pow2mod((uint64_t)ds.b * (uint64_t)(prev_s - s), mp.p);
-        prev_s = s;
-      }
-    }
-  set_shoup(P.g, ng, mp.p);
+  // the digit-pair groups of the shared builder (plain digit products, as
+  // the scratch holds no pair-sum planes), ending with the final multiplier
+  TcLeafArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.x = px;
+  a.y = py;
+  a.dx = a.dy = ds;
+  a.dx.nsum = a.dy.nsum = 0;
+  a.M = m;
+  a.N = n;
+  a.K = k;
+  a.exact_bits = 24;
+  a.lin = lin_of(1, 0, p);
+  int ng = 0, nprod = 0;
+  if (!build_groups(a, mp, P.g, &ng, &nprod))
+    return report_error(AAT_ERANGE, "leaf product does not fit the group table");
   P.ng = ng;
   P.out = C;
   P.ldo = ldc;
@@ -1238,7 +1453,7 @@ extern "C" AAT_API int aat_gemm_modp_noalloc(const int32_t *X, int64_t ldx, cons
   P.tiles = tiles_dev;
   P.ntiles = (int)(TI * TJ);
   if (!g_attr_set[dev]) {
-    ce = cudaFuncSetAttribute(leaf_tc_kernel<false, false, kEwLeaf>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    ce = cudaFuncSetAttribute(leaf_tc_kernel<kSingle, false, kEwLeaf>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)Shape<false, kEwLeaf>::SMEM);
     if (ce != cudaSuccess) return report_error(AAT_ECUDA, cudaGetErrorString(ce));
     g_attr_set[dev] = true;
@@ -1246,7 +1461,7 @@ extern "C" AAT_API int aat_gemm_modp_noalloc(const int32_t *X, int64_t ldx, cons
   int sms = 148;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = std::max(1, std::min(P.ntiles, sms));
-  leaf_tc_kernel<false, false, kEwLeaf>
+  leaf_tc_kernel<kSingle, false, kEwLeaf>
       <<<grid, Shape<false, kEwLeaf>::THREADS, Shape<false, kEwLeaf>::SMEM, st>>>(P);
   ce = cudaGetLastError();
   return ce == cudaSuccess ? AAT_OK : report_error(AAT_ECUDA, cudaGetErrorString(ce));

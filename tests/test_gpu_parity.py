@@ -462,3 +462,41 @@ def test_quaternion_aah_other_leaf_and_zero_upper(lib):
     for q in range(4):
         got = host(H[q])
         assert low_equal(got, want[q]) and not np.triu(got, 1).any()
+
+
+_FORM_SCRIPT = r"""
+import sys
+import numpy as np
+import torch
+import oracle
+import paper_2101_01025_gb300 as aat
+from paper_2101_01025_gb300 import synth
+for p in (65521, 2**31 - 1):
+    for n, k, levels in ((1536, 1024, 1), (1024, 2048, 2), (520, 264, 1)):
+        A = synth.residues(n * 3 + k + p % 97, (n, k), p)
+        C = aat.aat_modp(torch.from_numpy(A).cuda(), p, levels=levels)
+        torch.cuda.synchronize()
+        got = np.tril(C.cpu().numpy().astype(np.int64))
+        ref = np.tril(np.asarray(oracle.aat_modp_low(A, p), dtype=np.int64))
+        if not np.array_equal(got, ref):
+            print("MISMATCH", p, n, k, levels)
+            sys.exit(1)
+assert aat.aat_device_status() == 0
+print("OK")
+"""
+
+
+@pytest.mark.parametrize("env", [{"AAT_LEAF_FUSE": "0"}, {"AAT_LEAF_PAIR": "1"},
+                                 {"AAT_LEAF_PAIR": "0"}])
+def test_leaf_launch_forms(env):
+    """The last level's four independent products run as one launch by
+    default; the same results with one launch per product (AAT_LEAF_FUSE=0)
+    and with every leaf forced onto the CTA-pair or the one-CTA form (these
+    switches are read once per process, so each runs in a child process)."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _FORM_SCRIPT], cwd=root,
+                       env={**os.environ, **env}, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0 and "OK" in r.stdout, r.stdout + r.stderr
