@@ -18,6 +18,11 @@ one level, on the locations the table names.
 Sec. 6.2 over F_p.
 
 ``two_m`` takes the steps of Algorithm 2 (Sec. 6.1) with K = R, E = C.
+
+``winograd_gemm`` takes the steps of one level of Winograd's variant of
+Strassen's algorithm (7 block products, 15 block additions; the MM_omega of
+Theorem 3.1 and Table 1 with omega = log2 7) for a general product X Y^T mod
+p; ``alg1_low_aat`` can use it for its two general products P3 and P4.
 """
 from __future__ import annotations
 
@@ -61,11 +66,13 @@ def dense_y(ykind, ya, yb, p, kappa):
     raise ValueError("unknown ykind")
 
 
-def alg1_low_aat(A, p, ykind, ya, yb, levels, trace=None):
+def alg1_low_aat(A, p, ykind, ya, yb, levels, trace=None, gemm=None):
     """Low(A A^T) mod p by Algorithm 1 applied ``levels`` times.
 
     ``trace`` (a list) receives, for the top level, a dict with S1..S4,
-    P1..P5, U1..U5 (all mod p) when given."""
+    P1..P5, U1..U5 (all mod p) when given.  ``gemm(X, Y, p)`` (X Y^T mod p)
+    computes the general products P3 and P4 of every level when given;
+    otherwise they are plain products."""
     A = _obj(A) % p
     n, k = A.shape
     need = 4 if ykind == 2 else 2
@@ -81,11 +88,15 @@ def alg1_low_aat(A, p, ykind, ya, yb, levels, trace=None):
     S3 = (S1 - A22) % p
     S4 = (S3 + A12) % p
     # 3 recursive and 2 general products
-    P1 = alg1_low_aat(A11, p, ykind, ya, yb, levels - 1)
-    P2 = alg1_low_aat(A12, p, ykind, ya, yb, levels - 1)
-    P3 = (A22 @ S4.T) % p
-    P4 = (S1 @ S2.T) % p
-    P5 = alg1_low_aat(S3, p, ykind, ya, yb, levels - 1)
+    P1 = alg1_low_aat(A11, p, ykind, ya, yb, levels - 1, gemm=gemm)
+    P2 = alg1_low_aat(A12, p, ykind, ya, yb, levels - 1, gemm=gemm)
+    if gemm is None:
+        P3 = (A22 @ S4.T) % p
+        P4 = (S1 @ S2.T) % p
+    else:
+        P3 = _obj(gemm(A22, S4, p)) % p
+        P4 = _obj(gemm(S1, S2, p)) % p
+    P5 = alg1_low_aat(S3, p, ykind, ya, yb, levels - 1, gemm=gemm)
     # 3 half additions and 2 complete additions
     U1_low = (P1 + P5) % p
     U3_low = (P1 + P2) % p
@@ -215,3 +226,61 @@ def two_m(Are, Aim, conj=True):
     else:
         im = H + H.T          # H i + i H^T
     return re, im
+
+
+def winograd_gemm(X, Y, p, trace=None):
+    """X Y^T mod p by one level of Winograd's form of Strassen's algorithm.
+
+    With A = X (M x K) and B = Y^T (K x N), both cut into 2 x 2 blocks (M, N,
+    K even), Winograd's form takes 8 additions before the products
+        S1 = A21 + A22, S2 = S1 - A11, S3 = A11 - A21, S4 = A12 - S2,
+        T1 = B12 - B11, T2 = B22 - T1, T3 = B22 - B12, T4 = T2 - B21,
+    7 block products
+        P1 = A11 B11, P2 = A12 B21, P3 = S4 B22, P4 = A22 T4,
+        P5 = S1 T1,   P6 = S2 T2,   P7 = S3 T3,
+    and 7 additions after them
+        U1 = P1 + P2, U2 = P1 + P6, U3 = U2 + P7, U4 = U2 + P5,
+        U5 = U4 + P3, U6 = U3 - P4, U7 = U3 + P5,
+    giving C11 = U1, C12 = U5, C21 = U6, C22 = U7.  Every block sum is taken
+    mod p.  ``trace`` receives the blocks when given."""
+    X = _obj(X) % p
+    Y = _obj(Y) % p
+    M, K = X.shape
+    N = Y.shape[0]
+    if M % 2 or N % 2 or K % 2:
+        raise ValueError("M, N and K must be even")
+    m, n, k = M // 2, N // 2, K // 2
+    B = Y.T
+    A11, A12, A21, A22 = X[:m, :k], X[:m, k:], X[m:, :k], X[m:, k:]
+    B11, B12, B21, B22 = B[:k, :n], B[:k, n:], B[k:, :n], B[k:, n:]
+    S1 = (A21 + A22) % p
+    S2 = (S1 - A11) % p
+    S3 = (A11 - A21) % p
+    S4 = (A12 - S2) % p
+    T1 = (B12 - B11) % p
+    T2 = (B22 - T1) % p
+    T3 = (B22 - B12) % p
+    T4 = (T2 - B21) % p
+    P1 = (A11 @ B11) % p
+    P2 = (A12 @ B21) % p
+    P3 = (S4 @ B22) % p
+    P4 = (A22 @ T4) % p
+    P5 = (S1 @ T1) % p
+    P6 = (S2 @ T2) % p
+    P7 = (S3 @ T3) % p
+    U1 = (P1 + P2) % p
+    U2 = (P1 + P6) % p
+    U3 = (U2 + P7) % p
+    U4 = (U2 + P5) % p
+    U5 = (U4 + P3) % p
+    U6 = (U3 - P4) % p
+    U7 = (U3 + P5) % p
+    C = np.zeros((M, N), dtype=object)
+    C[:m, :n] = U1
+    C[:m, n:] = U5
+    C[m:, :n] = U6
+    C[m:, n:] = U7
+    if trace is not None:
+        trace.append(dict(S=(S1, S2, S3, S4), T=(T1, T2, T3, T4),
+                          P=(P1, P2, P3, P4, P5, P6, P7)))
+    return C

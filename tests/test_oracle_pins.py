@@ -609,3 +609,76 @@ def test_quat_6m_algorithm_equals_definition(p):
     got = alg1.quat_6m(A, B, C, D, p)
     for q in range(4):
         assert np.array_equal(np.asarray(got[q], dtype=np.int64), want[q].astype(np.int64)), q
+
+
+# --------------------------------------------- Winograd's form of Strassen
+
+@pytest.mark.parametrize("p", [3, 13, 65521, 131071, 2**31 - 1])
+@pytest.mark.parametrize("M,N,K", [(2, 2, 2), (4, 6, 8), (10, 4, 6), (12, 12, 20)])
+def test_winograd_equals_definition(p, M, N, K):
+    """One Winograd level equals the plain product X Y^T mod p."""
+    X = synth.residues(p % 1000 + M * 7 + K, (M, K), p).astype(object)
+    Y = synth.residues(p % 999 + N * 5 + K, (N, K), p).astype(object)
+    ref = (X @ Y.T) % p
+    tr = []
+    got = alg1.winograd_gemm(X, Y, p, trace=tr)
+    assert np.array_equal(got, ref)
+    assert len(tr[0]["P"]) == 7            # seven block products
+    # the C oracle's general product agrees as well
+    assert np.array_equal(oracle.gemm_modp(X.astype(np.int64).astype(np.int32),
+                                           Y.astype(np.int64).astype(np.int32), p)
+                          .astype(np.int64).astype(object), ref)
+
+
+def test_winograd_scalar_blocks_exhaustive_f3():
+    """Every 2 x 2 X and Y over F_3 (1 x 1 blocks): 3^8 cases, brute force."""
+    import itertools
+    p = 3
+    vals = list(itertools.product(range(3), repeat=4))
+    for x in vals:
+        X = np.array(x, dtype=object).reshape(2, 2)
+        for y in vals:
+            Y = np.array(y, dtype=object).reshape(2, 2)
+            ref = np.array([[sum(X[i, l] * Y[j, l] for l in range(2)) % p for j in range(2)]
+                            for i in range(2)], dtype=object)
+            assert np.array_equal(alg1.winograd_gemm(X, Y, p), ref)
+
+
+def test_winograd_every_product_contributes():
+    """Dropping any one of the seven products changes the result: each
+    block of C uses the products Winograd's form assigns to it."""
+    p = 65521
+    X = synth.residues(5, (4, 4), p).astype(object)
+    Y = synth.residues(6, (4, 4), p).astype(object)
+    tr = []
+    alg1.winograd_gemm(X, Y, p, trace=tr)
+    P = tr[0]["P"]
+    uses = {0: {(0, 0), (0, 1), (1, 0), (1, 1)}, 1: {(0, 0)}, 2: {(0, 1)}, 3: {(1, 0)},
+            4: {(0, 1), (1, 1)}, 5: {(0, 1), (1, 0), (1, 1)}, 6: {(1, 0), (1, 1)}}
+    ref = (X @ Y.T) % p
+    for q in range(7):
+        assert np.any(P[q] % p != 0)
+        # U1..U7 rebuilt without product q: the blocks that use it change
+        Pz = [P[i] if i != q else 0 * P[i] for i in range(7)]
+        U2 = Pz[0] + Pz[5]
+        U3 = U2 + Pz[6]
+        U4 = U2 + Pz[4]
+        blocks = {(0, 0): Pz[0] + Pz[1], (0, 1): U4 + Pz[2], (1, 0): U3 - Pz[3],
+                  (1, 1): U3 + Pz[4]}
+        for (bi, bj), B in blocks.items():
+            same = np.array_equal(B % p, ref[2 * bi:2 * bi + 2, 2 * bj:2 * bj + 2])
+            assert same == ((bi, bj) not in uses[q])
+
+
+@pytest.mark.parametrize("p", [65521, 131071, 2**31 - 1])
+@pytest.mark.parametrize("n,k", [(8, 8), (16, 16), (16, 24)])
+def test_alg1_with_winograd_general_products(p, n, k):
+    """Algorithm 1 with Winograd's form for P3 and P4 gives the definition."""
+    kind, a, b = oracle.skew_unitary_params(p)
+    A = synth.residues(p % 1000 + 3 * n + k, (n, k), p)
+    ref = _exact_low(A, p)
+    for levels in (1, 2):
+        if (n >> levels) % 2 or (k >> levels) % 2:
+            continue
+        C = alg1.alg1_low_aat(A, p, kind, a, b, levels, gemm=alg1.winograd_gemm)
+        assert np.array_equal(C.astype(np.int64), ref), levels
