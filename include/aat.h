@@ -68,6 +68,12 @@ extern "C" {
 /* tensor-core leaf: one product per digit pair (i, j) instead of the
  * pair-sum form that needs L + L(L-1)/2 products (comparison path). */
 #define AAT_DIGITS_PLAIN (1u << 12)
+/* tensor-core leaf: the two general products P3, P4 of the last recursion
+ * level by one level of Winograd's form of Strassen's algorithm (7 products
+ * of half the size instead of 8; the MM_omega of Theorem 3.1 and Table 1
+ * with omega = log2 7).  Applies where the last level's blocks have even
+ * sides; the result is the same. */
+#define AAT_WINOGRAD (1u << 13)
 
 /*
  * Low(A A^T) mod p (Algorithm 1, Sec. 3; Low as defined in Sec. 2).
@@ -311,6 +317,7 @@ AAT_API int aat_device_status(int reset);
 #define AAT_K_COPY 6
 #define AAT_K_LEAF_F32 7
 #define AAT_K_LEAF_MMA 8
+#define AAT_K_WINOGRAD 9 /* Winograd operand and combine kernels */
 #define AAT_K_NCLASS 10
 typedef struct {
   int64_t launches[AAT_K_NCLASS];

@@ -17,7 +17,7 @@ import os
 
 from . import _native
 from ._native import (AAT_C_BF16, AAT_C_BF16X3, AAT_C_FP32, AAT_DIGITS_PLAIN,  # noqa: F401
-                      AAT_IN_BALANCED, AAT_LEAF_F64, AAT_LEAF_I8, AAT_LEAF_SIMT, AAT_LEAF_TC, AAT_LEVELS, AAT_ZERO_UPPER, AatError, PlanStats, check, last_error, lib)
+                      AAT_IN_BALANCED, AAT_LEAF_F64, AAT_LEAF_I8, AAT_LEAF_SIMT, AAT_LEAF_TC, AAT_LEVELS, AAT_WINOGRAD, AAT_ZERO_UPPER, AatError, PlanStats, check, last_error, lib)
 
 __all__ = [
     "aat_modp", "aat_syrk_modp", "aah_quat_modp", "aat_gemm_modp", "aat_modp_host", "aat_modp_host_d2h_bytes", "aat_workspace_size",

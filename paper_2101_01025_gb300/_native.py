@@ -29,6 +29,7 @@ AAT_LEAF_SIMT = 1 << 4
 AAT_LEAF_I8 = 2 << 4
 AAT_LEAF_F64 = 3 << 4
 AAT_DIGITS_PLAIN = 1 << 12
+AAT_WINOGRAD = 1 << 13
 AAT_C_FP32 = 0 << 16
 AAT_C_BF16X3 = 1 << 16
 AAT_C_BF16 = 2 << 16
@@ -111,7 +112,7 @@ class PlanStats(ctypes.Structure):
 
 #: kernel classes of aat_profile_t
 K_CLASSES = ["sblocks", "split", "leaf_tc", "leaf_simt", "postadd", "add_low", "copy", "leaf_f32",
-             "leaf_mma", "unused"]
+             "leaf_mma", "winograd"]
 
 
 class Profile(ctypes.Structure):

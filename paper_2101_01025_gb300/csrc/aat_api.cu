@@ -401,6 +401,7 @@ struct Ctx {
   // device complete at these events; the stream waits for them
   cudaEvent_t in_a11 = nullptr, in_rest = nullptr;
   uint32_t alpha = 1;  // scale of every product (the SYRK update's alpha)
+  bool wino = false;   // last level's P3, P4 by Winograd's form (AAT_WINOGRAD)
 };
 
 static Planes planes_for(const DigitSpec &ds, int64_t rows, int64_t cols) {
@@ -535,7 +536,8 @@ struct LevelOps {
 // pA11: digit planes of A11 already split (the end-to-end path computes P1
 // before the rest of A arrives), or none.
 static LevelOps sblocks_step(Ctx &c, const int32_t *A, int64_t lda, int64_t h, int64_t kap,
-                             int32_t *S3, int64_t ldS3, bool last, Planes pA11 = Planes{}) {
+                             int32_t *S3, int64_t ldS3, bool last, Planes pA11 = Planes{},
+                             bool wino = false) {
   const bool tc = (c.leaf == AAT_LEAF_TC);
   const int32_t *A22 = A + h * lda + kap;
   SKernelOut o;
@@ -549,10 +551,22 @@ static LevelOps sblocks_step(Ctx &c, const int32_t *A, int64_t lda, int64_t h, i
   L.oA22 = Operand{A22, lda, no_planes()};
   L.pA11 = L.pA12 = L.pS3 = no_planes();
   if (tc) {
-    o.sp[0] = L.oS1.pl = planes_alloc(c, h, kap);
-    o.sp[1] = L.oS2.pl = planes_alloc(c, h, kap);
-    o.sp[3] = L.oS4.pl = planes_alloc(c, h, kap);
-    o.a22 = L.oA22.pl = planes_alloc(c, h, kap);
+    if (wino) {
+      // Winograd's form forms its own operand blocks from int32 S1, S2, S4
+      // (and from A22 itself)
+      for (int q : {0, 1, 3}) {
+        o.s[q] = (int32_t *)c.ar.get((size_t)h * kap * 4);
+        o.lds[q] = kap;
+      }
+      L.oS1 = Operand{o.s[0], kap, no_planes()};
+      L.oS2 = Operand{o.s[1], kap, no_planes()};
+      L.oS4 = Operand{o.s[3], kap, no_planes()};
+    } else {
+      o.sp[0] = L.oS1.pl = planes_alloc(c, h, kap);
+      o.sp[1] = L.oS2.pl = planes_alloc(c, h, kap);
+      o.sp[3] = L.oS4.pl = planes_alloc(c, h, kap);
+      o.a22 = L.oA22.pl = planes_alloc(c, h, kap);
+    }
     if (last) {
       if (pA11.L)
         L.pA11 = pA11;
@@ -585,12 +599,61 @@ static void count_level(Ctx &c) {
   }
 }
 
-// The independent leaf products of a last level in one launch (default), or
-// one launch per product with AAT_LEAF_FUSE=0.
-static bool fuse_leaves() {
-  static const bool v = [] {
+// Steps 2-5 of a last level with Winograd's form for the general products:
+// P4^T = S2 S1^T and P3 = A22 S4^T each become seven products of half the
+// size (operand blocks from one pass over S2, S1, A22, S4), which run in one
+// persistent launch together with the symmetric products `sym` (P5, and P1
+// unless it ran first); the seven additions after them write C22 and C21.
+static void wino_products(Ctx &c, const LevelOps &L, const int32_t *A22, int64_t lda, int64_t h,
+                          int64_t kap, int32_t *C21, int32_t *C22, int64_t ldc,
+                          const TcLeafArgs *sym, int nsym) {
+  const int64_t R = h / 2, Kq = kap / 2, ldw = (R + 3) / 4 * 4;
+  WinoPlanes w[4];  // left and right operands of P4^T, then of P3
+  for (WinoPlanes &wp : w)
+    for (Planes &q : wp.q) q = planes_alloc(c, R, Kq);
+  int32_t *W4 = (int32_t *)c.ar.get((size_t)7 * R * ldw * 4);
+  int32_t *W3 = (int32_t *)c.ar.get((size_t)7 * R * ldw * 4);
+  if (!c.ar.dry && c.err == AAT_OK) {
+    check(c, launch_wino_operands(L.oS2.x, L.oS2.ld, R, Kq, c.m, c.ds.b, false, w[0], c.st),
+          "Winograd operands");
+    check(c, launch_wino_operands(L.oS1.x, L.oS1.ld, R, Kq, c.m, c.ds.b, true, w[1], c.st),
+          "Winograd operands");
+    check(c, launch_wino_operands(A22, lda, R, Kq, c.m, c.ds.b, false, w[2], c.st),
+          "Winograd operands");
+    check(c, launch_wino_operands(L.oS4.x, L.oS4.ld, R, Kq, c.m, c.ds.b, true, w[3], c.st),
+          "Winograd operands");
+  }
+  // products W_q = left[lx[q]] right[ry[q]]^T: X11 Y11^T, X12 Y12^T,
+  // S4 Y22^T, X22 V4^T, S1 V1^T, S2 V2^T, S3 V3^T
+  static const int lx[7] = {0, 1, 6, 2, 3, 4, 5}, ry[7] = {0, 1, 2, 6, 3, 4, 5};
+  TcLeafArgs fa[16];
+  int n = 0;
+  for (int side = 0; side < 2; ++side) {
+    int32_t *W = side ? W3 : W4;
+    for (int q = 0; q < 7; ++q) {
+      fa[n] = tc_args(c, w[2 * side].q[lx[q]], w[2 * side + 1].q[ry[q]], R, R, Kq,
+                      W + (size_t)q * R * ldw, ldw, 0, 0);
+      count_leaf(c, R, R, Kq, 0);
+      ++n;
+    }
+  }
+  for (int q = 0; q < nsym; ++q) {
+    fa[n++] = sym[q];
+    count_leaf(c, sym[q].M, sym[q].N, sym[q].K, sym[q].lower);
+  }
+  if (c.ar.dry || c.err != AAT_OK) return;
+  check(c, launch_leaf_tc_multi(fa, n, c.m, c.st), "leaf (tensor cores, Winograd products)");
+  check(c, launch_wino_combine(W4, ldw, R * ldw, C22, ldc, R, R, c.m, c.st), "Winograd sums");
+  check(c, launch_wino_combine(W3, ldw, R * ldw, C21, ldc, R, R, c.m, c.st), "Winograd sums");
+}
+
+// The independent leaf products of a last level in one launch or one launch
+// per product: AAT_LEAF_FUSE=1 / 0 forces either, otherwise the launcher
+// decides from the idle share of the separate launches' last waves.
+static int fuse_override() {
+  static const int v = [] {
     const char *e = getenv("AAT_LEAF_FUSE");
-    return !(e && atoi(e) == 0);
+    return e ? (atoi(e) != 0 ? 1 : 0) : -1;
   }();
   return v;
 }
@@ -639,26 +702,30 @@ static void rec(Ctx &c, const int32_t *A, int64_t lda, int64_t n, int64_t k, int
     S3 = (int32_t *)c.ar.get((size_t)h * kap * 4);
     ldS3 = kap;
   }
+  // Winograd's form for the last level's general products (blocks of even
+  // sides only)
+  const bool wino = last && c.leaf == AAT_LEAF_TC && c.wino && h % 2 == 0 && kap % 2 == 0;
   // 1. S1..S4 (4 additions, 2 products by Y) in one pass over A
-  const LevelOps L = sblocks_step(c, A, lda, h, kap, S3, ldS3, last, pA11_early);
-  if (last && c.leaf == AAT_LEAF_TC && fuse_leaves()) {
-    // 2-5 at the last level: P4^T, P5, P3 and P1 read only digit planes
-    // written by step 1 and write four different blocks of C, so they run
-    // as one persistent launch over the tiles of all four
-    TcLeafArgs a[4];
-    int np = 0;
-    count_leaf(c, h, h, kap, 0);
-    a[np++] = tc_args(c, L.oS2.pl, L.oS1.pl, h, h, kap, C22, ldc, 0, 0);
-    count_leaf(c, h, h, kap, 1);
-    a[np++] = tc_args(c, L.pS3, L.pS3, h, h, kap, C12, ldc, 1, 0);
-    count_leaf(c, h, h, kap, 0);
-    a[np++] = tc_args(c, L.oA22.pl, L.oS4.pl, h, h, kap, C21, ldc, 0, 0);
-    if (!p1_first) {
-      count_leaf(c, h, h, kap, 1);
-      a[np++] = tc_args(c, L.pA11, L.pA11, h, h, kap, C11, ldc, 1, 0);
-    }
+  const LevelOps L = sblocks_step(c, A, lda, h, kap, S3, ldS3, last, pA11_early, wino);
+  // 2-5 at the last level: P4^T, P5, P3 and P1 read only digit planes
+  // written by step 1 and write four different blocks of C, so they may run
+  // as one persistent launch over the tiles of all four
+  TcLeafArgs fa[4];
+  int nfa = 0;
+  if (last && c.leaf == AAT_LEAF_TC) {
+    fa[nfa++] = tc_args(c, L.oS2.pl, L.oS1.pl, h, h, kap, C22, ldc, 0, 0);
+    fa[nfa++] = tc_args(c, L.pS3, L.pS3, h, h, kap, C12, ldc, 1, 0);
+    fa[nfa++] = tc_args(c, L.oA22.pl, L.oS4.pl, h, h, kap, C21, ldc, 0, 0);
+    if (!p1_first) fa[nfa++] = tc_args(c, L.pA11, L.pA11, h, h, kap, C11, ldc, 1, 0);
+  }
+  const int fo = fuse_override();
+  if (wino) {
+    const TcLeafArgs sym[2] = {fa[1], fa[nfa - 1]};  // P5, and P1 unless it ran first
+    wino_products(c, L, A + h * lda + kap, lda, h, kap, C21, C22, ldc, sym, p1_first ? 1 : 2);
+  } else if (nfa > 0 && (fo == 1 || (fo < 0 && leaf_tc_fuse_pays(fa, nfa)))) {
+    for (int q = 0; q < nfa; ++q) count_leaf(c, fa[q].M, fa[q].N, fa[q].K, fa[q].lower);
     if (!c.ar.dry && c.err == AAT_OK)
-      check(c, launch_leaf_tc_multi(a, np, c.m, c.st), "leaf (tensor cores, P1 P3 P4 P5)");
+      check(c, launch_leaf_tc_multi(fa, nfa, c.m, c.st), "leaf (tensor cores, P1 P3 P4 P5)");
   } else {
     // 2. P4^T = S2 S1^T -> C22
     leaf(c, L.oS2, L.oS1, false, h, h, kap, C22, ldc, 0, 0);
@@ -833,6 +900,8 @@ static int setup(Ctx &c, uint32_t p, uint32_t flags, cudaStream_t st) {
   // FP64 leaf: partial sums of 16 products of ((p-1)/2)^2 must stay below 2^53
   if (c.leaf == AAT_LEAF_F64 && (double)c.m.half * (double)c.m.half * 16.0 >= 9.0e15)
     return fail(AAT_ERANGE, "p too large for the exact FP64 leaf");
+  const char *ew = getenv("AAT_WINOGRAD");
+  c.wino = (flags & AAT_WINOGRAD) != 0 || (ew && atoi(ew) != 0);
   const char *eb = getenv("AAT_EXACT_BITS");
   c.exact_bits = eb ? atoi(eb) : 24;
   c.st = st;

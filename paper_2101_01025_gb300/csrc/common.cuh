@@ -272,6 +272,19 @@ cudaError_t launch_sblocks(const int32_t *A, int64_t lda, int64_t h, int64_t kap
                            const ModP &m, const YParams &y, int b,
                            const SKernelOut &o, cudaStream_t st);
 
+// Winograd's form of Strassen's algorithm for a general product X Y^T (one
+// level): the digit planes of the seven operand blocks of one side (left:
+// X11, X12, X22, S1..S4; right: Y11, Y12, Y22, V1..V4, see k_adds.cu), and
+// the seven additions after the products.
+struct WinoPlanes {
+  Planes q[7];
+};
+cudaError_t launch_wino_operands(const int32_t *Z, int64_t ldz, int64_t R, int64_t K, const ModP &m,
+                                 int b, bool right, const WinoPlanes &o, cudaStream_t st);
+cudaError_t launch_wino_combine(const int32_t *W, int64_t ldw, int64_t wstride, int32_t *C,
+                                int64_t ldc, int64_t R, int64_t N, const ModP &m,
+                                cudaStream_t st);
+
 // Split an int32 residue block into digit planes.
 cudaError_t launch_split(const int32_t *X, int64_t ldx, int64_t rows, int64_t cols,
                          const ModP &m, int b, const Planes &P, cudaStream_t st);
@@ -365,6 +378,9 @@ cudaError_t launch_leaf_tc(const TcLeafArgs &a, const ModP &m, cudaStream_t st);
 // persistent launch (one tile list over all of them).
 cudaError_t launch_leaf_tc_multi(const TcLeafArgs *as, int count, const ModP &m,
                                  cudaStream_t st);
+// Whether that one launch is expected to beat one launch per product (the
+// idle share of the separate launches' last waves).
+bool leaf_tc_fuse_pays(const TcLeafArgs *as, int count);
 void leaf_tc_release();
 
 // A batched tensor-core leaf launch: device tables (per-problem tensor maps,

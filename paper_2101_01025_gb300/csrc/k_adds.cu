@@ -157,6 +157,96 @@ __global__ void split_kernel(const int32_t *__restrict__ X, int64_t ldx, int64_t
   }
 }
 
+// Winograd's form of Strassen's algorithm for a general product X Y^T: the
+// seven operand blocks of one side from the 2 x 2 blocks Z11, Z12, Z21, Z22
+// of an int32 residue block Z (2R x 2K), written as digit planes (R x K).
+//   left operand (A = X):        X11, X12, X22, S1 = X21 + X22, S2 = S1 - X11,
+//                                S3 = X11 - X21, S4 = X12 - S2
+//   right operand (B = Y^T, kept in Y's row layout, so T_i = V_i^T):
+//                                Y11, Y12, Y22, V1 = Y21 - Y11, V2 = Y22 - V1,
+//                                V3 = Y22 - Y21, V4 = V2 - Y12
+// The seven products are then X11 Y11^T, X12 Y12^T, S4 Y22^T, X22 V4^T,
+// S1 V1^T, S2 V2^T, S3 V3^T.
+template <int V, int NB>
+__global__ void wino_operands_kernel(const int32_t *__restrict__ Z, int64_t ldz, int64_t R,
+                                     int64_t K, ModP m, int b, int right, WinoPlanes o) {
+  const int64_t ncols = K / V;
+  const int64_t total = R * ncols;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / ncols;
+    const int64_t j = (t - i * ncols) * V;
+    const int32_t *r1 = Z + i * ldz, *r2 = Z + (R + i) * ldz;
+    int32_t z11[V], z12[V], z21[V], z22[V];
+    ldv_bal<V>(r1 + j, m, z11);
+    ldv_bal<V>(r1 + K + j, m, z12);
+    ldv_bal<V>(r2 + j, m, z21);
+    ldv_bal<V>(r2 + K + j, m, z22);
+    int32_t u[4][V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      if (right) {
+        u[0][v] = sub_bal(z21[v], z11[v], m);   // V1
+        u[1][v] = sub_bal(z22[v], u[0][v], m);  // V2
+        u[2][v] = sub_bal(z22[v], z21[v], m);   // V3
+        u[3][v] = sub_bal(u[1][v], z12[v], m);  // V4
+      } else {
+        u[0][v] = add_bal(z21[v], z22[v], m);   // S1
+        u[1][v] = sub_bal(u[0][v], z11[v], m);  // S2
+        u[2][v] = sub_bal(z11[v], z21[v], m);   // S3
+        u[3][v] = sub_bal(z12[v], u[1][v], m);  // S4
+      }
+    }
+    store_digits_t<NB, V>(o.q[0], i, j, z11, b);
+    store_digits_t<NB, V>(o.q[1], i, j, z12, b);
+    store_digits_t<NB, V>(o.q[2], i, j, z22, b);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) store_digits_t<NB, V>(o.q[3 + q], i, j, u[q], b);
+  }
+}
+
+// The seven additions after Winograd's products W1..W7 (canonical int32,
+// R x N each, W_q at W + q wstride): C11 = W1 + W2, U2 = W1 + W6,
+// U3 = U2 + W7, U4 = U2 + W5, C12 = U4 + W3, C21 = U3 - W4, C22 = U3 + W5;
+// C (2R x 2N) canonical.
+template <int V>
+__global__ void wino_combine_kernel(const int32_t *__restrict__ W, int64_t ldw, int64_t wstride,
+                                    int32_t *C, int64_t ldc, int64_t R, int64_t N, ModP m) {
+  const int64_t ncols = N / V;
+  const int64_t total = R * ncols;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / ncols;
+    const int64_t j = (t - i * ncols) * V;
+    int32_t w[7][V];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) ldv_bal<V>(W + q * wstride + i * ldw + j, m, w[q]);
+    int32_t c11[V], c12[V], c21[V], c22[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      c11[v] = add_bal(w[0][v], w[1][v], m);
+      const int32_t u2 = add_bal(w[0][v], w[5][v], m);
+      const int32_t u3 = add_bal(u2, w[6][v], m);
+      const int32_t u4 = add_bal(u2, w[4][v], m);
+      c12[v] = add_bal(u4, w[2][v], m);
+      c21[v] = sub_bal(u3, w[3][v], m);
+      c22[v] = add_bal(u3, w[4][v], m);
+    }
+    int32_t *o1 = C + i * ldc + j, *o2 = C + (R + i) * ldc + j;
+    if constexpr (V == 4) {
+      st4_canon(o1, c11, m);
+      st4_canon(o1 + N, c12, m);
+      st4_canon(o2, c21, m);
+      st4_canon(o2 + N, c22, m);
+    } else {
+      o1[0] = (int32_t)bal_to_canon(c11[0], m);
+      o1[N] = (int32_t)bal_to_canon(c12[0], m);
+      o2[0] = (int32_t)bal_to_canon(c21[0], m);
+      o2[N] = (int32_t)bal_to_canon(c22[0], m);
+    }
+  }
+}
+
 // Batched split: every problem owns ceil(rows / kSplitRows) consecutive
 // blocks (first_block ascending), so the work of a block does not depend on
 // how large its problem is; a block finds its problem by binary search and
@@ -437,6 +527,51 @@ cudaError_t launch_sblocks(const int32_t *A, int64_t lda, int64_t h, int64_t kap
       return cudaErrorInvalidValue;
   }
 #undef AAT_SB
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wino_operands(const int32_t *Z, int64_t ldz, int64_t R, int64_t K, const ModP &m,
+                                 int b, bool right, const WinoPlanes &o, cudaStream_t st) {
+  const int64_t total = R * K;
+  if (total <= 0) return cudaSuccess;
+  const int nb = o.q[0].nbase;
+  for (int q = 0; q < 7; ++q)
+    if (!o.q[q].ptr || o.q[q].nbase != nb || o.q[q].rows != R || o.q[q].cols != K)
+      return cudaErrorInvalidValue;
+  ProfScope prof(AAT_K_WINOGRAD, st, (double)total * (16.0 + 7.0 * 2.0 * o.q[0].L));
+  bool vec = (K % 4 == 0) && (ldz % 4 == 0) && (((uintptr_t)Z & 15) == 0);
+  for (int q = 0; q < 7; ++q) vec = vec && (((uintptr_t)o.q[q].ptr & 15) == 0);
+  const int g = grid_for(vec ? total / 4 : total);
+  const int rt = right ? 1 : 0;
+#define AAT_WO(NBV)                                                                          \
+  case NBV:                                                                                  \
+    if (vec)                                                                                 \
+      wino_operands_kernel<4, NBV><<<g, kThreads, 0, st>>>(Z, ldz, R, K, m, b, rt, o);       \
+    else                                                                                     \
+      wino_operands_kernel<1, NBV><<<g, kThreads, 0, st>>>(Z, ldz, R, K, m, b, rt, o);       \
+    break;
+  switch (nb) {
+    AAT_WO(1) AAT_WO(2) AAT_WO(3) AAT_WO(4) AAT_WO(5)
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef AAT_WO
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wino_combine(const int32_t *W, int64_t ldw, int64_t wstride, int32_t *C,
+                                int64_t ldc, int64_t R, int64_t N, const ModP &m,
+                                cudaStream_t st) {
+  const int64_t total = R * N;
+  if (total <= 0) return cudaSuccess;
+  ProfScope prof(AAT_K_WINOGRAD, st, (double)total * (7.0 + 4.0) * 4.0);
+  const bool vec = (N % 4 == 0) && (ldw % 4 == 0) && (wstride % 4 == 0) && (ldc % 4 == 0) &&
+                   (((uintptr_t)W & 15) == 0) && (((uintptr_t)C & 15) == 0);
+  const int g = grid_for(vec ? total / 4 : total);
+  if (vec)
+    wino_combine_kernel<4><<<g, kThreads, 0, st>>>(W, ldw, wstride, C, ldc, R, N, m);
+  else
+    wino_combine_kernel<1><<<g, kThreads, 0, st>>>(W, ldw, wstride, C, ldc, R, N, m);
   return cudaGetLastError();
 }
 

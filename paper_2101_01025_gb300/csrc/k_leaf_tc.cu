@@ -34,6 +34,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -675,20 +676,25 @@ cudaError_t encode_planes(CUtensorMap *tm, const Planes &P, int box_rows) {
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-// Tile order: super-blocks of 2048 x 2048 outputs (16 x 8 tiles of 128 x 256,
-// or 8 x 8 of 256 x 256) swept row-major, tiles inside a super-block
-// row-major, so that the CTAs running at the same time share rows of X and
-// columns of Y in L2.  `tm` is the tile height (128 or 256).
+// Tile order: bands of 2048 output rows (8 tile rows of 256, or 16 of 128),
+// each swept column by column.  The persistent CTAs take tiles round robin,
+// so the tiles in flight at any time are about a full wave of consecutive
+// entries: 76 pairs (or 152 CTAs) cover 8 (16) tile rows by ~9.5 tile
+// columns, whose X row panels and Y column panels are read from DRAM once
+// and shared through L2 by every tile of the wave (18 panels per wave of 76
+// tiles against 24 for 8 x 8 super-blocks swept row by row).  `tm` is the
+// tile height (128 or 256).
 void tile_order(int64_t M, int64_t N, int lower, int tm, std::vector<int2> &v) {
   const int64_t TI = (M + tm - 1) / tm, TJ = (N + BN - 1) / BN;
-  const int64_t SI = 2048 / tm, SJ = 8;
-  for (int64_t bi = 0; bi < TI; bi += SI)
-    for (int64_t bj = 0; bj < TJ; bj += SJ)
-      for (int64_t i = bi; i < std::min(TI, bi + SI); ++i)
-        for (int64_t j = bj; j < std::min(TJ, bj + SJ); ++j) {
-          if (lower && j * BN > i * tm + tm - 1) continue;
-          v.push_back(make_int2((int)i, (int)j));
-        }
+  const int64_t band = std::max<int64_t>(1, 2048 / tm);
+  for (int64_t bi = 0; bi < TI; bi += band) {
+    const int64_t iend = std::min(TI, bi + band);
+    for (int64_t j = 0; j < TJ; ++j)
+      for (int64_t i = bi; i < iend; ++i) {
+        if (lower && j * BN > i * tm + tm - 1) continue;
+        v.push_back(make_int2((int)i, (int)j));
+      }
+  }
 }
 
 template <class T>
@@ -997,6 +1003,50 @@ cudaError_t launch_leaf_tc(const TcLeafArgs &a, const ModP &m, cudaStream_t st) 
   }
   delete P;
   return cudaGetLastError();
+}
+
+int64_t tile_count(int64_t M, int64_t N, int lower, int tm) {
+  const int64_t TI = (M + tm - 1) / tm, TJ = (N + BN - 1) / BN;
+  if (!lower) return TI * TJ;
+  int64_t c = 0;
+  for (int64_t i = 0; i < TI; ++i) c += std::min(TJ, (i * tm + tm - 1) / BN + 1);
+  return c;
+}
+
+// Whether one launch over the tiles of several products beats one launch
+// per product: the launches of single products leave part of the GPU idle
+// in their last wave (tiles / units rounded up).  Measured on GB300: one
+// launch wins by 5-10 % when those last waves waste 10-16 % of the slots
+// (4096-sized products), and loses ~5 % at 3-4 % (8192-sized products in
+// a second-long run under the power cap, where idle tails let the clock
+// rise).  So: one launch when more than 6 % of the slots would be idle.
+bool leaf_tc_fuse_pays(const TcLeafArgs *as, int count) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int units = 0;
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    units = pair_units(dev);
+  }
+  double idle = 0.0, all = 0.0;
+  for (int i = 0; i < count; ++i) {
+    const TcLeafArgs &a = as[i];
+    bool pair = false;
+    if (units > 0 && a.M >= 256) {
+      const int64_t pt = ((a.M + 255) / 256) * ((a.N + BN - 1) / BN);
+      const int ov = a.form > 0 ? a.form - 1 : pair_override();
+      pair = ov >= 0 ? ov > 0 : (a.lower ? pt / 2 : pt) >= units;
+    }
+    const int u = pair ? units : sms;
+    const double nt = (double)tile_count(a.M, a.N, a.lower, pair ? 256 : 128);
+    const double slots = std::ceil(nt / u) * u;
+    const double kb = (double)((a.K + BK - 1) / BK);
+    idle += (slots - nt) * kb;
+    all += slots * kb;
+  }
+  return all > 0.0 && idle > 0.06 * all;
 }
 
 // Several independent products of one modulus and digit base in one

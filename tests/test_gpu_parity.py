@@ -336,14 +336,15 @@ def _sample_pairs(n, levels, count, seed):
     return np.array(pairs, dtype=np.int64)
 
 
-def _full_check(lib, A, p, levels_expected_min=1, nsample=3000, nvec=2, levels=None):
+def _full_check(lib, A, p, levels_expected_min=1, nsample=3000, nvec=2, levels=None, flags=0):
     """levels None: the default launch configuration (as bench.py)."""
     from paper_2101_01025_gb300 import _native
     from paper_2101_01025_gb300 import testing as T
     n, k = A.shape
-    st = T.plan_stats(n, k, p) if levels is None else T.plan_stats(n, k, p, _native.AAT_LEVELS(levels))
+    lvf = 0 if levels is None else _native.AAT_LEVELS(levels)
+    st = T.plan_stats(n, k, p, lvf | flags)
     assert st.levels >= levels_expected_min
-    C = lib.aat_modp(dev(A), p, levels=levels)
+    C = lib.aat_modp(dev(A), p, levels=levels, flags=flags)
     Ch = host(C)
     del C
     ij = _sample_pairs(n, st.levels, nsample, seed=n + k)
@@ -355,11 +356,22 @@ def _full_check(lib, A, p, levels_expected_min=1, nsample=3000, nvec=2, levels=N
     return st
 
 
+@functools.lru_cache(maxsize=1)
+def _bench_input():
+    return synth.residues(synth.SEED_BASE + 2, (16384, 16384), 2**31 - 1, balanced=True)
+
+
 def test_full_size_n16384_p2_31m1(lib):
     p = 2**31 - 1
-    A = synth.residues(synth.SEED_BASE + 2, (16384, 16384), p, balanced=True)
-    st = _full_check(lib, A, p, levels_expected_min=1)
+    st = _full_check(lib, _bench_input(), p, levels_expected_min=1)
     assert st.n_pad == 16384
+
+
+def test_full_size_n16384_p2_31m1_winograd(lib):
+    """The bench workload with Winograd's form for the last level's P3, P4."""
+    p = 2**31 - 1
+    st = _full_check(lib, _bench_input(), p, levels_expected_min=1, flags=lib.AAT_WINOGRAD)
+    assert st.general_products == 14 * 3 ** (st.levels - 1) + 2 * (3 ** (st.levels - 1) - 1) // 2
 
 
 @functools.lru_cache(maxsize=4)
@@ -500,3 +512,26 @@ def test_leaf_launch_forms(env):
     r = subprocess.run([sys.executable, "-c", _FORM_SCRIPT], cwd=root,
                        env={**os.environ, **env}, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0 and "OK" in r.stdout, r.stdout + r.stderr
+
+
+# ------------------------------------- Winograd's form for P3 and P4 (Thm 3.1)
+
+@pytest.mark.parametrize("p", PRIMES + [13])
+@pytest.mark.parametrize("n,k", [(8, 8), (300, 200), (256, 512), (640, 640), (1024, 2048),
+                                 (1032, 520), (513, 257)])
+@pytest.mark.parametrize("levels", [1, 2])
+def test_aat_modp_winograd_matches_oracle(lib, p, n, k, levels):
+    """AAT_WINOGRAD: the last level's general products by Winograd's form
+    (ragged quarter blocks, k > n, padded shapes, both kinds of Y)."""
+    A = synth.residues(11 * n + k + levels, (n, k), p)
+    C = host(lib.aat_modp(dev(A), p, levels=levels, flags=lib.AAT_WINOGRAD))
+    assert low_equal(C, oracle.aat_modp_low(A, p))
+
+
+def test_aat_modp_winograd_host_path(lib):
+    """The end-to-end path (P1 computed while the rest of A arrives) with
+    Winograd's form."""
+    p = 2**31 - 1
+    A = synth.residues(17, (1536, 1024), p, balanced=True)
+    C = lib.aat_modp_host(A, p, levels=1, flags=lib.AAT_WINOGRAD)
+    assert low_equal(C, oracle.aat_modp_low(A, p))

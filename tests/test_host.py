@@ -300,3 +300,21 @@ def test_tuning_table_save_load_and_lookup(tmp_path):
     aat.tune_clear()
     with pytest.raises(aat.AatError):
         aat.tune_load(str(tmp_path / "missing.json"))
+
+
+@pytest.mark.parametrize("p", [65521, 2**31 - 1])
+@pytest.mark.parametrize("lv", [1, 2])
+def test_plan_counts_with_winograd(p, lv):
+    """With AAT_WINOGRAD the last level's two general products become 7
+    products of half the size each: ring multiply-adds of the general
+    products at that level fall to 7/8; everything else is unchanged."""
+    n = k = 1024
+    base = T.plan_stats(n, k, p, _native.AAT_LEVELS(lv))
+    st = T.plan_stats(n, k, p, _native.AAT_LEVELS(lv) | _native.AAT_WINOGRAD)
+    last_nodes = 3 ** (lv - 1)                    # nodes of the last level
+    assert st.general_products == base.general_products + 12 * last_nodes
+    assert st.syrk_leaves == base.syrk_leaves
+    assert st.recursive_products == base.recursive_products
+    h, kap = n >> lv, k >> lv
+    saved = last_nodes * 2 * (h * h * kap) / 8    # 1/8 of each general product
+    assert abs((base.ring_macs - st.ring_macs) - saved) < 1e-6 * base.ring_macs
