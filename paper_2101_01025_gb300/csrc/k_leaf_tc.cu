@@ -765,6 +765,19 @@ void set_shoup(Group *g, int ng, uint32_t p) {
   for (int i = 0; i < ng; ++i) g[i].ratio_sh = (uint32_t)(((uint64_t)g[i].ratio << 32) / p);
 }
 
+// K segment of the groups in K blocks: every plane product runs over one
+// segment of K before the next segment starts, so that the tiles in flight
+// share the segment's panels in L2 (AAT_KSEG: the width in K elements, a
+// multiple of 64; default 8192).
+int kseg_blocks() {
+  static const int v = [] {
+    const char *e = getenv("AAT_KSEG");
+    const int w = e ? atoi(e) : 8192;
+    return std::max(1, (w > 0 ? w : 8192) / BK);
+  }();
+  return v;
+}
+
 // Groups of the leaf product: plane pairs with integer weights turned into a
 // Horner sequence (see the file header).  Returns false when the product does
 // not fit the group table or a bound cannot be met.
@@ -818,7 +831,7 @@ bool build_groups(const TcLeafArgs &a, const ModP &m, Group *out, int *ng_out, i
   // epilogue multiplies its accumulator by w_prev / w_cur between groups and
   // by the last weight in a final group without K blocks (Horner).
   const int kblocks = (int)((a.K + BK - 1) / BK);
-  const int kseg = 8192 / BK;
+  const int kseg = kseg_blocks();
   const int ebits = std::min(std::max(a.exact_bits, 8), 24);
   const int64_t room = ((int64_t)1 << 31) - 1 - (int64_t)m.half;
   int ng = 0;
