@@ -212,6 +212,28 @@ def gpu_index(local_rank):
     return local_rank
 
 
+# ------------------------------------------------------------ replicas
+
+def max_over_ranks(x, world, device):
+    """The largest x over all ranks (the slowest rank's time); the process
+    group (NCCL on the GPUs, gloo in the CPU tests) must be initialised when
+    world > 1."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, ms_step):
+    """Whole-job throughput in effective n^2 k GOPS: every rank computes its
+    own product of the workload's size (replicas, no exchange), and the job
+    takes as long as its slowest rank (ms_step, already the max over ranks)."""
+    return world * N * N * K / (ms_step * 1e-3) / 1e9
+
+
 # ------------------------------------------------------------ GPU arm
 
 def run_ours(args):
@@ -234,13 +256,6 @@ def run_ours(args):
     def barrier():
         if world > 1:
             dist.barrier()
-
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
 
     A_host = make_input()
     A = torch.from_numpy(A_host).cuda()
@@ -276,9 +291,9 @@ def run_ours(args):
     prof = _native.Profile()
     _native.check(_native.lib().aat_profile_end(prof))
     clk = clocks.stop()
-    ms_total = max_over_ranks(ev0.elapsed_time(ev1))
+    ms_total = max_over_ranks(ev0.elapsed_time(ev1), world, "cuda")
     ms_step = ms_total / args.steps
-    value = world * N * N * K / (ms_step * 1e-3) / 1e9
+    value = job_value(world, ms_step)
     status = aat.aat_device_status()
 
     profd = prof.as_dict()
