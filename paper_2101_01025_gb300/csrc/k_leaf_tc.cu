@@ -27,6 +27,11 @@
 //   warps 2..9    epilogue: tcgen05.ld of the finished chunk, float -> int32,
 //                 accumulate; mod-p Horner step at digit-pair boundaries;
 //                 canonical store (lower triangle only for SYRK leaves)
+// The tile list is taken round robin by the persistent CTAs (or CTA pairs).
+// One launch computes one product (kSingle), a batch of products of
+// different moduli with tables in global memory (kBatch), or up to
+// MAX_MULTI independent products of one modulus with their tensor maps in
+// the kernel parameters (kMulti).
 // Every mbarrier wait is bounded (kTimeoutNs): on expiry the CTA sets the
 // device status word to AAT_ETIMEOUT, stops issuing work, waits (bounded) for
 // its copies and MMAs in flight, frees its TMEM and returns.
