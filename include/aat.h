@@ -146,17 +146,19 @@ AAT_API int64_t aat_modp_host_d2h_bytes(int64_t n, uint32_t flags);
  * The choices tuned: the recursion depth (the cut-off of Algorithm 1's
  * recursion, Sec. 3; the paper leaves it to the implementation, Sec. 7), the
  * leaf kernel form (form 1: one CTA per 128 x 256 tile; form 2: CTA pairs,
- * 256 x 256 tiles) and the digit-product form (plain_digits 1: one product
- * per digit pair).  aat_tune_modp runs every candidate on synthetic balanced
+ * 256 x 256 tiles), the digit-product form (plain_digits 1: one product per
+ * digit pair) and Winograd's form for the last level's general products
+ * (winograd 1, as AAT_WINOGRAD).  aat_tune_modp runs every candidate on
+ * synthetic balanced
  * residues of shape n x k on `stream` (one untimed run, then `reps` timed
  * ones; it allocates n k + n^2 int32 of device memory for the duration and
  * synchronises), keeps the fastest in a per-process table and returns it
  * with its time and the untuned choice's time (ms_default).  aat_modp_ex,
- * aat_modp_host and the batched plans take levels, form and digit form from
- * the table for a (n, k, p) it holds whenever their flags set neither
- * AAT_LEVELS nor AAT_DIGITS_PLAIN.  flags: AAT_LEAF_TC only (others give
- * AAT_EUNSUPPORTED); AAT_LEVELS, AAT_DIGITS_PLAIN and AAT_ZERO_UPPER are
- * ignored.
+ * aat_modp_host and the batched plans take levels, form, digit form and
+ * Winograd's form from the table for a (n, k, p) it holds whenever their
+ * flags set neither AAT_LEVELS nor AAT_DIGITS_PLAIN.  flags: AAT_LEAF_TC
+ * only (others give AAT_EUNSUPPORTED); AAT_LEVELS, AAT_DIGITS_PLAIN,
+ * AAT_WINOGRAD and AAT_ZERO_UPPER are ignored.
  * aat_tune_lookup: 1 and *out (may be NULL) if the table holds (n, k, p), else 0.
  * aat_tune_save: writes the table as JSON (with the GPU's name); returns the
  * entry count.  aat_tune_load: adds the entries of such a file, skipping a
@@ -167,7 +169,7 @@ typedef struct {
   int32_t levels;       /* recursion levels */
   int32_t form;         /* leaf kernel form: 1 one CTA, 2 CTA pairs */
   int32_t plain_digits; /* 1: one plane product per digit pair */
-  int32_t reserved;
+  int32_t winograd;     /* 1: Winograd's form for the last level's P3, P4 */
   double ms;            /* mean time of the chosen configuration */
   double ms_default;    /* mean time of the untuned choice */
 } aat_tune_t;

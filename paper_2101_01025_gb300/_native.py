@@ -78,14 +78,15 @@ class Tune(ctypes.Structure):
         ("levels", ctypes.c_int32),
         ("form", ctypes.c_int32),
         ("plain_digits", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("winograd", ctypes.c_int32),
         ("ms", ctypes.c_double),
         ("ms_default", ctypes.c_double),
     ]
 
     def as_dict(self):
         return dict(levels=int(self.levels), form=int(self.form),
-                    plain_digits=int(self.plain_digits), ms=float(self.ms),
+                    plain_digits=int(self.plain_digits), winograd=int(self.winograd),
+                    ms=float(self.ms),
                     ms_default=float(self.ms_default))
 
 

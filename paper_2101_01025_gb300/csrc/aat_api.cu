@@ -821,6 +821,7 @@ static void syrk_rec(Ctx &c, const int32_t *A, int64_t lda, int64_t n, int64_t k
 struct TuneVal {
   int levels, form, plain;
   double ms, ms_default;
+  int wino = 0;  // Winograd's form for the last level's general products
 };
 static std::mutex g_tune_mu;
 static std::map<std::tuple<int64_t, int64_t, uint32_t>, TuneVal> g_tune;
@@ -921,6 +922,7 @@ static size_t run_plan_in(Ctx &c, const int32_t *A, int64_t n, int64_t k, int64_
     flags |= AAT_LEVELS(tv.levels);
     c.form = tv.form;
     if (tv.plain) c.ds.nsum = 0;
+    if (tv.wino) c.wino = true;
   }
   Prepared pr = prepare(n, k, c.m.p, c.y, flags);
   const bool early = !pr.padded && pr.levels >= 1 && !beta;
@@ -1359,7 +1361,7 @@ int aat_tune_modp(int64_t n, int64_t k, uint32_t p, uint32_t flags, int reps, vo
   if ((flags & AAT_LEAF_MASK) != AAT_LEAF_TC)
     return fail(AAT_EUNSUPPORTED, "tuning covers the tensor-core leaf");
   // the tuned choices themselves are not flags of the candidates
-  flags &= ~(AAT_LEVELS_MASK | AAT_DIGITS_PLAIN | AAT_ZERO_UPPER);
+  flags &= ~(AAT_LEVELS_MASK | AAT_DIGITS_PLAIN | AAT_WINOGRAD | AAT_ZERO_UPPER);
   cudaStream_t st = (cudaStream_t)stream;
   int e;
   {
@@ -1387,9 +1389,10 @@ int aat_tune_modp(int64_t n, int64_t k, uint32_t p, uint32_t flags, int reps, vo
     uint32_t flags;
     int levels, form, plain;
     double ms;
+    int wino;
   };
   std::vector<Cand> cands;
-  cands.push_back({flags, -1, 0, 0, 1e300});
+  cands.push_back({flags, -1, 0, 0, 1e300, 0});
   int maxl = 0;
   while (maxl < 3 && (n >> (maxl + 1)) >= 512 && (k >> (maxl + 1)) >= 128) ++maxl;
   const bool sums = make_digits(p).nsum > 0;
@@ -1398,7 +1401,10 @@ int aat_tune_modp(int64_t n, int64_t k, uint32_t p, uint32_t flags, int reps, vo
       if (form == 2 && (n >> l) < 256) continue;  // no leaf tall enough for a pair
       for (int plain = 0; plain <= (sums ? 1 : 0); ++plain)
         cands.push_back({flags | AAT_LEVELS(l) | (plain ? AAT_DIGITS_PLAIN : 0u), l, form, plain,
-                         1e300});
+                         1e300, 0});
+      // Winograd's form for the last level's general products (default digits)
+      if (l >= 1)
+        cands.push_back({flags | AAT_LEVELS(l) | AAT_WINOGRAD, l, form, 0, 1e300, 1});
     }
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -1429,7 +1435,8 @@ int aat_tune_modp(int64_t n, int64_t k, uint32_t p, uint32_t flags, int reps, vo
   if (cands.size() < 2 || cands[bi].ms > 0.98 * ms_default)
     best = TuneVal{prepare_levels(n, k, p, flags), 0, 0, ms_default, 0.0};
   else
-    best = TuneVal{cands[bi].levels, cands[bi].form, cands[bi].plain, cands[bi].ms, 0.0};
+    best = TuneVal{cands[bi].levels, cands[bi].form, cands[bi].plain, cands[bi].ms, 0.0,
+                   cands[bi].wino};
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaStreamSynchronize(st);
@@ -1444,7 +1451,7 @@ int aat_tune_modp(int64_t n, int64_t k, uint32_t p, uint32_t flags, int reps, vo
   out->levels = best.levels;
   out->form = best.form;
   out->plain_digits = best.plain;
-  out->reserved = 0;
+  out->winograd = best.wino;
   out->ms = best.ms;
   out->ms_default = best.ms_default;
   return AAT_OK;
@@ -1457,7 +1464,7 @@ int aat_tune_lookup(int64_t n, int64_t k, uint32_t p, aat_tune_t *out) {
     out->levels = v.levels;
     out->form = v.form;
     out->plain_digits = v.plain;
-    out->reserved = 0;
+    out->winograd = v.wino;
     out->ms = v.ms;
     out->ms_default = v.ms_default;
   }
@@ -1494,10 +1501,10 @@ int aat_tune_save(const char *path) {
     const TuneVal &v = kv.second;
     fprintf(f,
             "  {\"n\": %lld, \"k\": %lld, \"p\": %u, \"levels\": %d, \"form\": %d, "
-            "\"plain_digits\": %d, \"ms\": %.6f, \"ms_default\": %.6f}%s\n",
+            "\"plain_digits\": %d, \"ms\": %.6f, \"ms_default\": %.6f, \"winograd\": %d}%s\n",
             (long long)std::get<0>(kv.first), (long long)std::get<1>(kv.first),
             (unsigned)std::get<2>(kv.first), v.levels, v.form, v.plain, v.ms, v.ms_default,
-            ++i < g_tune.size() ? "," : "");
+            v.wino, ++i < g_tune.size() ? "," : "");
   }
   fprintf(f, "]}\n");
   const bool ok = (fclose(f) == 0);
@@ -1527,19 +1534,22 @@ int aat_tune_load(const char *path) {
   while ((pos = text.find("{\"n\":", pos)) != std::string::npos) {
     long long n = 0, k = 0;
     unsigned p = 0;
-    int levels = -1, form = -1, plain = -1;
+    int levels = -1, form = -1, plain = -1, wino = 0;
     double ms = 0.0, msd = 0.0;
+    // "winograd" is optional (files written before it was tuned lack it)
     const int m = sscanf(text.c_str() + pos,
                          "{\"n\": %lld, \"k\": %lld, \"p\": %u, \"levels\": %d, \"form\": %d, "
-                         "\"plain_digits\": %d, \"ms\": %lf, \"ms_default\": %lf}",
-                         &n, &k, &p, &levels, &form, &plain, &ms, &msd);
+                         "\"plain_digits\": %d, \"ms\": %lf, \"ms_default\": %lf, "
+                         "\"winograd\": %d}",
+                         &n, &k, &p, &levels, &form, &plain, &ms, &msd, &wino);
     ++pos;
-    if (m != 8 || n <= 0 || k <= 0 || n > (1 << 30) || k > (1 << 30) || levels < 0 ||
-        levels > 14 || form < 0 || form > 2 || (plain != 0 && plain != 1) || validate(p) != AAT_OK)
+    if (m < 8 || n <= 0 || k <= 0 || n > (1 << 30) || k > (1 << 30) || levels < 0 ||
+        levels > 14 || form < 0 || form > 2 || (plain != 0 && plain != 1) ||
+        (wino != 0 && wino != 1) || validate(p) != AAT_OK)
       continue;
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune[std::make_tuple((int64_t)n, (int64_t)k, (uint32_t)p)] =
-        TuneVal{levels, form, plain, ms, msd};
+        TuneVal{levels, form, plain, ms, msd, wino};
     ++count;
   }
   g_last_error.clear();

@@ -318,3 +318,33 @@ def test_plan_counts_with_winograd(p, lv):
     h, kap = n >> lv, k >> lv
     saved = last_nodes * 2 * (h * h * kap) / 8    # 1/8 of each general product
     assert abs((base.ring_macs - st.ring_macs) - saved) < 1e-6 * base.ring_macs
+
+
+def test_tuning_table_carries_winograd_choice(tmp_path):
+    """A tuned shape whose entry chose Winograd's form runs its last level's
+    general products as 7 products each; entries written without the key
+    load as the plain form."""
+    import json
+    import paper_2101_01025_gb300 as aat
+    aat.tune_clear()
+    src = tmp_path / "tune.json"
+    entries = [
+        {"n": 1024, "k": 1024, "p": 131071, "levels": 1, "form": 0, "plain_digits": 0,
+         "ms": 1.0, "ms_default": 1.1, "winograd": 1},
+        {"n": 2048, "k": 1024, "p": 131071, "levels": 1, "form": 0, "plain_digits": 0,
+         "ms": 1.0, "ms_default": 1.1},
+        {"n": 1024, "k": 512, "p": 131071, "levels": 1, "form": 0, "plain_digits": 0,
+         "ms": 1.0, "ms_default": 1.1, "winograd": 3},          # invalid
+    ]
+    src.write_text('{"gpu": "", "entries": [\n' +
+                   ",\n".join("  " + json.dumps(e) for e in entries) + "\n]}\n")
+    assert aat.tune_load(str(src)) == 2
+    assert aat.tune_lookup(1024, 1024, 131071)["winograd"] == 1
+    assert aat.tune_lookup(2048, 1024, 131071)["winograd"] == 0
+    assert T.plan_stats(1024, 1024, 131071).general_products == 14
+    assert T.plan_stats(2048, 1024, 131071).general_products == 2
+    out = tmp_path / "saved.json"
+    assert aat.tune_save(str(out)) == 2
+    saved = {(e["n"], e["k"]): e["winograd"] for e in json.loads(out.read_text())["entries"]}
+    assert saved == {(1024, 1024): 1, (2048, 1024): 0}
+    aat.tune_clear()
