@@ -51,7 +51,7 @@ extern "C" {
 #define AAT_ENOMEM (-4)       /* device workspace allocation failed */
 #define AAT_ECUDA (-5)        /* CUDA error (launch, no device, wrong arch) */
 #define AAT_ETIMEOUT (-6)     /* a bounded device wait gave up */
-#define AAT_EUNSUPPORTED (-7) /* valid request this build does not provide */
+#define AAT_EUNSUPPORTED (-7) /* valid request the library does not provide */
 
 /* flags */
 #define AAT_IN_BALANCED (1u << 0) /* informational: A holds balanced residues */
