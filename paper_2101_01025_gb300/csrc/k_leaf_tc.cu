@@ -610,6 +610,36 @@ __global__ void __launch_bounds__(Shape<PAIR, EW>::THREADS, 1)
 #pragma unroll
         for (int j = 0; j < XB; ++j) xs[lane * (XB + 1) + j] = acc[cb + j];
         __syncwarp();
+        if constexpr (EW == 8) {
+          // accumulating product (8 epilogue warps): the old values are
+          // loaded four at a time, so four DRAM latencies overlap instead of
+          // one round trip per store
+          if (accum) {
+            constexpr int G = 4;
+#pragma unroll 1
+            for (int i0 = 0; i0 < XB; i0 += G) {
+              int32_t oldv[G];
+#pragma unroll
+              for (int g = 0; g < G; ++g) {
+                const int rr = RPI * (i0 + g) + lr, cl = cb + lc;
+                oldv[g] = (rr < mlim && cl < nlim && cl - rr <= dl)
+                              ? base[(int64_t)rr * ldo + cl] : 0;
+              }
+#pragma unroll
+              for (int g = 0; g < G; ++g) {
+                const int rr = RPI * (i0 + g) + lr, cl = cb + lc;
+                if (rr < mlim && cl < nlim && cl - rr <= dl) {
+                  int32_t old = bal(oldv[g], m);
+                  if (beta != 1u) old = mulmod_shoup(old, beta, beta_sh, m);
+                  const int32_t x = xs[rr * (XB + 1) + lc];
+                  base[(int64_t)rr * ldo + cl] =
+                      (int32_t)bal_to_canon(add_bal(to_bal((uint32_t)x, m), old, m), m);
+                }
+              }
+            }
+            continue;
+          }
+        }
 #pragma unroll 1
         for (int i = 0; i < XB; ++i) {
           const int rr = RPI * i + lr, cl = cb + lc;
