@@ -47,12 +47,12 @@ P = 2**31 - 1
 SEED_OFFSET = 2
 # DRAM traffic of the dominant kernel from one ncu capture of three 8192^3
 # leaf products mod 2^31-1 (dram__bytes_read.sum + dram__bytes_write.sum:
-# 19.37, 21.14 and 21.36 GB, mean 20.62 GB for 10.995 TFLOP of algorithmic
+# 12.51, 13.56 and 12.66 GB, mean 12.91 GB for 10.995 TFLOP of algorithmic
 # work each; CTA-pair form, tiles in bands of 2048 rows;
 # profiles/leaf_tc_kernel_gemm8192_p2p31m1.md), scaled to the average launch
 # of the step by its algorithmic work.  None whenever the kernel has changed
 # since the counters were taken.
-LEAF_TC_BYTES_PER_FLOP = 20.62e9 / 10.995e12
+LEAF_TC_BYTES_PER_FLOP = 12.91e9 / 10.995e12
 
 
 def parse():
