@@ -164,6 +164,19 @@ struct YParams {
 // magnitude <= 256, exactly representable in bf16.  Plane d, row r, column c
 // lives at ptr[(d * rows + r) * kstride + c]; kstride is a multiple of 8
 // (16-byte rows for the tensor memory accelerator).
+// (I, J), I >= J >= 0, of entry pid of a lower triangle numbered row by row
+// (pid = I (I + 1) / 2 + J): a single-precision square root as the guess,
+// made exact by integer steps (this GPU has few FP64 units, and every thread
+// of a block computes it).
+__device__ __forceinline__ void tri_index(int64_t pid, int64_t &I, int64_t &J) {
+  int64_t i = (int64_t)((sqrtf(8.0f * (float)pid + 1.0f) - 1.0f) * 0.5f);
+  if (i < 0) i = 0;
+  while (i * (i + 1) / 2 > pid) --i;
+  while ((i + 1) * (i + 2) / 2 <= pid) ++i;
+  I = i;
+  J = pid - i * (i + 1) / 2;
+}
+
 struct Planes {
   __nv_bfloat16 *ptr;
   int64_t rows;

@@ -584,10 +584,8 @@ __device__ __forceinline__ void combine2m_tile(const float *__restrict__ G,
                                                int64_t pid, float (&hij)[T][T + 1],
                                                float (&hji)[T][T + 1]) {
   const int64_t ntiles = (n + T - 1) / T;
-  int64_t I = (int64_t)((sqrt(8.0 * (double)pid + 1.0) - 1.0) * 0.5);
-  while (I * (I + 1) / 2 > pid) --I;
-  while ((I + 1) * (I + 2) / 2 <= pid) ++I;
-  const int64_t J = pid - I * (I + 1) / 2;
+  int64_t I, J;
+  tri_index(pid, I, J);
   if (I >= ntiles) return;
   const int tx = threadIdx.x % T, ty = threadIdx.x / T;
   const int64_t r0 = I * T, c0 = J * T;
@@ -979,10 +977,8 @@ __global__ void cpostadd_kernel(const float2 *__restrict__ C11, const float2 *__
   __shared__ float2 u1_ij[T][T + 1];
   const int64_t ntiles = (h + T - 1) / T;
   int64_t pid = blockIdx.x;
-  int64_t I = (int64_t)((sqrt(8.0 * (double)pid + 1.0) - 1.0) * 0.5);
-  while (I * (I + 1) / 2 > pid) --I;
-  while ((I + 1) * (I + 2) / 2 <= pid) ++I;
-  const int64_t J = pid - I * (I + 1) / 2;
+  int64_t I, J;
+  tri_index(pid, I, J);
   if (I >= ntiles) return;
   const int tx = threadIdx.x % T, ty = threadIdx.x / T;
   const int64_t r0 = I * T, c0 = J * T;
