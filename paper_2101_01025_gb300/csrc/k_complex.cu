@@ -1131,15 +1131,14 @@ static void c_two_m(CCtx &c, const float2 *A, int64_t lda, int64_t n, int64_t k,
   float *H = (float *)c.ar.get((size_t)n * n * 4);
   float *G = (float *)c.ar.get((size_t)n * n * 4);
   if (!c.ar.dry) {
-    CSplitOut ox, oy;
-    std::memset(&ox, 0, sizeof(ox));
-    std::memset(&oy, 0, sizeof(oy));
-    ox.re = Xr;
-    ox.s = Xs;
-    oy.im = Yi;
-    if (!herm) oy.d = Ysd;
-    csplit(c, A, lda, n, k, ox);
-    csplit(c, A, lda, n, k, oy);
+    // every piece set in one pass over A
+    CSplitOut o;
+    std::memset(&o, 0, sizeof(o));
+    o.re = Xr;
+    o.s = Xs;
+    o.im = Yi;
+    if (!herm) o.d = Ysd;
+    csplit(c, A, lda, n, k, o);
     // H = Ar Ai^T (all entries), G = (Ar + Ai)(Ar +- Ai)^T (lower tiles)
     if (c.err == AAT_OK)
       cchk(c, launch_leaf_f32({FTerm{&Xr, &Yi, false}}, c.np, n, n, k, H, n, 0, c.st), "2M H");
