@@ -391,6 +391,17 @@ def test_full_size_config2(lib, n, k, p, levels):
         assert st.levels == levels
 
 
+@pytest.mark.parametrize("leaf", ["i8", "f64"])
+@pytest.mark.parametrize("n,k,p", [(8192, 8192, 65521), (16384, 4096, 131071)])
+def test_full_size_config2_mma_leaves(lib, leaf, n, k, p):
+    """The INT8 and FP64 mma.sync leaves at full size with 2 levels: sampled
+    entries and Freivalds, bit-exact like the BF16-digit leaf."""
+    A = _config2_input(n, k, p)
+    st = _full_check(lib, A, p, levels_expected_min=2, nsample=800, nvec=1, levels=2,
+                     flags=LEAFKINDS[leaf])
+    assert st.levels == 2
+
+
 # ------------------------------------------------------- SYRK form (Sec. 7)
 
 @pytest.mark.parametrize("p", PRIMES)
