@@ -6,6 +6,8 @@
     python -m paper_2101_01025_gb300.cases full 16384 ...
 
 leaf: one leaf product X Y^T mod p of n x n x n (digit planes split first);
+aah / aatc2m / aatc: complex A A^H by 2M, A A^T by 2M, A A^T by Algorithm 1
+with Y = i I (--prec: BF16 pieces per FP32 value);
 syrk: Low(X X^T) with 0 recursion levels; aat: Low(A A^T) by Algorithm 1;
 full: the plain full product A A^T.  Inputs are seeded uniform residues
 generated on the device.  Prints the mean time per repetition.
@@ -18,7 +20,8 @@ import json
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["leaf", "syrk", "aat", "full", "aah", "aatc2m", "batch"])
+    ap.add_argument("case", choices=["leaf", "syrk", "aat", "full", "aah", "aatc2m", "aatc",
+                                     "batch"])
     ap.add_argument("n", type=int)
     ap.add_argument("--k", type=int, default=None)
     ap.add_argument("--p", type=int, default=2**31 - 1)
@@ -49,16 +52,19 @@ def main(argv=None):
     half = (p - 1) // 2
     if a.case == "batch":
         return batch_case(a)
-    if a.case in ("aah", "aatc2m"):
+    if a.case in ("aah", "aatc2m", "aatc"):
         cflags = {"fp32": aat.AAT_C_FP32, "bf16x3": aat.AAT_C_BF16X3, "bf16": aat.AAT_C_BF16}[a.prec]
         Z = torch.randn((n, k), dtype=torch.complex64, device="cuda")
         CZ = torch.empty((n, n), dtype=torch.complex64, device="cuda")
-        f = aat.aah_complex if a.case == "aah" else aat.aat_complex_2m
-        fn = lambda: f(Z, C=CZ, flags=cflags)  # noqa: E731
+        if a.case == "aatc":   # Algorithm 1 with Y = i I
+            fn = lambda: aat.aat_complex(Z, C=CZ, flags=cflags, levels=a.levels)  # noqa: E731
+        else:
+            f = aat.aah_complex if a.case == "aah" else aat.aat_complex_2m
+            fn = lambda: f(Z, C=CZ, flags=cflags)  # noqa: E731
     else:
         X = torch.randint(-half, half + 1, (n, k), dtype=torch.int32, device="cuda")
         C = torch.empty((n, n), dtype=torch.int32, device="cuda")
-    if a.case in ("aah", "aatc2m"):
+    if a.case in ("aah", "aatc2m", "aatc"):
         pass
     elif a.case == "leaf":
         Y = torch.randint(-half, half + 1, (n, k), dtype=torch.int32, device="cuda")
