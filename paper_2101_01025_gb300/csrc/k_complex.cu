@@ -725,7 +725,10 @@ cudaError_t encode_c(CUtensorMap *tm, const Planes &P, int box_rows) {
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-// tm: tile height (128, or 256 for CTA pairs); super-blocks of 2048 x 2048
+// tm: tile height (128, or 256 for CTA pairs).  Bands of 2048 output rows
+// swept column by column: the tiles in flight at one time (about a wave of
+// consecutive entries) span few row and column panels, which they share
+// through L2.
 cudaError_t tiles_c(int dev, int64_t M, int64_t N, int lower, int tm, int2 **out, int *count) {
   auto key = std::make_tuple(dev, M, N, lower, tm);
   auto it = g_tiles_c.find(key);
@@ -735,15 +738,14 @@ cudaError_t tiles_c(int dev, int64_t M, int64_t N, int lower, int tm, int2 **out
     return cudaSuccess;
   }
   const int64_t TI = (M + tm - 1) / tm, TJ = (N + BN - 1) / BN;
-  const int64_t SI = 2048 / tm;
+  const int64_t band = std::max<int64_t>(1, 2048 / tm);
   std::vector<int2> v;
-  for (int64_t bi = 0; bi < TI; bi += SI)
-    for (int64_t bj = 0; bj < TJ; bj += 8)
-      for (int64_t i = bi; i < std::min(TI, bi + SI); ++i)
-        for (int64_t j = bj; j < std::min(TJ, bj + 8); ++j) {
-          if (lower && j * BN > i * tm + tm - 1) continue;
-          v.push_back(make_int2((int)i, (int)j));
-        }
+  for (int64_t bi = 0; bi < TI; bi += band)
+    for (int64_t j = 0; j < TJ; ++j)
+      for (int64_t i = bi; i < std::min(TI, bi + band); ++i) {
+        if (lower && j * BN > i * tm + tm - 1) continue;
+        v.push_back(make_int2((int)i, (int)j));
+      }
   int2 *d = nullptr;
   if (!v.empty()) {
     cudaError_t e = cudaMalloc(&d, v.size() * sizeof(int2));
