@@ -48,11 +48,15 @@ SEED_OFFSET = 2
 # DRAM traffic of the dominant kernel from one ncu capture of three 8192^3
 # leaf products mod 2^31-1 (dram__bytes_read.sum + dram__bytes_write.sum:
 # 12.51, 13.56 and 12.66 GB, mean 12.91 GB for 10.995 TFLOP of algorithmic
-# work each; CTA-pair form, tiles in bands of 2048 rows;
-# profiles/leaf_tc_kernel_gemm8192_p2p31m1.md), scaled to the average launch
-# of the step by its algorithmic work.  None whenever the kernel has changed
-# since the counters were taken.
+# work each; CTA-pair form, tiles in bands of 2048 rows), scaled to the
+# average launch of the step by its algorithmic work.  None whenever the
+# kernel has changed since the counters were taken.
 LEAF_TC_BYTES_PER_FLOP = 12.91e9 / 10.995e12
+# Dense BF16 rate of the tensor pipe per SM and clock (a 128 x 256 x 16
+# tcgen05.mma every 128 cycles) and the SM count: the nominal rate at the
+# clock the run was sampled at.
+BF16_FLOP_PER_SM_CLK = 8192
+SMS = 152
 
 
 def parse():
@@ -65,6 +69,8 @@ def parse():
                     help="skip baselines, e2e and the CPU oracle (quick runs)")
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the autotuning of levels / leaf form / digit form")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other workloads (512^2, 8192^2, 16384x4096, complex, batch)")
     return ap.parse_args()
 
 
@@ -236,6 +242,104 @@ def job_value(world, ms_step):
 
 # ------------------------------------------------------------ GPU arm
 
+def bf16_peaks(peaks):
+    """(peak, its source, sustained peak) in TFLOP/s: the measured burst rate
+    for a kernel timed over a sub-second region, the sustained one beside it."""
+    if "bf16_tflops" in peaks:
+        return (float(peaks["bf16_tflops"]), "of measured (bf16 burst)",
+                float(peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])))
+    return 1900.0, "of fallback (bf16 burst)", 1700.0
+
+
+def run_configs(peaks):
+    """The other workloads, each timed with CUDA events (one untimed run, then
+    repetitions) with the library's per-kernel profile: ms, effective n^2 k
+    GOPS and the leaf's achieved rate against the BF16 burst peak."""
+    import torch
+
+    import paper_2101_01025_gb300 as aat
+    from paper_2101_01025_gb300 import _native, synth, testing
+    peak, peak_src, _ = bf16_peaks(peaks)
+    gen = torch.Generator(device="cuda")
+    out = {}
+
+    def measure(name, fn, work, reps, what, leaf_cls):
+        fn()
+        torch.cuda.synchronize()
+        _native.lib().aat_profile_begin()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        prof = _native.Profile()
+        _native.check(_native.lib().aat_profile_end(prof))
+        ms = e0.elapsed_time(e1) / reps
+        lf = prof.as_dict().get(leaf_cls, {"launches": 0, "ms": 0.0, "work": 0.0})
+        ach = lf["work"] / max(lf["ms"], 1e-9) / 1e9
+        out[name] = {"what": what, "ms": ms, "gops": work / (ms * 1e-3) / 1e9,
+                     "roofline": {"kernel": leaf_cls, "bound": "tensor", "achieved": ach,
+                                  "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                                  "peak_source": peak_src,
+                                  "share": lf["ms"] / max(ms * reps, 1e-9)}}
+
+    def residues(n, k, p, seed):
+        gen.manual_seed(seed)
+        return torch.randint(0, p, (n, k), dtype=torch.int32, device="cuda", generator=gen)
+
+    # 512 x 512 over F_131071, one level then the leaf
+    A = torch.from_numpy(synth.residues(synth.SEED_BASE, (512, 512), 131071)).cuda()
+    C = torch.empty((512, 512), dtype=torch.int32, device="cuda")
+    measure("512x512_p131071_l1", lambda: aat.aat_modp(A, 131071, C=C, levels=1),
+            512.0**3, 20, "Low(A A^T) mod 131071, one recursion level, tensor-core leaf",
+            "leaf_tc")
+    # 8192^2 and 16384 x 4096 over F_65521 and F_131071 (default depth)
+    for (n, k) in ((8192, 8192), (16384, 4096)):
+        for p in (65521, 131071):
+            A = residues(n, k, p, synth.SEED_BASE + 1)
+            C = torch.empty((n, n), dtype=torch.int32, device="cuda")
+            lv = testing.plan_stats(n, k, p).levels
+            measure("%dx%d_p%d" % (n, k, p), lambda: aat.aat_modp(A, p, C=C), float(n) * n * k,
+                    5, "Low(A A^T) mod %d, %d recursion levels (default depth)" % (p, lv),
+                    "leaf_tc")
+            del A, C
+    # complex 8192 x 8192: A A^H by 2M and A A^T by Algorithm 1, FP32 class
+    gen.manual_seed(synth.SEED_BASE + 3)
+    Z = torch.view_as_complex(torch.randn((8192, 8192, 2), device="cuda", generator=gen))
+    CZ = torch.empty((8192, 8192), dtype=torch.complex64, device="cuda")
+    measure("complex8192_aah_2m_fp32", lambda: aat.aah_complex(Z, C=CZ), 8192.0**3, 5,
+            "Low(A A^H) by 2M, FP32-accurate (3 BF16 pieces)", "leaf_f32")
+    measure("complex8192_aat_alg1_fp32", lambda: aat.aat_complex(Z, C=CZ), 8192.0**3, 5,
+            "Low(A A^T) by Algorithm 1 (Y = i I, default depth), FP32-accurate", "leaf_f32")
+    del Z, CZ
+    # batch: 256 problems over F_65521 + 64 complex A A^H, log-uniform sizes
+    ns = synth.log_uniform_ints(synth.SEED_BASE + 4, 256, 64, 2048)
+    ks = synth.log_uniform_ints(synth.SEED_BASE + 5, 256, 64, 4096)
+    cn = synth.log_uniform_ints(synth.SEED_BASE + 6, 64, 64, 2048)
+    ck = synth.log_uniform_ints(synth.SEED_BASE + 7, 64, 64, 4096)
+    gen.manual_seed(synth.SEED_BASE + 5)
+    fp = [("modp", torch.randint(0, 65521, (int(n), int(k)), dtype=torch.int32, device="cuda",
+                                 generator=gen),
+           torch.empty((int(n), int(n)), dtype=torch.int32, device="cuda"), 65521, 0)
+          for n, k in zip(ns, ks)]
+    cx = [("aah", torch.view_as_complex(torch.randn((int(n), int(k), 2), device="cuda",
+                                                    generator=gen)),
+           torch.empty((int(n), int(n)), dtype=torch.complex64, device="cuda"), 0, 0)
+          for n, k in zip(cn, ck)]
+    for name, probs, cls in (("batch256_p65521", fp, "leaf_tc"), ("batch64_complex_aah", cx,
+                                                                   "leaf_f32"),
+                             ("batch256_p65521_plus_64_complex", fp + cx, "leaf_tc")):
+        plan = aat.Plan(probs)
+        work = sum(float(Ap.shape[0]) ** 2 * Ap.shape[1] for _, Ap, _, _, _ in probs)
+        measure(name, plan.execute, work, 10,
+                "one plan (one CUDA graph launch), sum of n^2 k over its problems", cls)
+        out[name]["plan"] = plan.info()
+        plan.close()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -305,15 +409,20 @@ def run_ours(args):
         pass
     leaf = profd.get("leaf_tc", {"launches": 0, "ms": 0.0, "work": 0.0})
     achieved = leaf["work"] / max(leaf["ms"], 1e-9) / 1e9  # TFLOP/s
-    if "bf16_tflops_sustained" in peaks:
-        peak, peak_src = float(peaks["bf16_tflops_sustained"]), "of measured (bf16 sustained)"
-    else:
-        peak, peak_src = 1700.0, "of fallback (bf16 sustained)"
+    peak, peak_src, sust = bf16_peaks(peaks)
+    sm_mhz = clk.get("sm_mhz")
     roofline = {
         "bound": "tensor",
         "kernel": "leaf_tc_kernel (tcgen05 kind::f16, CTA pairs, BF16 digits)",
         "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
         "peak_source": peak_src,
+        "frac_of_sustained": achieved / sust,
+        "clock_normalised": None if not sm_mhz else {
+            "sm_mhz": sm_mhz,
+            "nominal_tflops_at_clock": SMS * BF16_FLOP_PER_SM_CLK * sm_mhz * 1e6 / 1e12,
+            "frac": achieved / (SMS * BF16_FLOP_PER_SM_CLK * sm_mhz * 1e6 / 1e12),
+            "what": "achieved over the tensor pipe's dense BF16 rate (8192 FLOP per SM and "
+                    "clock, 152 SMs) at the median SM clock sampled in the timed region"},
         "traffic": (None if LEAF_TC_BYTES_PER_FLOP is None else
                     LEAF_TC_BYTES_PER_FLOP * leaf["work"] / max(leaf["launches"], 1)),
         "launches": leaf["launches"],
@@ -378,6 +487,10 @@ def run_ours(args):
                       "triangle of C back in row bands, the rows below n/2 while the last "
                       "product runs)"}
 
+    configs = None
+    if not args.no_configs and rank == 0:
+        configs = run_configs(peaks)
+
     cpu = None
     if not args.no_extras and rank == 0 and world == 1:
         v, t, desc, threads, _ = oracle_sample(A_host, 12.0)
@@ -394,7 +507,7 @@ def run_ours(args):
             "data": "synthetic", "config": dict(workload_config(levels), tuned=tuned),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk, "kernels": kernels,
-            "device_status": status,
+            "device_status": status, "configs": configs,
         }
         line.update(extras)
         print(json.dumps(line), flush=True)

@@ -1,16 +1,19 @@
 """Named single-GPU workloads for profiling the kernels in isolation.
 
-    python -m paper_2101_01025_gb300.cases leaf 8192 [--p P] [--reps R]
-    python -m paper_2101_01025_gb300.cases syrk 8192 [--k K] ...
-    python -m paper_2101_01025_gb300.cases aat 16384 [--k K] [--levels L] ...
-    python -m paper_2101_01025_gb300.cases full 16384 ...
+    python bench_cases.py leaf 8192 [--p P] [--reps R]
+    python bench_cases.py syrk 8192 [--k K] ...
+    python bench_cases.py aat 16384 [--k K] [--levels L] ...
+    python bench_cases.py full 16384 ...
+    python bench_cases.py peaks 4 --reps 5
 
 leaf: one leaf product X Y^T mod p of n x n x n (digit planes split first);
 aah / aatc2m / aatc: complex A A^H by 2M, A A^T by 2M, A A^T by Algorithm 1
 with Y = i I (--prec: BF16 pieces per FP32 value);
 syrk: Low(X X^T) with 0 recursion levels; aat: Low(A A^T) by Algorithm 1;
-full: the plain full product A A^T.  Inputs are seeded uniform residues
-generated on the device.  Prints the mean time per repetition.
+full: the plain full product A A^T; peaks: the rates of the mma.sync
+instructions of the INT8 and FP64 leaves (n blocks per SM).  Inputs are
+seeded uniform residues generated on the device.  Prints the time of each
+repetition.
 """
 from __future__ import annotations
 
@@ -21,7 +24,7 @@ import json
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=["leaf", "syrk", "aat", "full", "aah", "aatc2m", "aatc",
-                                     "batch"])
+                                     "batch", "peaks"])
     ap.add_argument("n", type=int)
     ap.add_argument("--k", type=int, default=None)
     ap.add_argument("--p", type=int, default=2**31 - 1)
@@ -52,6 +55,8 @@ def main(argv=None):
     half = (p - 1) // 2
     if a.case == "batch":
         return batch_case(a)
+    if a.case == "peaks":
+        return peaks_case(a)
     if a.case in ("aah", "aatc2m", "aatc"):
         cflags = {"fp32": aat.AAT_C_FP32, "bf16x3": aat.AAT_C_BF16X3, "bf16": aat.AAT_C_BF16}[a.prec]
         Z = torch.randn((n, k), dtype=torch.complex64, device="cuda")
@@ -111,6 +116,63 @@ def profile_end(reps):
         out[name] = {"launches": v["launches"] / reps, "ms": v["ms"] / reps,
                      ("tflops" if leafy else "gbs"): per_s / 1e12 if leafy else per_s / 1e9}
     return out
+
+
+def peaks_case(a):
+    """Peak rates of the legacy tensor instructions the INT8 and FP64 leaves
+    use (mma.sync m16n8k32 s8, m8n8k4 f64), from register-only loops on every
+    SM (n blocks per SM), with the SM clock sampled during each run."""
+    import ctypes
+    import subprocess
+    import statistics
+    import tempfile
+    import os
+    import torch
+
+    from paper_2101_01025_gb300 import _native
+    L = _native.lib()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    blocks = sms * max(1, a.n)
+    sink = torch.zeros(1, dtype=torch.int64, device="cuda")
+    st = torch.cuda.current_stream().cuda_stream
+    out = {"case": "peaks", "sms": sms, "blocks": blocks}
+    for kind, name in ((0, "int8_mma_sync_m16n8k32"), (1, "fp64_mma_sync_m8n8k4")):
+        ops = ctypes.c_double()
+        iters = 2000
+        # calibrate to ~0.3 s per launch
+        for _ in range(3):
+            _native.check(L.aatx_mma_peak(kind, iters, blocks, sink.data_ptr(),
+                                          ctypes.byref(ops), st))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _native.check(L.aatx_mma_peak(kind, iters, blocks, sink.data_ptr(),
+                                          ctypes.byref(ops), st))
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            iters = max(1, int(iters * 300.0 / max(ms, 1e-3)))
+        fd, path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        smi = subprocess.Popen(["nvidia-smi", "-i", "0", "--query-gpu=clocks.sm",
+                                "--format=csv,noheader,nounits", "-lms", "100"],
+                               stdout=open(path, "w"), stderr=subprocess.DEVNULL)
+        rates = []
+        for _ in range(a.reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _native.check(L.aatx_mma_peak(kind, iters, blocks, sink.data_ptr(),
+                                          ctypes.byref(ops), st))
+            e1.record()
+            torch.cuda.synchronize()
+            rates.append(ops.value / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+        smi.terminate()
+        smi.wait()
+        mhz = [float(x) for x in open(path).read().split() if x.strip().isdigit()]
+        os.unlink(path)
+        out[name] = {"tops": max(rates), "tops_runs": rates, "iters": iters,
+                     "sm_mhz_median": statistics.median(mhz) if mhz else None,
+                     "unit": "TOPS (int8)" if kind == 0 else "TFLOP/s (fp64)"}
+    print(json.dumps(out))
 
 
 def batch_case(a):

@@ -222,13 +222,23 @@ AAT_API int aat_gemm_modp_noalloc(const int32_t *X, int64_t ldx, const int32_t *
 
 /* ------------------------------------------------------------------ C
  * Complex inputs and outputs are complex64, interleaved (re, im) floats,
- * row-major with strides in complex elements.  Real products run on the
- * tensor cores with BF16 pieces of the FP32 values (flags):
- *   AAT_C_FP32    3 pieces, 6 piece products (close to FP32 accuracy)
- *   AAT_C_BF16X3  2 pieces, 3 piece products
- *   AAT_C_BF16    1 piece (plain BF16 products)
- * with FP32 accumulation.  Only the lower triangle of C (diagonal included)
- * is written.
+ * row-major with strides in complex elements.  No product runs in FP32
+ * arithmetic: every real product runs on the BF16 tensor cores with the FP32
+ * values split into BF16 pieces (x = x0 + x1 + x2, x0 = bf16(x),
+ * x1 = bf16(x - x0), ...), piece products of weight >= 2^-16 kept, FP32
+ * accumulation.  The precision flags name the accuracy class:
+ *   AAT_C_FP32    FP32-accurate: 3 pieces, 6 piece products per real
+ *                 product (relative Frobenius error <= 1e-5)
+ *   AAT_C_BF16X3  2 pieces, 3 piece products (<= 1e-4)
+ *   AAT_C_BF16    plain BF16 (<= 3e-3): one piece per input value; the 2M
+ *                 form's sum operand (Ar + Ai or Ar - Ai) keeps 2 pieces (3
+ *                 piece products for G), because one piece there would put
+ *                 the whole rounding error of G into Re C (3.3e-3 measured).
+ *                 Algorithm 1 with recursion levels is refused in this class
+ *                 (AAT_EUNSUPPORTED): each level roughly doubles the error.
+ * Errors are relative Frobenius errors of Low(C) against FP64 sums, for
+ * inputs with i.i.d. N(0, 1) parts.  Only the lower triangle of C (diagonal
+ * included) is written.
  */
 #define AAT_C_PREC_MASK (3u << 16)
 #define AAT_C_FP32 (0u << 16)
@@ -252,7 +262,9 @@ AAT_API int aat_complex_2m(const void *A, int64_t n, int64_t k, int64_t lda, voi
  * Y = i I (Sec. 4.1: multiplying by Y swaps real and imaginary parts with one
  * sign flip).  The general products P3, P4 use 3 real products (3M), the
  * recursion ends in Algorithm 2 (eps = -1).  flags: AAT_C_* precision, and
- * AAT_LEVELS(l) (no level bits: one level once n/2 >= 4096, k/2 >= 2048). */
+ * AAT_LEVELS(l) (no level bits: one level once n/2 >= 4096, k/2 >= 2048; no
+ * level with AAT_C_BF16, which refuses AAT_LEVELS(l >= 1) with
+ * AAT_EUNSUPPORTED). */
 AAT_API int aat_complex(const void *A, int64_t n, int64_t k, void *C, void *stream);
 AAT_API int aat_complex_ex(const void *A, int64_t n, int64_t k, int64_t lda, void *C,
                            int64_t ldc, uint32_t flags, void *stream);

@@ -84,6 +84,34 @@ AAT_API int aatx_leaf(const int32_t *X, int64_t ldx, const int32_t *Y, int64_t l
 /* The fused post-additions (U4 over C21, Low(U5) over C22) of one level. */
 AAT_API int aatx_postadd(int32_t *C, int64_t ldc, int64_t h, uint32_t p, void *stream);
 
+/* ---- failure paths (no GPU fault: limits and waits that run out) ---- */
+
+/* Workspace requests of more than `bytes` fail with AAT_ENOMEM, as a failed
+ * cudaMalloc would, before any CUDA call (SIZE_MAX restores the default: no
+ * limit).  Covers the library's shared workspace (aat_modp_ex, aat_syrk_modp,
+ * complex products, tuning), not plans. */
+AAT_API void aatx_set_alloc_limit(size_t bytes);
+/* Grows the shared workspace of the current device to `bytes` (AAT_OK, or
+ * AAT_ENOMEM from the limit above or from cudaMalloc). */
+AAT_API int aatx_workspace_reserve(size_t bytes);
+/* One thread waits, with the bounded mbarrier wait of the leaf kernels and a
+ * limit of limit_ns (at most 2 s), for a barrier phase that nothing
+ * completes; when the limit runs out it records AAT_ETIMEOUT in the status
+ * word that aat_device_status reads: which = 0 the library's word, which = 1
+ * the allocation-free entry point's.  No fault, no trap: the kernel returns
+ * and the context stays usable.  Asynchronous on stream. */
+AAT_API int aatx_wait_probe(int which, int64_t limit_ns, void *stream);
+
+/* ---- instruction peaks (the denominators of the mma.sync leaves) ---- */
+
+/* Launches `blocks` blocks of 8 warps; each warp issues iters x 8
+ * independent mma.sync on register operands: kind 0 m16n8k32 s8 (INT8,
+ * INT32 accumulation), kind 1 m8n8k4 f64.  *ops receives the operations the
+ * launch performs (2 M N K per instruction); divide by its CUDA-event time.
+ * sink: device memory of 8 bytes (written only for an impossible value). */
+AAT_API int aatx_mma_peak(int kind, int64_t iters, int blocks, void *sink, double *ops,
+                          void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -51,6 +51,7 @@ EXPORTS = [
     "aat_plan_destroy",
     "aatx_is_prime", "aatx_sqrt_mod", "aatx_sos", "aatx_y_params", "aatx_digit_spec",
     "aatx_plan_stats", "aatx_leaf_groups", "aatx_sblocks", "aatx_split", "aatx_leaf", "aatx_postadd",
+    "aatx_set_alloc_limit", "aatx_workspace_reserve", "aatx_wait_probe", "aatx_mma_peak",
 ]
 
 
@@ -196,6 +197,11 @@ def lib():
         L.aatx_leaf.argtypes = [vp, i64, vp, i64, i64, i64, i64, u32, vp, i64, i32, i32, u32,
                                 i32, vp]
         L.aatx_postadd.argtypes = [vp, i64, i64, u32, vp]
+        L.aatx_set_alloc_limit.argtypes = [ctypes.c_size_t]
+        L.aatx_set_alloc_limit.restype = None
+        L.aatx_workspace_reserve.argtypes = [ctypes.c_size_t]
+        L.aatx_wait_probe.argtypes = [i32, i64, vp]
+        L.aatx_mma_peak.argtypes = [i32, i64, i32, vp, ctypes.POINTER(ctypes.c_double), vp]
         _lib = L
         return L
 

@@ -8,6 +8,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -300,7 +301,15 @@ int32_t *device_status_ptr() {
   return s.status;
 }
 
+// Test hook: workspace requests above this many bytes fail with AAT_ENOMEM
+// as a failed cudaMalloc would, before any CUDA call (SIZE_MAX: no limit).
+static std::atomic<size_t> g_alloc_limit{SIZE_MAX};
+
 static int ensure_workspace(size_t bytes, void **out) {
+  if (bytes > g_alloc_limit.load())
+    return fail(AAT_ENOMEM, "workspace allocation of " + std::to_string(bytes) +
+                                " bytes refused (test allocation limit " +
+                                std::to_string(g_alloc_limit.load()) + ")");
   std::lock_guard<std::mutex> lock(g_state_mu);
   DeviceState &s = state();
   if (s.ws_size < bytes) {
@@ -1611,7 +1620,9 @@ int aat_device_status(int reset) {
   int32_t v = 0;
   cudaMemcpy(&v, d, sizeof(v), cudaMemcpyDeviceToHost);
   if (reset) cudaMemset(d, 0, sizeof(int32_t));
-  return v;
+  // the allocation-free entry point keeps its own word in its static array
+  const int w = noalloc_status(reset);
+  return v != AAT_OK ? v : w;
 }
 
 void aat_shutdown(void) {
@@ -1771,6 +1782,13 @@ int aatx_leaf(const int32_t *X, int64_t ldx, const int32_t *Y, int64_t ldy, int6
     need = c.ar.peak;
   }
   return c.err;
+}
+
+void aatx_set_alloc_limit(size_t bytes) { g_alloc_limit.store(bytes); }
+
+int aatx_workspace_reserve(size_t bytes) {
+  void *ws = nullptr;
+  return ensure_workspace(bytes, &ws);
 }
 
 int aatx_postadd(int32_t *C, int64_t ldc, int64_t h, uint32_t p, void *stream) {

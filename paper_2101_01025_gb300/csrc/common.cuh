@@ -395,6 +395,8 @@ cudaError_t launch_leaf_tc_multi(const TcLeafArgs *as, int count, const ModP &m,
 // idle share of the separate launches' last waves).
 bool leaf_tc_fuse_pays(const TcLeafArgs *as, int count);
 void leaf_tc_release();
+// status word of the allocation-free entry point (AAT_OK if it never ran)
+int noalloc_status(int reset);
 
 // A batched tensor-core leaf launch: device tables (per-problem tensor maps,
 // group tables, one tile list over every problem) built once, then one

@@ -815,8 +815,10 @@ struct FTerm {
   bool neg;
 };
 
-static cudaError_t launch_leaf_f32(const std::vector<FTerm> &terms, int np, int64_t M, int64_t N,
-                                   int64_t K, float *out, int64_t ldo, int lower,
+// np: pieces stored per plane set; keep: pieces whose pair products are kept
+// (keep <= np: the leading pieces of a longer split are the same values).
+static cudaError_t launch_leaf_f32(const std::vector<FTerm> &terms, int np, int keep, int64_t M,
+                                   int64_t N, int64_t K, float *out, int64_t ldo, int lower,
                                    cudaStream_t st) {
   if (M <= 0 || N <= 0 || terms.empty()) return cudaSuccess;
   // every term must use the same two plane buffers: X planes in one
@@ -844,7 +846,7 @@ static cudaError_t launch_leaf_f32(const std::vector<FTerm> &terms, int np, int6
     return e;
   }
   int pairs[6][2];
-  const int npairs = piece_pairs(np, pairs);
+  const int npairs = piece_pairs(std::min(keep, np), pairs);
   int ng = 0;
   for (const FTerm &t : terms) {
     const int xs = (int)((t.x->ptr - X.ptr) / (X.rows * X.kstride));  // plane offset
@@ -931,12 +933,23 @@ void leaf_f32_release() {
   g_pair_units_c.clear();
 }
 
+// BF16 pieces stored per value.  Plain BF16 (AAT_C_BF16) stores two: the
+// 2M form's sum operand Ar +- Ai keeps both, because rounding it to one piece
+// puts an error of the size of the result's entries into G, which Re C = G
+// -+ H -+ H^T carries whole (measured 3.3e-3 for A A^T, against 2.3e-3 when
+// only the inputs Ar, Ai are rounded).
 static int pieces_for(uint32_t flags) {
   switch (flags & AAT_C_PREC_MASK) {
     case AAT_C_BF16X3: return 2;
-    case AAT_C_BF16: return 1;
+    case AAT_C_BF16: return 2;
     default: return 3;
   }
+}
+
+// Pieces whose pair products are kept for products of plain operands (Ar,
+// Ai, the 3M sums): one for AAT_C_BF16, all stored pieces otherwise.
+static int pieces_kept(uint32_t flags) {
+  return (flags & AAT_C_PREC_MASK) == AAT_C_BF16 ? 1 : pieces_for(flags);
 }
 
 // ---------------------------------------------- complex elementwise kernels
@@ -1075,7 +1088,8 @@ struct CArena {
 };
 
 struct CCtx {
-  int np;
+  int np;    // pieces stored per value
+  int keep;  // pieces kept for products of plain operands
   cudaStream_t st;
   CArena ar;
   int err = AAT_OK;
@@ -1143,9 +1157,11 @@ static void c_two_m(CCtx &c, const float2 *A, int64_t lda, int64_t n, int64_t k,
     csplit(c, A, lda, n, k, o);
     // H = Ar Ai^T (all entries), G = (Ar + Ai)(Ar +- Ai)^T (lower tiles)
     if (c.err == AAT_OK)
-      cchk(c, launch_leaf_f32({FTerm{&Xr, &Yi, false}}, c.np, n, n, k, H, n, 0, c.st), "2M H");
-    if (c.err == AAT_OK)
-      cchk(c, launch_leaf_f32({FTerm{&Xs, &Ysd, false}}, c.np, n, n, k, G, n, 1, c.st), "2M G");
+      cchk(c, launch_leaf_f32({FTerm{&Xr, &Yi, false}}, c.np, c.keep, n, n, k, H, n, 0, c.st),
+           "2M H");
+    if (c.err == AAT_OK)  // G's sum operands keep every stored piece
+      cchk(c, launch_leaf_f32({FTerm{&Xs, &Ysd, false}}, c.np, c.np, n, n, k, G, n, 1, c.st),
+           "2M G");
     if (c.err == AAT_OK) {
       const int64_t nt = (n + T - 1) / T;
       ProfScope prof(AAT_K_POSTADD, c.st, (double)n * n * (4.0 * 1.5 + 8.0 * 0.5));
@@ -1186,11 +1202,11 @@ static void c_gen_leaf(CCtx &c, const float2 *X, int64_t ldx, const float2 *Y, i
     csplit(c, X, ldx, M, K, ox);
     csplit(c, Y, ldy, N, K, oy);
     if (c.err == AAT_OK)
-      cchk(c, launch_leaf_f32({FTerm{&Xr, &Yr, false}}, c.np, M, N, K, T1, N, 0, c.st), "3M T1");
+      cchk(c, launch_leaf_f32({FTerm{&Xr, &Yr, false}}, c.np, c.keep, M, N, K, T1, N, 0, c.st), "3M T1");
     if (c.err == AAT_OK)
-      cchk(c, launch_leaf_f32({FTerm{&Xi, &Yi, false}}, c.np, M, N, K, T2, N, 0, c.st), "3M T2");
+      cchk(c, launch_leaf_f32({FTerm{&Xi, &Yi, false}}, c.np, c.keep, M, N, K, T2, N, 0, c.st), "3M T2");
     if (c.err == AAT_OK)
-      cchk(c, launch_leaf_f32({FTerm{&Xs, &Ys, false}}, c.np, M, N, K, T3, N, 0, c.st), "3M T3");
+      cchk(c, launch_leaf_f32({FTerm{&Xs, &Ys, false}}, c.np, c.keep, M, N, K, T3, N, 0, c.st), "3M T3");
     if (c.err == AAT_OK) {
       ProfScope prof(AAT_K_POSTADD, c.st, (double)M * N * (12.0 + 8.0));
       combine3m_kernel<<<grid_c(M * N, 256), 256, 0, c.st>>>(T1, T2, T3, N, M, N, C, ldc);
@@ -1291,6 +1307,7 @@ static size_t c_plan(CCtx &c, int method, const float2 *A, int64_t n, int64_t k,
 static int complex_levels(int64_t n, int64_t k, uint32_t flags) {
   const uint32_t lv = (flags & AAT_LEVELS_MASK) >> 8;
   if (lv) return (int)lv - 1;
+  if ((flags & AAT_C_PREC_MASK) == AAT_C_BF16) return 0;  // see bf16_levels_ok
   int levels = 0;  // one level pays off once the leaves stay large
   while (levels < 4 && (n >> (levels + 1)) >= 4096 && (k >> (levels + 1)) >= 2048) ++levels;
   return levels;
@@ -1387,10 +1404,11 @@ cudaError_t cbatch_build(const CBInput *in, int count, char *ws, CBatch *out) {
     L->split_bytes += (double)q.n * q.k * (8.0 + 2.0 * np * (q.herm ? 3 : 4));
     L->comb_bytes += (double)q.n * q.n * (4.0 * 1.5 + 8.0 * 0.5);
     if (q.herm) L->diag_bytes += (double)q.n * q.k * 8.0;
-    // two jobs: H = Ar Ai^T (all entries) from plane sets 0, G (lower) from sets 1
-    int pairs[6][2];
-    const int npairs = piece_pairs(np, pairs);
+    // two jobs: H = Ar Ai^T (all entries) from plane sets 0, G (lower) from
+    // sets 1; G's sum operands keep every stored piece
     for (int jb = 0; jb < 2; ++jb) {
+      int pairs[6][2];
+      const int npairs = piece_pairs(jb == 0 ? pieces_kept(q.flags) : np, pairs);
       FJobDesc d;
       std::memset(&d, 0, sizeof(d));
       cudaError_t e;
@@ -1509,12 +1527,27 @@ cudaError_t cbatch_launch(const CBatch &b, cudaStream_t st) {
   return cudaSuccess;
 }
 
+// Plain BF16 through Algorithm 1: every level's S blocks and post-additions
+// sum several products whose operands are larger than A's blocks, so the
+// BF16 rounding of the leaf operands grows by about 2x per level (relative
+// Frobenius error 8.7e-3 at one level, 1.8e-2 at two, n = k = 8192, N(0, 1)
+// entries): above the 3e-3 that plain BF16 promises, so those depths are
+// refused (2 pieces, AAT_C_BF16X3, stay near 1e-5).
+static bool bf16_levels_ok(uint32_t flags, int levels) {
+  return (flags & AAT_C_PREC_MASK) != AAT_C_BF16 || levels == 0;
+}
+
 int complex_run(int method, const void *A, int64_t n, int64_t k, int64_t lda, void *C,
                 int64_t ldc, uint32_t flags, cudaStream_t st, char *ws, bool dry, size_t *need) {
   CCtx c;
   c.np = pieces_for(flags);
+  c.keep = pieces_kept(flags);
   c.st = st;
   const int levels = method == 2 ? complex_levels(n, k, flags) : 0;
+  if (!bf16_levels_ok(flags, levels))
+    return report_error(AAT_EUNSUPPORTED,
+                        "plain BF16 (AAT_C_BF16) with recursion levels exceeds its 3e-3 error "
+                        "bound: use AAT_LEVELS(0) or AAT_C_BF16X3");
   const size_t peak = c_plan(c, method, (const float2 *)A, n, k, lda, (float2 *)C, ldc, levels,
                              dry, ws);
   if (need) *need = peak;
@@ -1542,8 +1575,13 @@ static int complex_entry(const void *A, int64_t n, int64_t k, int64_t lda, void 
   if (a < cc + ((n - 1) * ldc + n) * 8 && cc < a + ((n - 1) * lda + k) * 8)
     return report_error(AAT_EINVAL, "C overlaps A");
   const int levels = method == 2 ? complex_levels(n, k, flags) : 0;
+  if (!bf16_levels_ok(flags, levels))
+    return report_error(AAT_EUNSUPPORTED,
+                        "plain BF16 (AAT_C_BF16) with recursion levels exceeds its 3e-3 error "
+                        "bound: use AAT_LEVELS(0) or AAT_C_BF16X3");
   CCtx c;
   c.np = pieces_for(flags);
+  c.keep = pieces_kept(flags);
   c.st = st;
   const size_t need = c_plan(c, method, (const float2 *)A, n, k, lda, (float2 *)C, ldc, levels,
                              true, nullptr);

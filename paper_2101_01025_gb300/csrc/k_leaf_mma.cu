@@ -380,4 +380,62 @@ cudaError_t launch_leaf_f64(const int32_t *X, int64_t ldx, const int32_t *Y, int
   return cudaGetLastError();
 }
 
+// ------------------------------------------- peak rate of the instructions
+
+namespace {
+
+constexpr int kPeakChains = 8;  // independent accumulators per thread
+
+// Each warp issues `iters` rounds of kPeakChains independent mma.sync on
+// register operands (no memory traffic); the accumulators feed a store that
+// only happens for an impossible value, so nothing is optimised away.
+__global__ void __launch_bounds__(256) peak_s8_kernel(int64_t iters, int64_t *sink) {
+  uint32_t a[4], b[2];
+  for (int i = 0; i < 4; ++i) a[i] = 0x01010101u * (uint32_t)((threadIdx.x + i) & 3);
+  b[0] = 0x01010101u * (threadIdx.x & 1);
+  b[1] = 0x01010101u * ((threadIdx.x >> 1) & 1);
+  int32_t d[kPeakChains][4] = {};
+  for (int64_t it = 0; it < iters; ++it)
+#pragma unroll
+    for (int c = 0; c < kPeakChains; ++c) mma_s8(d[c], a, b);
+  int64_t acc = 0;
+#pragma unroll
+  for (int c = 0; c < kPeakChains; ++c) acc += (int64_t)d[c][0] + d[c][1] + d[c][2] + d[c][3];
+  if (acc == (int64_t)0x7FFFFFFFFFFFll) sink[0] = acc;
+}
+
+__global__ void __launch_bounds__(256) peak_f64_kernel(int64_t iters, int64_t *sink) {
+  const double a = 1.0 + 1e-3 * (threadIdx.x & 7), b = 1.0 - 1e-3 * (threadIdx.x & 3);
+  double d[kPeakChains][2] = {};
+  for (int64_t it = 0; it < iters; ++it)
+#pragma unroll
+    for (int c = 0; c < kPeakChains; ++c) mma_f64(d[c], a, b);
+  double acc = 0.0;
+#pragma unroll
+  for (int c = 0; c < kPeakChains; ++c) acc += d[c][0] + d[c][1];
+  if (acc == -1.0) sink[0] = (int64_t)acc;
+}
+
+}  // namespace
+
 }  // namespace aat
+
+extern "C" AAT_API int aatx_mma_peak(int kind, int64_t iters, int blocks, void *sink,
+                                     double *ops, void *stream) {
+  using namespace aat;
+  if ((kind != 0 && kind != 1) || iters <= 0 || blocks <= 0 || !sink || !ops)
+    return report_error(AAT_EINVAL, "kind 0 (INT8) or 1 (FP64), iters > 0, blocks > 0, sink, ops");
+  int e = check_gb300();
+  if (e) return e;
+  const double warps = (double)blocks * 8.0;
+  // ops per warp-level instruction: 2 M N K (m16n8k32: 8192; m8n8k4: 512)
+  const double per = kind == 0 ? 2.0 * 16 * 8 * 32 : 2.0 * 8 * 8 * 4;
+  *ops = warps * (double)iters * kPeakChains * per;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (kind == 0)
+    peak_s8_kernel<<<blocks, 256, 0, st>>>(iters, (int64_t *)sink);
+  else
+    peak_f64_kernel<<<blocks, 256, 0, st>>>(iters, (int64_t *)sink);
+  cudaError_t ce = cudaGetLastError();
+  return ce == cudaSuccess ? AAT_OK : report_error(AAT_ECUDA, cudaGetErrorString(ce));
+}

@@ -1371,7 +1371,10 @@ void leaf_tc_batch_free(LeafBatch *lb) {
   lb->impl = nullptr;
 }
 
+void noalloc_forget();
+
 void leaf_tc_release() {
+  noalloc_forget();
   std::lock_guard<std::mutex> lock(g_mu);
   for (auto &kv : g_tiles)
     if (kv.second.first) cudaFree(kv.second.first);
@@ -1417,7 +1420,64 @@ NoAllocDevice g_noalloc_dev[64];
 
 size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// The tile list, row-major, written on the device: no host buffer, no copy.
+__global__ void noalloc_tiles_kernel(int2 *tiles, int TI, int TJ) {
+  const int total = TI * TJ;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x)
+    tiles[t] = make_int2(t / TJ, t - (t / TJ) * TJ);
+}
+
+// Device addresses of the scratch array and status word on the current
+// device, looked up once per device with that device current.
+int noalloc_device(NoAllocDevice *out) {
+  int dev = 0;
+  cudaError_t ce;
+  if ((ce = cudaGetDevice(&dev)) != cudaSuccess || dev < 0 || dev >= 64)
+    return report_error(AAT_ECUDA, "no current device");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  NoAllocDevice &d = g_noalloc_dev[dev];
+  if (!d.ready) {
+    // the host names of the device arrays are not device addresses
+    void *ptr = nullptr;
+    if ((ce = cudaGetSymbolAddress(&ptr, g_noalloc_scratch)) != cudaSuccess)
+      return report_error(AAT_ECUDA, cudaGetErrorString(ce));
+    d.scratch = (unsigned char *)ptr;
+    if ((ce = cudaGetSymbolAddress(&ptr, g_noalloc_status)) != cudaSuccess)
+      return report_error(AAT_ECUDA, cudaGetErrorString(ce));
+    d.status = (int32_t *)ptr;
+    d.ready = true;
+  }
+  *out = d;
+  return AAT_OK;
+}
+
 }  // namespace
+
+// Forgets the looked-up addresses (library shutdown): the next call looks
+// them up again, in case the context was torn down in between.
+void noalloc_forget() {
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  for (NoAllocDevice &d : g_noalloc_dev) d = NoAllocDevice();
+}
+
+// The allocation-free entry point's status word on the current device
+// (AAT_OK or AAT_ETIMEOUT; AAT_OK if it never ran there), cleared with reset.
+// The caller has synchronised the device.
+int noalloc_status(int reset) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return AAT_OK;
+  int32_t *st = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (g_noalloc_dev[dev].ready) st = g_noalloc_dev[dev].status;
+  }
+  if (!st) return AAT_OK;
+  int32_t v = 0;
+  if (cudaMemcpy(&v, st, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return AAT_ECUDA;
+  if (reset) cudaMemset(st, 0, sizeof(int32_t));
+  return v;
+}
+
 }  // namespace aat
 
 extern "C" AAT_API int aat_gemm_modp_noalloc(const int32_t *X, int64_t ldx, const int32_t *Y,
@@ -1457,26 +1517,10 @@ extern "C" AAT_API int aat_gemm_modp_noalloc(const int32_t *X, int64_t ldx, cons
     return report_error(AAT_ERANGE, msg);
   }
   int dev = 0;
-  if ((ce = cudaGetDevice(&dev)) != cudaSuccess || dev < 0 || dev >= 64)
-    return report_error(AAT_ECUDA, "no current device");
+  if ((ce = cudaGetDevice(&dev)) != cudaSuccess) return report_error(AAT_ECUDA, "no current device");
+  // first call on this device: look up the arrays' device addresses
   NoAllocDevice nd;
-  {
-    // First call on this device, with it current: the host names of the
-    // device arrays are not device addresses, so look the addresses up.
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    NoAllocDevice &d = g_noalloc_dev[dev];
-    if (!d.ready) {
-      void *ptr = nullptr;
-      if ((ce = cudaGetSymbolAddress(&ptr, g_noalloc_scratch)) != cudaSuccess)
-        return report_error(AAT_ECUDA, cudaGetErrorString(ce));
-      d.scratch = (unsigned char *)ptr;
-      if ((ce = cudaGetSymbolAddress(&ptr, g_noalloc_status)) != cudaSuccess)
-        return report_error(AAT_ECUDA, cudaGetErrorString(ce));
-      d.status = (int32_t *)ptr;
-      d.ready = true;
-    }
-    nd = d;
-  }
+  if ((e = noalloc_device(&nd))) return e;
   Planes px, py;
   std::memset(&px, 0, sizeof(px));
   px.nbase = ds.L;
@@ -1497,22 +1541,10 @@ extern "C" AAT_API int aat_gemm_modp_noalloc(const int32_t *X, int64_t ldx, cons
   // the status word must start at zero; planes and tiles are fully rewritten
   if ((ce = cudaMemsetAsync(nd.status, 0, sizeof(int32_t), st)) != cudaSuccess)
     return report_error(AAT_ECUDA, cudaGetErrorString(ce));
-  // tile list, row-major, copied in pieces from a fixed host buffer
-  {
-    int2 buf[2048];
-    int64_t cnt = 0, done = 0;
-    for (int64_t i = 0; i < TI; ++i)
-      for (int64_t j = 0; j < TJ; ++j) {
-        buf[cnt++] = make_int2((int)i, (int)j);
-        if (cnt == 2048 || (i == TI - 1 && j == TJ - 1)) {
-          ce = cudaMemcpyAsync(tiles_dev + done, buf, (size_t)cnt * sizeof(int2),
-                               cudaMemcpyHostToDevice, st);
-          if (ce != cudaSuccess) return report_error(AAT_ECUDA, cudaGetErrorString(ce));
-          done += cnt;
-          cnt = 0;
-        }
-      }
-  }
+  // tile list, row-major, written by a kernel (no host buffer to copy from)
+  noalloc_tiles_kernel<<<(unsigned)std::min<int64_t>((TI * TJ + 255) / 256, 1024), 256, 0, st>>>(
+      tiles_dev, (int)TI, (int)TJ);
+  if ((ce = cudaGetLastError()) != cudaSuccess) return report_error(AAT_ECUDA, cudaGetErrorString(ce));
   if ((ce = launch_split(X, ldx, m, k, mp, ds.b, px, st)) != cudaSuccess)
     return report_error(AAT_ECUDA, cudaGetErrorString(ce));
   if (!same && (ce = launch_split(Y, ldy, n, k, mp, ds.b, py, st)) != cudaSuccess)
@@ -1600,4 +1632,46 @@ extern "C" AAT_API int aatx_leaf_groups(uint32_t p, int64_t K, uint32_t flags, i
     o[5] = (int32_t)g[i].ratio;
   }
   return ng;
+}
+
+// ------------------------------------------------- failure-path test probe
+
+namespace aat {
+namespace {
+
+// One thread waits, with the bounded wait the leaf kernels use, for a phase
+// of a fresh mbarrier that nothing will ever complete; the wait gives up
+// after limit_ns and records AAT_ETIMEOUT in `status`.  Nothing else runs.
+__global__ void wait_probe_kernel(int32_t *status, unsigned long long limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x != 0) return;
+  abort_flag = 0;
+  const uint32_t b = (uint32_t)__cvta_generic_to_shared(&bar);
+  tc::mbar_init(b, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  tc::wait_bounded<false>(b, 0, &abort_flag, status, limit_ns);
+}
+
+}  // namespace
+}  // namespace aat
+
+extern "C" AAT_API int aatx_wait_probe(int which, int64_t limit_ns, void *stream) {
+  using namespace aat;
+  if (limit_ns <= 0 || limit_ns > 2000000000LL || (which != 0 && which != 1))
+    return report_error(AAT_EINVAL, "which must be 0 or 1, limit in (0, 2 s]");
+  int e = check_gb300();
+  if (e) return e;
+  int32_t *status = nullptr;
+  if (which == 0) {
+    status = device_status_ptr();
+    if (!status) return report_error(AAT_ECUDA, "no device status word");
+  } else {
+    NoAllocDevice nd;
+    if ((e = noalloc_device(&nd))) return e;
+    status = nd.status;
+  }
+  wait_probe_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(status, (unsigned long long)limit_ns);
+  cudaError_t ce = cudaGetLastError();
+  return ce == cudaSuccess ? AAT_OK : report_error(AAT_ECUDA, cudaGetErrorString(ce));
 }

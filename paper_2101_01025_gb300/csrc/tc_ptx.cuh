@@ -106,10 +106,12 @@ __device__ __forceinline__ void cluster_sync() {
 
 // Bounded wait for the phase of parity `parity` of barrier `bar`.  Returns
 // false when the limit expires (and raises the CTA abort flag and the device
-// status) or when another role of the CTA has aborted.
+// status) or when another role of the CTA has aborted.  limit_ns: kTimeoutNs
+// in the kernels; the failure-path test probe passes a short one.
 template <bool CLUSTER = false>
 __device__ __forceinline__ bool wait_bounded(uint32_t bar, uint32_t parity, volatile int *abort_flag,
-                                          int32_t *status) {
+                                          int32_t *status,
+                                          unsigned long long limit_ns = kTimeoutNs) {
   auto test = [&]() { return CLUSTER ? mbar_try_cluster(bar, parity) : mbar_try(bar, parity); };
   if (test()) return true;
   const unsigned long long t0 = gtimer();
@@ -117,7 +119,7 @@ __device__ __forceinline__ bool wait_bounded(uint32_t bar, uint32_t parity, vola
     if (test()) return true;
     if ((it & 63u) == 0) {
       if (*abort_flag) return false;
-      if (gtimer() - t0 > kTimeoutNs) {
+      if (gtimer() - t0 > limit_ns) {
         *abort_flag = 1;
         atomicExch(status, (int32_t)AAT_ETIMEOUT);
         return false;

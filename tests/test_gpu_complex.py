@@ -4,10 +4,9 @@ Error metric (per result): relative Frobenius error of the lower triangle,
 ||Low(C) - Low(C_ref)||_F / ||Low(C_ref)||_F, against the oracle's fp64
 sums.  Bounds: 1e-5 for AAT_C_FP32 (3 BF16 pieces, 6 piece products),
 1e-4 for AAT_C_BF16X3 (2 pieces: dropped terms of relative size 2^-16),
-3e-3 for AAT_C_BF16 with A A^H.  A A^T by 2M with plain BF16 gets 5e-3:
-there Re C = G + H - H^T adds the BF16 rounding errors (2^-9 per input) of
-three products of the same size as the result, and no FP64 diagonal takes
-a large share of the norm.  Small-integer inputs are exact in every mode.
+3e-3 for AAT_C_BF16 (plain BF16) in every form it is offered in: A A^H and
+A A^T by 2M, and Algorithm 1 at depth 0; deeper Algorithm 1 is refused in
+plain BF16.  Small-integer inputs are exact in every mode.
 """
 import numpy as np
 import pytest
@@ -19,7 +18,6 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL = {0: 1e-5, 1 << 16: 1e-4, 2 << 16: 3e-3}
-TOL_T_BF16 = 5e-3   # A A^T by 2M, plain BF16
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -56,8 +54,16 @@ def test_complex_matches_oracle(lib, herm, flags, n, k):
     C = run(lib, A, herm, flags)
     ref = oracle.complex_low(A.astype(np.complex128), conj=herm)
     err = rel_low_err(C, ref)
-    tol = TOL_T_BF16 if (not herm and flags == 2 << 16) else TOL[flags]
-    assert err <= tol, err
+    if flags == 2 << 16 and n * (n + 1) // 2 < 64:
+        # a handful of entries: the Frobenius bound is a statement about many
+        # rounding errors; one product of two BF16-rounded values can be off
+        # by 2 * 2^-8 of |a||b|, so check that componentwise bound instead
+        A64 = A.astype(np.complex128)
+        mag = np.abs(A64.real) + np.abs(A64.imag)
+        bound = 4 * 2.0**-8 * (mag @ mag.T) + 1e-6
+        assert np.all(np.abs(np.tril(C) - np.tril(ref)) <= np.tril(bound))
+    else:
+        assert err <= TOL[flags], err
     if herm:
         d = np.diag(C)
         assert np.all(d.imag == 0) and np.all(d.real >= 0)
@@ -66,7 +72,7 @@ def test_complex_matches_oracle(lib, herm, flags, n, k):
 
 
 @pytest.mark.parametrize("herm", [True, False])
-@pytest.mark.parametrize("flags", [0, 1 << 16])
+@pytest.mark.parametrize("flags", [0, 1 << 16, 2 << 16])
 def test_complex_ill_scaled_rows(lib, herm, flags):
     A = synth.complex_normal(99, (400, 300), ill_scaled=True)
     C = run(lib, A, herm, flags)
@@ -134,11 +140,11 @@ def test_complex_n16384_sampled(lib):
 
 # ----------------------------------------- A A^T over C by Algorithm 1 (Y = iI)
 
-# Plain BF16 through the recursion: each level forms sums and differences
-# of blocks (S1..S4, U1..U5) whose BF16 input rounding (2^-9) is relative to
-# the larger intermediate blocks, so the error grows with the depth.
-TOL_ALG1 = {0: 1e-5, 1 << 16: 1e-4}
-TOL_ALG1_BF16 = {0: 5e-3, 1: 1e-2, 2: 4e-2}
+# Plain BF16 is offered at depth 0 only (where Algorithm 1 is the 2M form):
+# each level forms sums and differences of blocks (S1..S4, U1..U5) whose BF16
+# rounding is relative to the larger intermediate blocks, so the error grows
+# past 3e-3 and those depths are refused.
+TOL_ALG1 = {0: 1e-5, 1 << 16: 1e-4, 2 << 16: 3e-3}
 
 
 @pytest.mark.parametrize("flags", [0, 1 << 16, 2 << 16])
@@ -147,12 +153,68 @@ TOL_ALG1_BF16 = {0: 5e-3, 1: 1e-2, 2: 4e-2}
 def test_aat_complex_alg1_matches_oracle(lib, flags, n, k, levels):
     A = synth.complex_normal(n * 3 + k + levels, (n, k))
     Ad = torch.from_numpy(np.ascontiguousarray(A)).cuda()
+    if flags == 2 << 16 and levels > 0:
+        with pytest.raises(lib.AatError) as ei:
+            lib.aat_complex(Ad, flags=flags, levels=levels)
+        assert ei.value.code == lib._native.AAT_EUNSUPPORTED
+        return
     C = lib.aat_complex(Ad, flags=flags, levels=levels)
     torch.cuda.synchronize()
     ref = oracle.complex_low(A.astype(np.complex128), conj=False)
     err = rel_low_err(C.cpu().numpy(), ref)
-    tol = TOL_ALG1_BF16[levels] if flags == 2 << 16 else TOL_ALG1[flags]
-    assert err <= tol, err
+    assert err <= TOL_ALG1[flags], err
+
+
+def test_aat_complex_bf16_default_depth_is_zero(lib):
+    """Without level bits, plain BF16 runs Algorithm 1 at depth 0 (the 2M
+    form) even where the FP32 classes would recurse (n/2 >= 4096)."""
+    n, k = 8192, 4096
+    A = synth.complex_normal(synth.SEED_BASE + 41, (n, k))
+    Ad = torch.from_numpy(A).cuda()
+    C = lib.aat_complex(Ad, flags=2 << 16)
+    torch.cuda.synchronize()
+    ij = _sample_ij(n, 2000, 41)
+    ref = oracle.complex_entries(A.astype(np.complex128), ij, conj=False)
+    got = C[torch.from_numpy(ij[:, 0]).cuda(), torch.from_numpy(ij[:, 1]).cuda()]
+    got = got.cpu().numpy().astype(np.complex128)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 3e-3
+
+
+def _sample_ij(n, count, seed):
+    """Random lower entries, every block boundary of the recursion (rows and
+    columns at multiples of n/4, +-1) and every 97th diagonal entry."""
+    rng = np.random.default_rng(seed)
+    i = rng.integers(0, n, count)
+    j = rng.integers(0, n, count)
+    ij = np.stack([np.maximum(i, j), np.minimum(i, j)], 1)
+    edges = sorted({e + d for e in range(0, n + 1, n // 4) for d in (-1, 0) if 0 <= e + d < n})
+    bd = np.array([[a, b] for a in edges for b in edges if a >= b])
+    dg = np.array([[r, r] for r in range(0, n, 97)])
+    return np.concatenate([ij, bd, dg])
+
+
+@pytest.mark.parametrize("ill", [False, True])
+def test_aat_complex_alg1_n8192_sampled(lib, ill):
+    """Algorithm 1 over C (Y = i I) at n = k = 8192 (the complex workload),
+    at 1 and 2 levels in the FP32 and 2-piece classes, plus plain BF16 at
+    depth 0 (its only depth), on N(0, 1) entries and on the ill-scaled
+    variant (row i times 10^u_i, u_i uniform in [-3, 3]): sampled entries
+    against the oracle's FP64 sums, every class within its bound."""
+    n = k = 8192
+    A = synth.complex_normal(synth.SEED_BASE + 3 + (50 if ill else 0), (n, k), ill_scaled=ill)
+    Ad = torch.from_numpy(A).cuda()
+    ij = _sample_ij(n, 3000, 7)
+    ref = oracle.complex_entries(A.astype(np.complex128), ij, conj=False)
+    for flags, levels in [(0, 1), (0, 2), (1 << 16, 1), (1 << 16, 2), (2 << 16, 0)]:
+        C = lib.aat_complex(Ad, flags=flags, levels=levels)
+        torch.cuda.synchronize()
+        got = C[torch.from_numpy(ij[:, 0]).cuda(), torch.from_numpy(ij[:, 1]).cuda()]
+        got = got.cpu().numpy().astype(np.complex128)
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert err <= TOL_ALG1[flags], (flags, levels, err)
+        del C
+    with pytest.raises(lib.AatError):
+        lib.aat_complex(Ad, flags=2 << 16, levels=1)
 
 
 def test_aat_complex_alg1_small_integers_exact(lib):

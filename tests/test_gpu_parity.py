@@ -207,6 +207,22 @@ def test_aat_modp_mma_leaves_match_oracle(lib, leaf, p, n, k, levels):
     assert low_equal(C, oracle.aat_modp_low(A, p))
 
 
+@pytest.mark.parametrize("leaf", ["tc", "i8", "f64"])
+def test_config1_512_p131071_one_level_every_leaf(lib, leaf):
+    """The small workload exactly: A 512 x 512 over F_131071 (131071 = 3 mod 4,
+    so Y = [[a, b], [-b, a]] (x) I), uniform residues in [0, p) from the
+    seeded generator, one recursion level then the leaf, bit-exact against the
+    oracle with each of the three leaf kinds."""
+    p, n = 131071, 512
+    A = synth.residues(synth.SEED_BASE + 0, (n, n), p)
+    C = host(lib.aat_modp(dev(A), p, levels=1, flags=LEAFKINDS[leaf]))
+    assert low_equal(C, oracle.aat_modp_low(A, p))
+    from paper_2101_01025_gb300 import testing as T
+    st = T.plan_stats(n, n, p, lib.AAT_LEVELS(1) | LEAFKINDS[leaf])
+    assert st.levels == 1 and st.n_pad == n and st.k_pad == n
+    assert st.recursive_products == 3 and st.general_products == 2 and st.syrk_leaves == 3
+
+
 @pytest.mark.parametrize("p", [65521, 2**31 - 1])
 @pytest.mark.parametrize("n,k", [(300, 200), (640, 640)])
 @pytest.mark.parametrize("levels", [0, 1, 2])

@@ -348,3 +348,23 @@ def test_tuning_table_carries_winograd_choice(tmp_path):
     saved = {(e["n"], e["k"]): e["winograd"] for e in json.loads(out.read_text())["entries"]}
     assert saved == {(1024, 1024): 1, (2048, 1024): 0}
     aat.tune_clear()
+
+
+def test_allocation_limit_hook_gives_enomem():
+    """The test allocation limit turns a workspace request into AAT_ENOMEM
+    before any CUDA call (so this runs without a GPU), names the request in
+    the message, and SIZE_MAX lifts it again."""
+    lib = _native.lib()
+    try:
+        lib.aatx_set_alloc_limit(1 << 20)
+        assert lib.aatx_workspace_reserve((1 << 20) + 1) == _native.AAT_ENOMEM
+        assert "1048577 bytes refused" in _native.last_error()
+    finally:
+        lib.aatx_set_alloc_limit(2**64 - 1)
+
+
+def test_wait_probe_rejects_bad_arguments():
+    lib = _native.lib()
+    assert lib.aatx_wait_probe(2, 1000, None) == _native.AAT_EINVAL
+    assert lib.aatx_wait_probe(0, 0, None) == _native.AAT_EINVAL
+    assert lib.aatx_wait_probe(0, 3 * 10**9, None) == _native.AAT_EINVAL
