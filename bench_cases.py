@@ -36,6 +36,8 @@ def main(argv=None):
                     help="leaf kind of the F_p cases")
     ap.add_argument("--plain-digits", action="store_true",
                     help="one product per digit pair instead of the pair-sum form")
+    ap.add_argument("--low-memory", action="store_true",
+                    help="the low-memory schedule (plane passes, AAT_LOW_MEMORY)")
     ap.add_argument("--profile", action="store_true",
                     help="per kernel class: launches, ms per repetition and the rate of "
                          "its algorithmic work (bytes or FLOPs) over the timed repetitions")
@@ -50,6 +52,8 @@ def main(argv=None):
     torch.manual_seed(0x2101)
     n, k, p = a.n, a.k or a.n, a.p
     flags = aat.AAT_DIGITS_PLAIN if a.plain_digits else 0
+    if a.low_memory:
+        flags |= aat.AAT_LOW_MEMORY
     flags |= {"tc": aat.AAT_LEAF_TC, "i8": aat.AAT_LEAF_I8, "f64": aat.AAT_LEAF_F64,
               "simt": aat.AAT_LEAF_SIMT}[a.leaf]
     half = (p - 1) // 2

@@ -74,6 +74,20 @@ extern "C" {
  * with omega = log2 7).  Applies where the last level's blocks have even
  * sides; the result is the same. */
 #define AAT_WINOGRAD (1u << 13)
+/* Low-memory schedule (Sec. 7: Table 3 keeps every S and P block of a level
+ * in C, with only C12 as temporary storage).  The fast schedule keeps the
+ * BF16 digit planes of every leaf operand whole: for p = 2^31 - 1 that is
+ * 20 bytes per element of each operand block (8.75 GiB of workspace at
+ * n = k = 16384).  With this flag each leaf product runs in passes over
+ * windows of its plane sequence: a pass re-forms the S blocks from A (or
+ * splits A's blocks), writes one plane of each operand and runs that plane
+ * product, accumulating into the blocks of C where Table 3 puts them.  The
+ * workspace is then at most 3 n k bytes for k <= n (three quarters of A's
+ * int32 size; 768 MiB at n = k = 16384), at the cost of one pass over A per
+ * plane and a read-modify-write of C per plane.  Applies to the tensor-core
+ * leaf with the pair-sum digit form (p = 2^31 - 1, 65521, ...); other leaf
+ * and digit forms run the fast schedule.  The result is the same. */
+#define AAT_LOW_MEMORY (1u << 14)
 
 /*
  * Low(A A^T) mod p (Algorithm 1, Sec. 3; Low as defined in Sec. 2).
@@ -302,6 +316,14 @@ AAT_API void aat_plan_destroy(aat_plan_t *plan);
 
 /* Bytes of device workspace aat_modp_ex would use for (n, k, p, flags). */
 AAT_API size_t aat_workspace_size(int64_t n, int64_t k, uint32_t p, uint32_t flags);
+
+/* Workspace limit of aat_modp_ex and aat_modp_host (per process, all
+ * devices): a product whose fast schedule needs more than `bytes` of library
+ * workspace runs the low-memory schedule (AAT_LOW_MEMORY) instead.  SIZE_MAX
+ * (the default) sets no limit.  Independently of the limit, a product whose
+ * fast workspace cannot be allocated (cudaMalloc fails) retries with the
+ * low-memory schedule before it reports AAT_ENOMEM. */
+AAT_API void aat_set_workspace_limit(size_t bytes);
 
 /* Message for the last error of the calling thread ("" if none). */
 AAT_API const char *aat_last_error(void);

@@ -108,7 +108,7 @@ AAT_API int aatx_wait_probe(int which, int64_t limit_ns, void *stream);
  * independent mma.sync on register operands: kind 0 m16n8k32 s8 (INT8,
  * INT32 accumulation), kind 1 m8n8k4 f64.  *ops receives the operations the
  * launch performs (2 M N K per instruction); divide by its CUDA-event time.
- * sink: device memory of 8 bytes (written only for an impossible value). */
+ * sink: device memory of 8 bytes (never written; it keeps the loop alive). */
 AAT_API int aatx_mma_peak(int kind, int64_t iters, int blocks, void *sink, double *ops,
                           void *stream);
 

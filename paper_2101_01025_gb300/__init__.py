@@ -17,10 +17,12 @@ import os
 
 from . import _native
 from ._native import (AAT_C_BF16, AAT_C_BF16X3, AAT_C_FP32, AAT_DIGITS_PLAIN,  # noqa: F401
-                      AAT_IN_BALANCED, AAT_LEAF_F64, AAT_LEAF_I8, AAT_LEAF_SIMT, AAT_LEAF_TC, AAT_LEVELS, AAT_WINOGRAD, AAT_ZERO_UPPER, AatError, PlanStats, check, last_error, lib)
+                      AAT_IN_BALANCED, AAT_LEAF_F64, AAT_LEAF_I8, AAT_LEAF_SIMT, AAT_LEAF_TC,
+                      AAT_LEVELS, AAT_LOW_MEMORY, AAT_WINOGRAD, AAT_ZERO_UPPER, AatError,
+                      PlanStats, check, last_error, lib)
 
 __all__ = [
-    "aat_modp", "aat_syrk_modp", "aah_quat_modp", "aat_gemm_modp", "aat_modp_host", "aat_modp_host_d2h_bytes", "aat_workspace_size",
+    "aat_modp", "aat_syrk_modp", "aah_quat_modp", "aat_gemm_modp", "aat_modp_host", "aat_modp_host_d2h_bytes", "aat_workspace_size", "aat_set_workspace_limit",
     "aat_device_status", "tune_modp", "tune_lookup", "tune_save", "tune_load", "tune_clear",
     "aat_shutdown", "aat_version", "aah_complex", "aat_complex_2m", "aat_complex", "Plan", "AAT_LEVELS", "AAT_LEAF_TC", "AAT_LEAF_SIMT",
     "AAT_ZERO_UPPER", "AAT_IN_BALANCED", "AatError",
@@ -285,6 +287,12 @@ class Plan:
 
 def aat_workspace_size(n: int, k: int, p: int, flags: int = 0) -> int:
     return int(lib().aat_workspace_size(n, k, p, flags))
+
+
+def aat_set_workspace_limit(nbytes: int | None) -> None:
+    """Products whose fast schedule needs more workspace than ``nbytes`` run
+    the low-memory schedule (AAT_LOW_MEMORY); None removes the limit."""
+    lib().aat_set_workspace_limit(2**64 - 1 if nbytes is None else int(nbytes))
 
 
 def aat_device_status(reset: bool = False) -> int:

@@ -30,6 +30,7 @@ AAT_LEAF_I8 = 2 << 4
 AAT_LEAF_F64 = 3 << 4
 AAT_DIGITS_PLAIN = 1 << 12
 AAT_WINOGRAD = 1 << 13
+AAT_LOW_MEMORY = 1 << 14
 AAT_C_FP32 = 0 << 16
 AAT_C_BF16X3 = 1 << 16
 AAT_C_BF16 = 2 << 16
@@ -44,7 +45,7 @@ EXPORTS = [
     "aat_modp", "aat_modp_ex", "aat_syrk_modp", "aah_quat_modp", "aat_modp_host", "aat_modp_host_d2h_bytes", "aat_gemm_modp",
     "aat_gemm_modp_noalloc", "aat_tune_modp", "aat_tune_lookup", "aat_tune_save", "aat_tune_load",
     "aat_tune_clear",
-    "aat_workspace_size",
+    "aat_workspace_size", "aat_set_workspace_limit",
     "aat_last_error", "aat_device_status", "aat_shutdown", "aat_version",
     "aat_profile_begin", "aat_profile_end", "aah_complex", "aah_complex_ex", "aat_complex_2m",
     "aat_complex", "aat_complex_ex", "aat_plan_create", "aat_plan_execute", "aat_plan_info",
@@ -167,6 +168,8 @@ def lib():
         L.aat_tune_clear.restype = None
         L.aat_workspace_size.argtypes = [i64, i64, u32, u32]
         L.aat_workspace_size.restype = ctypes.c_size_t
+        L.aat_set_workspace_limit.argtypes = [ctypes.c_size_t]
+        L.aat_set_workspace_limit.restype = None
         L.aat_last_error.restype = ctypes.c_char_p
         L.aat_device_status.argtypes = [i32]
         L.aat_shutdown.restype = None

@@ -304,6 +304,9 @@ int32_t *device_status_ptr() {
 // Test hook: workspace requests above this many bytes fail with AAT_ENOMEM
 // as a failed cudaMalloc would, before any CUDA call (SIZE_MAX: no limit).
 static std::atomic<size_t> g_alloc_limit{SIZE_MAX};
+// aat_set_workspace_limit: products whose fast schedule needs more workspace
+// run the low-memory plane passes (SIZE_MAX: no limit).
+static std::atomic<size_t> g_ws_limit{SIZE_MAX};
 
 static int ensure_workspace(size_t bytes, void **out) {
   if (bytes > g_alloc_limit.load())
@@ -411,6 +414,10 @@ struct Ctx {
   cudaEvent_t in_a11 = nullptr, in_rest = nullptr;
   uint32_t alpha = 1;  // scale of every product (the SYRK update's alpha)
   bool wino = false;   // last level's P3, P4 by Winograd's form (AAT_WINOGRAD)
+  // low-memory plane passes (AAT_LOW_MEMORY): every leaf product runs as
+  // passes over windows of pass_w planes of its operands' plane sequence
+  bool passes = false;
+  int pass_w = 1;
 };
 
 static Planes planes_for(const DigitSpec &ds, int64_t rows, int64_t cols) {
@@ -438,6 +445,25 @@ static Planes planes_alloc(Ctx &c, int64_t rows, int64_t cols) {
 static Planes no_planes() {
   Planes P;
   std::memset(&P, 0, sizeof(P));
+  return P;
+}
+
+// The low-memory plane passes apply to the tensor-core leaf with the
+// pair-sum digit form, where every plane product reads one plane of each
+// operand (plane q of X with plane q of Y): a pass over the plane window
+// [q0, q0 + w) needs only those w planes of each operand.
+static bool pass_mode(const Ctx &c) {
+  return c.passes && c.leaf == AAT_LEAF_TC && c.ds.nsum > 0;
+}
+
+static int plane_count(const Ctx &c) { return c.ds.L + c.ds.nsum; }
+
+// Planes q0 .. q0 + w - 1 of an r x c block, in the arena.
+static Planes planes_window(Ctx &c, int64_t rows, int64_t cols, int q0, int w) {
+  Planes P = planes_for(c.ds, rows, cols);
+  P.q0 = q0;
+  P.L = w;
+  P.ptr = (__nv_bfloat16 *)c.ar.get((size_t)w * rows * P.kstride * 2);
   return P;
 }
 
@@ -517,6 +543,31 @@ static void leaf(Ctx &c, Operand X, Operand Y, bool same, int64_t M, int64_t N, 
     return;
   }
   const size_t mark = c.ar.used;
+  if (pass_mode(c) && X.pl.L == 0 && (same || Y.pl.L == 0)) {
+    // low-memory plane passes: split a window of planes, run its plane
+    // products, accumulate (the first pass with live terms takes beta)
+    const int Q = plane_count(c);
+    bool first = true;
+    for (int q0 = 0; q0 < Q; q0 += c.pass_w) {
+      const int w = std::min(c.pass_w, Q - q0);
+      const size_t mk = c.ar.used;
+      Planes px = planes_window(c, M, K, q0, w), py = px;
+      if (!same) py = planes_window(c, N, K, q0, w);
+      const TcLeafArgs a = tc_args(c, px, py, M, N, K, out, ldo, lower, first ? beta : 1);
+      if (!c.ar.dry && c.err == AAT_OK && leaf_tc_terms(a, c.m) > 0) {
+        check(c, launch_split(X.x, X.ld, M, K, c.m, c.ds.b, px, c.st), "split");
+        if (!same) check(c, launch_split(Y.x, Y.ld, N, K, c.m, c.ds.b, py, c.st), "split");
+        check(c, launch_leaf_tc(a, c.m, c.st), "leaf (tensor cores, plane pass)");
+        first = false;
+      }
+      c.ar.used = mk;
+    }
+    if (!c.ar.dry && first && beta == 0)  // every term vanished mod p
+      check(c, cudaMemset2DAsync(out, (size_t)ldo * 4, 0, (size_t)N * 4, (size_t)M, c.st),
+            "zero product");
+    c.ar.used = mark;
+    return;
+  }
   if (X.pl.L == 0) {
     X.pl = planes_alloc(c, M, K);
     if (!c.ar.dry) check(c, launch_split(X.x, X.ld, M, K, c.m, c.ds.b, X.pl, c.st), "split");
@@ -671,12 +722,19 @@ static int fuse_override() {
 // c.alpha).  n must be divisible by 2^levels and k by 2^levels (2^(levels+1)
 // for a kind-2 Y).  `ap` optionally holds the digit planes of A
 // (tensor-core leaf).  Memory placement of Table 3 (Sec. 7).
+static void rec_passes(Ctx &c, const int32_t *A, int64_t lda, int64_t n, int64_t k, int32_t *C,
+                       int64_t ldc, int levels);
+
 static void rec(Ctx &c, const int32_t *A, int64_t lda, int64_t n, int64_t k, int32_t *C,
                 int64_t ldc, int levels, Planes ap) {
   if (c.err != AAT_OK) return;
   if (levels == 0 || n < 2 || k < 2) {
     Operand X{A, lda, ap};
     leaf(c, X, X, true, n, n, k, C, ldc, 1, 0);
+    return;
+  }
+  if (pass_mode(c)) {
+    rec_passes(c, A, lda, n, k, C, ldc, levels);
     return;
   }
   const int64_t h = n / 2, kap = k / 2;
@@ -758,6 +816,148 @@ static void rec(Ctx &c, const int32_t *A, int64_t lda, int64_t n, int64_t k, int
     rec(c, A12, lda, h, kap, C12, ldc, levels - 1, no_planes());
     if (!c.ar.dry) check(c, launch_add_low(C11, ldc, C12, ldc, h, c.m, c.st), "add_low");
   }
+  c.ar.used = mark;
+}
+
+// One level of Algorithm 1 in low-memory plane passes (Sec. 7: the point of
+// Table 3's placement is that C itself holds the S and P blocks; here the
+// digit planes of the leaf operands, which the fast schedule keeps whole,
+// exist only one window at a time).  Each pass re-forms the S blocks from A
+// in one pass over A, writes the window's planes of the operands and runs
+// the window's plane products, which accumulate into the blocks of C where
+// Table 3 puts the products (P4^T -> C22, P5 -> C12, P3 -> C21, P1 -> C11);
+// the first pass stores.  The post-additions and P2 (accumulating onto P1 in
+// C11, U3 = P1 + P2) follow as in the fast schedule.  Above the last level,
+// S3 is written as int32 into C21 (Table 3) in the first pass of P4^T for the
+// recursive P5, and P3's passes run after P5's recursion, since P3's output
+// overwrites S3 in C21.
+static void rec_passes(Ctx &c, const int32_t *A, int64_t lda, int64_t n, int64_t k, int32_t *C,
+                       int64_t ldc, int levels) {
+  const int64_t h = n / 2, kap = k / 2;
+  int32_t *C11 = C, *C12 = C + h, *C21 = C + h * ldc, *C22 = C + h * ldc + h;
+  const int32_t *A11 = A, *A12 = A + kap;
+  const size_t mark = c.ar.used;
+  const int Q = plane_count(c);
+  const bool dry = c.ar.dry;
+  count_level(c);
+  // one pass: the S-block kernel writes the listed outputs; returns whether
+  // the window has live plane products (otherwise nothing runs)
+  auto sblocks_pass = [&](SKernelOut &o, const TcLeafArgs &probe) {
+    if (dry || c.err != AAT_OK || leaf_tc_terms(probe, c.m) == 0) return false;
+    return check(c, launch_sblocks(A, lda, h, kap, c.m, c.y, c.ds.b, o, c.st), "sblocks");
+  };
+  if (levels == 1) {
+    for (int q = 0; q < 4; ++q) count_leaf(c, h, h, kap, q == 1 || q == 3);
+    bool first = true;
+    for (int q0 = 0; q0 < Q; q0 += c.pass_w) {
+      const int w = std::min(c.pass_w, Q - q0);
+      const size_t mk = c.ar.used;
+      SKernelOut o;
+      std::memset(&o, 0, sizeof(o));
+      for (int q = 0; q < 4; ++q) o.sp[q] = planes_window(c, h, kap, q0, w);
+      o.a22 = planes_window(c, h, kap, q0, w);
+      o.a11 = planes_window(c, h, kap, q0, w);
+      const uint32_t beta = first ? 0 : 1;
+      TcLeafArgs fa[4] = {tc_args(c, o.sp[1], o.sp[0], h, h, kap, C22, ldc, 0, beta),  // P4^T
+                          tc_args(c, o.sp[2], o.sp[2], h, h, kap, C12, ldc, 1, beta),  // P5
+                          tc_args(c, o.a22, o.sp[3], h, h, kap, C21, ldc, 0, beta),    // P3
+                          tc_args(c, o.a11, o.a11, h, h, kap, C11, ldc, 1, beta)};     // P1
+      if (sblocks_pass(o, fa[0])) {
+        const int fo = fuse_override();
+        if (fo == 1 || (fo < 0 && leaf_tc_fuse_pays(fa, 4))) {
+          check(c, launch_leaf_tc_multi(fa, 4, c.m, c.st), "leaf (tensor cores, plane pass)");
+        } else {
+          for (const TcLeafArgs &a : fa)
+            check(c, launch_leaf_tc(a, c.m, c.st), "leaf (tensor cores, plane pass)");
+        }
+        first = false;
+      }
+      c.ar.used = mk;
+    }
+    if (!dry && first) {  // every term vanished mod p: the four products are zero
+      for (int32_t *B : {C11, C12, C21, C22})
+        check(c, cudaMemset2DAsync(B, (size_t)ldc * 4, 0, (size_t)h * 4, (size_t)h, c.st),
+              "zero products");
+    }
+    if (!dry) check(c, launch_postadd(C11, ldc, C12, C21, C22, ldc, h, c.m, c.st), "postadd");
+    if (c.split_ev && levels == c.top_levels && !dry && c.err == AAT_OK)
+      cudaEventRecord(c.split_ev, c.st);
+    // P2 = Low(A12 A12^T) accumulated onto P1 in C11: U3 = P1 + P2
+    Operand X{A12, lda, no_planes()};
+    leaf(c, X, X, true, h, h, kap, C11, ldc, 1, 1);
+    c.ar.used = mark;
+    return;
+  }
+  // S3 for the recursive P5: C21 (Table 3), or workspace when kappa > h
+  int32_t *S3;
+  int64_t ldS3;
+  if (kap <= h) {
+    S3 = C21;
+    ldS3 = ldc;
+  } else {
+    S3 = (int32_t *)c.ar.get((size_t)h * kap * 4);
+    ldS3 = kap;
+  }
+  // P4^T = S2 S1^T -> C22 in passes; the first pass also writes S3
+  count_leaf(c, h, h, kap, 0);
+  bool first = true;
+  for (int q0 = 0; q0 < Q; q0 += c.pass_w) {
+    const int w = std::min(c.pass_w, Q - q0);
+    const size_t mk = c.ar.used;
+    SKernelOut o;
+    std::memset(&o, 0, sizeof(o));
+    o.sp[0] = planes_window(c, h, kap, q0, w);
+    o.sp[1] = planes_window(c, h, kap, q0, w);
+    if (q0 == 0) {
+      o.s[2] = S3;
+      o.lds[2] = ldS3;
+    }
+    const TcLeafArgs a = tc_args(c, o.sp[1], o.sp[0], h, h, kap, C22, ldc, 0, first ? 0 : 1);
+    if (!dry && c.err == AAT_OK && q0 == 0 && leaf_tc_terms(a, c.m) == 0) {
+      // S3 is needed whether or not this window has live terms
+      SKernelOut s3;
+      std::memset(&s3, 0, sizeof(s3));
+      s3.s[2] = S3;
+      s3.lds[2] = ldS3;
+      check(c, launch_sblocks(A, lda, h, kap, c.m, c.y, c.ds.b, s3, c.st), "sblocks");
+    }
+    if (sblocks_pass(o, a)) {
+      check(c, launch_leaf_tc(a, c.m, c.st), "leaf (tensor cores, plane pass)");
+      first = false;
+    }
+    c.ar.used = mk;
+  }
+  if (!dry && first)
+    check(c, cudaMemset2DAsync(C22, (size_t)ldc * 4, 0, (size_t)h * 4, (size_t)h, c.st), "zero");
+  // P5 = Low(S3 S3^T) -> C12 (recursive)
+  rec(c, S3, ldS3, h, kap, C12, ldc, levels - 1, no_planes());
+  // P3 = A22 S4^T -> C21 in passes (S3 is no longer needed)
+  count_leaf(c, h, h, kap, 0);
+  first = true;
+  for (int q0 = 0; q0 < Q; q0 += c.pass_w) {
+    const int w = std::min(c.pass_w, Q - q0);
+    const size_t mk = c.ar.used;
+    SKernelOut o;
+    std::memset(&o, 0, sizeof(o));
+    o.sp[3] = planes_window(c, h, kap, q0, w);
+    o.a22 = planes_window(c, h, kap, q0, w);
+    const TcLeafArgs a = tc_args(c, o.a22, o.sp[3], h, h, kap, C21, ldc, 0, first ? 0 : 1);
+    if (sblocks_pass(o, a)) {
+      check(c, launch_leaf_tc(a, c.m, c.st), "leaf (tensor cores, plane pass)");
+      first = false;
+    }
+    c.ar.used = mk;
+  }
+  if (!dry && first)
+    check(c, cudaMemset2DAsync(C21, (size_t)ldc * 4, 0, (size_t)h * 4, (size_t)h, c.st), "zero");
+  // P1 = Low(A11 A11^T) -> C11 (recursive)
+  rec(c, A11, lda, h, kap, C11, ldc, levels - 1, no_planes());
+  if (!dry) check(c, launch_postadd(C11, ldc, C12, C21, C22, ldc, h, c.m, c.st), "postadd");
+  if (c.split_ev && levels == c.top_levels && !dry && c.err == AAT_OK)
+    cudaEventRecord(c.split_ev, c.st);
+  // P2 = Low(A12 A12^T) -> C12 (recursive), U3 = P1 + P2 -> C11
+  rec(c, A12, lda, h, kap, C12, ldc, levels - 1, no_planes());
+  if (!dry) check(c, launch_add_low(C11, ldc, C12, ldc, h, c.m, c.st), "add_low");
   c.ar.used = mark;
 }
 
@@ -912,6 +1112,9 @@ static int setup(Ctx &c, uint32_t p, uint32_t flags, cudaStream_t st) {
     return fail(AAT_ERANGE, "p too large for the exact FP64 leaf");
   const char *ew = getenv("AAT_WINOGRAD");
   c.wino = (flags & AAT_WINOGRAD) != 0 || (ew && atoi(ew) != 0);
+  c.passes = (flags & AAT_LOW_MEMORY) != 0;
+  const char *epw = getenv("AAT_PASS_PLANES");  // planes per pass (default 1)
+  c.pass_w = epw ? std::max(1, atoi(epw)) : 1;
   const char *eb = getenv("AAT_EXACT_BITS");
   c.exact_bits = eb ? atoi(eb) : 24;
   c.st = st;
@@ -934,7 +1137,7 @@ static size_t run_plan_in(Ctx &c, const int32_t *A, int64_t n, int64_t k, int64_
     if (tv.wino) c.wino = true;
   }
   Prepared pr = prepare(n, k, c.m.p, c.y, flags);
-  const bool early = !pr.padded && pr.levels >= 1 && !beta;
+  const bool early = !pr.padded && pr.levels >= 1 && !beta && !pass_mode(c);
   // end-to-end path: with no top level to overlap, wait for all of A
   // before anything reads it
   const cudaEvent_t in_a11 = c.in_a11, in_rest = c.in_rest;
@@ -1133,9 +1336,21 @@ static int modp_device(const int32_t *A, int64_t n, int64_t k, int64_t lda, uint
   c.form = form;
   c.in_a11 = in_a11;
   c.in_rest = in_rest;
-  const size_t need = run_plan(c, A, n, k, lda, C, ldc, flags, true, nullptr);
+  size_t need = run_plan(c, A, n, k, lda, C, ldc, flags, true, nullptr);
+  // the low-memory plane passes when the fast schedule's workspace is above
+  // the limit or cannot be allocated
+  if (!c.passes && need > g_ws_limit.load()) {
+    c.passes = true;
+    need = run_plan(c, A, n, k, lda, C, ldc, flags, true, nullptr);
+  }
   void *ws = nullptr;
-  if ((e = ensure_workspace(need, &ws))) return e;
+  if ((e = ensure_workspace(need, &ws))) {
+    if (e != AAT_ENOMEM || c.passes) return e;
+    c.passes = true;
+    const size_t low = run_plan(c, A, n, k, lda, C, ldc, flags, true, nullptr);
+    if (low >= need || (e = ensure_workspace(low, &ws))) return e ? e : AAT_ENOMEM;
+    g_last_error.clear();
+  }
   c.err = AAT_OK;
   c.split_ev = split_ev;
   run_plan(c, A, n, k, lda, C, ldc, flags, false, (char *)ws);
@@ -1609,8 +1824,13 @@ int aat_gemm_modp(const int32_t *X, int64_t ldx, const int32_t *Y, int64_t ldy, 
 size_t aat_workspace_size(int64_t n, int64_t k, uint32_t p, uint32_t flags) {
   Ctx c;
   if (n <= 0 || k <= 0 || setup(c, p, flags, nullptr)) return 0;
+  const size_t need = run_plan(c, nullptr, n, k, k, nullptr, n, flags, true, nullptr);
+  if (c.passes || need <= g_ws_limit.load()) return need;
+  c.passes = true;
   return run_plan(c, nullptr, n, k, k, nullptr, n, flags, true, nullptr);
 }
+
+void aat_set_workspace_limit(size_t bytes) { g_ws_limit.store(bytes); }
 
 int aat_device_status(int reset) {
   int32_t *d = device_status_ptr();

@@ -182,10 +182,11 @@ struct Planes {
   int64_t rows;
   int64_t cols;
   int64_t kstride;
-  int L;        // planes stored (nbase + nsum)
-  int nbase;    // digit planes
-  int nsum;     // pair-sum planes
+  int L;        // planes stored: planes q0 .. q0 + L - 1 of the sequence
+  int nbase;    // digit planes of the sequence
+  int nsum;     // pair-sum planes of the sequence (after the digit planes)
   int8_t si[8], sj[8];  // pair of plane nbase + q (always (0,1), (0,2), ...)
+  int q0;       // first stored plane (0 unless only a window of the planes is kept)
 };
 
 struct DigitSpec {
@@ -209,7 +210,8 @@ __device__ __forceinline__ uint2 pack4(float a, float b, float c, float d) {
 // c..c+V-1 (all digits but the last in [-2^(b-1), 2^(b-1) - 1], the last
 // carries the rest), written to the NB digit planes; then, if P.nsum > 0,
 // the pair sums d_i + d_j for i < j in the order (0,1), (0,2), ...,
-// (NB-2,NB-1).  V = 4 needs c % 4 == 0 and 8-byte aligned rows (one 8-byte
+// (NB-2,NB-1).  Only the planes of P's window [q0, q0 + L) of that sequence
+// are stored.  V = 4 needs c % 4 == 0 and 8-byte aligned rows (one 8-byte
 // store per plane).
 template <int NB, int V>
 __device__ __forceinline__ void store_digits_t(const Planes &P, int64_t r, int64_t c,
@@ -229,12 +231,15 @@ __device__ __forceinline__ void store_digits_t(const Planes &P, int64_t r, int64
     }
     dig[NB - 1][v] = x;
   }
+  // only the planes of the window [q0, q0 + L) are stored, at 0 .. L - 1
   auto put = [&](int pl, const int32_t (&w)[V]) {
+    const int s = pl - P.q0;
+    if ((unsigned)s >= (unsigned)P.L) return;
     if constexpr (V == 4) {
-      *reinterpret_cast<uint2 *>(dst + pl * plane) =
+      *reinterpret_cast<uint2 *>(dst + s * plane) =
           pack4((float)w[0], (float)w[1], (float)w[2], (float)w[3]);
     } else {
-      dst[pl * plane] = __float2bfloat16_rn((float)w[0]);
+      dst[s * plane] = __float2bfloat16_rn((float)w[0]);
     }
   };
 #pragma unroll
@@ -394,6 +399,10 @@ cudaError_t launch_leaf_tc_multi(const TcLeafArgs *as, int count, const ModP &m,
 // Whether that one launch is expected to beat one launch per product (the
 // idle share of the separate launches' last waves).
 bool leaf_tc_fuse_pays(const TcLeafArgs *as, int count);
+// Plane products with a non-zero weight mod p that the leaf runs for a
+// (only the terms whose planes the operands' plane windows hold); -1 when
+// the product does not fit the group table.
+int leaf_tc_terms(const TcLeafArgs &a, const ModP &m);
 void leaf_tc_release();
 // status word of the allocation-free entry point (AAT_OK if it never ran)
 int noalloc_status(int reset);

@@ -847,6 +847,20 @@ bool build_groups(const TcLeafArgs &a, const ModP &m, Group *out, int *ng_out, i
         terms.push_back({i, j, zp(s2), (int64_t)a.dx.dmax[i] * a.dy.dmax[j]});
       }
   }
+  // Planes that keep only a window of the sequence (the low-memory plane
+  // passes): the terms whose two planes are both stored, indexed within the
+  // windows.
+  {
+    std::vector<Term> kept;
+    for (Term t : terms) {
+      const int xs = t.xp - a.x.q0, ys = t.yp - a.y.q0;
+      if (xs < 0 || xs >= a.x.L || ys < 0 || ys >= a.y.L) continue;
+      t.xp = xs;
+      t.yp = ys;
+      kept.push_back(t);
+    }
+    terms.swap(kept);
+  }
   auto modw = [&](int64_t w) {
     int64_t r = w % (int64_t)m.p;
     return (uint32_t)(r < 0 ? r + (int64_t)m.p : r);
@@ -916,6 +930,12 @@ bool build_groups(const TcLeafArgs &a, const ModP &m, Group *out, int *ng_out, i
   return true;
 }
 
+// The stored planes form a window of the plane sequence (all of it, or the
+// planes of one low-memory pass).
+bool window_ok(const Planes &P) {
+  return P.L >= 1 && P.q0 >= 0 && P.q0 + P.L <= P.nbase + P.nsum;
+}
+
 // Co-resident CTA pairs of the pair kernel on this device (0: none).
 int pair_units(int dev) {
   auto it = g_pair_units.find(dev);
@@ -958,8 +978,8 @@ int pair_override() {
 
 cudaError_t launch_leaf_tc(const TcLeafArgs &a, const ModP &m, cudaStream_t st) {
   if (a.M <= 0 || a.N <= 0) return cudaSuccess;
-  if (a.dx.b != a.dy.b || a.x.nbase != a.dx.L || a.y.nbase != a.dy.L ||
-      a.x.L != a.x.nbase + a.x.nsum || a.y.L != a.y.nbase + a.y.nsum)
+  if (a.dx.b != a.dy.b || a.x.nbase != a.dx.L || a.y.nbase != a.dy.L || !window_ok(a.x) ||
+      !window_ok(a.y))
     return cudaErrorInvalidValue;
   if (a.x.kstride % 8 || a.y.kstride % 8 || a.x.cols != a.K || a.y.cols != a.K)
     return cudaErrorInvalidValue;
@@ -1068,6 +1088,13 @@ int64_t tile_count(int64_t M, int64_t N, int lower, int tm) {
 // (4096-sized products), and loses ~5 % at 3-4 % (8192-sized products in
 // a second-long run under the power cap, where idle tails let the clock
 // rise).  So: one launch when more than 6 % of the slots would be idle.
+int leaf_tc_terms(const TcLeafArgs &a, const ModP &m) {
+  std::vector<Group> g(MAX_GROUPS);
+  int ng = 0, nprod = 0;
+  if (!build_groups(a, m, g.data(), &ng, &nprod)) return -1;
+  return nprod;
+}
+
 bool leaf_tc_fuse_pays(const TcLeafArgs *as, int count) {
   int dev = 0;
   cudaGetDevice(&dev);
@@ -1108,7 +1135,7 @@ cudaError_t launch_leaf_tc_multi(const TcLeafArgs *as, int count, const ModP &m,
     const TcLeafArgs &a = as[i];
     if (a.M <= 0 || a.N <= 0) return cudaErrorInvalidValue;
     if (a.dx.b != as[0].dx.b || a.dx.b != a.dy.b || a.x.nbase != a.dx.L ||
-        a.y.nbase != a.dy.L || a.x.L != a.x.nbase + a.x.nsum || a.y.L != a.y.nbase + a.y.nsum)
+        a.y.nbase != a.dy.L || !window_ok(a.x) || !window_ok(a.y))
       return cudaErrorInvalidValue;
     if (a.x.kstride % 8 || a.y.kstride % 8 || a.x.cols != a.K || a.y.cols != a.K)
       return cudaErrorInvalidValue;

@@ -60,7 +60,9 @@ def test_workspace_allocation_failure_gives_enomem(lib):
     A = torch.from_numpy(synth.residues(78, (n, k), p, balanced=True)).cuda()
     C = torch.full((n, n), -7, dtype=torch.int32, device="cuda")
     lib.aat_shutdown()                       # drop the workspace grown so far
-    need = lib.aat_workspace_size(n, k, p)
+    # below even the low-memory schedule's need (which the library falls back
+    # to when the fast schedule's workspace cannot be allocated)
+    need = lib.aat_workspace_size(n, k, p, lib.AAT_LOW_MEMORY)
     assert need > 0
     try:
         nat.aatx_set_alloc_limit(need // 2)

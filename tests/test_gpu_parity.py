@@ -207,6 +207,62 @@ def test_aat_modp_mma_leaves_match_oracle(lib, leaf, p, n, k, levels):
     assert low_equal(C, oracle.aat_modp_low(A, p))
 
 
+@pytest.mark.parametrize("p", [65521, 2**31 - 1, 1000003, 13])
+@pytest.mark.parametrize("n,k", [(1, 1), (17, 33), (256, 512), (300, 200), (513, 257),
+                                 (640, 640), (1024, 96)])
+@pytest.mark.parametrize("levels", [0, 1, 2, 3])
+def test_aat_modp_low_memory_matches_oracle(lib, p, n, k, levels):
+    """The low-memory schedule (one plane of each operand per pass, products
+    accumulated in C) is bit-exact at every depth, ragged and k > n shapes,
+    both kinds of Y (65521 = 1 mod 4; 2^31 - 1, 1000003 = 3 mod 4)."""
+    A = synth.residues(p + n * 37 + k, (n, k), p)
+    C = host(lib.aat_modp(dev(A), p, levels=levels, flags=lib.AAT_LOW_MEMORY))
+    assert low_equal(C, oracle.aat_modp_low(A, p))
+
+
+@pytest.mark.parametrize("width", [2, 3, 4])
+def test_aat_modp_low_memory_plane_windows(lib, monkeypatch, width):
+    """Passes over windows of 2, 3 or 4 planes (the last window narrower),
+    at 1 and 2 levels over F_{2^31-1}."""
+    monkeypatch.setenv("AAT_PASS_PLANES", str(width))
+    p = 2**31 - 1
+    for levels, (n, k) in ((1, (640, 512)), (2, (520, 780))):
+        A = synth.residues(width * 100 + levels, (n, k), p, balanced=True)
+        C = host(lib.aat_modp(dev(A), p, levels=levels, flags=lib.AAT_LOW_MEMORY))
+        assert low_equal(C, oracle.aat_modp_low(A, p))
+
+
+def test_workspace_limit_selects_low_memory(lib):
+    """A workspace limit below the fast schedule's need runs the low-memory
+    schedule (same result); an allocation failure of the fast workspace falls
+    back to it too; below the low-memory need the call reports AAT_ENOMEM."""
+    from paper_2101_01025_gb300 import _native
+    p = 2**31 - 1
+    n, k = 1024, 768
+    A = synth.residues(99, (n, k), p, balanced=True)
+    ref = oracle.aat_modp_low(A, p)
+    fast = lib.aat_workspace_size(n, k, p, lib.AAT_LEVELS(1))
+    low = lib.aat_workspace_size(n, k, p, lib.AAT_LEVELS(1) | lib.AAT_LOW_MEMORY)
+    assert low * 4 <= fast
+    nat = _native.lib()
+    try:
+        lib.aat_set_workspace_limit(low)
+        assert lib.aat_workspace_size(n, k, p, lib.AAT_LEVELS(1)) == low
+        assert low_equal(host(lib.aat_modp(dev(A), p, levels=1)), ref)
+    finally:
+        lib.aat_set_workspace_limit(None)
+    lib.aat_shutdown()
+    try:
+        nat.aatx_set_alloc_limit(low)           # the fast workspace cannot be had
+        assert low_equal(host(lib.aat_modp(dev(A), p, levels=1)), ref)
+        nat.aatx_set_alloc_limit(low // 2)      # nor the low-memory one
+        with pytest.raises(lib.AatError) as ei:
+            lib.aat_modp(dev(A), p, levels=1)
+        assert ei.value.code == _native.AAT_ENOMEM
+    finally:
+        nat.aatx_set_alloc_limit(2**64 - 1)
+
+
 @pytest.mark.parametrize("leaf", ["tc", "i8", "f64"])
 def test_config1_512_p131071_one_level_every_leaf(lib, leaf):
     """The small workload exactly: A 512 x 512 over F_131071 (131071 = 3 mod 4,
@@ -388,6 +444,15 @@ def test_full_size_n16384_p2_31m1_winograd(lib):
     p = 2**31 - 1
     st = _full_check(lib, _bench_input(), p, levels_expected_min=1, flags=lib.AAT_WINOGRAD)
     assert st.general_products == 14 * 3 ** (st.levels - 1) + 2 * (3 ** (st.levels - 1) - 1) // 2
+
+
+def test_full_size_n16384_p2_31m1_low_memory(lib):
+    """The bench workload on the low-memory schedule (plane passes, 768 MiB of
+    workspace instead of 8.75 GiB): sampled entries and Freivalds."""
+    p = 2**31 - 1
+    assert lib.aat_workspace_size(16384, 16384, p, lib.AAT_LOW_MEMORY) <= 3 * 16384 * 16384
+    st = _full_check(lib, _bench_input(), p, levels_expected_min=1, flags=lib.AAT_LOW_MEMORY)
+    assert st.n_pad == 16384
 
 
 @functools.lru_cache(maxsize=4)
