@@ -819,145 +819,70 @@ static void rec(Ctx &c, const int32_t *A, int64_t lda, int64_t n, int64_t k, int
   c.ar.used = mark;
 }
 
-// One level of Algorithm 1 in low-memory plane passes (Sec. 7: the point of
-// Table 3's placement is that C itself holds the S and P blocks; here the
-// digit planes of the leaf operands, which the fast schedule keeps whole,
-// exist only one window at a time).  Each pass re-forms the S blocks from A
-// in one pass over A, writes the window's planes of the operands and runs
-// the window's plane products, which accumulate into the blocks of C where
-// Table 3 puts the products (P4^T -> C22, P5 -> C12, P3 -> C21, P1 -> C11);
-// the first pass stores.  The post-additions and P2 (accumulating onto P1 in
-// C11, U3 = P1 + P2) follow as in the fast schedule.  Above the last level,
-// S3 is written as int32 into C21 (Table 3) in the first pass of P4^T for the
-// recursive P5, and P3's passes run after P5's recursion, since P3's output
-// overwrites S3 in C21.
+// One level of Algorithm 1 in the low-memory schedule: Table 3's placement
+// and order (Sec. 7), with every leaf product in plane passes.  The S blocks
+// are int32 residues in the blocks of C that Table 3 assigns them (S1 -> C21,
+// S2 -> C12; then S3 -> C21 over S1 and S4 -> C11), each product reads them
+// there and writes where Table 3 puts it (P4^T -> C22, P5 -> C12 over S2,
+// P3 -> C21 over S3, P1 -> C11 over S4), so the only workspace is one pass's
+// digit planes (leaf()).  The S-block kernel forms the S blocks from A in
+// two passes over A (S1 and S2; then S3 and S4).  With k > n the S blocks do
+// not fit into C's blocks (Table 3 needs k <= n): two h x kappa int32
+// buffers of workspace hold them instead (S1, S2, then S3, S4).
 static void rec_passes(Ctx &c, const int32_t *A, int64_t lda, int64_t n, int64_t k, int32_t *C,
                        int64_t ldc, int levels) {
   const int64_t h = n / 2, kap = k / 2;
   int32_t *C11 = C, *C12 = C + h, *C21 = C + h * ldc, *C22 = C + h * ldc + h;
-  const int32_t *A11 = A, *A12 = A + kap;
+  const int32_t *A11 = A, *A12 = A + kap, *A22 = A + h * lda + kap;
+  const bool last = (levels == 1);
   const size_t mark = c.ar.used;
-  const int Q = plane_count(c);
-  const bool dry = c.ar.dry;
   count_level(c);
-  // one pass: the S-block kernel writes the listed outputs; returns whether
-  // the window has live plane products (otherwise nothing runs)
-  auto sblocks_pass = [&](SKernelOut &o, const TcLeafArgs &probe) {
-    if (dry || c.err != AAT_OK || leaf_tc_terms(probe, c.m) == 0) return false;
-    return check(c, launch_sblocks(A, lda, h, kap, c.m, c.y, c.ds.b, o, c.st), "sblocks");
+  // where S1 / S3 and S2 / S4 live
+  int32_t *Sa = C21, *Sb = C12;
+  int64_t lda_s = ldc, ldb_s = ldc;
+  if (kap > h) {
+    Sa = (int32_t *)c.ar.get((size_t)h * kap * 4);
+    Sb = (int32_t *)c.ar.get((size_t)h * kap * 4);
+    lda_s = ldb_s = kap;
+  }
+  auto sblocks = [&](int q0, int32_t *p0, int64_t l0, int q1, int32_t *p1, int64_t l1) {
+    if (c.ar.dry || c.err != AAT_OK) return;
+    SKernelOut o;
+    std::memset(&o, 0, sizeof(o));
+    o.s[q0] = p0;
+    o.lds[q0] = l0;
+    o.s[q1] = p1;
+    o.lds[q1] = l1;
+    check(c, launch_sblocks(A, lda, h, kap, c.m, c.y, c.ds.b, o, c.st), "sblocks");
   };
-  if (levels == 1) {
-    for (int q = 0; q < 4; ++q) count_leaf(c, h, h, kap, q == 1 || q == 3);
-    bool first = true;
-    for (int q0 = 0; q0 < Q; q0 += c.pass_w) {
-      const int w = std::min(c.pass_w, Q - q0);
-      const size_t mk = c.ar.used;
-      SKernelOut o;
-      std::memset(&o, 0, sizeof(o));
-      for (int q = 0; q < 4; ++q) o.sp[q] = planes_window(c, h, kap, q0, w);
-      o.a22 = planes_window(c, h, kap, q0, w);
-      o.a11 = planes_window(c, h, kap, q0, w);
-      const uint32_t beta = first ? 0 : 1;
-      TcLeafArgs fa[4] = {tc_args(c, o.sp[1], o.sp[0], h, h, kap, C22, ldc, 0, beta),  // P4^T
-                          tc_args(c, o.sp[2], o.sp[2], h, h, kap, C12, ldc, 1, beta),  // P5
-                          tc_args(c, o.a22, o.sp[3], h, h, kap, C21, ldc, 0, beta),    // P3
-                          tc_args(c, o.a11, o.a11, h, h, kap, C11, ldc, 1, beta)};     // P1
-      if (sblocks_pass(o, fa[0])) {
-        const int fo = fuse_override();
-        if (fo == 1 || (fo < 0 && leaf_tc_fuse_pays(fa, 4))) {
-          check(c, launch_leaf_tc_multi(fa, 4, c.m, c.st), "leaf (tensor cores, plane pass)");
-        } else {
-          for (const TcLeafArgs &a : fa)
-            check(c, launch_leaf_tc(a, c.m, c.st), "leaf (tensor cores, plane pass)");
-        }
-        first = false;
-      }
-      c.ar.used = mk;
-    }
-    if (!dry && first) {  // every term vanished mod p: the four products are zero
-      for (int32_t *B : {C11, C12, C21, C22})
-        check(c, cudaMemset2DAsync(B, (size_t)ldc * 4, 0, (size_t)h * 4, (size_t)h, c.st),
-              "zero products");
-    }
-    if (!dry) check(c, launch_postadd(C11, ldc, C12, C21, C22, ldc, h, c.m, c.st), "postadd");
-    if (c.split_ev && levels == c.top_levels && !dry && c.err == AAT_OK)
-      cudaEventRecord(c.split_ev, c.st);
-    // P2 = Low(A12 A12^T) accumulated onto P1 in C11: U3 = P1 + P2
-    Operand X{A12, lda, no_planes()};
-    leaf(c, X, X, true, h, h, kap, C11, ldc, 1, 1);
-    c.ar.used = mark;
-    return;
-  }
-  // S3 for the recursive P5: C21 (Table 3), or workspace when kappa > h
-  int32_t *S3;
-  int64_t ldS3;
-  if (kap <= h) {
-    S3 = C21;
-    ldS3 = ldc;
-  } else {
-    S3 = (int32_t *)c.ar.get((size_t)h * kap * 4);
-    ldS3 = kap;
-  }
-  // P4^T = S2 S1^T -> C22 in passes; the first pass also writes S3
-  count_leaf(c, h, h, kap, 0);
-  bool first = true;
-  for (int q0 = 0; q0 < Q; q0 += c.pass_w) {
-    const int w = std::min(c.pass_w, Q - q0);
-    const size_t mk = c.ar.used;
-    SKernelOut o;
-    std::memset(&o, 0, sizeof(o));
-    o.sp[0] = planes_window(c, h, kap, q0, w);
-    o.sp[1] = planes_window(c, h, kap, q0, w);
-    if (q0 == 0) {
-      o.s[2] = S3;
-      o.lds[2] = ldS3;
-    }
-    const TcLeafArgs a = tc_args(c, o.sp[1], o.sp[0], h, h, kap, C22, ldc, 0, first ? 0 : 1);
-    if (!dry && c.err == AAT_OK && q0 == 0 && leaf_tc_terms(a, c.m) == 0) {
-      // S3 is needed whether or not this window has live terms
-      SKernelOut s3;
-      std::memset(&s3, 0, sizeof(s3));
-      s3.s[2] = S3;
-      s3.lds[2] = ldS3;
-      check(c, launch_sblocks(A, lda, h, kap, c.m, c.y, c.ds.b, s3, c.st), "sblocks");
-    }
-    if (sblocks_pass(o, a)) {
-      check(c, launch_leaf_tc(a, c.m, c.st), "leaf (tensor cores, plane pass)");
-      first = false;
-    }
-    c.ar.used = mk;
-  }
-  if (!dry && first)
-    check(c, cudaMemset2DAsync(C22, (size_t)ldc * 4, 0, (size_t)h * 4, (size_t)h, c.st), "zero");
-  // P5 = Low(S3 S3^T) -> C12 (recursive)
-  rec(c, S3, ldS3, h, kap, C12, ldc, levels - 1, no_planes());
-  // P3 = A22 S4^T -> C21 in passes (S3 is no longer needed)
-  count_leaf(c, h, h, kap, 0);
-  first = true;
-  for (int q0 = 0; q0 < Q; q0 += c.pass_w) {
-    const int w = std::min(c.pass_w, Q - q0);
-    const size_t mk = c.ar.used;
-    SKernelOut o;
-    std::memset(&o, 0, sizeof(o));
-    o.sp[3] = planes_window(c, h, kap, q0, w);
-    o.a22 = planes_window(c, h, kap, q0, w);
-    const TcLeafArgs a = tc_args(c, o.a22, o.sp[3], h, h, kap, C21, ldc, 0, first ? 0 : 1);
-    if (sblocks_pass(o, a)) {
-      check(c, launch_leaf_tc(a, c.m, c.st), "leaf (tensor cores, plane pass)");
-      first = false;
-    }
-    c.ar.used = mk;
-  }
-  if (!dry && first)
-    check(c, cudaMemset2DAsync(C21, (size_t)ldc * 4, 0, (size_t)h * 4, (size_t)h, c.st), "zero");
-  // P1 = Low(A11 A11^T) -> C11 (recursive)
+  // 1-2. S1 = (A21 - A11) Y -> C21, S2 = A22 - A21 Y -> C12
+  sblocks(0, Sa, lda_s, 1, Sb, ldb_s);
+  // 3. P4^T = S2 S1^T -> C22
+  leaf(c, Operand{Sb, ldb_s, no_planes()}, Operand{Sa, lda_s, no_planes()}, false, h, h, kap,
+       C22, ldc, 0, 0);
+  // 4, 6. S3 = S1 - A22 -> C21 (over S1), S4 = S3 + A12 -> C11 (or workspace)
+  int32_t *S4 = (kap > h) ? Sb : C11;
+  const int64_t ld4 = (kap > h) ? ldb_s : ldc;
+  sblocks(2, Sa, lda_s, 3, S4, ld4);
+  // 5. P5 = Low(S3 S3^T) -> C12 (over S2)
+  rec(c, Sa, lda_s, h, kap, C12, ldc, levels - 1, no_planes());
+  // 7. P3 = A22 S4^T -> C21 (over S3)
+  leaf(c, Operand{A22, lda, no_planes()}, Operand{S4, ld4, no_planes()}, false, h, h, kap, C21,
+       ldc, 0, 0);
+  // 8. P1 = Low(A11 A11^T) -> C11 (over S4)
   rec(c, A11, lda, h, kap, C11, ldc, levels - 1, no_planes());
-  if (!dry) check(c, launch_postadd(C11, ldc, C12, C21, C22, ldc, h, c.m, c.st), "postadd");
-  if (c.split_ev && levels == c.top_levels && !dry && c.err == AAT_OK)
+  // 9-12. U1 = P1 + P5, U2 = U1 + P4, U4 = U2 + P3 -> C21, Low(U5) -> C22
+  if (!c.ar.dry) check(c, launch_postadd(C11, ldc, C12, C21, C22, ldc, h, c.m, c.st), "postadd");
+  if (c.split_ev && levels == c.top_levels && !c.ar.dry && c.err == AAT_OK)
     cudaEventRecord(c.split_ev, c.st);
-  // P2 = Low(A12 A12^T) -> C12 (recursive), U3 = P1 + P2 -> C11
-  rec(c, A12, lda, h, kap, C12, ldc, levels - 1, no_planes());
-  if (!dry) check(c, launch_add_low(C11, ldc, C12, ldc, h, c.m, c.st), "add_low");
+  // 13-14. P2 = Low(A12 A12^T), U3 = P1 + P2 -> C11
+  if (last) {
+    Operand X{A12, lda, no_planes()};
+    leaf(c, X, X, true, h, h, kap, C11, ldc, 1, 1);  // accumulates onto P1
+  } else {
+    rec(c, A12, lda, h, kap, C12, ldc, levels - 1, no_planes());
+    if (!c.ar.dry) check(c, launch_add_low(C11, ldc, C12, ldc, h, c.m, c.st), "add_low");
+  }
   c.ar.used = mark;
 }
 
@@ -1113,8 +1038,7 @@ static int setup(Ctx &c, uint32_t p, uint32_t flags, cudaStream_t st) {
   const char *ew = getenv("AAT_WINOGRAD");
   c.wino = (flags & AAT_WINOGRAD) != 0 || (ew && atoi(ew) != 0);
   c.passes = (flags & AAT_LOW_MEMORY) != 0;
-  const char *epw = getenv("AAT_PASS_PLANES");  // planes per pass (default 1)
-  c.pass_w = epw ? std::max(1, atoi(epw)) : 1;
+  c.pass_w = 1;  // set by choose_schedule
   const char *eb = getenv("AAT_EXACT_BITS");
   c.exact_bits = eb ? atoi(eb) : 24;
   c.st = st;
@@ -1192,6 +1116,38 @@ static size_t run_plan(Ctx &c, const int32_t *A, int64_t n, int64_t k, int64_t l
   c.ar.dry = dry;
   c.ar.base = ws;
   return run_plan_in(c, A, n, k, lda, C, ldc, flags, dry, beta);
+}
+
+// The schedule of one product and its workspace (a dry run): the fast one,
+// unless the flags ask for the low-memory one (AAT_LOW_MEMORY) or the fast
+// one needs more than the workspace limit.  The low-memory schedule takes
+// the widest plane window (fewest passes) whose workspace fits under the
+// limit, or under A's own size (4 n k bytes) when no limit is set; one plane
+// per pass when none fits.  AAT_PASS_PLANES (environment) fixes the width.
+// Measured at n = k = 16384 over F_{2^31-1} (one level; ms, workspace):
+// windows of 1, 2, 3, 4, 5, 10 planes 37.9 / 0.25 GiB, 30.7 / 0.5, 28.4 /
+// 0.75, 27.9 / 1.0, 26.2 / 1.25, 25.7 / 2.5; the fast schedule 24.9 / 8.75.
+static size_t choose_schedule(Ctx &c, const int32_t *A, int64_t n, int64_t k, int64_t lda,
+                              int32_t *C, int64_t ldc, uint32_t flags) {
+  const size_t limit = g_ws_limit.load();
+  if (!c.passes) {
+    const size_t need = run_plan(c, A, n, k, lda, C, ldc, flags, true, nullptr);
+    if (need <= limit) return need;
+    c.passes = true;
+  }
+  const char *epw = getenv("AAT_PASS_PLANES");
+  if (epw) {
+    c.pass_w = std::max(1, atoi(epw));
+    return run_plan(c, A, n, k, lda, C, ldc, flags, true, nullptr);
+  }
+  const size_t target = limit != SIZE_MAX ? limit : (size_t)4 * (size_t)n * (size_t)k;
+  size_t need = 0;
+  for (int w = c.ds.L + c.ds.nsum; w >= 1; --w) {
+    c.pass_w = w;
+    need = run_plan(c, A, n, k, lda, C, ldc, flags, true, nullptr);
+    if (need <= target) break;
+  }
+  return need;
 }
 
 // M M^H mod p for the quaternion matrix M = A + B i + C j + D k (Sec. 6.2,
@@ -1336,18 +1292,13 @@ static int modp_device(const int32_t *A, int64_t n, int64_t k, int64_t lda, uint
   c.form = form;
   c.in_a11 = in_a11;
   c.in_rest = in_rest;
-  size_t need = run_plan(c, A, n, k, lda, C, ldc, flags, true, nullptr);
-  // the low-memory plane passes when the fast schedule's workspace is above
-  // the limit or cannot be allocated
-  if (!c.passes && need > g_ws_limit.load()) {
-    c.passes = true;
-    need = run_plan(c, A, n, k, lda, C, ldc, flags, true, nullptr);
-  }
+  size_t need = choose_schedule(c, A, n, k, lda, C, ldc, flags);
   void *ws = nullptr;
   if ((e = ensure_workspace(need, &ws))) {
+    // the fast schedule's workspace cannot be had: the low-memory schedule
     if (e != AAT_ENOMEM || c.passes) return e;
     c.passes = true;
-    const size_t low = run_plan(c, A, n, k, lda, C, ldc, flags, true, nullptr);
+    const size_t low = choose_schedule(c, A, n, k, lda, C, ldc, flags);
     if (low >= need || (e = ensure_workspace(low, &ws))) return e ? e : AAT_ENOMEM;
     g_last_error.clear();
   }
@@ -1824,10 +1775,7 @@ int aat_gemm_modp(const int32_t *X, int64_t ldx, const int32_t *Y, int64_t ldy, 
 size_t aat_workspace_size(int64_t n, int64_t k, uint32_t p, uint32_t flags) {
   Ctx c;
   if (n <= 0 || k <= 0 || setup(c, p, flags, nullptr)) return 0;
-  const size_t need = run_plan(c, nullptr, n, k, k, nullptr, n, flags, true, nullptr);
-  if (c.passes || need <= g_ws_limit.load()) return need;
-  c.passes = true;
-  return run_plan(c, nullptr, n, k, k, nullptr, n, flags, true, nullptr);
+  return choose_schedule(c, nullptr, n, k, k, nullptr, n, flags);
 }
 
 void aat_set_workspace_limit(size_t bytes) { g_ws_limit.store(bytes); }
