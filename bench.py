@@ -47,11 +47,11 @@ P = 2**31 - 1
 SEED_OFFSET = 2
 # DRAM traffic of the dominant kernel from one ncu capture of three 8192^3
 # leaf products mod 2^31-1 (dram__bytes_read.sum + dram__bytes_write.sum:
-# 12.51, 13.56 and 12.66 GB, mean 12.91 GB for 10.995 TFLOP of algorithmic
+# 11.99, 14.37 and 12.78 GB, mean 13.05 GB for 10.995 TFLOP of algorithmic
 # work each; CTA-pair form, tiles in bands of 2048 rows), scaled to the
 # average launch of the step by its algorithmic work.  None whenever the
 # kernel has changed since the counters were taken.
-LEAF_TC_BYTES_PER_FLOP = 12.91e9 / 10.995e12
+LEAF_TC_BYTES_PER_FLOP = 13.05e9 / 10.995e12
 # Dense BF16 rate of the tensor pipe per SM and clock (a 128 x 256 x 16
 # tcgen05.mma every 128 cycles) and the SM count: the nominal rate at the
 # clock the run was sampled at.

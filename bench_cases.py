@@ -203,7 +203,15 @@ def batch_case(a):
           for n, k in zip(cn, ck)]
     out = {"case": "batch", "problems": count, "complex": count // 4}
     for name, probs in (("modp", fp), ("aah", cx), ("all", fp + cx)):
+        if a.profile:
+            # the plan's first run is eager (outside the graph): its kernels
+            # carry the library's per-launch events
+            torch.cuda.synchronize()
+            from paper_2101_01025_gb300 import _native
+            _native.lib().aat_profile_begin()
         plan = aat.Plan(probs)
+        if a.profile:
+            out[name + "_eager_kernels"] = profile_end(1)
         work = sum(float(A.shape[0]) ** 2 * A.shape[1] for _, A, _, _, _ in probs)
         plan.execute()
         torch.cuda.synchronize()

@@ -93,22 +93,27 @@ def test_complex_small_integers_exact(lib, herm, flags):
     assert np.array_equal(np.tril(C.astype(np.complex128)), np.tril(ref))
 
 
-def test_complex_full_size_sampled(lib):
-    """8192 x 8192 complex A (Re, Im i.i.d. N(0, 1)): sampled entries at
-    every 32-row boundary and random positions against the oracle."""
+@pytest.mark.parametrize("ill", [False, True])
+def test_complex_full_size_sampled(lib, ill):
+    """8192 x 8192 complex A (Re, Im i.i.d. N(0, 1), and the ill-scaled
+    variant), A A^H and A A^T by 2M in every precision class: sampled
+    entries at random positions and every 97th diagonal entry against the
+    oracle, each class within its bound."""
     n = k = 8192
-    A = synth.complex_normal(synth.SEED_BASE + 3, (n, k))
+    A = synth.complex_normal(synth.SEED_BASE + 3 + (50 if ill else 0), (n, k), ill_scaled=ill)
+    rng = np.random.default_rng(5)
+    i = rng.integers(0, n, 3000)
+    j = rng.integers(0, n, 3000)
+    ij = np.stack([np.maximum(i, j), np.minimum(i, j)], 1)
+    ij = np.concatenate([ij, np.array([[r, r] for r in range(0, n, 97)])])
     for herm in (True, False):
-        C = run(lib, A, herm, 0)
-        rng = np.random.default_rng(5)
-        i = rng.integers(0, n, 3000)
-        j = rng.integers(0, n, 3000)
-        ij = np.stack([np.maximum(i, j), np.minimum(i, j)], 1)
-        ij = np.concatenate([ij, np.array([[r, r] for r in range(0, n, 97)])])
         ref = oracle.complex_entries(A.astype(np.complex128), ij, conj=herm)
-        got = C[ij[:, 0], ij[:, 1]].astype(np.complex128)
-        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
-        assert err <= 1e-5, err
+        for flags in (0, 1 << 16, 2 << 16):
+            C = run(lib, A, herm, flags)
+            got = C[ij[:, 0], ij[:, 1]].astype(np.complex128)
+            err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+            print("2M n=k=8192 herm=%d ill=%d flags=%#x err=%.3e" % (herm, ill, flags, err))
+            assert err <= TOL[flags], err
 
 
 def test_complex_n16384_sampled(lib):
@@ -211,6 +216,7 @@ def test_aat_complex_alg1_n8192_sampled(lib, ill):
         got = C[torch.from_numpy(ij[:, 0]).cuda(), torch.from_numpy(ij[:, 1]).cuda()]
         got = got.cpu().numpy().astype(np.complex128)
         err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        print("Alg1 n=k=8192 ill=%d flags=%#x levels=%d err=%.3e" % (ill, flags, levels, err))
         assert err <= TOL_ALG1[flags], (flags, levels, err)
         del C
     with pytest.raises(lib.AatError):
