@@ -1243,7 +1243,9 @@ int modp_run(const int32_t *A, int64_t n, int64_t k, int64_t lda, uint32_t p, in
   Ctx c;
   int e = setup(c, p, flags, st);
   if (e) return e;
-  const size_t peak = run_plan(c, A, n, k, lda, C, ldc, flags, dry, ws);
+  // the schedule as for a single call (fast, or low-memory by flag or limit)
+  size_t peak = choose_schedule(c, A, n, k, lda, C, ldc, flags);
+  if (!dry) peak = run_plan(c, A, n, k, lda, C, ldc, flags, false, ws);
   if (need) *need = peak;
   return c.err;
 }

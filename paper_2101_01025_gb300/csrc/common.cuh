@@ -91,6 +91,25 @@ __host__ __device__ __forceinline__ uint32_t bal_to_canon(int32_t x, const ModP 
   return x < 0 ? (uint32_t)(x + (int32_t)m.p) : (uint32_t)x;
 }
 
+// a * w mod p, balanced, for p < 2^30 and any int32 a, with the multiplier
+// balanced (wb = w or w - p, |wb| <= (p - 1)/2) and wsh = floor(wb 2^32 / p)
+// (|wsh| < 2^31; Shoup's method with signed operands): q = floor(a wsh /
+// 2^32), the signed high word, leaves r = a wb - q p = a t / 2^32 + p s / 2^32
+// with t = wb 2^32 - wsh p in [0, p) and s in [0, 2^32), so r lies in
+// (-p/2, 3p/2) (inside int32 for p < 2^30) and one conditional subtraction
+// makes it balanced.  Five instructions instead of the unsigned form's ten.
+__host__ __device__ __forceinline__ int32_t mulmod_shoup_s(int32_t a, int32_t wb, int32_t wsh,
+                                                           const ModP &m) {
+#ifdef __CUDA_ARCH__
+  const int32_t q = __mulhi(a, wsh);
+#else
+  const int32_t q = (int32_t)(((int64_t)a * wsh) >> 32);
+#endif
+  int32_t r = (int32_t)((uint32_t)a * (uint32_t)wb - (uint32_t)q * m.p);
+  if (r > (int32_t)m.half) r -= (int32_t)m.p;
+  return r;
+}
+
 // a * w mod p, balanced, for any int32 a and a fixed w in [0, p) with
 // wsh = floor(w 2^32 / p) (Shoup's modular multiplication): with |a| < 2^32,
 // |a| w - floor(|a| wsh / 2^32) p lies in [0, 2p), so 32-bit arithmetic and

@@ -515,14 +515,32 @@ __global__ void __launch_bounds__(Shape<PAIR, EW>::THREADS, 1)
       } else {
         ng = tile_ng<MODE>(P, t);
       }
+      // this warp's 32 x VALS block of the tile: when it lies wholly outside
+      // the product (rows >= M, columns >= N, or above the diagonal of a
+      // lower product) the warp only keeps the barrier protocol going
+      bool live;
+      {
+        const OutView o = tile_out<MODE>(P, t);
+        const int2 ij = tile_ij<MODE>(P, t);
+        const int64_t r0 = (int64_t)ij.x * S::TM + (int64_t)rank * BM + quarter * 32;
+        const int64_t c0 = (int64_t)ij.y * BN + cpart * VALS;
+        live = r0 < o.M && c0 < o.N && !(o.lower && c0 > r0 + 31);
+      }
       int32_t acc[VALS];
 #pragma unroll
       for (int i = 0; i < VALS; ++i) acc[i] = 0;
       for (int gi = 0; gi < ng && ok; ++gi) {
         const Group g = (MODE == kBatch && gi < 32) ? gcache[gi] : tile_group<MODE>(P, t, gi);
-        if (gi > 0) {
+        if (gi > 0 && live) {
+          if (m.p < (1u << 30)) {  // the signed form (set_shoup stored its quotient)
+            const int32_t wb = g.ratio > m.half ? (int32_t)g.ratio - (int32_t)m.p : (int32_t)g.ratio;
+            const int32_t wsh = (int32_t)g.ratio_sh;
 #pragma unroll
-          for (int i = 0; i < VALS; ++i) acc[i] = mulmod_shoup(acc[i], g.ratio, g.ratio_sh, m);
+            for (int i = 0; i < VALS; ++i) acc[i] = mulmod_shoup_s(acc[i], wb, wsh, m);
+          } else {
+#pragma unroll
+            for (int i = 0; i < VALS; ++i) acc[i] = mulmod_shoup(acc[i], g.ratio, g.ratio_sh, m);
+          }
         }
         for (int kb = g.kb0; kb < g.kb1;) {
           const int kend = min(kb + g.kchunk, g.kb1);
@@ -532,16 +550,18 @@ __global__ void __launch_bounds__(Shape<PAIR, EW>::THREADS, 1)
             break;
           }
           tc_fence_after();
-          const uint32_t ta = tmem + lane_base + buf * ACC_COLS + (uint32_t)(cpart * VALS);
-          tmem_drain16<0>(ta, acc);
-          tmem_drain16<16>(ta + 16u, acc);
-          tmem_drain16<32>(ta + 32u, acc);
-          tmem_drain16<48>(ta + 48u, acc);
-          if constexpr (VALS == 128) {
-            tmem_drain16<64>(ta + 64u, acc);
-            tmem_drain16<80>(ta + 80u, acc);
-            tmem_drain16<96>(ta + 96u, acc);
-            tmem_drain16<112>(ta + 112u, acc);
+          if (live) {
+            const uint32_t ta = tmem + lane_base + buf * ACC_COLS + (uint32_t)(cpart * VALS);
+            tmem_drain16<0>(ta, acc);
+            tmem_drain16<16>(ta + 16u, acc);
+            tmem_drain16<32>(ta + 32u, acc);
+            tmem_drain16<48>(ta + 48u, acc);
+            if constexpr (VALS == 128) {
+              tmem_drain16<64>(ta + 64u, acc);
+              tmem_drain16<80>(ta + 80u, acc);
+              tmem_drain16<96>(ta + 96u, acc);
+              tmem_drain16<112>(ta + 112u, acc);
+            }
           }
           tc_fence_before();
           __syncwarp();
@@ -556,6 +576,7 @@ __global__ void __launch_bounds__(Shape<PAIR, EW>::THREADS, 1)
         }
       }
       if (!ok) break;
+      if (!live) continue;
       const int2 ij = tile_ij<MODE>(P, t);
       const int64_t row = (int64_t)ij.x * S::TM + (int64_t)rank * BM + quarter * 32 + lane;
       const int64_t col0 = (int64_t)ij.y * BN + cpart * VALS;
@@ -795,9 +816,21 @@ cudaError_t get_multi_tiles(int dev, const TcLeafArgs *as, const int *order, int
   return cudaSuccess;
 }
 
-// Shoup quotients of the Horner ratios.
+// Shoup quotients of the Horner ratios: floor(ratio 2^32 / p) for the
+// unsigned form, or, for p < 2^30, floor(wb 2^32 / p) of the balanced ratio
+// wb (the signed form, mulmod_shoup_s), as int32 bits.
 void set_shoup(Group *g, int ng, uint32_t p) {
-  for (int i = 0; i < ng; ++i) g[i].ratio_sh = (uint32_t)(((uint64_t)g[i].ratio << 32) / p);
+  for (int i = 0; i < ng; ++i) {
+    if (p < (1u << 30)) {
+      const int64_t wb = g[i].ratio > (p - 1) / 2 ? (int64_t)g[i].ratio - p : (int64_t)g[i].ratio;
+      const int64_t num = wb * ((int64_t)1 << 32);
+      int64_t q = num / (int64_t)p;
+      if (num % (int64_t)p != 0 && num < 0) q -= 1;  // floor
+      g[i].ratio_sh = (uint32_t)(int32_t)q;
+    } else {
+      g[i].ratio_sh = (uint32_t)(((uint64_t)g[i].ratio << 32) / p);
+    }
+  }
 }
 
 // K segment of the groups in K blocks: every plane product runs over one

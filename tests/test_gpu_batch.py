@@ -166,6 +166,32 @@ def test_plan_complex_batch_precisions(lib, flags):
     plan.close()
 
 
+def test_plan_with_low_memory_problems(lib):
+    """Recursive products on the low-memory schedule (S blocks in C, plane
+    passes) inside a plan's graph, run twice with new inputs."""
+    problems, hosts = [], []
+    for q, (n, k, p, lv) in enumerate([(1024, 768, 2**31 - 1, 1), (1024, 1024, 65521, 2),
+                                       (776, 520, 2**31 - 1, 2)]):
+        A = synth.residues(400 + q, (n, k), p)
+        Ad = torch.from_numpy(A).cuda()
+        Cd = torch.full((n, n), -1, dtype=torch.int32, device="cuda")
+        problems.append(("modp", Ad, Cd, p, lib.AAT_LEVELS(lv) | lib.AAT_LOW_MEMORY))
+        hosts.append((A, Ad, Cd, p))
+    plan = lib.Plan(problems)
+    assert plan.info()["solo"] == 3
+    for rnd in range(2):
+        if rnd == 1:
+            for idx, (A, Ad, Cd, p) in enumerate(hosts):
+                A2 = synth.residues(800 + idx, A.shape, p)
+                Ad.copy_(torch.from_numpy(A2))
+                hosts[idx] = (A2, Ad, Cd, p)
+        plan.execute()
+        torch.cuda.synchronize()
+        for A, Ad, Cd, p in hosts:
+            _fp_check(A, Cd.cpu().numpy(), p, full=True)
+    plan.close()
+
+
 def test_plan_with_winograd_problems(lib):
     """Recursive products with Winograd's form for their last level's
     general products, captured in the plan's graph and run twice."""
