@@ -229,8 +229,11 @@ AAT_API int aat_gemm_modp(const int32_t *X, int64_t ldx, const int32_t *Y, int64
  *   - Every call shares the one array and overwrites it: calls that overlap
  *     on the GPU (other streams, other host threads) race and give wrong
  *     results.  The array keeps the last call's contents; each call rewrites
- *     everything it reads and clears its status word.
+ *     everything it reads (the tile list is written by a kernel, not copied
+ *     from the host) and clears its own status word, which aat_device_status
+ *     reports beside the library's (AAT_ETIMEOUT if a bounded wait gave up).
  *   - Calls no cudaMalloc, cudaFree or allocating library routine.
+ *     aat_shutdown() makes the next call look the array's address up again.
  * Arguments, layout and return codes as aat_gemm_modp (tensor-core leaf).
  */
 AAT_API int aat_gemm_modp_noalloc(const int32_t *X, int64_t ldx, const int32_t *Y, int64_t ldy,
@@ -332,9 +335,10 @@ AAT_API void aat_set_workspace_limit(size_t bytes);
 AAT_API const char *aat_last_error(void);
 
 /*
- * Synchronises the device and reports the sticky device-side status word
- * that bounded waits in the kernels set when they give up: AAT_OK or
- * AAT_ETIMEOUT.  reset != 0 clears it afterwards.
+ * Synchronises the device and reports the sticky device-side status words
+ * that bounded waits in the kernels set when they give up (the library's, and
+ * aat_gemm_modp_noalloc's own, on the current device): AAT_OK or
+ * AAT_ETIMEOUT.  reset != 0 clears them afterwards.
  */
 AAT_API int aat_device_status(int reset);
 
