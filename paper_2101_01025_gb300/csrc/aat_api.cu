@@ -280,6 +280,7 @@ struct DeviceState {
   cudaStream_t e2e_stream2 = nullptr;  // copies rows that are final early
   cudaEvent_t e2e_split = nullptr;
   cudaEvent_t e2e_a11 = nullptr, e2e_rest = nullptr;  // copies of A in
+  std::vector<cudaEvent_t> e2e_bands;  // row bands of the rest of A in
 };
 
 static std::mutex g_state_mu;
@@ -410,8 +411,13 @@ struct Ctx {
   int64_t split_row = 0;
   int form = 0;  // leaf kernel form (TcLeafArgs::form)
   // optional (end-to-end path): A11's and the rest of A's copies to the
-  // device complete at these events; the stream waits for them
+  // device complete at these events; the stream waits for them.  The rest
+  // may also come in nbands row bands (rows [b h / nbands, (b+1) h / nbands)
+  // of A12 and of the bottom half, event in_bands[b]): the top level's
+  // S-block kernel then runs band by band as they arrive.
   cudaEvent_t in_a11 = nullptr, in_rest = nullptr;
+  const cudaEvent_t *in_bands = nullptr;
+  int nbands = 0;
   uint32_t alpha = 1;  // scale of every product (the SYRK update's alpha)
   bool wino = false;   // last level's P3, P4 by Winograd's form (AAT_WINOGRAD)
   // low-memory plane passes (AAT_LOW_MEMORY): every leaf product runs as
@@ -597,7 +603,7 @@ struct LevelOps {
 // before the rest of A arrives), or none.
 static LevelOps sblocks_step(Ctx &c, const int32_t *A, int64_t lda, int64_t h, int64_t kap,
                              int32_t *S3, int64_t ldS3, bool last, Planes pA11 = Planes{},
-                             bool wino = false) {
+                             bool wino = false, bool banded = false) {
   const bool tc = (c.leaf == AAT_LEAF_TC);
   const int32_t *A22 = A + h * lda + kap;
   SKernelOut o;
@@ -647,7 +653,16 @@ static LevelOps sblocks_step(Ctx &c, const int32_t *A, int64_t lda, int64_t h, i
     L.oS4.x = o.s[3];
     L.oS4.ld = kap;
   }
-  if (!c.ar.dry) check(c, launch_sblocks(A, lda, h, kap, c.m, c.y, c.ds.b, o, c.st), "sblocks");
+  if (!c.ar.dry && banded) {
+    // each band as soon as its rows of A are on the device
+    for (int b = 0; b < c.nbands && c.err == AAT_OK; ++b) {
+      const int64_t r0 = h * b / c.nbands, r1 = h * (b + 1) / c.nbands;
+      check(c, cudaStreamWaitEvent(c.st, c.in_bands[b], 0), "wait for A");
+      check(c, launch_sblocks(A, lda, h, kap, c.m, c.y, c.ds.b, o, c.st, r0, r1), "sblocks");
+    }
+  } else if (!c.ar.dry) {
+    check(c, launch_sblocks(A, lda, h, kap, c.m, c.y, c.ds.b, o, c.st), "sblocks");
+  }
   return L;
 }
 
@@ -756,8 +771,9 @@ static void rec(Ctx &c, const int32_t *A, int64_t lda, int64_t n, int64_t k, int
         check(c, launch_split(A11, lda, h, kap, c.m, c.ds.b, pA11_early, c.st), "split");
     }
     rec(c, A11, lda, h, kap, C11, ldc, levels - 1, pA11_early);
-    if (!c.ar.dry) cudaStreamWaitEvent(c.st, c.in_rest, 0);
+    if (!c.ar.dry && c.nbands == 0) cudaStreamWaitEvent(c.st, c.in_rest, 0);
   }
+  const bool banded = p1_first && c.nbands > 0;
   // S3: the input of the recursive product P5.  Table 3 keeps it in C21
   // (needs kappa <= h, i.e. k <= n); otherwise it takes workspace.
   int32_t *S3;
@@ -773,7 +789,9 @@ static void rec(Ctx &c, const int32_t *A, int64_t lda, int64_t n, int64_t k, int
   // sides only)
   const bool wino = last && c.leaf == AAT_LEAF_TC && c.wino && h % 2 == 0 && kap % 2 == 0;
   // 1. S1..S4 (4 additions, 2 products by Y) in one pass over A
-  const LevelOps L = sblocks_step(c, A, lda, h, kap, S3, ldS3, last, pA11_early, wino);
+  const LevelOps L = sblocks_step(c, A, lda, h, kap, S3, ldS3, last, pA11_early, wino, banded);
+  // everything after the S blocks may read any row of A
+  if (banded && !c.ar.dry) cudaStreamWaitEvent(c.st, c.in_rest, 0);
   // 2-5 at the last level: P4^T, P5, P3 and P1 read only digit planes
   // written by step 1 and write four different blocks of C, so they may run
   // as one persistent launch over the tiles of all four
@@ -1065,12 +1083,14 @@ static size_t run_plan_in(Ctx &c, const int32_t *A, int64_t n, int64_t k, int64_
   // end-to-end path: with no top level to overlap, wait for all of A
   // before anything reads it
   const cudaEvent_t in_a11 = c.in_a11, in_rest = c.in_rest;
+  const int nbands = c.nbands;
   if (in_rest && !early) {
     if (!dry) {
       cudaStreamWaitEvent(c.st, in_a11, 0);
       cudaStreamWaitEvent(c.st, in_rest, 0);
     }
     c.in_a11 = c.in_rest = nullptr;
+    c.nbands = 0;
   }
   const int32_t *Aw = A;
   int64_t ldaw = lda;
@@ -1106,6 +1126,7 @@ static size_t run_plan_in(Ctx &c, const int32_t *A, int64_t n, int64_t k, int64_
   if (!dry && !early && c.split_ev && c.err == AAT_OK) cudaEventRecord(c.split_ev, c.st);
   c.in_a11 = in_a11;
   c.in_rest = in_rest;
+  c.nbands = nbands;
   return c.ar.peak;
 }
 
@@ -1273,7 +1294,8 @@ const char *aat_last_error(void) { return g_last_error.c_str(); }
 static int modp_device(const int32_t *A, int64_t n, int64_t k, int64_t lda, uint32_t p, int32_t *C,
                        int64_t ldc, uint32_t flags, cudaStream_t stream, cudaEvent_t split_ev,
                        int64_t *split_row, int form = 0, cudaEvent_t in_a11 = nullptr,
-                       cudaEvent_t in_rest = nullptr) {
+                       cudaEvent_t in_rest = nullptr, const cudaEvent_t *in_bands = nullptr,
+                       int nbands = 0) {
   if (split_row) *split_row = n;
   if (n < 0 || k < 0) return fail(AAT_EINVAL, "negative size");
   if (n > (1 << 30) || k > (1 << 30)) return fail(AAT_EINVAL, "size too large");
@@ -1294,6 +1316,8 @@ static int modp_device(const int32_t *A, int64_t n, int64_t k, int64_t lda, uint
   c.form = form;
   c.in_a11 = in_a11;
   c.in_rest = in_rest;
+  c.in_bands = in_bands;
+  c.nbands = in_bands ? nbands : 0;
   size_t need = choose_schedule(c, A, n, k, lda, C, ldc, flags);
   void *ws = nullptr;
   if ((e = ensure_workspace(need, &ws))) {
@@ -1316,6 +1340,8 @@ static int modp_device(const int32_t *A, int64_t n, int64_t k, int64_t lda, uint
 // [a, b) copies columns [0, b) of its rows, so a band carries b (b - a)
 // entries (the triangle plus (b - a)^2 / 2 entries above it).
 constexpr int64_t kHostBand = 512;
+// Row bands in which the end-to-end path copies A (after A11) to the device.
+constexpr int kHostInBands = 8;
 
 static int64_t low_band_entries(int64_t r0, int64_t r1) {
   int64_t total = 0;
@@ -1443,7 +1469,13 @@ int aat_modp_host(const int32_t *A_host, int64_t n, int64_t k, uint32_t p, int32
     if (!s->e2e_split) cudaEventCreateWithFlags(&s->e2e_split, cudaEventDisableTiming);
     if (!s->e2e_a11) cudaEventCreateWithFlags(&s->e2e_a11, cudaEventDisableTiming);
     if (!s->e2e_rest) cudaEventCreateWithFlags(&s->e2e_rest, cudaEventDisableTiming);
-    if (!s->e2e_stream || !s->e2e_stream2 || !s->e2e_split || !s->e2e_a11 || !s->e2e_rest)
+    while ((int)s->e2e_bands.size() < kHostInBands) {
+      cudaEvent_t ev = nullptr;
+      if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) break;
+      s->e2e_bands.push_back(ev);
+    }
+    if (!s->e2e_stream || !s->e2e_stream2 || !s->e2e_split || !s->e2e_a11 || !s->e2e_rest ||
+        (int)s->e2e_bands.size() < kHostInBands)
       return fail(AAT_ECUDA, "e2e streams");
     if (s->e2e_a_size < abytes) {
       if (s->e2e_a) cudaFree(s->e2e_a);
@@ -1466,26 +1498,42 @@ int aat_modp_host(const int32_t *A_host, int64_t n, int64_t k, uint32_t p, int32
   if (!(flags & AAT_ZERO_UPPER) && n >= 2 && k >= 2) {
     // A comes in on the second stream, its top-left block A11 (rows and
     // columns below n/2, k/2) first: when a recursion level runs, the
-    // product P1 = Low(A11 A11^T) starts while the rest of A is in flight
+    // product P1 = Low(A11 A11^T) starts while the rest of A is in flight.
+    // The rest follows in row bands (rows [i0, i1) of A12 and rows
+    // [h + i0, h + i1) of the bottom half), so that the top level's S-block
+    // kernel, which needs the rows i and h + i of all four blocks, runs on
+    // each band as soon as it is on the device.
     int32_t *Ad = (int32_t *)s->e2e_a;
     const int64_t h = n / 2, kap = k / 2;
     cudaStream_t s2 = s->e2e_stream2;
     if ((ce = cudaMemcpy2DAsync(Ad, (size_t)k * 4, A_host, (size_t)k * 4, (size_t)kap * 4,
                                 (size_t)h, cudaMemcpyHostToDevice, s2)) != cudaSuccess ||
-        (ce = cudaEventRecord(s->e2e_a11, s2)) != cudaSuccess ||
-        (ce = cudaMemcpy2DAsync(Ad + kap, (size_t)k * 4, A_host + kap, (size_t)k * 4,
-                                (size_t)(k - kap) * 4, (size_t)h, cudaMemcpyHostToDevice, s2)) !=
-            cudaSuccess ||
-        (ce = cudaMemcpyAsync(Ad + h * k, A_host + h * k, (size_t)(n - h) * k * 4,
-                              cudaMemcpyHostToDevice, s2)) != cudaSuccess ||
-        (ce = cudaEventRecord(s->e2e_rest, s2)) != cudaSuccess)
+        (ce = cudaEventRecord(s->e2e_a11, s2)) != cudaSuccess)
+      return cuda_fail(ce, "copy A to the device");
+    for (int b = 0; b < kHostInBands; ++b) {
+      const int64_t i0 = h * b / kHostInBands, i1 = h * (b + 1) / kHostInBands;
+      // the last band also carries the bottom row of an odd n
+      const int64_t j1 = (b == kHostInBands - 1) ? n : h + i1;
+      if (i1 > i0 && (ce = cudaMemcpy2DAsync(Ad + i0 * k + kap, (size_t)k * 4,
+                                             A_host + i0 * k + kap, (size_t)k * 4,
+                                             (size_t)(k - kap) * 4, (size_t)(i1 - i0),
+                                             cudaMemcpyHostToDevice, s2)) != cudaSuccess)
+        return cuda_fail(ce, "copy A to the device");
+      if (j1 > h + i0 && (ce = cudaMemcpyAsync(Ad + (h + i0) * k, A_host + (h + i0) * k,
+                                               (size_t)(j1 - h - i0) * k * 4,
+                                               cudaMemcpyHostToDevice, s2)) != cudaSuccess)
+        return cuda_fail(ce, "copy A to the device");
+      if ((ce = cudaEventRecord(s->e2e_bands[b], s2)) != cudaSuccess)
+        return cuda_fail(ce, "copy A to the device");
+    }
+    if ((ce = cudaEventRecord(s->e2e_rest, s2)) != cudaSuccess)
       return cuda_fail(ce, "copy A to the device");
     // only the lower triangle is defined: copy it in row bands; the rows
     // below the top-level split are final before the last product P2 runs
     // and go back on the second stream meanwhile
     int64_t split = n;
     e = modp_device(Ad, n, k, k, p, (int32_t *)Cd, n, flags, st, s->e2e_split, &split, 0,
-                    s->e2e_a11, s->e2e_rest);
+                    s->e2e_a11, s->e2e_rest, s->e2e_bands.data(), kHostInBands);
     if (e) return e;
     if (split < n) {
       if ((ce = cudaStreamWaitEvent(s2, s->e2e_split, 0)) != cudaSuccess ||
@@ -1814,6 +1862,7 @@ void aat_shutdown(void) {
     if (s.e2e_split) cudaEventDestroy(s.e2e_split);
     if (s.e2e_a11) cudaEventDestroy(s.e2e_a11);
     if (s.e2e_rest) cudaEventDestroy(s.e2e_rest);
+    for (cudaEvent_t ev : s.e2e_bands) cudaEventDestroy(ev);
     cudaSetDevice(cur);
   }
   g_states.clear();

@@ -305,9 +305,11 @@ struct SKernelOut {
   Planes sp[4];
   Planes a11, a12, a22;
 };
+// Rows [r0, r1) of the four blocks (default: all h rows).
 cudaError_t launch_sblocks(const int32_t *A, int64_t lda, int64_t h, int64_t kappa,
                            const ModP &m, const YParams &y, int b,
-                           const SKernelOut &o, cudaStream_t st);
+                           const SKernelOut &o, cudaStream_t st, int64_t r0 = 0,
+                           int64_t r1 = -1);
 
 // Winograd's form of Strassen's algorithm for a general product X Y^T (one
 // level): the digit planes of the seven operand blocks of one side (left:

@@ -83,15 +83,17 @@ __device__ __forceinline__ void ldv_bal(const int32_t *p, const ModP &m, int32_t
 // V = 4 needs kappa/2 (kind 2) or kappa (kind 1), lda, every output stride
 // and every plane stride to be multiples of 4 and 16-byte aligned bases.
 // NB: digits per residue of every plane output.
+// Rows [r0, r1) of the blocks (all of them: r0 = 0, r1 = h).
 template <int V, int NB>
 __global__ void sblocks_kernel(const int32_t *__restrict__ A, int64_t lda, int64_t h,
-                               int64_t kappa, ModP m, YParams y, int b, SKernelOut o) {
+                               int64_t kappa, ModP m, YParams y, int b, SKernelOut o,
+                               int64_t r0, int64_t r1) {
   const int64_t ncols = ((y.kind == 2) ? kappa / 2 : kappa) / V;
-  const int64_t total = h * ncols;
+  const int64_t total = (r1 - r0) * ncols;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = t / ncols;
-    const int64_t j = (t - i * ncols) * V;
+    const int64_t i = r0 + t / ncols;
+    const int64_t j = (t - (i - r0) * ncols) * V;
     const int32_t *r1 = A + i * lda;        // row i of [A11 A12]
     const int32_t *r2 = A + (h + i) * lda;  // row i of [A21 A22]
     if (y.kind == 2) {
@@ -485,17 +487,20 @@ int grid_for(int64_t total) {
 
 cudaError_t launch_sblocks(const int32_t *A, int64_t lda, int64_t h, int64_t kappa,
                            const ModP &m, const YParams &y, int b, const SKernelOut &o,
-                           cudaStream_t st) {
+                           cudaStream_t st, int64_t r0, int64_t r1) {
+  if (r1 < 0) r1 = h;
+  if (r0 < 0 || r0 > r1 || r1 > h) return cudaErrorInvalidValue;
+  const int64_t rows = r1 - r0;
   const int64_t ncols = (y.kind == 2) ? kappa / 2 : kappa;
-  const int64_t total = h * ncols;
+  const int64_t total = rows * ncols;
   if (total <= 0) return cudaSuccess;
-  double bytes = 16.0 * h * kappa;  // A11, A12, A21, A22 read once
+  double bytes = 16.0 * rows * kappa;  // A11, A12, A21, A22 read once
   for (int q = 0; q < 4; ++q) {
-    if (o.s[q]) bytes += 4.0 * h * kappa;
-    if (o.sp[q].ptr) bytes += 2.0 * o.sp[q].L * h * kappa;
+    if (o.s[q]) bytes += 4.0 * rows * kappa;
+    if (o.sp[q].ptr) bytes += 2.0 * o.sp[q].L * rows * kappa;
   }
   for (const Planes *P : {&o.a11, &o.a12, &o.a22})
-    if (P->ptr) bytes += 2.0 * P->L * h * kappa;
+    if (P->ptr) bytes += 2.0 * P->L * rows * kappa;
   ProfScope prof(AAT_K_SBLOCKS, st, bytes);
   // 16-byte vector path when every address it touches is aligned
   auto al16 = [](const void *ptr) { return ((uintptr_t)ptr & 15) == 0; };
@@ -517,9 +522,9 @@ cudaError_t launch_sblocks(const int32_t *A, int64_t lda, int64_t h, int64_t kap
 #define AAT_SB(NBV)                                                                     \
   case NBV:                                                                             \
     if (vec)                                                                            \
-      sblocks_kernel<4, NBV><<<g, kThreads, 0, st>>>(A, lda, h, kappa, m, y, b, o);     \
-    else                                                                                \
-      sblocks_kernel<1, NBV><<<g, kThreads, 0, st>>>(A, lda, h, kappa, m, y, b, o);     \
+      sblocks_kernel<4, NBV><<<g, kThreads, 0, st>>>(A, lda, h, kappa, m, y, b, o, r0, r1); \
+    else                                                                                    \
+      sblocks_kernel<1, NBV><<<g, kThreads, 0, st>>>(A, lda, h, kappa, m, y, b, o, r0, r1); \
     break;
   switch (nb) {
     AAT_SB(1) AAT_SB(2) AAT_SB(3) AAT_SB(4) AAT_SB(5)
