@@ -552,10 +552,12 @@ static void leaf(Ctx &c, Operand X, Operand Y, bool same, int64_t M, int64_t N, 
   if (pass_mode(c) && X.pl.L == 0 && (same || Y.pl.L == 0)) {
     // low-memory plane passes: split a window of planes, run its plane
     // products, accumulate (the first pass with live terms takes beta)
-    const int Q = plane_count(c);
+    // a product of an operand by itself splits one operand per pass, so its
+    // windows are twice as wide in the same workspace
+    const int Q = plane_count(c), W = same ? 2 * c.pass_w : c.pass_w;
     bool first = true;
-    for (int q0 = 0; q0 < Q; q0 += c.pass_w) {
-      const int w = std::min(c.pass_w, Q - q0);
+    for (int q0 = 0; q0 < Q; q0 += W) {
+      const int w = std::min(W, Q - q0);
       const size_t mk = c.ar.used;
       Planes px = planes_window(c, M, K, q0, w), py = px;
       if (!same) py = planes_window(c, N, K, q0, w);

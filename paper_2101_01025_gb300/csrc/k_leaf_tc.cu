@@ -740,9 +740,19 @@ cudaError_t encode_planes(CUtensorMap *tm, const Planes &P, int box_rows) {
 // and shared through L2 by every tile of the wave (18 panels per wave of 76
 // tiles against 24 for 8 x 8 super-blocks swept row by row).  `tm` is the
 // tile height (128 or 256).
+// Band height in output rows (AAT_TILE_BAND, default 2048).
+int64_t band_rows() {
+  static const int64_t v = [] {
+    const char *e = getenv("AAT_TILE_BAND");
+    const long long r = e ? atoll(e) : 2048;
+    return (int64_t)(r >= 128 ? r : 2048);
+  }();
+  return v;
+}
+
 void tile_order(int64_t M, int64_t N, int lower, int tm, std::vector<int2> &v) {
   const int64_t TI = (M + tm - 1) / tm, TJ = (N + BN - 1) / BN;
-  const int64_t band = std::max<int64_t>(1, 2048 / tm);
+  const int64_t band = std::max<int64_t>(1, band_rows() / tm);
   for (int64_t bi = 0; bi < TI; bi += band) {
     const int64_t iend = std::min(TI, bi + band);
     for (int64_t j = 0; j < TJ; ++j)
