@@ -447,76 +447,82 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_f32_kernel(const __grid_const
 
 // ----------------------------------------------------------- split / combine
 
-// BF16 pieces of v: v = p0 + p1 + p2 + (rest), each p the BF16 rounding of
-// what is left (the differences are exact in FP32).
-__device__ __forceinline__ void pieces(float v, int np, __nv_bfloat16 (&o)[3]) {
-  float r = v;
-#pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    if (q < np) {
-      o[q] = __float2bfloat16_rn(r);
-      r = r - __bfloat162float(o[q]);
-    }
-  }
-}
-
 struct CSplitOut {
   Planes re, im, s, d;  // pieces of Re, Im, Re + Im, Re - Im (each optional)
 };
 
-// One thread per 4 consecutive columns of a row (rows over blockIdx.y, a
-// grid-stride loop over column quads): the pieces of 4 values go out as one
-// 8-byte store per plane (kstride is a multiple of 8); a ragged last quad
-// stores element by element.
-__device__ __forceinline__ void csplit_quad(const float2 *__restrict__ a_row, int64_t r,
-                                            int64_t q4, int64_t cols, int np, const CSplitOut &o) {
+// Up to 4 consecutive values of a row (zeros past nv), 16-byte loads when the
+// row is aligned.
+__device__ __forceinline__ void cload4(const float2 *__restrict__ a_row, int64_t c0, int nv,
+                                       float2 (&a)[4]) {
+  if (nv == 4 && (reinterpret_cast<uintptr_t>(a_row) & 15) == 0) {
+    const float4 u0 = reinterpret_cast<const float4 *>(a_row + c0)[0];
+    const float4 u1 = reinterpret_cast<const float4 *>(a_row + c0)[1];
+    a[0] = make_float2(u0.x, u0.y);
+    a[1] = make_float2(u0.z, u0.w);
+    a[2] = make_float2(u1.x, u1.y);
+    a[3] = make_float2(u1.z, u1.w);
+  } else {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) a[v] = v < nv ? a_row[c0 + v] : make_float2(0.f, 0.f);
+  }
+}
+
+// The pieces of 4 consecutive values a[0..nv) of row r, columns c0.., into
+// every plane set of o: one 8-byte store per plane (kstride is a multiple of
+// 8); a ragged last quad stores element by element.
+__device__ __forceinline__ void csplit_store(const float2 (&a)[4], int64_t r, int64_t c0, int nv,
+                                             int np, const CSplitOut &o) {
   const Planes *outs[4] = {&o.re, &o.im, &o.s, &o.d};
-  {
-    {
-      const int64_t c0 = 4 * q4;
-      const int nv = (int)min((int64_t)4, cols - c0);
-      float2 a[4];
-      if (nv == 4 && (reinterpret_cast<uintptr_t>(a_row) & 15) == 0) {
-        const float4 u0 = reinterpret_cast<const float4 *>(a_row + c0)[0];
-        const float4 u1 = reinterpret_cast<const float4 *>(a_row + c0)[1];
-        a[0] = make_float2(u0.x, u0.y);
-        a[1] = make_float2(u0.z, u0.w);
-        a[2] = make_float2(u1.x, u1.y);
-        a[3] = make_float2(u1.z, u1.w);
-      } else {
 #pragma unroll
-        for (int v = 0; v < 4; ++v) a[v] = v < nv ? a_row[c0 + v] : make_float2(0.f, 0.f);
+  for (int w = 0; w < 4; ++w) {
+    const Planes &P = *outs[w];
+    if (!P.ptr) continue;
+    float x[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+      x[v] = w == 0 ? a[v].x : w == 1 ? a[v].y : w == 2 ? a[v].x + a[v].y : a[v].x - a[v].y;
+    // pieces of two values per conversion instruction (round to nearest),
+    // the rest carried in FP32 (exact: each rest is an FP32 difference of a
+    // value and its BF16 rounding)
+    __nv_bfloat162 lo[3], hi[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      if (q < np) {
+        lo[q] = __floats2bfloat162_rn(x[0], x[1]);
+        hi[q] = __floats2bfloat162_rn(x[2], x[3]);
+        const float2 fl = __bfloat1622float2(lo[q]), fh = __bfloat1622float2(hi[q]);
+        x[0] -= fl.x;
+        x[1] -= fl.y;
+        x[2] -= fh.x;
+        x[3] -= fh.y;
       }
-#pragma unroll
-      for (int w = 0; w < 4; ++w) {
-        const Planes &P = *outs[w];
-        if (!P.ptr) continue;
-        __nv_bfloat16 pc[4][3];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          const float x = w == 0 ? a[v].x : w == 1 ? a[v].y : w == 2 ? a[v].x + a[v].y : a[v].x - a[v].y;
-          pieces(x, np, pc[v]);
-        }
-        const int64_t plane = P.rows * P.kstride;
-        __nv_bfloat16 *dst = P.ptr + r * P.kstride + c0;
-        for (int q = 0; q < np; ++q) {
-          if (nv == 4) {
-            __nv_bfloat162 lo, hi;
-            lo.x = pc[0][q];
-            lo.y = pc[1][q];
-            hi.x = pc[2][q];
-            hi.y = pc[3][q];
-            uint2 u;
-            u.x = *reinterpret_cast<uint32_t *>(&lo);
-            u.y = *reinterpret_cast<uint32_t *>(&hi);
-            *reinterpret_cast<uint2 *>(dst + q * plane) = u;
-          } else {
-            for (int v = 0; v < nv; ++v) dst[q * plane + v] = pc[v][q];
-          }
-        }
+    }
+    const int64_t plane = P.rows * P.kstride;
+    __nv_bfloat16 *dst = P.ptr + r * P.kstride + c0;
+    for (int q = 0; q < np; ++q) {
+      if (nv == 4) {
+        uint2 u;
+        u.x = *reinterpret_cast<uint32_t *>(&lo[q]);
+        u.y = *reinterpret_cast<uint32_t *>(&hi[q]);
+        *reinterpret_cast<uint2 *>(dst + q * plane) = u;
+      } else {
+        const __nv_bfloat16 pv[4] = {lo[q].x, lo[q].y, hi[q].x, hi[q].y};
+        for (int v = 0; v < nv; ++v) dst[q * plane + v] = pv[v];
       }
     }
   }
+}
+
+// One thread per 4 consecutive columns of a row (rows over blockIdx.y, a
+// grid-stride loop over column quads).
+__device__ __forceinline__ void csplit_quad(const float2 *__restrict__ a_row, int64_t r,
+                                            int64_t q4, int64_t cols, int np, const CSplitOut &o) {
+  const int64_t c0 = 4 * q4;
+  const int nv = (int)min((int64_t)4, cols - c0);
+  float2 a[4];
+  cload4(a_row, c0, nv, a);
+  csplit_store(a, r, c0, nv, np, o);
 }
 
 __global__ void csplit_kernel(const float2 *__restrict__ A, int64_t lda, int64_t rows, int64_t cols,
@@ -924,11 +930,200 @@ static cudaError_t launch_leaf_f32(const std::vector<FTerm> &terms, int np, int 
   return cudaGetLastError();
 }
 
+// ------------------------------------ several real products in one launch
+
+// One real product of a fused launch: out (M x N FP32, row stride ldo) =
+// X_xs Y_ys^T over the piece pairs of `keep` pieces, where X_xs is plane set
+// xs of the plane buffer X (np pieces per set), likewise Y; lower: only the
+// tiles on or below the diagonal.
+struct FusedJob {
+  const Planes *X, *Y;
+  int xs, ys, keep;
+  float *out;
+  int64_t ldo, M, N;
+  int lower;
+};
+
+constexpr int MAX_FUSED = 16;
+constexpr int MAX_FUSED_GROUPS = MAX_FUSED * 6;
+
+// The job table of a fused launch, passed by value to one small kernel that
+// writes it into device memory (no host buffer, no copy).
+struct FusedTable {
+  FJobDesc jobs[MAX_FUSED];
+  FGroup g[MAX_FUSED_GROUPS];
+  int njobs, ng;
+};
+
+size_t fused_table_bytes() {
+  return ((sizeof(FJobDesc) * MAX_FUSED + 255) & ~(size_t)255) + sizeof(FGroup) * MAX_FUSED_GROUPS;
+}
+
+namespace {
+
+__global__ void fused_table_kernel(const __grid_constant__ FusedTable T, FJobDesc *jobs,
+                                   FGroup *gtab) {
+  for (int i = threadIdx.x; i < T.njobs; i += blockDim.x) jobs[i] = T.jobs[i];
+  for (int i = threadIdx.x; i < T.ng; i += blockDim.x) gtab[i] = T.g[i];
+}
+
+// Tile lists of fused launches, per device, tile height and job shapes: each
+// job's tiles in bands of 2048 rows swept column by column, jobs in order.
+std::map<std::vector<int64_t>, std::pair<int4 *, int>> g_ftiles;
+std::map<int, bool> g_fattr[2];
+
+}  // namespace
+
+// All jobs in one persistent launch of the FP32 leaf (tcgen05, CTA pairs when
+// the tiles fill every co-resident pair), so that no product's last wave
+// leaves SMs idle.  table_mem: fused_table_bytes() of device memory, 256-byte
+// aligned, for the job table.
+static cudaError_t launch_leaf_f32_fused(const std::vector<FusedJob> &jobs, int np, int64_t K,
+                                         void *table_mem, cudaStream_t st) {
+  const int nj = (int)jobs.size();
+  if (nj < 1 || nj > MAX_FUSED || K <= 0) return cudaErrorInvalidValue;
+  std::lock_guard<std::mutex> lock(g_mu_c);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int units = pair_units_c(dev);
+  bool pair = units > 0;
+  int64_t pt = 0;
+  for (const FusedJob &j : jobs) {
+    pair = pair && j.M >= 256;
+    const int64_t t = ((j.M + 255) / 256) * ((j.N + BN - 1) / BN);
+    pt += j.lower ? t / 2 : t;
+  }
+  const char *ev = getenv("AAT_LEAF_PAIR");
+  pair = ev ? (atoi(ev) > 0 && units > 0) : (pair && pt >= units);
+  const int tm = pair ? FShape<true>::TM : FShape<false>::TM;
+  FusedTable *T = new FusedTable;
+  std::memset(T, 0, sizeof(FusedTable));
+  cudaError_t e = cudaSuccess;
+  double work = 0.0;
+  const int kblocks = (int)((K + BK - 1) / BK);
+  for (int i = 0; i < nj && e == cudaSuccess; ++i) {
+    const FusedJob &j = jobs[i];
+    FJobDesc &d = T->jobs[i];
+    if ((e = encode_c(&d.tmx, *j.X, BM)) != cudaSuccess ||
+        (e = encode_c(&d.tmy, *j.Y, pair ? FShape<true>::YROWS : FShape<false>::YROWS)) !=
+            cudaSuccess)
+      break;
+    d.out = j.out;
+    d.ldo = j.ldo;
+    d.M = j.M;
+    d.N = j.N;
+    d.lower = j.lower;
+    d.kblocks = kblocks;
+    d.goff = T->ng;
+    int pairs[6][2];
+    const int npairs = piece_pairs(std::min(j.keep, np), pairs);
+    d.ng = npairs;
+    for (int q = 0; q < npairs; ++q) {
+      FGroup &g = T->g[T->ng++];
+      g.xp = (int16_t)(j.xs * np + pairs[q][0]);
+      g.yp = (int16_t)(j.ys * np + pairs[q][1]);
+      g.neg = 0;
+    }
+    const double macs = j.lower ? 0.5 * (double)j.M * (double)(j.M + 1) * K : (double)j.M * j.N * K;
+    work += 2.0 * npairs * macs;
+  }
+  T->njobs = nj;
+  // the tile list, cached per shape list
+  std::vector<int64_t> key = {dev, tm};
+  for (const FusedJob &j : jobs) key.insert(key.end(), {j.M, j.N, (int64_t)j.lower});
+  int4 *tiles = nullptr;
+  int nt = 0;
+  if (e == cudaSuccess) {
+    auto it = g_ftiles.find(key);
+    if (it != g_ftiles.end()) {
+      tiles = it->second.first;
+      nt = it->second.second;
+    } else {
+      std::vector<int4> v;
+      for (int i = 0; i < nj; ++i) {
+        const FusedJob &j = jobs[i];
+        const int64_t TI = (j.M + tm - 1) / tm, TJ = (j.N + BN - 1) / BN;
+        const int64_t band = std::max<int64_t>(1, 2048 / tm);
+        for (int64_t bi = 0; bi < TI; bi += band)
+          for (int64_t jj = 0; jj < TJ; ++jj)
+            for (int64_t ii = bi; ii < std::min(TI, bi + band); ++ii) {
+              if (j.lower && jj * BN > ii * tm + tm - 1) continue;
+              v.push_back(make_int4(i, (int)ii, (int)jj, 0));
+            }
+      }
+      if ((e = cudaMalloc(&tiles, std::max<size_t>(v.size(), 1) * sizeof(int4))) == cudaSuccess &&
+          (e = cudaMemcpy(tiles, v.data(), v.size() * sizeof(int4), cudaMemcpyHostToDevice)) ==
+              cudaSuccess) {
+        nt = (int)v.size();
+        g_ftiles[key] = std::make_pair(tiles, nt);
+      }
+    }
+  }
+  if (e == cudaSuccess && !g_fattr[pair][dev]) {
+    e = pair ? cudaFuncSetAttribute(leaf_f32_kernel<true, true>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)FShape<true>::SMEM)
+             : cudaFuncSetAttribute(leaf_f32_kernel<false, true>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)FShape<false>::SMEM);
+    if (e == cudaSuccess) g_fattr[pair][dev] = true;
+  }
+  if (e != cudaSuccess) {
+    delete T;
+    return e;
+  }
+  FJobDesc *jobs_dev = (FJobDesc *)table_mem;
+  FGroup *gtab_dev =
+      (FGroup *)((char *)table_mem + ((sizeof(FJobDesc) * MAX_FUSED + 255) & ~(size_t)255));
+  fused_table_kernel<<<1, 64, 0, st>>>(*T, jobs_dev, gtab_dev);
+  delete T;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  FParams *P = new FParams;
+  std::memset(P, 0, sizeof(FParams));
+  P->kchunk = 8;  // as launch_leaf_f32
+  P->ntiles = nt;
+  P->status = device_status_ptr();
+  P->jobs = jobs_dev;
+  P->btiles = tiles;
+  P->gtab = gtab_dev;
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (nt > 0) {
+    ProfScope prof(AAT_K_LEAF_F32, st, work);
+    if (pair) {
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = 2;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3(2 * std::max(1, std::min(nt, units)), 1, 1);
+      cfg.blockDim = dim3(THREADS, 1, 1);
+      cfg.dynamicSmemBytes = FShape<true>::SMEM;
+      cfg.stream = st;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      e = cudaLaunchKernelEx(&cfg, leaf_f32_kernel<true, true>, *P);
+    } else {
+      leaf_f32_kernel<false, true><<<std::max(1, std::min(nt, sms)), THREADS, FShape<false>::SMEM,
+                                     st>>>(*P);
+      e = cudaGetLastError();
+    }
+  }
+  delete P;
+  return e;
+}
+
 void leaf_f32_release() {
   std::lock_guard<std::mutex> lock(g_mu_c);
   for (auto &kv : g_tiles_c)
     if (kv.second.first) cudaFree(kv.second.first);
   g_tiles_c.clear();
+  for (auto &kv : g_ftiles)
+    if (kv.second.first) cudaFree(kv.second.first);
+  g_ftiles.clear();
+  g_fattr[0].clear();
+  g_fattr[1].clear();
   g_attr_c.clear();
   g_pair_units_c.clear();
 }
@@ -981,6 +1176,45 @@ __global__ void csblocks_kernel(const float2 *__restrict__ A, int64_t lda, int64
     if (S3) S3[i * ld3 + j] = s3;
     if (S4) S4[i * ld4 + j] = s4;
   }
+}
+
+// The last level of Algorithm 1 over C (Y = i I) in one pass over A: the S
+// blocks S1 = (A21 - A11) i, S2 = A22 - A21 i, S3 = S1 - A22, S4 = S3 + A12
+// are formed in registers and, with A11, A12, A22, written straight out as
+// the BF16 pieces of the operand sets of the level's fused products.
+struct CLevelOut {
+  CSplitOut s2, s1, a22, s4, s3, a11, a12;
+};
+
+__global__ void csblocks_split_kernel(const float2 *__restrict__ A, int64_t lda, int64_t h,
+                                      int64_t kap, int np, CLevelOut o) {
+  const int64_t cq = (kap + 3) / 4;
+  for (int64_t r = blockIdx.y; r < h; r += gridDim.y)
+    for (int64_t q4 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q4 < cq;
+         q4 += (int64_t)gridDim.x * blockDim.x) {
+      const int64_t c0 = 4 * q4;
+      const int nv = (int)min((int64_t)4, kap - c0);
+      float2 a11[4], a12[4], a21[4], a22[4], s[4];
+      cload4(A + r * lda, c0, nv, a11);
+      cload4(A + r * lda + kap, c0, nv, a12);
+      cload4(A + (h + r) * lda, c0, nv, a21);
+      cload4(A + (h + r) * lda + kap, c0, nv, a22);
+      csplit_store(a11, r, c0, nv, np, o.a11);
+      csplit_store(a12, r, c0, nv, np, o.a12);
+      csplit_store(a22, r, c0, nv, np, o.a22);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) s[v] = csub(a22[v], ci(a21[v]));  // S2
+      csplit_store(s, r, c0, nv, np, o.s2);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) s[v] = ci(csub(a21[v], a11[v]));  // S1
+      csplit_store(s, r, c0, nv, np, o.s1);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) s[v] = csub(s[v], a22[v]);  // S3
+      csplit_store(s, r, c0, nv, np, o.s3);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) s[v] = cadd(s[v], a12[v]);  // S4
+      csplit_store(s, r, c0, nv, np, o.s4);
+    }
 }
 
 // Post-additions of Algorithm 1 over C (phi = transposition, so Up(U1) is
@@ -1216,6 +1450,123 @@ static void c_gen_leaf(CCtx &c, const float2 *X, int64_t ldx, const float2 *Y, i
   c.ar.used = mark;
 }
 
+// The last level of Algorithm 1 over C (Sec. 4.1, Y = i I) with the twelve
+// real products of its leaves in ONE launch: P4^T = S2 S1^T and P3 = A22 S4^T
+// by 3M (T1 = Xr Yr^T, T2 = Xi Yi^T, T3 = (Xr + Xi)(Yr + Yi)^T each), P5 =
+// Low(S3 S3^T), P1 = Low(A11 A11^T) and P2 = Low(A12 A12^T) by 2M with eps =
+// -1 (H = Re Im^T, G = Low((Re + Im)(Re - Im)^T) each).  One pass over A
+// forms the S blocks in registers and writes the BF16 pieces of every
+// operand; every product reads only its operands' pieces and writes its own
+// buffer, so all of them run as one persistent launch; the combines then form
+// P4^T -> C22, P3 -> C21, P5 -> C12, P1 -> C11, the post-additions run, and
+// P2's combine (into C12, free after them) and U3 = P1 + P2 close.
+static void c_last_level_fused(CCtx &c, const float2 *A, int64_t lda, int64_t n, int64_t k,
+                               float2 *C, int64_t ldc) {
+  const int64_t h = n / 2, kap = k / 2;
+  float2 *C11 = C, *C12 = C + h, *C21 = C + h * ldc, *C22 = C + h * ldc + h;
+  const size_t mark = c.ar.used;
+  // the pieces: 3M operands in 3 sets (re, im, re + im), 2M operands in 2
+  // sets per side (re, re + im | im, re - im); the S blocks themselves exist
+  // only in registers (one pass over A writes every set)
+  Planes PX4 = cplanes(c, h, kap, 3), PY4 = cplanes(c, h, kap, 3);  // S2, S1
+  Planes PX3 = cplanes(c, h, kap, 3), PY3 = cplanes(c, h, kap, 3);  // A22, S4
+  Planes X2[3], Y2[3];                                              // S3, A11, A12
+  for (int q = 0; q < 3; ++q) {
+    X2[q] = cplanes(c, h, kap, 2);
+    Y2[q] = cplanes(c, h, kap, 2);
+  }
+  float *T4[3], *T3[3], *Hb[3], *Gb[3];
+  for (int q = 0; q < 3; ++q) {
+    T4[q] = (float *)c.ar.get((size_t)h * h * 4);
+    T3[q] = (float *)c.ar.get((size_t)h * h * 4);
+    Hb[q] = (float *)c.ar.get((size_t)h * h * 4);
+    Gb[q] = (float *)c.ar.get((size_t)h * h * 4);
+  }
+  void *table = c.ar.get(fused_table_bytes());
+  if (!c.ar.dry && c.err == AAT_OK) {
+    auto three = [&](const Planes &P) {
+      CSplitOut o;
+      std::memset(&o, 0, sizeof(o));
+      o.re = subset(P, 0, c.np);
+      o.im = subset(P, 1, c.np);
+      o.s = subset(P, 2, c.np);
+      return o;
+    };
+    auto two = [&](const Planes &X, const Planes &Y) {
+      CSplitOut o;
+      std::memset(&o, 0, sizeof(o));
+      o.re = subset(X, 0, c.np);
+      o.s = subset(X, 1, c.np);
+      o.im = subset(Y, 0, c.np);
+      o.d = subset(Y, 1, c.np);
+      return o;
+    };
+    CLevelOut lo;
+    lo.s2 = three(PX4);
+    lo.s1 = three(PY4);
+    lo.a22 = three(PX3);
+    lo.s4 = three(PY3);
+    lo.s3 = two(X2[0], Y2[0]);
+    lo.a11 = two(X2[1], Y2[1]);
+    lo.a12 = two(X2[2], Y2[2]);
+    {
+      // 4 blocks read, 24 sets of c.np pieces written
+      ProfScope prof(AAT_K_SBLOCKS, c.st, (double)h * kap * (32.0 + 24.0 * 2.0 * c.np));
+      const int64_t cq = (kap + 3) / 4;
+      const dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((cq + 255) / 256, 64)),
+                      (unsigned)std::max<int64_t>(1, std::min<int64_t>(h, 65535)));
+      csblocks_split_kernel<<<grid, 256, 0, c.st>>>(A, lda, h, kap, c.np, lo);
+      cchk(c, cudaGetLastError(), "complex S blocks and pieces");
+    }
+    std::vector<FusedJob> jobs;
+    for (int q = 0; q < 3; ++q) {
+      jobs.push_back(FusedJob{&PX4, &PY4, q, q, c.keep, T4[q], h, h, h, 0});
+      jobs.push_back(FusedJob{&PX3, &PY3, q, q, c.keep, T3[q], h, h, h, 0});
+    }
+    for (int q = 0; q < 3; ++q) {
+      jobs.push_back(FusedJob{&X2[q], &Y2[q], 0, 0, c.keep, Hb[q], h, h, h, 0});
+      jobs.push_back(FusedJob{&X2[q], &Y2[q], 1, 1, c.np, Gb[q], h, h, h, 1});
+    }
+    if (c.err == AAT_OK)
+      cchk(c, launch_leaf_f32_fused(jobs, c.np, kap, table, c.st), "fused complex leaves");
+    const int64_t nt = (h + T - 1) / T;
+    if (c.err == AAT_OK) {
+      ProfScope prof(AAT_K_POSTADD, c.st, (double)h * h * 2.0 * (12.0 + 8.0));
+      combine3m_kernel<<<grid_c(h * h, 256), 256, 0, c.st>>>(T4[0], T4[1], T4[2], h, h, h, C22,
+                                                            ldc);
+      combine3m_kernel<<<grid_c(h * h, 256), 256, 0, c.st>>>(T3[0], T3[1], T3[2], h, h, h, C21,
+                                                            ldc);
+      cchk(c, cudaGetLastError(), "3M combine");
+    }
+    if (c.err == AAT_OK) {
+      ProfScope prof(AAT_K_POSTADD, c.st, 2.0 * (double)h * h * (4.0 * 1.5 + 8.0 * 0.5));
+      combine2m_kernel<<<(unsigned)(nt * (nt + 1) / 2), T * 8, 0, c.st>>>(Gb[0], Hb[0], h, h, C12,
+                                                                          ldc, 0);
+      combine2m_kernel<<<(unsigned)(nt * (nt + 1) / 2), T * 8, 0, c.st>>>(Gb[1], Hb[1], h, h, C11,
+                                                                          ldc, 0);
+      cchk(c, cudaGetLastError(), "2M combine");
+    }
+    if (c.err == AAT_OK) {  // U4 -> C21, Low(U5) -> C22
+      ProfScope prof(AAT_K_POSTADD, c.st, (double)h * h * 8.0 * 4.5);
+      cpostadd_kernel<<<(unsigned)(nt * (nt + 1) / 2), T * 8, 0, c.st>>>(C11, C12, C21, C22, ldc,
+                                                                         h);
+      cchk(c, cudaGetLastError(), "complex post-additions");
+    }
+    if (c.err == AAT_OK) {  // P2 -> C12, Low(U3) = Low(P1 + P2) -> C11
+      ProfScope prof(AAT_K_POSTADD, c.st, (double)h * h * (4.0 * 1.5 + 8.0 * 0.5));
+      combine2m_kernel<<<(unsigned)(nt * (nt + 1) / 2), T * 8, 0, c.st>>>(Gb[2], Hb[2], h, h, C12,
+                                                                          ldc, 0);
+      cchk(c, cudaGetLastError(), "2M combine");
+    }
+    if (c.err == AAT_OK) {
+      ProfScope prof(AAT_K_ADD_LOW, c.st, (double)h * h * 8.0 * 1.5);
+      cadd_low_kernel<<<grid_c(h * h, 256), 256, 0, c.st>>>(C11, C12, ldc, h);
+      cchk(c, cudaGetLastError(), "complex U3");
+    }
+  }
+  c.ar.used = mark;
+}
+
 // Algorithm 1 over C with phi = transposition and Y = i I (Sec. 4.1):
 // Low(A A^T) -> Low(C).  n divisible by 2^levels, k by 2^levels.
 static void c_rec(CCtx &c, const float2 *A, int64_t lda, int64_t n, int64_t k, float2 *C,
@@ -1223,6 +1574,14 @@ static void c_rec(CCtx &c, const float2 *A, int64_t lda, int64_t n, int64_t k, f
   if (c.err) return;
   if (levels == 0 || n < 2 || k < 2) {
     c_two_m(c, A, lda, n, k, C, ldc, 0);
+    return;
+  }
+  static const bool unfused = [] {
+    const char *e = getenv("AAT_C_UNFUSED");  // 1: one launch per real product
+    return e && atoi(e) != 0;
+  }();
+  if (levels == 1 && !unfused) {
+    c_last_level_fused(c, A, lda, n, k, C, ldc);
     return;
   }
   const int64_t h = n / 2, kap = k / 2;
