@@ -1380,6 +1380,7 @@ static void c_two_m(CCtx &c, const float2 *A, int64_t lda, int64_t n, int64_t k,
   Planes Yi = subset(Y, 0, c.np), Ysd = herm ? Xs : subset(Y, 1, c.np);
   float *H = (float *)c.ar.get((size_t)n * n * 4);
   float *G = (float *)c.ar.get((size_t)n * n * 4);
+  void *table = c.ar.get(fused_table_bytes());
   if (!c.ar.dry) {
     // every piece set in one pass over A
     CSplitOut o;
@@ -1389,13 +1390,14 @@ static void c_two_m(CCtx &c, const float2 *A, int64_t lda, int64_t n, int64_t k,
     o.im = Yi;
     if (!herm) o.d = Ysd;
     csplit(c, A, lda, n, k, o);
-    // H = Ar Ai^T (all entries), G = (Ar + Ai)(Ar +- Ai)^T (lower tiles)
-    if (c.err == AAT_OK)
-      cchk(c, launch_leaf_f32({FTerm{&Xr, &Yi, false}}, c.np, c.keep, n, n, k, H, n, 0, c.st),
-           "2M H");
-    if (c.err == AAT_OK)  // G's sum operands keep every stored piece
-      cchk(c, launch_leaf_f32({FTerm{&Xs, &Ysd, false}}, c.np, c.np, n, n, k, G, n, 1, c.st),
-           "2M G");
+    // H = Ar Ai^T (all entries) and G = (Ar + Ai)(Ar +- Ai)^T (lower tiles)
+    // in one launch; G's sum operands keep every stored piece
+    if (c.err == AAT_OK) {
+      const std::vector<FusedJob> jobs = {
+          FusedJob{&X, &Y, 0, 0, c.keep, H, n, n, n, 0},
+          FusedJob{&X, herm ? &X : &Y, 1, 1, c.np, G, n, n, n, 1}};
+      cchk(c, launch_leaf_f32_fused(jobs, c.np, k, table, c.st), "2M H and G");
+    }
     if (c.err == AAT_OK) {
       const int64_t nt = (n + T - 1) / T;
       ProfScope prof(AAT_K_POSTADD, c.st, (double)n * n * (4.0 * 1.5 + 8.0 * 0.5));
