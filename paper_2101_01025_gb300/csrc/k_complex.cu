@@ -275,36 +275,40 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_f32_kernel(const __grid_const
       int stage = 0;
       uint32_t ph = 0, chunk = 0;
       bool ok = true;
+      // shared-memory descriptors: stage and K step move the start-address
+      // field (16-byte units) only, so they are formed by adds
+      const uint64_t da0 = sw128_desc(sbase);
       for (int t = (int)unit0; t < P.ntiles && ok; t += (int)nunits) {
         const FJob jb = fjob<BATCH>(P, t);
-        int inchunk = 0;
-        uint32_t dt = 0;
-        for (int gi = 0; gi < jb.ng && ok; ++gi) {
-          const uint32_t idesc = S::IDESC | (jb.g[gi].neg ? NEG_A : 0u);
-          for (int kb = 0; kb < jb.kblocks; ++kb) {
-            if (inchunk == 0) {
-              const uint32_t buf = chunk & 1u, use = chunk >> 1;
-              if (!wait_bounded<PAIR>(AEMPTY(buf), (use & 1u) ^ 1u, abort_flag, P.status)) {
-                ok = false;
-                break;
-              }
-              tc_fence_after();
-              dt = tmem + buf * ACC_COLS;
-            }
+        // chunks of kchunk K blocks over the flattened (group, K block)
+        // sequence: a chunk may span two groups (one FP32 sum)
+        const int total = jb.ng * jb.kblocks;
+        int gi = 0, kbi = 0;
+        uint32_t idesc = S::IDESC | ((jb.ng > 0 && jb.g[0].neg) ? NEG_A : 0u);
+        for (int q0 = 0; q0 < total && ok; q0 += P.kchunk) {
+          const int q1 = min(q0 + P.kchunk, total);
+          const uint32_t buf = chunk & 1u, use = chunk >> 1;
+          if (!wait_bounded<PAIR>(AEMPTY(buf), (use & 1u) ^ 1u, abort_flag, P.status)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t dt = tmem + buf * ACC_COLS;
+          for (int q = q0; q < q1; ++q) {
             if (!wait_bounded<PAIR>(FULL(stage), ph, abort_flag, P.status)) {
               ok = false;
               break;
             }
             tc_fence_after();
-            const uint32_t sa = sbase + (uint32_t)(stage * S::STAGE_BYTES);
-            const uint32_t sb = sa + S::A_BYTES;
+            const uint64_t da = da0 + (uint64_t)((uint32_t)(stage * S::STAGE_BYTES) >> 4);
+            const uint64_t db = da + (uint64_t)(S::A_BYTES >> 4);
 #pragma unroll
             for (int s = 0; s < BK / 16; ++s) {
-              const uint32_t acc = (inchunk == 0 && s == 0) ? 0u : 1u;
+              const uint32_t acc = (q > q0 || s > 0) ? 1u : 0u;
               if constexpr (PAIR)
-                tc_mma_pair(dt, sw128_desc(sa + 32u * s), sw128_desc(sb + 32u * s), idesc, acc);
+                tc_mma_pair(dt, da + 2u * s, db + 2u * s, idesc, acc);
               else
-                tc_mma(dt, sw128_desc(sa + 32u * s), sw128_desc(sb + 32u * s), idesc, acc);
+                tc_mma(dt, da + 2u * s, db + 2u * s, idesc, acc);
             }
             if constexpr (PAIR)
               tc_commit_pair(EMPTY(stage), 3);
@@ -314,16 +318,17 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_f32_kernel(const __grid_const
               stage = 0;
               ph ^= 1u;
             }
-            const bool last = (gi == jb.ng - 1) && (kb == jb.kblocks - 1);
-            if (++inchunk == P.kchunk || last) {
-              if constexpr (PAIR)
-                tc_commit_pair(AFULL(chunk & 1u), 3);
-              else
-                tc_commit(AFULL(chunk & 1u));
-              ++chunk;
-              inchunk = 0;
+            if (++kbi == jb.kblocks) {
+              kbi = 0;
+              if (++gi < jb.ng) idesc = S::IDESC | (jb.g[gi].neg ? NEG_A : 0u);
             }
           }
+          if (!ok) break;
+          if constexpr (PAIR)
+            tc_commit_pair(AFULL(buf), 3);
+          else
+            tc_commit(AFULL(buf));
+          ++chunk;
         }
       }
       if (!ok) {
