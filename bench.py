@@ -490,6 +490,18 @@ def run_ours(args):
         Ch = torch.empty((N, N), dtype=torch.int32).pin_memory()
         del A
         torch.cuda.empty_cache()
+        # the host link alone (untimed for the metric): 256 MiB of A from
+        # pinned memory, median of 5 copies
+        probe = torch.empty((N // 4, K), dtype=torch.int32, device="cuda")
+        link = []
+        for _ in range(6):
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            probe.copy_(Ah[: N // 4], non_blocking=True)
+            torch.cuda.synchronize()
+            link.append(probe.numel() * 4 / (time.perf_counter() - t1) / 1e9)
+        link_gbs = sorted(link[1:])[2]
+        del probe
         for _ in range(max(1, args.warmup)):
             aat.aat_modp_host(Ah, P, C=Ch)
         barrier()
@@ -504,6 +516,7 @@ def run_ours(args):
                "ms_per_step": 1e3 * t_e2e,
                "ms_per_call_min_median_max": [min(calls), sorted(calls)[len(calls) // 2],
                                               max(calls)],
+               "host_link_h2d_gbs": link_gbs,
                "h2d_bytes_per_step": N * K * 4,
                "d2h_bytes_per_step": aat.aat_modp_host_d2h_bytes(N),
                "api": "aat_modp_host (pinned host A and C; copies inside the call: A11 "

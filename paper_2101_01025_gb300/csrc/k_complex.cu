@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_f32_kernel(const __grid_const
       }
     }
   } else if (warp == 1) {
-    if (lane == 0 && leader) {  // MMA issuer: chunks of kchunk K blocks over (group, K block)
+    if (leader) {  // MMA issuer: the whole warp runs the loop, one elected lane issues
       int stage = 0;
       uint32_t ph = 0, chunk = 0;
       bool ok = true;
@@ -288,32 +288,36 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_f32_kernel(const __grid_const
         for (int q0 = 0; q0 < total && ok; q0 += P.kchunk) {
           const int q1 = min(q0 + P.kchunk, total);
           const uint32_t buf = chunk & 1u, use = chunk >> 1;
-          if (!wait_bounded<PAIR>(AEMPTY(buf), (use & 1u) ^ 1u, abort_flag, P.status)) {
+          if (!__all_sync(0xffffffffu, wait_bounded<PAIR>(AEMPTY(buf), (use & 1u) ^ 1u, abort_flag,
+                                                          P.status))) {
             ok = false;
             break;
           }
           tc_fence_after();
           const uint32_t dt = tmem + buf * ACC_COLS;
           for (int q = q0; q < q1; ++q) {
-            if (!wait_bounded<PAIR>(FULL(stage), ph, abort_flag, P.status)) {
+            if (!__all_sync(0xffffffffu, wait_bounded<PAIR>(FULL(stage), ph, abort_flag, P.status))) {
               ok = false;
               break;
             }
             tc_fence_after();
             const uint64_t da = da0 + (uint64_t)((uint32_t)(stage * S::STAGE_BYTES) >> 4);
             const uint64_t db = da + (uint64_t)(S::A_BYTES >> 4);
+            if (elect_one()) {
 #pragma unroll
-            for (int s = 0; s < BK / 16; ++s) {
-              const uint32_t acc = (q > q0 || s > 0) ? 1u : 0u;
+              for (int s = 0; s < BK / 16; ++s) {
+                const uint32_t acc = (q > q0 || s > 0) ? 1u : 0u;
+                if constexpr (PAIR)
+                  tc_mma_pair(dt, da + 2u * s, db + 2u * s, idesc, acc);
+                else
+                  tc_mma(dt, da + 2u * s, db + 2u * s, idesc, acc);
+              }
               if constexpr (PAIR)
-                tc_mma_pair(dt, da + 2u * s, db + 2u * s, idesc, acc);
+                tc_commit_pair(EMPTY(stage), 3);
               else
-                tc_mma(dt, da + 2u * s, db + 2u * s, idesc, acc);
+                tc_commit(EMPTY(stage));
             }
-            if constexpr (PAIR)
-              tc_commit_pair(EMPTY(stage), 3);
-            else
-              tc_commit(EMPTY(stage));
+            __syncwarp();
             if (++stage == STAGES) {
               stage = 0;
               ph ^= 1u;
@@ -324,20 +328,24 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_f32_kernel(const __grid_const
             }
           }
           if (!ok) break;
-          if constexpr (PAIR)
-            tc_commit_pair(AFULL(buf), 3);
-          else
-            tc_commit(AFULL(buf));
+          if (elect_one()) {
+            if constexpr (PAIR)
+              tc_commit_pair(AFULL(buf), 3);
+            else
+              tc_commit(AFULL(buf));
+          }
+          __syncwarp();
           ++chunk;
         }
       }
-      if (!ok) {
+      if (!ok && elect_one()) {
         if constexpr (PAIR)
           tc_commit_pair(DONE, 1);
         else
           tc_commit(DONE);
         wait_quiet(DONE, 0);
       }
+      __syncwarp();
     }
   } else {  // epilogue: chunks -> FP32 registers -> global (lower if asked)
     const int e = warp - 2;

@@ -425,7 +425,9 @@ __global__ void __launch_bounds__(Shape<PAIR, EW>::THREADS, 1)
     }
   } else if (warp == 1) {
     // ---------------------------------------------------------- MMA issuer
-    if (lane == 0 && leader) {
+    // the whole warp runs the loop in uniform control flow (its state stays
+    // in uniform registers); one elected lane issues the MMAs and commits
+    if (leader) {
       int stage = 0;
       uint32_t ph = 0, chunk = 0;
       bool ok = true;
@@ -436,54 +438,62 @@ __global__ void __launch_bounds__(Shape<PAIR, EW>::THREADS, 1)
           for (int kb = g.kb0; kb < g.kb1 && ok;) {
             const int kend = min(kb + g.kchunk, g.kb1);
             const uint32_t buf = chunk & 1u, use = chunk >> 1;
-            if (!wait_bounded<PAIR>(AEMPTY(buf), (use & 1u) ^ 1u, abort_flag, P.status)) {
+            if (!__all_sync(0xffffffffu, wait_bounded<PAIR>(AEMPTY(buf), (use & 1u) ^ 1u, abort_flag,
+                                                            P.status))) {
               ok = false;
               break;
             }
             tc_fence_after();
             const uint32_t dt = tmem + buf * ACC_COLS;
             for (int k = kb; k < kend; ++k) {
-              if (!wait_bounded<PAIR>(FULL(stage), ph, abort_flag, P.status)) {
+              if (!__all_sync(0xffffffffu, wait_bounded<PAIR>(FULL(stage), ph, abort_flag, P.status))) {
                 ok = false;
                 break;
               }
               tc_fence_after();
               const uint32_t sa = sbase + (uint32_t)(stage * S::STAGE_BYTES);
               const uint32_t sb = sa + S::A_BYTES;
+              if (elect_one()) {
 #pragma unroll
-              for (int s = 0; s < BK / 16; ++s) {
-                const uint32_t acc = (k > kb || s > 0) ? 1u : 0u;
+                for (int s = 0; s < BK / 16; ++s) {
+                  const uint32_t acc = (k > kb || s > 0) ? 1u : 0u;
+                  if constexpr (PAIR)
+                    tc_mma_pair(dt, sw128_desc(sa + 32u * s), sw128_desc(sb + 32u * s), S::IDESC, acc);
+                  else
+                    tc_mma(dt, sw128_desc(sa + 32u * s), sw128_desc(sb + 32u * s), S::IDESC, acc);
+                }
                 if constexpr (PAIR)
-                  tc_mma_pair(dt, sw128_desc(sa + 32u * s), sw128_desc(sb + 32u * s), S::IDESC, acc);
+                  tc_commit_pair(EMPTY(stage), 3);
                 else
-                  tc_mma(dt, sw128_desc(sa + 32u * s), sw128_desc(sb + 32u * s), S::IDESC, acc);
+                  tc_commit(EMPTY(stage));
               }
-              if constexpr (PAIR)
-                tc_commit_pair(EMPTY(stage), 3);
-              else
-                tc_commit(EMPTY(stage));
+              __syncwarp();
               if (++stage == STAGES) {
                 stage = 0;
                 ph ^= 1u;
               }
             }
             if (!ok) break;
-            if constexpr (PAIR)
-              tc_commit_pair(AFULL(buf), 3);
-            else
-              tc_commit(AFULL(buf));
+            if (elect_one()) {
+              if constexpr (PAIR)
+                tc_commit_pair(AFULL(buf), 3);
+              else
+                tc_commit(AFULL(buf));
+            }
+            __syncwarp();
             ++chunk;
             kb = kend;
           }
         }
       }
-      if (!ok) {
+      if (!ok && elect_one()) {
         if constexpr (PAIR)
           tc_commit_pair(DONE, 1);
         else
           tc_commit(DONE);
         wait_quiet(DONE, 0);
       }
+      __syncwarp();
     }
   } else {
     // ---------------------------------------------------------- epilogue

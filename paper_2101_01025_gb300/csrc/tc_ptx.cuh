@@ -183,6 +183,19 @@ __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint3
 // for both CTAs (A: 128 rows from each CTA's shared memory, B: half of the N
 // rows from each, D: 128 TMEM lanes in each CTA); the commit arrives on the
 // barrier at the same offset in every CTA of `mask`.
+// One lane of a converged warp (the lowest active one), chosen by
+// elect.sync: the warp runs the issuing loop in uniform control flow and the
+// elected lane issues the single-thread tcgen05 instructions.
+__device__ __forceinline__ bool elect_one() {
+  uint32_t pred = 0;
+  asm volatile(
+      "{\n\t.reg .pred P;\n\t"
+      "elect.sync _|P, 0xffffffff;\n\t"
+      "selp.u32 %0, 1, 0, P;\n\t}"
+      : "=r"(pred));
+  return pred != 0;
+}
+
 __device__ __forceinline__ void tc_mma_pair(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
                                             uint32_t acc) {
   asm volatile(
