@@ -47,11 +47,11 @@ P = 2**31 - 1
 SEED_OFFSET = 2
 # DRAM traffic of the dominant kernel from one ncu capture of three 8192^3
 # leaf products mod 2^31-1 (dram__bytes_read.sum + dram__bytes_write.sum:
-# 19.38, 17.96 and 17.80 GB, mean 18.38 GB for 10.995 TFLOP of algorithmic
-# work each; CTA-pair form, tiles in bands of 2048 rows), scaled to the
-# average launch of the step by its algorithmic work.  None whenever the
-# kernel has changed since the counters were taken.
-LEAF_TC_BYTES_PER_FLOP = 18.38e9 / 10.995e12
+# 11.63, 11.63 and 11.63 GB for 10.995 TFLOP of algorithmic work each;
+# CTA-pair form, tiles in bands of 2048 rows), scaled to the average launch
+# of the step by its algorithmic work.  None whenever the kernel has changed
+# since the counters were taken.
+LEAF_TC_BYTES_PER_FLOP = 11.63e9 / 10.995e12
 # Dense BF16 rate of the tensor pipe per SM and clock (a 128 x 256 x 16
 # tcgen05.mma every 128 cycles) and the SM count: the nominal rate at the
 # clock the run was sampled at.
@@ -264,19 +264,23 @@ def run_configs(peaks):
     out = {}
 
     def measure(name, fn, work, reps, what, leaf_cls, plan_flops=None):
-        fn()
+        for _ in range(2):
+            fn()
         torch.cuda.synchronize()
         _native.lib().aat_profile_begin()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
+        # one event pair per call, all calls back to back: the median call
+        # (one slow call does not move it)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(reps)]
+        for a, b in ev:
+            a.record()
             fn()
-        e1.record()
+            b.record()
         torch.cuda.synchronize()
         prof = _native.Profile()
         _native.check(_native.lib().aat_profile_end(prof))
-        ms = e0.elapsed_time(e1) / reps
+        calls = sorted(a.elapsed_time(b) for a, b in ev)
+        ms = calls[len(calls) // 2]
         lf = prof.as_dict().get(leaf_cls, {"launches": 0, "ms": 0.0, "work": 0.0})
         if plan_flops is not None:
             # a graph launch carries no per-kernel events: the plan's
@@ -290,8 +294,9 @@ def run_configs(peaks):
             ach = lf["work"] / max(lf["ms"], 1e-9) / 1e9
             rf = {"kernel": leaf_cls, "bound": "tensor", "achieved": ach, "peak": peak,
                   "unit": "TFLOP/s", "frac": ach / peak, "peak_source": peak_src,
-                  "share": lf["ms"] / max(ms * reps, 1e-9)}
-        out[name] = {"what": what, "ms": ms, "gops": work / (ms * 1e-3) / 1e9, "roofline": rf}
+                  "share": lf["ms"] / max(sum(calls), 1e-9)}
+        out[name] = {"what": what, "ms": ms, "ms_min_median_max": [calls[0], ms, calls[-1]],
+                     "calls": reps, "gops": work / (ms * 1e-3) / 1e9, "roofline": rf}
 
     def residues(n, k, p, seed):
         gen.manual_seed(seed)
