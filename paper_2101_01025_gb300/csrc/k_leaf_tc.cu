@@ -20,7 +20,10 @@
 //   warp 0        TMA producer: 128x64 tile of X_i and 256x64 tile of Y_j per
 //                 stage into 128B-swizzled shared memory (4 stages); in the
 //                 CTA-pair form 128x64 of each per CTA (6 stages)
-//   warp 1        TMEM allocator + single-thread tcgen05.mma issuer,
+//   warp 1        TMEM allocator + tcgen05.mma issuer: the warp runs the
+//                 K loop in uniform control flow and the lane chosen by
+//                 elect.sync issues each MMA and commit (a loop run by one
+//                 divergent lane could not issue as fast as the MMAs ran);
 //                 M=128 N=256 K=16 per instruction (CTA pair: M=256 across
 //                 the pair, issued by the leader), FP32 accumulator in one of
 //                 two 256-column TMEM buffers (double buffered per chunk)
