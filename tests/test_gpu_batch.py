@@ -216,3 +216,26 @@ def test_plan_with_winograd_problems(lib):
         for A, Ad, Cd, p in hosts:
             _fp_check(A, Cd.cpu().numpy(), p, full=True)
     plan.close()
+
+
+def test_plan_long_k_tiles_with_many_groups(lib):
+    """Batched depth-0 products over F_{2^31-1} whose K spans several 8192-wide
+    segments: 10 plane products per segment make 51 and 61 groups per tile,
+    more than the 32 the batched epilogue keeps in shared memory, so the
+    later groups come from global memory on every role of the kernel."""
+    p = 2**31 - 1
+    shapes = [(96, 41000), (130, 33000), (200, 300)]
+    problems, hosts = [], []
+    for q, (n, k) in enumerate(shapes):
+        A = synth.residues(700 + q, (n, k), p, balanced=(q % 2 == 0))
+        Ad = torch.from_numpy(A).cuda()
+        Cd = torch.full((n, n), -1, dtype=torch.int32, device="cuda")
+        problems.append(("modp", Ad, Cd, p, 0))
+        hosts.append((A, Cd))
+    plan = lib.Plan(problems)
+    assert plan.info()["batched"] == 3
+    plan.execute()
+    torch.cuda.synchronize()
+    for A, Cd in hosts:
+        _fp_check(A, Cd.cpu().numpy(), p, full=True)
+    plan.close()
